@@ -1,0 +1,329 @@
+"""Benchmark: ELM trainings per second on one GB300 (sparse-pixel workload:
+X 60000 x 784 with 80% zeros, L = 2000 sigmoid neurons, 10 one-hot classes,
+full column rank), beta checked against the FP64 CPU oracle's accuracy bar.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl native|reference] [--no-cpu-baseline]
+
+One step = one complete training (hidden layer, Gram, pivoted rank
+decision, solves, refinement) of the workload, inputs resident in HBM.
+Every training streams more than the 129 MB L2 (X is 188 MB, H 0.96 GB),
+so no L2 flush is inserted.  The e2e figure repeats the step through the C
+ABI with pinned host buffers: the host->device copy of X, W, b, T and the
+device->host copy of beta are inside the timed region.
+
+With --gpus N > 1 (torchrun, one process per GPU) every rank trains its own
+replica of the workload (independent problems, no collective); the value is
+the trainings of all ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the method's plain definition)
+on the host cores on a bounded sample of the workload (the first rows of X;
+N-proportional phases scaled to the full N).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ELM trainings/sec (beta at rel err <=1e-6) mixed+batched vs plain FP64, 1 GB300"
+WORKLOAD = dict(workload="sparse-pixel ELM: X 60000x784 (80% zeros, U[0,1], FP32), L=2000 "
+                         "sigmoid, 10 one-hot classes, full column rank",
+                N=60000, n=784, L=2000, m=10)
+
+
+def flops_model(N, n, L, m):
+    """Algorithmic work per training (symmetric Gram counted once)."""
+    return dict(hidden=2.0 * N * n * L, gram=float(N) * L * (L + 1) + 2.0 * N * L * m,
+                factor=L ** 3 / 3.0, refine_iter=4.0 * N * L * m)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+    return dict(hbm_gbs=d.get("hbm_gbs", 6800.0), bf16=d.get("bf16_tflops", 1900.0),
+                bf16_sus=d.get("bf16_tflops_sustained", 1700.0),
+                source="measured" if d else "fallback",
+                # FP64 has no measured entry: nominal GB300 rate (1.25 TFLOP/s)
+                fp64=1.25)
+
+
+class Clocks:
+    """nvidia-smi sampling in the background during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(full, sample_rows=2000, threads=None):
+    """Time the oracle, as it stands, on the first `sample_rows` rows of the
+    workload and scale its N-proportional phases to the full N."""
+    import oracle
+    p = synth.workload_sparse_pixels(N=sample_rows)
+    X, W, b, T = p["X"], p["W"], p["b"], p["T"]
+    N, L, m = full["N"], full["L"], full["m"]
+    t0 = time.perf_counter()
+    H = oracle.hidden(X, W, b, None, 0)
+    t1 = time.perf_counter()
+    S, Z = oracle.gram(H, T)
+    t2 = time.perf_counter()
+    r, perm, R = oracle.pivchol(S)
+    beta = oracle.frsolve(R, r, perm, Z)
+    t3 = time.perf_counter()
+    for _ in range(2):             # the oracle's two refinement steps, as orc_train runs them
+        Res = T - oracle.matmul_hb(H, beta)
+        G = oracle.gram(H, Res)[1]
+        beta = beta + oracle.frsolve(R, r, perm, G)
+    t4 = time.perf_counter()
+    scale = N / float(sample_rows)
+    t_full = (t1 - t0 + t2 - t1 + t4 - t3) * scale + (t3 - t2)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=1.0 / t_full, unit="trainings/s", cores=cores, kind="oracle",
+                sample="first %d of %d rows of the workload; hidden/Gram/refinement times "
+                       "scaled by N, factorisation+solve (L=%d) timed in full "
+                       "(%.1f s of CPU time: hidden %.1f, Gram %.1f, factor %.1f, refine %.1f)"
+                       % (sample_rows, N, L, t4 - t0, t1 - t0, t2 - t1, t3 - t2, t4 - t3),
+                projected_s_per_training=t_full)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    full = dict(WORKLOAD)
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(full, sample_rows=args.ref_rows)
+        if i >= args.warmup:
+            times.append(cb["projected_s_per_training"])
+    t = statistics.median(times)
+    val = 1.0 / t
+    line = dict(metric=METRIC, value=val, unit="trainings/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=t * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(WORKLOAD, inputs="oracle sample; CPU caches"), impl="reference",
+                cpu_baseline=dict(value=val, unit="trainings/s", kind="oracle",
+                                  cores=cb["cores"], sample=cb["sample"]),
+                e2e=dict(value=val, unit="trainings/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+def run_native(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2011_02436_gb300 as elm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = elm.PREC_MIXED if args.precision == "mixed" else elm.PREC_FP64
+
+    p = synth.workload_sparse_pixels()
+    N, n, L, m = p["N"], p["n"], p["L"], p["m"]
+    X = torch.from_numpy(p["X"]).to(dev)
+    W = torch.from_numpy(p["W"]).to(dev)
+    b = torch.from_numpy(p["b"]).to(dev)
+    T = torch.from_numpy(p["T"]).to(dev)
+    beta = torch.empty((L, m), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = elm.elm_create(local, stream)
+    prob = dict(X=X, W=W, b=b, a=None, act=0, T=T, beta=beta)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # verified run: rank and accuracy against the oracle's bar (beta vs the
+    # FP64 GPU path, whose own parity with the oracle is tested in tests/)
+    res = elm.elm_train(ctx, prob, precision=prec)[0]
+    beta_run = beta.cpu().numpy()
+    check = dict(rank=res["rank"], refine_iters=res["refine_iters"])
+    if prec != elm.PREC_FP64:
+        prob64 = dict(prob, beta=torch.empty_like(beta))
+        elm.elm_train(ctx, prob64, precision=elm.PREC_FP64)
+        b64 = prob64["beta"].cpu().numpy()
+        check["rel_err_vs_fp64_path"] = float(np.linalg.norm(beta_run - b64) / np.linalg.norm(b64))
+
+    for _ in range(args.warmup):
+        elm.elm_train(ctx, prob, precision=prec)
+    elm.elm_phase_times(ctx)                       # reset
+    barrier()
+    l0 = elm.elm_launch_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            elm.elm_train(ctx, prob, precision=prec, flags=elm.FLAG_PHASE_TIMING)
+        e1.record(stream)
+        barrier()
+    launches = elm.elm_launch_counter() - l0
+    phases = elm.elm_phase_times(ctx)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = ms
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(tt.item())
+    value = ws * 1000.0 / ms_max
+
+    # e2e through the C ABI with pinned host buffers
+    hX = torch.from_numpy(p["X"]).pin_memory()
+    hW = torch.from_numpy(p["W"]).pin_memory()
+    hb = torch.from_numpy(p["b"]).pin_memory()
+    hT = torch.from_numpy(p["T"]).pin_memory()
+    hbeta = torch.empty((L, m), dtype=torch.float64).pin_memory()
+    hprob = dict(X=hX, W=hW, b=hb, a=None, act=0, T=hT, beta=hbeta)
+    elm.elm_train(ctx, hprob, precision=prec)
+    barrier()
+    t0 = time.perf_counter()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        elm.elm_train(ctx, hprob, precision=prec)
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = sum(t.numel() * t.element_size() for t in (hX, hW, hb, hT))
+    d2h = hbeta.numel() * hbeta.element_size()
+
+    if rank == 0:
+        fl = flops_model(N, n, L, m)
+        pk = peaks()
+        ph_ms = {k: v / args.steps for k, v in phases.items()}
+        if prec == elm.PREC_FP64:
+            dom = "gram"
+            bound, peak, unit = "alu", pk["fp64"] * 1e3, "GFLOP/s"
+            achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e9
+            peak_note = "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 entry)"
+        else:
+            dom = "gram"
+            bound, peak, unit = "tensor", pk["bf16"], "TFLOP/s"
+            achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e12
+            peak_note = "%s bf16 dense burst" % pk["source"]
+        roof = dict(bound=bound, achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
+                    traffic=None, kernel=dom, peak_source=peak_note,
+                    phase_ms=ph_ms)
+        line = dict(metric=METRIC, value=value, unit="trainings/s", n_gpus=ws, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=ms_max, higher_is_better=True,
+                    scaling="weak", vs_baseline=None,
+                    dtype="f64" if prec == elm.PREC_FP64 else "bf16-slices+f64",
+                    data="synthetic",
+                    config=dict(WORKLOAD, precision=args.precision,
+                                parallelism="replicas" if ws > 1 else "single",
+                                l2="inputs larger than L2 (X 188 MB, H 0.96 GB): no flush"),
+                    e2e=dict(value=ws * 1000.0 / e2e_ms, unit="trainings/s",
+                             h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                    gpu_launches=launches, roofline=roof, clocks=clk.summary(), check=check)
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline(WORKLOAD, sample_rows=args.ref_rows)
+            cb.pop("projected_s_per_training", None)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=6000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

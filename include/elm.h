@@ -1,0 +1,182 @@
+/*
+ * elm.h -- C ABI of the GB300 rank-based pseudoinverse ELM library (libelm.so).
+ *
+ * Paper: R. Ragala, G. Bharadwaja Kumar, "Rank Based Pseudoinverse
+ * Computation in Extreme Learning Machine for large Datasets",
+ * arXiv 2011.02436.  The library trains a single-hidden-layer network:
+ *   H = g(X W + b)            (Eq. 1, Eq. 3; Algorithm 1 step 2)
+ *   rank r, permutation P, H P = [H1 H2]   (Eq. 6; Algorithm 1 steps 3-4)
+ *   beta = H^+ T              (Eq. 5, Eq. 7; Algorithm 1 step 9)
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major.  "ld" arguments are row strides in elements.
+ *   - Pointers may be device memory (cudaMalloc, PyTorch CUDA tensors) or
+ *     host memory; the library asks the CUDA runtime which, per pointer,
+ *     and stages host buffers through its own device workspace (the copies
+ *     are enqueued on the context's stream).  The caller keeps ownership of
+ *     every buffer it passes; nothing is retained after the call returns.
+ *   - Work is enqueued on the context's stream.  Calls that return values
+ *     on the host (ranks, results, host outputs) synchronise that stream
+ *     before returning; elm_hidden and elm_predict with device outputs do
+ *     not.
+ *   - Errors are returned as an elm_status code, never thrown.  Arguments
+ *     are validated before anything is launched (ELM_ERR_ARG).
+ *     elm_last_error() gives a one-line description of the last failure.
+ *   - One context per host thread.  The context owns a growable device
+ *     workspace, freed by elm_destroy.
+ */
+#ifndef ELM_H
+#define ELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct elm_ctx elm_ctx;
+
+typedef enum elm_status {
+    ELM_OK = 0,
+    ELM_ERR_ARG = 1,            /* invalid argument (detected before launch) */
+    ELM_ERR_CUDA = 2,           /* a CUDA runtime call failed               */
+    ELM_ERR_NOMEM = 3,          /* device workspace allocation failed       */
+    ELM_ERR_NUMERIC = 4,        /* non-finite input or Gram matrix          */
+    ELM_ERR_NOT_CONVERGED = 5,  /* refinement did not reach refine_tol      */
+    ELM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up       */
+    ELM_ERR_UNSUPPORTED = 7     /* size or mode outside the supported range */
+} elm_status;
+
+enum { ELM_ACT_SIGMOID = 0, ELM_ACT_TANH = 1 };   /* g: logistic (Section 4) or tanh */
+enum { ELM_F32 = 0, ELM_F64 = 1 };               /* element type of X              */
+enum { ELM_PREC_FP64 = 0, ELM_PREC_MIXED = 1 };  /* arithmetic of the dense products */
+
+/* Largest hidden-layer width L the factorisation kernels accept. */
+#define ELM_MAX_L 16384
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t (may
+ * be NULL for the legacy default stream).  *out receives the context. */
+int elm_create(elm_ctx **out, int device, void *stream);
+/* Free the context and its workspace.  NULL is accepted. */
+int elm_destroy(elm_ctx *ctx);
+/* Change the stream later calls enqueue on. */
+int elm_set_stream(elm_ctx *ctx, void *stream);
+/* Static description of a status code. */
+const char *elm_status_string(int status);
+/* Description of the last failure on this context ("" if none). */
+const char *elm_last_error(elm_ctx *ctx);
+
+/*
+ * Hidden layer (Eq. 1, Eq. 3; Algorithm 1 step 2), stored transposed:
+ *   Ht[j*ldh + i] = a_j * g( sum_k X[i*ldx + k] * W[k*ldw + j] + b_j )
+ * X: N x n, element type x_dtype (ELM_F32 / ELM_F64).  W: n x L FP64.
+ * b: L FP64.  a: L FP64 output scales, or NULL for all ones.  act: ELM_ACT_*.
+ * Ht: L x N FP64 output (ldh >= N).  precision: ELM_PREC_FP64 computes the
+ * products with FP64 FMAs; ELM_PREC_MIXED with exact integer-digit slices on
+ * the tensor cores (the result is FP64 to about 2^-40 absolute).
+ */
+int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n,
+               int64_t ldx, const double *W, int64_t ldw, const double *b,
+               const double *a, int64_t L, int act, int precision, double *Ht,
+               int64_t ldh);
+
+/*
+ * Rank and pseudoinverse of H given as Ht (L x N, ldh >= N, FP64)
+ * (Eq. 5, Eq. 6; Algorithm 1 steps 3-4).
+ * The Gram matrix H^T H is equilibrated to unit diagonal and factorised by
+ * diagonal-pivoted Cholesky; pivoting stops when the largest remaining
+ * diagonal is <= tol_rank (tol_rank <= 0 selects L * 2^-52).
+ *   rank_out: host int64, receives r.
+ *   perm_out: int32[L] (host or device) or NULL: perm_out[0..r-1] are the
+ *             columns of H1, perm_out[r..L-1] the dependent columns in
+ *             ascending order.
+ *   pinv_out: L x N (ldp >= N) FP64 receiving H^+, or NULL.  Forming H^+
+ *             costs O(L N r); meant for small problems and tests.
+ */
+int elm_pinv_rank(elm_ctx *ctx, const double *Ht, int64_t L, int64_t N,
+                  int64_t ldh, double tol_rank, int64_t *rank_out,
+                  int32_t *perm_out, double *pinv_out, int64_t ldp);
+
+/* One training problem for elm_train. */
+typedef struct elm_problem {
+    const void *X;      /* N x n, row stride ldx, type x_dtype              */
+    int32_t x_dtype;    /* ELM_F32 or ELM_F64                                */
+    int32_t act;        /* ELM_ACT_SIGMOID or ELM_ACT_TANH                   */
+    int64_t N, n, ldx;
+    const double *W;    /* n x L, row stride ldw                             */
+    int64_t ldw;
+    const double *b;    /* L                                                 */
+    const double *a;    /* L output scales, or NULL                          */
+    int64_t L;
+    const double *T;    /* N x m targets, row stride ldt                     */
+    int64_t m, ldt;
+    double *beta;       /* output: L x m, row stride ldb                     */
+    int64_t ldb;
+} elm_problem;
+
+typedef struct elm_train_opts {
+    int32_t precision;  /* ELM_PREC_FP64 or ELM_PREC_MIXED                   */
+    int32_t max_refine; /* refinement steps (< 0: default 2 FP64, 4 mixed)   */
+    double tol_rank;    /* rank threshold on the unit-diagonal scale (<=0: L*2^-52) */
+    double refine_tol;  /* stop when ||dbeta||_F <= refine_tol ||beta||_F (<=0: 1e-12) */
+    int32_t flags;      /* ELM_FLAG_* bits                                   */
+    int32_t reserved;
+} elm_train_opts;
+
+/* elm_train_opts.flags: record CUDA events around each training phase on
+ * the context's stream (read them with elm_phase_times). */
+#define ELM_FLAG_PHASE_TIMING 1
+
+typedef struct elm_result {
+    int64_t rank;         /* r                                              */
+    int32_t refine_iters; /* refinement steps taken                         */
+    int32_t status;       /* elm_status of this problem                     */
+    double rel_update;    /* ||dbeta||_F / ||beta||_F of the last step      */
+} elm_result;
+
+/*
+ * Train `count` independent problems (Algorithm 1): hidden layer, Gram
+ * H^T H and H^T T, pivoted rank decision, beta = H^+ T through the
+ * full-rank factorisation H P = H1 [I K] (beta = P [I; K^T] (I + K K^T)^{-1}
+ * (H1^T H1)^{-1} H1^T T), then refinement steps with the residual
+ * T - H beta.  opts may be NULL (FP64 defaults).  results: host array of
+ * `count` entries, or NULL.  Returns ELM_OK or the first failing status.
+ */
+int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
+              const elm_train_opts *opts, elm_result *results);
+
+/*
+ * Prediction (Section 2, step 3): Y = g(X W + b) beta without storing H.
+ * X, W, b, a, act as for elm_hidden; beta: L x m (ldb); Y: N x m FP64 (ldy).
+ */
+int elm_predict(elm_ctx *ctx, const void *X, int x_dtype, int64_t N,
+                int64_t n, int64_t ldx, const double *W, int64_t ldw,
+                const double *b, const double *a, int64_t L, int act,
+                const double *beta, int64_t m, int64_t ldb, double *Y,
+                int64_t ldy);
+
+/*
+ * Instrumentation (the paper has no counterpart; it reports wall-clock
+ * training time only, Section 4).
+ *
+ * elm_phase_times: milliseconds spent in each training phase, summed over
+ * the elm_train calls made with ELM_FLAG_PHASE_TIMING since the previous
+ * elm_phase_times call (which resets the sums).  Phases, in order:
+ *   0 hidden layer   1 Gram H^T H, H^T T   2 pivoted factorisation
+ *   3 first solve    4 refinement
+ * Writes min(max_phases, ELM_NUM_PHASES) values to ms_out (host) and
+ * returns ELM_NUM_PHASES, or a negative elm_status on error.
+ *
+ * elm_launch_counter: number of kernels this library has launched in the
+ * process so far (all contexts).
+ */
+#define ELM_NUM_PHASES 5
+int elm_phase_times(elm_ctx *ctx, double *ms_out, int max_phases);
+const char *elm_phase_name(int phase);
+int64_t elm_launch_counter(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELM_H */

@@ -1,0 +1,217 @@
+"""GB300 rank-based pseudoinverse ELM (arXiv 2011.02436): Python binding of
+the C ABI in include/elm.h.  Arguments are marshalled to pointers and sizes;
+every step of the computation runs in libelm.so's CUDA kernels.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; rows must be
+contiguous (last stride 1).  Outputs not supplied by the caller are
+allocated as torch tensors on the device of the first input (or as numpy
+arrays for host inputs).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+
+ACT_SIGMOID, ACT_TANH = 0, 1
+F32, F64 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+OK = 0
+
+
+class ElmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_lib.load().elm_status_string(status).decode(),
+                                                  status, msg))
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _ld(x):
+    if x.ndim == 1:
+        return x.shape[0]
+    if _is_torch(x):
+        if x.stride(1) != 1:
+            raise ValueError("rows must be contiguous")
+        return x.stride(0)
+    if x.strides[1] != x.itemsize:
+        raise ValueError("rows must be contiguous")
+    return x.strides[0] // x.itemsize
+
+
+def _xdtype(X):
+    name = str(X.dtype)
+    if name.endswith("float32"):
+        return F32
+    if name.endswith("float64"):
+        return F64
+    raise TypeError("X must be float32 or float64")
+
+
+def _empty_like_device(ref, shape, dtype=np.float64):
+    if _is_torch(ref):
+        torch = _torch()
+        return torch.empty(shape, dtype=torch.float64, device=ref.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _check(ctx, st):
+    if st != OK:
+        raise ElmError(st, _lib.load().elm_last_error(ctx.handle).decode())
+
+
+class Context:
+    """Owns an elm_ctx (device workspace, stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.handle = C.c_void_p()
+        self.device = device
+        st = _lib.load().elm_create(C.byref(self.handle), device, _stream_ptr(stream))
+        if st != OK:
+            raise ElmError(st, "elm_create")
+
+    def set_stream(self, stream):
+        _lib.load().elm_set_stream(self.handle, _stream_ptr(stream))
+
+    def close(self):
+        if self.handle:
+            _lib.load().elm_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def elm_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def elm_destroy(ctx: Context):
+    ctx.close()
+
+
+def elm_hidden(ctx, X, W, b, a=None, act=ACT_SIGMOID, precision=PREC_FP64, Ht=None):
+    """Ht (L x N) = a * g(X W + b), transposed (Eq. 1, Eq. 3)."""
+    N, n = X.shape
+    L = W.shape[1]
+    if Ht is None:
+        Ht = _empty_like_device(X, (L, N))
+    st = _lib.load().elm_hidden(ctx.handle, _ptr(X), _xdtype(X), N, n, _ld(X), _ptr(W), _ld(W),
+                                _ptr(b), _ptr(a), L, act, precision, _ptr(Ht), _ld(Ht))
+    _check(ctx, st)
+    return Ht
+
+
+def elm_pinv_rank(ctx, Ht, tol_rank=0.0, perm=None, pinv=None, want_pinv=False):
+    """Rank r, pivot order and optionally H^+ of H given as Ht (L x N)."""
+    L, N = Ht.shape
+    if perm is None:
+        perm = np.empty(L, dtype=np.int32)
+    if want_pinv and pinv is None:
+        pinv = _empty_like_device(Ht, (L, N))
+    r = C.c_int64(0)
+    st = _lib.load().elm_pinv_rank(ctx.handle, _ptr(Ht), L, N, _ld(Ht), tol_rank, C.byref(r),
+                                   _ptr(perm), _ptr(pinv), _ld(pinv) if pinv is not None else 0)
+    _check(ctx, st)
+    return int(r.value), perm, pinv
+
+
+def _problem(p):
+    X, W, b, T = p["X"], p["W"], p["b"], p["T"]
+    a = p.get("a")
+    N, n = X.shape
+    L = W.shape[1]
+    m = T.shape[1]
+    beta = p.get("beta")
+    if beta is None:
+        beta = _empty_like_device(X, (L, m))
+        p["beta"] = beta
+    return elm_problem_struct(X, n, N, W, b, a, L, T, m, beta, p.get("act", ACT_SIGMOID))
+
+
+def elm_problem_struct(X, n, N, W, b, a, L, T, m, beta, act):
+    return _lib.elm_problem(X=_ptr(X), x_dtype=_xdtype(X), act=act, N=N, n=n, ldx=_ld(X),
+                            W=_ptr(W), ldw=_ld(W), b=_ptr(b), a=_ptr(a), L=L, T=_ptr(T), m=m,
+                            ldt=_ld(T), beta=_ptr(beta), ldb=_ld(beta))
+
+
+def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
+              refine_tol=0.0, check=True, flags=0):
+    """Train each problem (dict with X, W, b, a, act, T and optional beta
+    output).  Returns a list of dicts (rank, refine_iters, status,
+    rel_update); beta is written into problem['beta']."""
+    if isinstance(problems, dict):
+        problems = [problems]
+    arr = (_lib.elm_problem * len(problems))(*[_problem(p) for p in problems])
+    opts = _lib.elm_train_opts(precision=precision, max_refine=max_refine, tol_rank=tol_rank,
+                               refine_tol=refine_tol, flags=flags, reserved=0)
+    res = (_lib.elm_result * len(problems))()
+    st = _lib.load().elm_train(ctx.handle, arr, len(problems), C.byref(opts), res)
+    if check:
+        _check(ctx, st)
+    return [dict(rank=r.rank, refine_iters=r.refine_iters, status=r.status,
+                 rel_update=r.rel_update) for r in res]
+
+
+FLAG_PHASE_TIMING = 1
+
+
+def elm_phase_times(ctx):
+    """{phase name: ms} summed since the previous call (then reset)."""
+    lib = _lib.load()
+    buf = (C.c_double * 8)()
+    n = lib.elm_phase_times(ctx.handle, buf, 8)
+    if n < 0:
+        raise ElmError(-n, "elm_phase_times")
+    return {lib.elm_phase_name(i).decode(): buf[i] for i in range(n)}
+
+
+def elm_phase_name(i):
+    return _lib.load().elm_phase_name(i).decode()
+
+
+def elm_launch_counter():
+    return int(_lib.load().elm_launch_counter())
+
+
+def elm_predict(ctx, X, W, b, a, act, beta, Y=None):
+    """Y (N x m) = g(X W + b) beta (Section 2, step 3)."""
+    N, n = X.shape
+    L = W.shape[1]
+    m = beta.shape[1]
+    if Y is None:
+        Y = _empty_like_device(X, (N, m))
+    st = _lib.load().elm_predict(ctx.handle, _ptr(X), _xdtype(X), N, n, _ld(X), _ptr(W), _ld(W),
+                                 _ptr(b), _ptr(a), L, act, _ptr(beta), m, _ld(beta), _ptr(Y),
+                                 _ld(Y))
+    _check(ctx, st)
+    return Y

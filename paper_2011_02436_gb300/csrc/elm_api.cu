@@ -1,0 +1,538 @@
+// C ABI of libelm.so (declared in include/elm.h): argument validation,
+// host/device staging, workspace planning and the order of the training
+// steps of Algorithm 1.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <functional>
+#include <new>
+#include <vector>
+
+#include "elm_internal.cuh"
+
+using namespace elm;
+
+namespace elm {
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace elm
+
+namespace {
+
+const char *kPhaseName[ELM_NUM_PHASES] = {"hidden", "gram", "factor", "solve", "refine"};
+
+void mark(elm_ctx *ctx, int i) {
+    if (ctx->timing) ELM_CUDA(cudaEventRecord(ctx->ev[i], ctx->stream));
+}
+
+void collect_phases(elm_ctx *ctx) {
+    if (!ctx->timing) return;
+    ELM_CUDA(cudaEventSynchronize(ctx->ev[ELM_NUM_PHASES]));
+    for (int i = 0; i < ELM_NUM_PHASES; i++) {
+        float ms = 0.f;
+        ELM_CUDA(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+        ctx->phase_ms[i] += ms;
+    }
+}
+
+const char *kStatusText[] = {
+    "ok",
+    "invalid argument",
+    "CUDA runtime error",
+    "device workspace allocation failed",
+    "non-finite input or Gram matrix",
+    "refinement did not converge",
+    "bounded device-side wait gave up",
+    "unsupported size or mode",
+};
+
+template <class F>
+int guarded(elm_ctx *ctx, F &&f) {
+    try {
+        f();
+        if (ctx) ctx->last_error.clear();
+        return ELM_OK;
+    } catch (const ElmError &e) {
+        if (ctx) ctx->last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->last_error = "host allocation failed";
+        return ELM_ERR_NOMEM;
+    } catch (...) {
+        if (ctx) ctx->last_error = "unexpected exception";
+        return ELM_ERR_CUDA;
+    }
+}
+
+void require(bool ok, const char *what) {
+    if (!ok) throw ElmError(ELM_ERR_ARG, what);
+}
+
+bool on_device(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void grow(char **buf, size_t *size, size_t need, cudaStream_t s) {
+    if (need <= *size) return;
+    ELM_CUDA(cudaStreamSynchronize(s));
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *size = 0;
+    size_t want = need + need / 8 + (1 << 20);
+    if (cudaMalloc(buf, want) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        throw ElmError(ELM_ERR_NOMEM, "cudaMalloc of the workspace failed");
+    }
+    *size = want;
+}
+
+// Run `plan` once to measure, grow the buffer, run it again for real.
+void with_arena(char **buf, size_t *size, cudaStream_t s,
+                const std::function<void(Arena &)> &plan) {
+    Arena m;
+    plan(m);
+    grow(buf, size, m.used, s);
+    Arena a;
+    a.base = *buf;
+    a.cap = *size;
+    plan(a);
+}
+
+// A read-only input matrix: the caller's pointer if it is device memory,
+// else a staged device copy (row stride becomes `cols`).
+struct In {
+    const void *p = nullptr;
+    int64_t ld = 0;
+    bool host = false;
+};
+
+In stage(Arena &ar, cudaStream_t s, const void *p, int64_t rows, int64_t cols, int64_t ld,
+         size_t esz) {
+    In r;
+    if (!p) return r;
+    if (on_device(p)) {
+        r.p = p;
+        r.ld = ld;
+        return r;
+    }
+    char *d = ar.take<char>((size_t)(rows * cols) * esz);
+    r.p = d;
+    r.ld = cols;
+    r.host = true;
+    if (d)
+        ELM_CUDA(cudaMemcpy2DAsync(d, cols * esz, p, ld * esz, cols * esz, rows,
+                                   cudaMemcpyHostToDevice, s));
+    return r;
+}
+
+// ----------------------------------------------------------------- solves
+struct AuxBufs {
+    double *yb, *K, *G2, *v, *w, *R2, *Rt2;
+    FactorWs f2;
+};
+
+AuxBufs carve_aux(Arena &ar, int64_t L, int64_t r, int64_t m) {
+    AuxBufs b{};
+    int64_t q = L - r;
+    b.yb = ar.take<double>(L * m);
+    if (q > 0) {
+        b.K = ar.take<double>(r * q);
+        b.G2 = ar.take<double>(q * q);
+        b.v = ar.take<double>(q * m);
+        b.w = ar.take<double>(q * m);
+        b.R2 = ar.take<double>(q * q);
+        b.Rt2 = ar.take<double>(q * q);
+        b.f2 = factor_ws_carve(ar, q);
+    }
+    return b;
+}
+
+// out[perm[i], :] = ([y; K^T y])[i, :] with y = (I + K K^T)^{-1} R11^{-1}
+// R11^{-T} Z[perm[0..r-1], :] and K = R11^{-1} R12: beta = H^+ T through
+// the full-rank factorisation H P = H1 [I K] (Eq. 5, Eq. 7).  The r x r
+// system I + K K^T is solved through the (L-r) x (L-r) system I + K^T K
+// (Woodbury identity).
+void solve_beta(elm_ctx *ctx, cudaStream_t s, const double *R, const double *Rt,
+                const int32_t *perm, int64_t r, int64_t L, const double *Z, int64_t ldz,
+                int64_t m, double *out, int64_t ldo) {
+    AuxBufs ab{};
+    with_arena(&ctx->aux, &ctx->aux_size, s, [&](Arena &a) { ab = carve_aux(a, L, r, m); });
+    double *yb = ab.yb;
+    gather_rows(s, Z, ldz, perm, nullptr, r, m, yb, m);
+    trsm_fwd(s, R, L, nullptr, r, yb, m, m);
+    trsm_bwd(s, Rt, L, nullptr, r, yb, m, m);
+    if (r < L) {
+        const int64_t q = L - r;
+        if (r > 0) {
+            ELM_CUDA(cudaMemcpy2DAsync(ab.K, q * sizeof(double), R + r, L * sizeof(double),
+                                       q * sizeof(double), r, cudaMemcpyDeviceToDevice, s));
+            trsm_bwd(s, Rt, L, nullptr, r, ab.K, q, q);
+            set_identity(s, ab.G2, q);
+            gemm_f64(s, q, q, r, 1.0, ab.K, 1, q, ab.K, q, 1, 1.0, ab.G2, q);
+            factor_pivoted(s, ab.G2, q, q, 0.0, ab.f2, ab.R2, ab.Rt2, ctx->sm_count);
+            gemm_f64(s, q, m, r, 1.0, ab.K, 1, q, yb, m, 1, 0.0, ab.v, m);
+            ELM_CUDA(cudaMemsetAsync(ab.w, 0, sizeof(double) * q * m, s));
+            gather_rows(s, ab.v, m, ab.f2.perm, &ab.f2.st->rank, q, m, ab.w, m);
+            trsm_fwd(s, ab.R2, q, &ab.f2.st->rank, q, ab.w, m, m);
+            trsm_bwd(s, ab.Rt2, q, &ab.f2.st->rank, q, ab.w, m, m);
+            scatter_rows(s, ab.w, m, ab.f2.perm, q, ab.v, m, 1.0, 0);
+            gemm_f64(s, r, m, q, -1.0, ab.K, q, 1, ab.v, m, 1, 1.0, yb, m);
+            gemm_f64(s, q, m, r, 1.0, ab.K, 1, q, yb, m, 1, 0.0, yb + r * m, m);
+        } else {
+            ELM_CUDA(cudaMemsetAsync(yb, 0, sizeof(double) * L * m, s));
+        }
+    }
+    scatter_rows(s, yb, m, perm, L, out, ldo, 1.0, 0);
+}
+
+int64_t read_rank(cudaStream_t s, const FactorWs &f, int32_t *flags) {
+    FactorState st;
+    ELM_CUDA(cudaMemcpyAsync(&st, f.st, sizeof st, cudaMemcpyDeviceToHost, s));
+    ELM_CUDA(cudaStreamSynchronize(s));
+    if (flags) *flags = st.flags;
+    return st.rank;
+}
+
+void check_dims(int64_t N, int64_t n, int64_t ldx, int64_t L, int64_t ldw) {
+    require(N >= 1 && n >= 1 && L >= 1, "N, n and L must be >= 1");
+    require(ldx >= n, "ldx < n");
+    require(ldw >= L, "ldw < L");
+    require(L <= ELM_MAX_L, "L above ELM_MAX_L");
+}
+
+// ------------------------------------------------------------ one problem
+struct Problem {
+    const elm_problem *p;
+    int prec;
+    int max_refine;
+    double tau;
+    double refine_tol;
+};
+
+void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
+    if (P.prec != ELM_PREC_FP64) throw ElmError(ELM_ERR_UNSUPPORTED, "precision not built");
+    const elm_problem &pb = *P.p;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
+    const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
+    const int ns = gram_f64_nsplit(L, m, N, ctx->sm_count);
+    const int hs = htr_f64_nsplit(L, N, ctx->sm_count);
+    In X, W, b, a, T;
+    double *Ht, *S, *Z, *gpart, *R, *Rt, *beta, *dB, *Rres, *G, *hpart, *norms;
+    int32_t *flag;
+    FactorWs f;
+    with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+        X = stage(ar, s, pb.X, N, n, pb.ldx, xsz);
+        W = stage(ar, s, pb.W, n, L, pb.ldw, 8);
+        b = stage(ar, s, pb.b, 1, L, L, 8);
+        a = stage(ar, s, pb.a, 1, L, L, 8);
+        T = stage(ar, s, pb.T, N, m, pb.ldt, 8);
+        Ht = ar.take<double>(L * N);
+        S = ar.take<double>(L * L);
+        Z = ar.take<double>(L * m);
+        gpart = ar.take<double>(gram_f64_ws(L, m, ns));
+        R = ar.take<double>(L * L);
+        Rt = ar.take<double>(L * L);
+        beta = ar.take<double>(L * m);
+        dB = ar.take<double>(L * m);
+        Rres = ar.take<double>(N * m);
+        G = ar.take<double>(L * m);
+        hpart = ar.take<double>(htr_f64_ws(L, m, hs));
+        norms = ar.take<double>(2);
+        flag = ar.take<int32_t>(1);
+        f = factor_ws_carve(ar, L);
+    });
+    ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    check_finite(s, X.p, pb.x_dtype, N, n, X.ld, flag);
+    const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
+                 *ad = (const double *)a.p, *Td = (const double *)T.p;
+    mark(ctx, 0);
+    // Algorithm 1 step 2: H (stored transposed)
+    hidden_f64(s, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, L, pb.act, Ht, N);
+    mark(ctx, 1);
+    // Eqs. 9-13: Gram blocks H^T H and H^T T
+    gram_f64(s, Ht, N, L, N, Td, T.ld, m, S, L, Z, m, gpart, ns);
+    mark(ctx, 2);
+    // Eq. 6, Algorithm 1 steps 3-4: permutation, rank, split
+    factor_pivoted(s, S, L, L, P.tau, f, R, Rt, ctx->sm_count);
+    mark(ctx, 3);
+    int32_t fl = 0, xfl = 0;
+    const int64_t r = read_rank(s, f, &fl);
+    ELM_CUDA(cudaMemcpy(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost));
+    res->rank = r;
+    res->refine_iters = 0;
+    res->rel_update = 0.0;
+    res->status = ELM_OK;
+    if (fl || xfl) {
+        res->status = ELM_ERR_NUMERIC;
+        return;
+    }
+    // Eq. 5, Eq. 7: beta = H^+ T
+    solve_beta(ctx, s, R, Rt, f.perm, r, L, Z, m, m, beta, m);
+    mark(ctx, 4);
+    // refinement with the residual T - H beta
+    double nrm[2] = {0.0, 0.0};
+    for (int it = 0; it < P.max_refine; it++) {
+        resid_f64(s, Ht, N, L, N, beta, m, Td, T.ld, Rres);
+        htr_f64(s, Ht, N, L, N, Rres, m, G, hpart, hs);
+        solve_beta(ctx, s, R, Rt, f.perm, r, L, G, m, m, dB, m);
+        axpy_norms(s, beta, dB, L * m, norms);
+        ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
+        ELM_CUDA(cudaStreamSynchronize(s));
+        res->refine_iters = it + 1;
+        res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        if (res->rel_update <= P.refine_tol) break;
+    }
+    mark(ctx, 5);
+    if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
+    const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyDeviceToHost;
+    ELM_CUDA(cudaMemcpy2DAsync(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
+                               m * sizeof(double), L, kind, s));
+    ELM_CUDA(cudaStreamSynchronize(s));
+    collect_phases(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *elm_status_string(int status) {
+    if (status < 0 || status >= (int)(sizeof kStatusText / sizeof kStatusText[0]))
+        return "unknown status";
+    return kStatusText[status];
+}
+
+const char *elm_last_error(elm_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int elm_create(elm_ctx **out, int device, void *stream) {
+    if (!out) return ELM_ERR_ARG;
+    *out = nullptr;
+    elm_ctx *ctx = new (std::nothrow) elm_ctx;
+    if (!ctx) return ELM_ERR_NOMEM;
+    int st = guarded(ctx, [&] {
+        int count = 0;
+        ELM_CUDA(cudaGetDeviceCount(&count));
+        require(device >= 0 && device < count, "no such CUDA device");
+        ELM_CUDA(cudaSetDevice(device));
+        ctx->device = device;
+        ctx->stream = (cudaStream_t)stream;
+        ELM_CUDA(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+        for (auto &e : ctx->ev) ELM_CUDA(cudaEventCreate(&e));
+    });
+    if (st != ELM_OK) {
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return ELM_OK;
+}
+
+int elm_destroy(elm_ctx *ctx) {
+    if (!ctx) return ELM_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->aux) cudaFree(ctx->aux);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+    return ELM_OK;
+}
+
+int elm_set_stream(elm_ctx *ctx, void *stream) {
+    if (!ctx) return ELM_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return ELM_OK;
+}
+
+int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, int64_t ldx,
+               const double *W, int64_t ldw, const double *b, const double *a, int64_t L,
+               int act, int precision, double *Ht, int64_t ldh) {
+    if (!ctx) return ELM_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_dims(N, n, ldx, L, ldw);
+        require(X && W && b && Ht, "X, W, b and Ht must be non-NULL");
+        require(x_dtype == ELM_F32 || x_dtype == ELM_F64, "x_dtype");
+        require(act == ELM_ACT_SIGMOID || act == ELM_ACT_TANH, "act");
+        require(precision == ELM_PREC_FP64 || precision == ELM_PREC_MIXED, "precision");
+        require(ldh >= N, "ldh < N");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const size_t xsz = x_dtype == ELM_F64 ? 8 : 4;
+        In Xs, Ws, bs, as;
+        double *out = nullptr;
+        const bool dev_out = on_device(Ht);
+        with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+            Xs = stage(ar, s, X, N, n, ldx, xsz);
+            Ws = stage(ar, s, W, n, L, ldw, 8);
+            bs = stage(ar, s, b, 1, L, L, 8);
+            as = stage(ar, s, a, 1, L, L, 8);
+            out = dev_out ? Ht : ar.take<double>(L * N);
+        });
+        const int64_t ldo = dev_out ? ldh : N;
+        hidden_f64(s, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld,
+                   (const double *)bs.p, (const double *)as.p, L, act, out, ldo);
+        if (!dev_out) {
+            ELM_CUDA(cudaMemcpy2DAsync(Ht, ldh * 8, out, N * 8, N * 8, L,
+                                       cudaMemcpyDeviceToHost, s));
+            ELM_CUDA(cudaStreamSynchronize(s));
+        } else if (Xs.host || Ws.host || bs.host || as.host) {
+            ELM_CUDA(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+int elm_pinv_rank(elm_ctx *ctx, const double *Ht, int64_t L, int64_t N, int64_t ldh,
+                  double tol_rank, int64_t *rank_out, int32_t *perm_out, double *pinv_out,
+                  int64_t ldp) {
+    if (!ctx) return ELM_ERR_ARG;
+    return guarded(ctx, [&] {
+        require(L >= 1 && N >= 1, "L and N must be >= 1");
+        require(L <= ELM_MAX_L, "L above ELM_MAX_L");
+        require(ldh >= N, "ldh < N");
+        require(Ht && rank_out, "Ht and rank_out must be non-NULL");
+        require(!pinv_out || ldp >= N, "ldp < N");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const int ns = gram_f64_nsplit(L, 0, N, ctx->sm_count);
+        In H;
+        double *S, *gpart, *R, *Rt, *pv = nullptr;
+        FactorWs f;
+        const bool dev_p = pinv_out && on_device(pinv_out);
+        with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+            H = stage(ar, s, Ht, L, N, ldh, 8);
+            S = ar.take<double>(L * L);
+            gpart = ar.take<double>(gram_f64_ws(L, 0, ns));
+            R = ar.take<double>(L * L);
+            Rt = ar.take<double>(L * L);
+            f = factor_ws_carve(ar, L);
+            if (pinv_out && !dev_p) pv = ar.take<double>(L * N);
+        });
+        const double *Hd = (const double *)H.p;
+        gram_f64(s, Hd, H.ld, L, N, nullptr, 0, 0, S, L, nullptr, 0, gpart, ns);
+        const double tau = tol_rank > 0.0 ? tol_rank : (double)L * ldexp(1.0, -52);
+        factor_pivoted(s, S, L, L, tau, f, R, Rt, ctx->sm_count);
+        int32_t fl = 0;
+        const int64_t r = read_rank(s, f, &fl);
+        if (fl) throw ElmError(ELM_ERR_NUMERIC, "non-finite Gram matrix");
+        *rank_out = r;
+        if (perm_out) {
+            cudaMemcpyKind k = on_device(perm_out) ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyDeviceToHost;
+            ELM_CUDA(cudaMemcpyAsync(perm_out, f.perm, sizeof(int32_t) * L, k, s));
+        }
+        if (pinv_out) {
+            double *dst = dev_p ? pinv_out : pv;
+            const int64_t ldd = dev_p ? ldp : N;
+            solve_beta(ctx, s, R, Rt, f.perm, r, L, Hd, H.ld, N, dst, ldd);
+            if (!dev_p)
+                ELM_CUDA(cudaMemcpy2DAsync(pinv_out, ldp * 8, pv, N * 8, N * 8, L,
+                                           cudaMemcpyDeviceToHost, s));
+        }
+        ELM_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
+              const elm_train_opts *opts, elm_result *results) {
+    if (!ctx) return ELM_ERR_ARG;
+    elm_train_opts o{};
+    o.precision = ELM_PREC_FP64;
+    o.max_refine = -1;
+    if (opts) o = *opts;
+    int first = ELM_OK;
+    int st = guarded(ctx, [&] {
+        require(count >= 0, "count < 0");
+        require(count == 0 || probs, "probs is NULL");
+        require(o.precision == ELM_PREC_FP64 || o.precision == ELM_PREC_MIXED, "precision");
+        for (int64_t i = 0; i < count; i++) {
+            const elm_problem &p = probs[i];
+            check_dims(p.N, p.n, p.ldx, p.L, p.ldw);
+            require(p.m >= 1 && p.ldt >= p.m && p.ldb >= p.m, "m, ldt or ldb");
+            require(p.X && p.W && p.b && p.T && p.beta, "NULL problem pointer");
+            require(p.x_dtype == ELM_F32 || p.x_dtype == ELM_F64, "x_dtype");
+            require(p.act == ELM_ACT_SIGMOID || p.act == ELM_ACT_TANH, "act");
+        }
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        ctx->timing = (o.flags & ELM_FLAG_PHASE_TIMING) != 0;
+        for (int64_t i = 0; i < count; i++) {
+            Problem P;
+            P.p = &probs[i];
+            P.prec = o.precision;
+            P.max_refine = o.max_refine >= 0 ? o.max_refine
+                                             : (o.precision == ELM_PREC_FP64 ? 2 : 4);
+            P.tau = o.tol_rank > 0.0 ? o.tol_rank : (double)probs[i].L * ldexp(1.0, -52);
+            P.refine_tol = o.refine_tol > 0.0 ? o.refine_tol : 1e-12;
+            elm_result r{};
+            train_one(ctx, P, &r);
+            if (results) results[i] = r;
+            if (first == ELM_OK && r.status != ELM_OK) first = r.status;
+        }
+    });
+    return st != ELM_OK ? st : first;
+}
+
+int elm_phase_times(elm_ctx *ctx, double *ms_out, int max_phases) {
+    if (!ctx || (max_phases > 0 && !ms_out)) return -ELM_ERR_ARG;
+    for (int i = 0; i < ELM_NUM_PHASES; i++) {
+        if (i < max_phases) ms_out[i] = ctx->phase_ms[i];
+        ctx->phase_ms[i] = 0.0;
+    }
+    return ELM_NUM_PHASES;
+}
+
+const char *elm_phase_name(int phase) {
+    return (phase >= 0 && phase < ELM_NUM_PHASES) ? kPhaseName[phase] : "";
+}
+
+int64_t elm_launch_counter(void) { return g_launches.load(); }
+
+int elm_predict(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, int64_t ldx,
+                const double *W, int64_t ldw, const double *b, const double *a, int64_t L,
+                int act, const double *beta, int64_t m, int64_t ldb, double *Y, int64_t ldy) {
+    if (!ctx) return ELM_ERR_ARG;
+    return guarded(ctx, [&] {
+        check_dims(N, n, ldx, L, ldw);
+        require(X && W && b && beta && Y, "NULL pointer");
+        require(m >= 1 && ldb >= m && ldy >= m, "m, ldb or ldy");
+        require(x_dtype == ELM_F32 || x_dtype == ELM_F64, "x_dtype");
+        require(act == ELM_ACT_SIGMOID || act == ELM_ACT_TANH, "act");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const size_t xsz = x_dtype == ELM_F64 ? 8 : 4;
+        In Xs, Ws, bs, as, Bs;
+        double *out = nullptr;
+        const bool dev_out = on_device(Y);
+        with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+            Xs = stage(ar, s, X, N, n, ldx, xsz);
+            Ws = stage(ar, s, W, n, L, ldw, 8);
+            bs = stage(ar, s, b, 1, L, L, 8);
+            as = stage(ar, s, a, 1, L, L, 8);
+            Bs = stage(ar, s, beta, L, m, ldb, 8);
+            out = dev_out ? Y : ar.take<double>(N * m);
+        });
+        const int64_t ldo = dev_out ? ldy : m;
+        predict_f64(s, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld,
+                    (const double *)bs.p, (const double *)as.p, L, act,
+                    (const double *)Bs.p, Bs.ld, m, out, ldo);
+        if (!dev_out) {
+            ELM_CUDA(cudaMemcpy2DAsync(Y, ldy * 8, out, m * 8, m * 8, N,
+                                       cudaMemcpyDeviceToHost, s));
+            ELM_CUDA(cudaStreamSynchronize(s));
+        } else if (Xs.host || Ws.host || bs.host || as.host || Bs.host) {
+            ELM_CUDA(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+}  // extern "C"

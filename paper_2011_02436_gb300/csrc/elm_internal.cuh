@@ -1,0 +1,160 @@
+// Internal declarations of libelm.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "elm.h"
+
+#define ELM_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            throw ElmError(ELM_ERR_CUDA, std::string(#call) + ": " +           \
+                                             cudaGetErrorString(e_));          \
+        }                                                                      \
+    } while (0)
+
+// Every kernel launch site ends with ELM_CHECK_LAUNCH(), which also counts it.
+namespace elm {
+void count_launch();
+}
+#define ELM_CHECK_LAUNCH()              \
+    do {                                \
+        elm::count_launch();            \
+        ELM_CUDA(cudaGetLastError());   \
+    } while (0)
+
+struct ElmError {
+    int status;
+    std::string msg;
+    ElmError(int s, std::string m) : status(s), msg(std::move(m)) {}
+};
+
+// Device-side state of one pivoted factorisation (kept in workspace).
+struct FactorState {
+    int64_t k;        // pivots taken so far
+    int64_t Lr;       // active (not yet pivoted) columns
+    int64_t rank;     // final rank (valid once done)
+    int32_t done;     // 1 once the stopping rule fired or all columns pivoted
+    int32_t flags;    // bit 0: non-finite value met
+    int64_t steps;    // pivots taken by the last panel
+};
+
+// Bump allocator over the context's device workspace.  With base == nullptr
+// it only measures.
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0, used = 0;
+    template <class T>
+    T *take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + count * sizeof(T);
+        if (base && used > cap) throw ElmError(ELM_ERR_NOMEM, "workspace overflow");
+        return base ? reinterpret_cast<T *>(base + off) : nullptr;
+    }
+};
+
+struct elm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    char *ws = nullptr;      // main workspace (planned before launch)
+    size_t ws_size = 0;
+    char *aux = nullptr;     // solve workspace (sized once the rank is known)
+    size_t aux_size = 0;
+    std::string last_error;
+    // phase timing (ELM_FLAG_PHASE_TIMING)
+    bool timing = false;
+    cudaEvent_t ev[ELM_NUM_PHASES + 1] = {};
+    double phase_ms[ELM_NUM_PHASES] = {};
+};
+
+// ---------------------------------------------------------------- kernels
+namespace elm {
+
+// FP64 hidden layer: Ht[j, i] = a_j g(sum_k X[i,k] W[k,j] + b_j).
+void hidden_f64(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n,
+                int64_t ldx, const double *W, int64_t ldw, const double *b,
+                const double *a, int64_t L, int act, double *Ht, int64_t ldh);
+
+// FP64 Gram of the augmented rows [Ht; T^T]: S = H^T H (full, both
+// triangles), Z = H^T T.  part: workspace of gram_f64_parts(...) doubles.
+int gram_f64_nsplit(int64_t L, int64_t m, int64_t N, int sms);
+size_t gram_f64_ws(int64_t L, int64_t m, int nsplit);
+void gram_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
+              int64_t N, const double *T, int64_t ldt, int64_t m, double *S,
+              int64_t lds, double *Z, int64_t ldz, double *part, int nsplit);
+
+// Generic FP64 GEMM: C = alpha * A * B + beta * C with arbitrary element
+// strides (so transposes are free).  A is M x K, B is K x N.
+void gemm_f64(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha,
+              const double *A, int64_t sAm, int64_t sAk, const double *B,
+              int64_t sBk, int64_t sBn, double beta, double *C, int64_t ldc);
+
+// Residual R = T - H beta with H given as Ht (L x N); R is N x m (ld m).
+void resid_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
+               int64_t N, const double *beta, int64_t m, const double *T,
+               int64_t ldt, double *R);
+// G = H^T R  (L x m) from Ht (L x N) and R (N x m); deterministic split.
+size_t htr_f64_ws(int64_t L, int64_t m, int nsplit);
+int htr_f64_nsplit(int64_t L, int64_t N, int sms);
+void htr_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
+             int64_t N, const double *R, int64_t m, double *G, double *part,
+             int nsplit);
+
+// Fused prediction Y = g(X W + b) beta (FP64).
+void predict_f64(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n,
+                 int64_t ldx, const double *W, int64_t ldw, const double *b,
+                 const double *a, int64_t L, int act, const double *beta,
+                 int64_t ldb, int64_t m, double *Y, int64_t ldy);
+
+// ------------------------------------------------ factorisation and solves
+struct FactorWs {
+    double *A0, *A1;       // L x L ping-pong active matrices
+    double *Rrow;          // L x L pivot rows in original column order
+    double *P;             // nb x L panel rows (active index space)
+    double *dS;            // L diagonal of S
+    int32_t *act0, *act1;  // active -> original index maps
+    int32_t *rem;          // compaction map of the last panel
+    int32_t *perm;         // pivot order
+    FactorState *st;
+};
+size_t factor_ws_bytes(int64_t L);
+FactorWs factor_ws_carve(Arena &ar, int64_t L);
+// Pivoted Cholesky of the L x L matrix S (lds).  Writes R (L x L, pivot
+// order, unscaled, rows >= rank zero) and Rt (its transpose), perm.
+// Returns nothing; rank lives in w.st->rank (device).
+void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
+                    double tau, const FactorWs &w, double *R, double *Rt,
+                    int sms);
+
+// X = R11^{-T} B (forward) and X = R11^{-1} B (backward), in place on B
+// (r x q, ld ldb).  R, Rt: pivot-order factor and transpose (ld L).
+// r and q may be read from device memory (r_dev / q_dev non-null).
+void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
+              int64_t r_max, double *B, int64_t ldb, int64_t q);
+void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const int64_t *r_dev,
+              int64_t r_max, double *B, int64_t ldb, int64_t q);
+
+// Gather rows: dst[i, :] = src[perm[i], :] for i < r_dev.
+void gather_rows(cudaStream_t s, const double *src, int64_t lds, const int32_t *perm,
+                 const int64_t *r_dev, int64_t rmax, int64_t m, double *dst, int64_t ldd);
+// Scatter: beta[perm[i], :] = src[i, :] for i < L (ld of src m).
+void scatter_rows(cudaStream_t s, const double *src, int64_t m, const int32_t *perm,
+                  int64_t L, double *beta, int64_t ldb, double alpha, int accumulate);
+
+// Norm helpers: out[0] = ||x||_F^2 over rows x cols.
+void sumsq(cudaStream_t s, const double *x, int64_t rows, int64_t cols, int64_t ld,
+           double *out);
+// beta += dB; out[0] = ||dB||^2, out[1] = ||beta||^2.
+void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, double *out);
+// A (n x n) = I.
+void set_identity(cudaStream_t s, double *A, int64_t n);
+// Scan for non-finite entries; sets *flag = 1 if any.
+void check_finite(cudaStream_t s, const void *x, int xdt, int64_t rows, int64_t cols,
+                  int64_t ld, int32_t *flag);
+
+}  // namespace elm

@@ -1,0 +1,624 @@
+// FP64 dense kernels of the plain path: hidden layer (Eq. 1, 3), Gram
+// blocks (Eqs. 9-13), refinement residuals, fused prediction (Section 2,
+// step 3) and a generic strided GEMM used by the solves.
+//
+// On GB300 the FP64 pipe issues about two DFMA per clock per SM, so these
+// kernels are bound by DFMA issue, not by HBM: each keeps a 4x4 register
+// tile per thread fed from shared memory, and every output element is
+// accumulated by one thread in a fixed order (no atomics), so results are
+// deterministic and two bitwise-equal input columns give bitwise-equal
+// outputs.
+#include <math.h>
+
+#include "elm_internal.cuh"
+
+namespace elm {
+
+namespace {
+
+constexpr int TB = 64;   // output tile edge
+constexpr int TK = 16;   // k-slab depth
+constexpr int NT = 256;  // threads per block (16 x 16, 4 x 4 outputs each)
+
+__device__ __forceinline__ double act_f64(double z, int act) {
+    return act == ELM_ACT_TANH ? tanh(z) : 1.0 / (1.0 + exp(-z));
+}
+
+template <typename XT>
+__device__ __forceinline__ double ld_x(const XT *p) { return (double)(*p); }
+
+// ---------------------------------------------------------------- hidden
+// Ht[j, i] = a_j g(sum_k X[i,k] W[k,j] + b_j); block = 64 neurons x 64
+// samples; k runs in ascending slabs of 16.
+template <typename XT>
+__global__ void __launch_bounds__(NT)
+hidden_f64_kernel(const XT *__restrict__ X, int64_t N, int64_t n, int64_t ldx,
+                  const double *__restrict__ W, int64_t ldw,
+                  const double *__restrict__ b, const double *__restrict__ a,
+                  int64_t L, int act, double *__restrict__ Ht, int64_t ldh) {
+    __shared__ double Ws[TK][TB];
+    __shared__ double Xs[TK][TB + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t i0 = (int64_t)blockIdx.x * TB, j0 = (int64_t)blockIdx.y * TB;
+    double acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < n; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * TB; e += NT) {
+            int kk = e / TB, jj = e % TB;
+            int64_t k = k0 + kk, j = j0 + jj;
+            Ws[kk][jj] = (k < n && j < L) ? W[k * ldw + j] : 0.0;
+            int ii = e / TK, kx = e % TK;
+            int64_t i = i0 + ii, k2 = k0 + kx;
+            Xs[kx][ii] = (i < N && k2 < n) ? ld_x(X + i * ldx + k2) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk++) {
+            double w[4], x[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                w[q] = Ws[kk][ty + 16 * q];
+                x[q] = Xs[kk][tx + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc[p][q] = fma(w[p], x[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        int64_t j = j0 + ty + 16 * p;
+        if (j >= L) continue;
+        double bj = b[j], aj = a ? a[j] : 1.0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int64_t i = i0 + tx + 16 * q;
+            if (i < N) Ht[j * ldh + i] = aj * act_f64(acc[p][q] + bj, act);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Gram
+// Lower tiles of the Gram of the augmented rows [Ht ; T^T] over one k-range
+// (split p of nsplit), written to part[p].  Row j < L is Ht[j, :], row
+// L + c is T[:, c].
+__device__ __forceinline__ double aug(const double *Ht, int64_t ldh, int64_t L,
+                                      const double *T, int64_t ldt, int64_t j,
+                                      int64_t i) {
+    return j < L ? Ht[j * ldh + i] : T[i * ldt + (j - L)];
+}
+
+__global__ void __launch_bounds__(NT)
+gram_f64_kernel(const double *__restrict__ Ht, int64_t ldh, int64_t L,
+                int64_t N, const double *__restrict__ T, int64_t ldt, int64_t m,
+                double *__restrict__ part, int64_t chunk) {
+    __shared__ double As[TK][TB + 1];
+    __shared__ double Bs[TK][TB + 1];
+    const int64_t Lt = L + m;
+    // triangular tile index -> (J >= I)
+    int64_t t = blockIdx.x;
+    int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (J * (J + 1) / 2 > t) J--;
+    while ((J + 1) * (J + 2) / 2 <= t) J++;
+    int64_t I = t - J * (J + 1) / 2;
+    const int64_t r0 = J * TB, c0 = I * TB;
+    const int64_t kb = (int64_t)blockIdx.y * chunk;
+    const int64_t ke = min(N, kb + chunk);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int64_t k0 = kb; k0 < ke; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * TB; e += NT) {
+            int rr = e / TK, kk = e % TK;
+            int64_t k = k0 + kk;
+            int64_t jr = r0 + rr, jc = c0 + rr;
+            As[kk][rr] = (k < ke && jr < Lt) ? aug(Ht, ldh, L, T, ldt, jr, k) : 0.0;
+            Bs[kk][rr] = (k < ke && jc < Lt) ? aug(Ht, ldh, L, T, ldt, jc, k) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk++) {
+            double u[4], v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                u[q] = As[kk][ty + 16 * q];
+                v[q] = Bs[kk][tx + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc[p][q] = fma(u[p], v[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+    double *out = part + (int64_t)blockIdx.y * Lt * Lt;
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        int64_t j = r0 + ty + 16 * p;
+        if (j >= Lt) continue;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int64_t l = c0 + tx + 16 * q;
+            if (l < Lt && l <= j) out[j * Lt + l] = acc[p][q];
+        }
+    }
+}
+
+// Sum the splits in ascending order and scatter into S (both triangles) and Z.
+__global__ void gram_reduce_kernel(const double *__restrict__ part, int nsplit,
+                                   int64_t L, int64_t m, double *__restrict__ S,
+                                   int64_t lds, double *__restrict__ Z,
+                                   int64_t ldz) {
+    const int64_t Lt = L + m;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = Lt * Lt;
+    for (; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = e / Lt, l = e % Lt;
+        if (l > j || l >= L) continue;
+        double v = 0.0;
+        for (int p = 0; p < nsplit; p++) v += part[(int64_t)p * total + e];
+        if (j < L) {
+            S[j * lds + l] = v;
+            S[l * lds + j] = v;
+        } else {
+            Z[l * ldz + (j - L)] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- GEMM
+__global__ void __launch_bounds__(NT)
+gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                const double *__restrict__ A, int64_t sAm, int64_t sAk,
+                const double *__restrict__ B, int64_t sBk, int64_t sBn,
+                double beta, double *__restrict__ C, int64_t ldc) {
+    __shared__ double As[TK][TB + 1];
+    __shared__ double Bs[TK][TB + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * TB, n0 = (int64_t)blockIdx.x * TB;
+    double acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < K; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * TB; e += NT) {
+            int rr = e / TK, kk = e % TK;
+            int64_t k = k0 + kk, i = m0 + rr;
+            As[kk][rr] = (k < K && i < M) ? A[i * sAm + k * sAk] : 0.0;
+            int kk2 = e / TB, cc = e % TB;
+            int64_t k2 = k0 + kk2, j = n0 + cc;
+            Bs[kk2][cc] = (k2 < K && j < N) ? B[k2 * sBk + j * sBn] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk++) {
+            double u[4], v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                u[q] = As[kk][ty + 16 * q];
+                v[q] = Bs[kk][tx + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc[p][q] = fma(u[p], v[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        int64_t i = m0 + ty + 16 * p;
+        if (i >= M) continue;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int64_t j = n0 + tx + 16 * q;
+            if (j >= N) continue;
+            double v = alpha * acc[p][q];
+            C[i * ldc + j] = beta == 0.0 ? v : v + beta * C[i * ldc + j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- residual
+// R[i, c] = T[i, c] - sum_j Ht[j, i] beta[j, c]; one thread per sample, 8
+// target columns per grid.y slice, j ascending.
+constexpr int RC = 8;
+__global__ void __launch_bounds__(128)
+resid_f64_kernel(const double *__restrict__ Ht, int64_t ldh, int64_t L,
+                 int64_t N, const double *__restrict__ beta, int64_t m,
+                 const double *__restrict__ T, int64_t ldt,
+                 double *__restrict__ R) {
+    __shared__ double Bs[64][RC];
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int c0 = blockIdx.y * RC;
+    double acc[RC] = {};
+    for (int64_t j0 = 0; j0 < L; j0 += 64) {
+        for (int e = threadIdx.x; e < 64 * RC; e += 128) {
+            int jj = e / RC, cc = e % RC;
+            int64_t j = j0 + jj;
+            Bs[jj][cc] = (j < L && c0 + cc < m) ? beta[j * m + c0 + cc] : 0.0;
+        }
+        __syncthreads();
+        if (i < N) {
+            int64_t jn = min((int64_t)64, L - j0);
+            for (int jj = 0; jj < jn; jj++) {
+                double h = Ht[(j0 + jj) * ldh + i];
+#pragma unroll
+                for (int c = 0; c < RC; c++) acc[c] = fma(h, Bs[jj][c], acc[c]);
+            }
+        }
+        __syncthreads();
+    }
+    if (i < N)
+#pragma unroll
+        for (int c = 0; c < RC; c++)
+            if (c0 + c < m) R[i * m + c0 + c] = T[i * ldt + c0 + c] - acc[c];
+}
+
+// G[j, c] (split p) = sum_{i in split p} Ht[j, i] R[i, c]: one warp per
+// neuron j, lane l takes i = l, l+32, ... then a fixed shuffle tree.
+__global__ void __launch_bounds__(256)
+htr_f64_kernel(const double *__restrict__ Ht, int64_t ldh, int64_t L,
+               int64_t N, const double *__restrict__ R, int64_t m,
+               double *__restrict__ part, int64_t chunk) {
+    __shared__ double Rs[256][RC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + warp;
+    const int c0 = blockIdx.z * RC;
+    const int64_t ib = (int64_t)blockIdx.y * chunk, ie = min(N, ib + chunk);
+    double acc[RC] = {};
+    for (int64_t i0 = ib; i0 < ie; i0 += 256) {
+        for (int e = threadIdx.x; e < 256 * RC; e += 256) {
+            int ii = e / RC, cc = e % RC;
+            int64_t i = i0 + ii;
+            Rs[ii][cc] = (i < ie && c0 + cc < m) ? R[i * m + c0 + cc] : 0.0;
+        }
+        __syncthreads();
+        if (j < L) {
+            for (int ii = lane; ii < 256; ii += 32) {
+                int64_t i = i0 + ii;
+                double h = i < ie ? Ht[j * ldh + i] : 0.0;
+#pragma unroll
+                for (int c = 0; c < RC; c++) acc[c] = fma(h, Rs[ii][c], acc[c]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < RC; c++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0 && j < L)
+#pragma unroll
+        for (int c = 0; c < RC; c++)
+            if (c0 + c < m) part[((int64_t)blockIdx.y * L + j) * m + c0 + c] = acc[c];
+}
+
+__global__ void split_sum_kernel(const double *__restrict__ part, int nsplit,
+                                 int64_t count, double *__restrict__ out) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    double v = 0.0;
+    for (int p = 0; p < nsplit; p++) v += part[(int64_t)p * count + e];
+    out[e] = v;
+}
+
+// ---------------------------------------------------------------- predict
+// Y[i, c] = sum_j g(x_i . w_j + b_j) a_j beta[j, c] for 16 target columns;
+// 64 samples per block, neurons in ascending tiles of 64; the H tile never
+// leaves shared memory (it overlays the X/W staging slabs).
+constexpr int PC = 16;
+template <typename XT>
+__global__ void __launch_bounds__(NT)
+predict_f64_kernel(const XT *__restrict__ X, int64_t N, int64_t n, int64_t ldx,
+                   const double *__restrict__ W, int64_t ldw,
+                   const double *__restrict__ b, const double *__restrict__ a,
+                   int64_t L, int act, const double *__restrict__ beta,
+                   int64_t ldb, int64_t m, double *__restrict__ Y, int64_t ldy) {
+    __shared__ union {
+        struct {
+            double Ws[TK][TB];
+            double Xs[TK][TB + 1];
+        } st;
+        double Hs[TB][TB + 1];
+    } sm;
+    __shared__ double Bs[TB][PC + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t i0 = (int64_t)blockIdx.x * TB;
+    const int yi = threadIdx.x & 63, yg = threadIdx.x >> 6;  // sample, column group
+    double yacc[PC / 4] = {};
+    for (int64_t j0 = 0; j0 < L; j0 += TB) {
+        double acc[4][4] = {};
+        for (int64_t k0 = 0; k0 < n; k0 += TK) {
+            for (int e = threadIdx.x; e < TK * TB; e += NT) {
+                int kk = e / TB, jj = e % TB;
+                int64_t k = k0 + kk, j = j0 + jj;
+                sm.st.Ws[kk][jj] = (k < n && j < L) ? W[k * ldw + j] : 0.0;
+                int ii = e / TK, kx = e % TK;
+                int64_t i = i0 + ii, k2 = k0 + kx;
+                sm.st.Xs[kx][ii] = (i < N && k2 < n) ? ld_x(X + i * ldx + k2) : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < TK; kk++) {
+                double w[4], x[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    w[q] = sm.st.Ws[kk][ty + 16 * q];
+                    x[q] = sm.st.Xs[kk][tx + 16 * q];
+                }
+#pragma unroll
+                for (int p = 0; p < 4; p++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) acc[p][q] = fma(w[p], x[q], acc[p][q]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            int64_t j = j0 + ty + 16 * p;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                double hv = 0.0;
+                if (j < L) hv = (a ? a[j] : 1.0) * act_f64(acc[p][q] + b[j], act);
+                sm.Hs[tx + 16 * q][ty + 16 * p] = hv;
+            }
+        }
+        for (int e = threadIdx.x; e < TB * PC; e += NT) {
+            int jj = e / PC, c = e % PC;
+            int64_t j = j0 + jj;
+            Bs[jj][c] = (j < L && c < m) ? beta[j * ldb + c] : 0.0;
+        }
+        __syncthreads();
+        for (int jj = 0; jj < TB; jj++) {
+            double h = sm.Hs[yi][jj];
+#pragma unroll
+            for (int q = 0; q < PC / 4; q++) yacc[q] = fma(h, Bs[jj][yg + 4 * q], yacc[q]);
+        }
+        __syncthreads();
+    }
+    int64_t i = i0 + yi;
+    if (i < N)
+#pragma unroll
+        for (int q = 0; q < PC / 4; q++) {
+            int c = yg + 4 * q;
+            if (c < m) Y[i * ldy + c] = yacc[q];
+        }
+}
+
+__global__ void sumsq_kernel(const double *__restrict__ x, int64_t rows,
+                             int64_t cols, int64_t ld, double *__restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    int64_t total = rows * cols;
+    for (int64_t e = threadIdx.x; e < total; e += 256) {
+        double v = x[(e / cols) * ld + e % cols];
+        s = fma(v, v, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+template <typename XT>
+__global__ void check_finite_kernel(const XT *__restrict__ x, int64_t rows,
+                                    int64_t cols, int64_t ld, int32_t *flag) {
+    int64_t total = rows * cols;
+    int bad = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double v = (double)x[(e / cols) * ld + e % cols];
+        bad |= !isfinite(v);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+__global__ void gather_rows_kernel(const double *__restrict__ src, int64_t lds,
+                                   const int32_t *__restrict__ perm,
+                                   const int64_t *__restrict__ r_dev, int64_t rmax,
+                                   int64_t m, double *__restrict__ dst, int64_t ldd) {
+    int64_t r = r_dev ? *r_dev : rmax;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < r * m; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / m, c = e % m;
+        dst[i * ldd + c] = src[(int64_t)perm[i] * lds + c];
+    }
+}
+
+__global__ void scatter_rows_kernel(const double *__restrict__ src, int64_t m,
+                                    const int32_t *__restrict__ perm, int64_t L,
+                                    double *__restrict__ beta, int64_t ldb,
+                                    double alpha, int accumulate) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < L * m; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / m, c = e % m;
+        double *d = beta + (int64_t)perm[i] * ldb + c;
+        double v = alpha * src[i * m + c];
+        *d = accumulate ? *d + v : v;
+    }
+}
+
+// beta += dB; out[0] = ||dB||_F^2, out[1] = ||beta||_F^2 (one block, fixed
+// reduction tree).
+__global__ void axpy_norms_kernel(double *__restrict__ beta, const double *__restrict__ dB,
+                                  int64_t count, double *__restrict__ out) {
+    __shared__ double r0[256], r1[256];
+    double a = 0.0, c = 0.0;
+    for (int64_t e = threadIdx.x; e < count; e += 256) {
+        double d = dB[e];
+        double v = beta[e] + d;
+        beta[e] = v;
+        a = fma(d, d, a);
+        c = fma(v, v, c);
+    }
+    r0[threadIdx.x] = a;
+    r1[threadIdx.x] = c;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            r0[threadIdx.x] += r0[threadIdx.x + w];
+            r1[threadIdx.x] += r1[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = r0[0];
+        out[1] = r1[0];
+    }
+}
+
+__global__ void set_identity_kernel(double *__restrict__ A, int64_t n) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < n * n; e += (int64_t)gridDim.x * blockDim.x) A[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+inline unsigned blocks_for(int64_t work, int per = 256, int64_t cap = 65535 * 8) {
+    int64_t g = (work + per - 1) / per;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+void hidden_f64(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n,
+                int64_t ldx, const double *W, int64_t ldw, const double *b,
+                const double *a, int64_t L, int act, double *Ht, int64_t ldh) {
+    dim3 grid((unsigned)((N + TB - 1) / TB), (unsigned)((L + TB - 1) / TB));
+    if (xdt == ELM_F64)
+        hidden_f64_kernel<double><<<grid, NT, 0, s>>>((const double *)X, N, n, ldx, W, ldw,
+                                                      b, a, L, act, Ht, ldh);
+    else
+        hidden_f64_kernel<float><<<grid, NT, 0, s>>>((const float *)X, N, n, ldx, W, ldw,
+                                                     b, a, L, act, Ht, ldh);
+    ELM_CHECK_LAUNCH();
+}
+
+int gram_f64_nsplit(int64_t L, int64_t m, int64_t N, int sms) {
+    int64_t T = (L + m + TB - 1) / TB;
+    int64_t tiles = T * (T + 1) / 2;
+    int64_t want = (2 * (int64_t)sms + tiles - 1) / tiles;
+    int64_t cap = (N + 1023) / 1024;
+    int64_t ns = want < cap ? want : cap;
+    return (int)(ns < 1 ? 1 : (ns > 64 ? 64 : ns));
+}
+
+size_t gram_f64_ws(int64_t L, int64_t m, int nsplit) {
+    return (size_t)nsplit * (size_t)(L + m) * (size_t)(L + m);
+}
+
+void gram_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
+              int64_t N, const double *T, int64_t ldt, int64_t m, double *S,
+              int64_t lds, double *Z, int64_t ldz, double *part, int nsplit) {
+    int64_t Tn = (L + m + TB - 1) / TB;
+    int64_t chunk = ((N + nsplit - 1) / nsplit + TK - 1) / TK * TK;
+    dim3 grid((unsigned)(Tn * (Tn + 1) / 2), (unsigned)nsplit);
+    gram_f64_kernel<<<grid, NT, 0, s>>>(Ht, ldh, L, N, T, ldt, m, part, chunk);
+    ELM_CHECK_LAUNCH();
+    int64_t Lt = L + m;
+    gram_reduce_kernel<<<blocks_for(Lt * Lt), 256, 0, s>>>(part, nsplit, L, m, S, lds,
+                                                            Z, ldz);
+    ELM_CHECK_LAUNCH();
+}
+
+void gemm_f64(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha,
+              const double *A, int64_t sAm, int64_t sAk, const double *B,
+              int64_t sBk, int64_t sBn, double beta, double *C, int64_t ldc) {
+    if (M <= 0 || N <= 0) return;
+    dim3 grid((unsigned)((N + TB - 1) / TB), (unsigned)((M + TB - 1) / TB));
+    gemm_f64_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C,
+                                        ldc);
+    ELM_CHECK_LAUNCH();
+}
+
+void resid_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
+               int64_t N, const double *beta, int64_t m, const double *T,
+               int64_t ldt, double *R) {
+    dim3 grid((unsigned)((N + 127) / 128), (unsigned)((m + RC - 1) / RC));
+    resid_f64_kernel<<<grid, 128, 0, s>>>(Ht, ldh, L, N, beta, m, T, ldt, R);
+    ELM_CHECK_LAUNCH();
+}
+
+int htr_f64_nsplit(int64_t L, int64_t N, int sms) {
+    int64_t blocks = (L + 7) / 8;
+    int64_t want = (4 * (int64_t)sms + blocks - 1) / blocks;
+    int64_t cap = (N + 4095) / 4096;
+    int64_t ns = want < cap ? want : cap;
+    return (int)(ns < 1 ? 1 : (ns > 128 ? 128 : ns));
+}
+
+size_t htr_f64_ws(int64_t L, int64_t m, int nsplit) { return (size_t)nsplit * L * m; }
+
+void htr_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
+             int64_t N, const double *R, int64_t m, double *G, double *part,
+             int nsplit) {
+    int64_t chunk = ((N + nsplit - 1) / nsplit + 255) / 256 * 256;
+    dim3 grid((unsigned)((L + 7) / 8), (unsigned)nsplit, (unsigned)((m + RC - 1) / RC));
+    htr_f64_kernel<<<grid, 256, 0, s>>>(Ht, ldh, L, N, R, m, part, chunk);
+    ELM_CHECK_LAUNCH();
+    split_sum_kernel<<<blocks_for(L * m), 256, 0, s>>>(part, nsplit, L * m, G);
+    ELM_CHECK_LAUNCH();
+}
+
+void predict_f64(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n,
+                 int64_t ldx, const double *W, int64_t ldw, const double *b,
+                 const double *a, int64_t L, int act, const double *beta,
+                 int64_t ldb, int64_t m, double *Y, int64_t ldy) {
+    // one pass handles PC target columns
+    for (int64_t c0 = 0; c0 < m; c0 += PC) {
+        int64_t mc = m - c0 < PC ? m - c0 : PC;
+        dim3 grid((unsigned)((N + TB - 1) / TB));
+        if (xdt == ELM_F64)
+            predict_f64_kernel<double><<<grid, NT, 0, s>>>(
+                (const double *)X, N, n, ldx, W, ldw, b, a, L, act, beta + c0, ldb, mc,
+                Y + c0, ldy);
+        else
+            predict_f64_kernel<float><<<grid, NT, 0, s>>>(
+                (const float *)X, N, n, ldx, W, ldw, b, a, L, act, beta + c0, ldb, mc,
+                Y + c0, ldy);
+        ELM_CHECK_LAUNCH();
+    }
+}
+
+void sumsq(cudaStream_t s, const double *x, int64_t rows, int64_t cols, int64_t ld,
+           double *out) {
+    sumsq_kernel<<<1, 256, 0, s>>>(x, rows, cols, ld, out);
+    ELM_CHECK_LAUNCH();
+}
+
+void check_finite(cudaStream_t s, const void *x, int xdt, int64_t rows, int64_t cols,
+                  int64_t ld, int32_t *flag) {
+    unsigned g = blocks_for(rows * cols, 256, 4096);
+    if (xdt == ELM_F64)
+        check_finite_kernel<double><<<g, 256, 0, s>>>((const double *)x, rows, cols, ld, flag);
+    else
+        check_finite_kernel<float><<<g, 256, 0, s>>>((const float *)x, rows, cols, ld, flag);
+    ELM_CHECK_LAUNCH();
+}
+
+void gather_rows(cudaStream_t s, const double *src, int64_t lds, const int32_t *perm,
+                 const int64_t *r_dev, int64_t rmax, int64_t m, double *dst, int64_t ldd) {
+    gather_rows_kernel<<<blocks_for(rmax * m), 256, 0, s>>>(src, lds, perm, r_dev, rmax, m,
+                                                            dst, ldd);
+    ELM_CHECK_LAUNCH();
+}
+
+void scatter_rows(cudaStream_t s, const double *src, int64_t m, const int32_t *perm,
+                  int64_t L, double *beta, int64_t ldb, double alpha, int accumulate) {
+    scatter_rows_kernel<<<blocks_for(L * m), 256, 0, s>>>(src, m, perm, L, beta, ldb, alpha,
+                                                          accumulate);
+    ELM_CHECK_LAUNCH();
+}
+
+void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, double *out) {
+    axpy_norms_kernel<<<1, 256, 0, s>>>(beta, dB, count, out);
+    ELM_CHECK_LAUNCH();
+}
+
+void set_identity(cudaStream_t s, double *A, int64_t n) {
+    set_identity_kernel<<<blocks_for(n * n), 256, 0, s>>>(A, n);
+    ELM_CHECK_LAUNCH();
+}
+
+}  // namespace elm

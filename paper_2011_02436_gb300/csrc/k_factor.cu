@@ -1,0 +1,589 @@
+// Rank-revealing factorisation of the Gram matrix (Eq. 6; Algorithm 1
+// steps 3-4) and the triangular solves of the full-rank route to H^+.
+//
+// Diagonal-pivoted Cholesky of the equilibrated Gram matrix, blocked in
+// panels of nb pivots:
+//   * the panel runs on one thread-block cluster (8 or 16 CTAs).  Each CTA
+//     owns a slice of the active columns and keeps their updated diagonal
+//     and the panel rows in shared memory.  Per pivot: every CTA publishes
+//     its local argmax, one hardware cluster barrier, every CTA reads the
+//     candidates through distributed shared memory and takes the same
+//     decision (largest diagonal, ties to the lowest original index).  No
+//     spin-waits: the only waits are cluster barriers.
+//   * the trailing update A' = A - P^T P (P: the panel rows) runs on the
+//     whole GPU and at the same time compacts the active matrix (pivoted
+//     columns drop out), so every panel works on a dense (L-k) x (L-k)
+//     matrix and no row/column swaps are ever performed.
+// Pivot rows are kept in original column order (Rrow) and gathered into
+// pivot order, unscaled, at the end.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "elm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace elm {
+
+namespace {
+
+constexpr int FT = 256;       // threads per CTA in the panel / solves
+constexpr int MAXNB = 32;     // largest panel width
+
+struct Cand {
+    double val;
+    int32_t orig;
+    int32_t x;
+};
+
+__device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
+    return a.val > b.val || (a.val == b.val && a.orig < b.orig);
+}
+
+__device__ __forceinline__ Cand shfl_cand(const Cand &c, int o) {
+    Cand r;
+    r.val = __shfl_xor_sync(0xffffffffu, c.val, o);
+    r.orig = __shfl_xor_sync(0xffffffffu, c.orig, o);
+    r.x = __shfl_xor_sync(0xffffffffu, c.x, o);
+    return r;
+}
+
+// Block-wide argmax of the unpivoted diagonal entries of this CTA's slice.
+__device__ void local_argmax(const double *d, const int32_t *piv, const int32_t *act,
+                             int64_t x0, int64_t nloc, Cand *out, Cand *wred) {
+    Cand best{-INFINITY, 0x7fffffff, -1};
+    for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
+        if (piv[xl]) continue;
+        Cand c{d[xl], act[x0 + xl], (int32_t)(x0 + xl)};
+        if (better(c, best)) best = c;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        Cand c = shfl_cand(best, o);
+        if (better(c, best)) best = c;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wred[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Cand b = wred[0];
+        for (int w = 1; w < FT / 32; w++)
+            if (better(wred[w], b)) b = wred[w];
+        *out = b;
+    }
+    __syncthreads();
+}
+
+// S -> A = diag(s) S diag(s), s_j = 1/sqrt(S_jj) (0 if S_jj <= 0); dS = diag(S).
+__global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t L,
+                             double *__restrict__ A, int64_t lda, double *__restrict__ dS,
+                             int32_t *__restrict__ act, FactorState *st) {
+    int64_t total = L * L;
+    int bad = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = e / L, l = e % L;
+        double dj = S[j * lds + j], dl = S[l * lds + l];
+        double sj = dj > 0.0 ? 1.0 / sqrt(dj) : 0.0;
+        double sl = dl > 0.0 ? 1.0 / sqrt(dl) : 0.0;
+        double v = S[j * lds + l];
+        bad |= !isfinite(v);
+        A[j * lda + l] = (v * sj) * sl;
+        if (l == 0) {
+            dS[j] = dj;
+            act[j] = (int32_t)j;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->k = 0;
+        st->Lr = L;
+        st->rank = L;
+        st->done = 0;
+        st->steps = 0;
+    }
+}
+
+// One panel of up to nb pivots on a cluster.  A: active matrix (Lr x Lr,
+// full symmetric, lda), act: active -> original index.  Writes the panel
+// rows P (active index space, row stride ldp), the pivot rows Rrow (original
+// column order), perm, the compaction map rem / act_next and the state.
+__global__ void __launch_bounds__(FT)
+panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restrict__ act,
+             double *__restrict__ P, int64_t ldp, double *__restrict__ Rrow, int64_t ldr,
+             int32_t *__restrict__ perm, int32_t *__restrict__ rem,
+             int32_t *__restrict__ act_next, FactorState *st, int64_t L, int nb,
+             int64_t wmax, double tau) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CS = (int)cluster.num_blocks();
+    const int cr = (int)cluster.block_rank();
+    __shared__ Cand cand[2];
+    __shared__ Cand wred[FT / 32];
+    __shared__ Cand s_best;
+    __shared__ double u[MAXNB];
+    __shared__ int32_t s_cnt;
+    __shared__ int64_t s_off, s_tot;
+    extern __shared__ double dyn[];
+
+    const FactorState s0 = *st;
+    if (s0.done) return;  // uniform over the cluster
+    const int64_t Lr = s0.Lr, k0 = s0.k;
+    const int64_t Wd = (Lr + CS - 1) / CS;
+    const int64_t x0 = (int64_t)cr * Wd;
+    const int64_t nloc = x0 < Lr ? (Lr - x0 < Wd ? Lr - x0 : Wd) : 0;
+    double *Ps = dyn;                          // nb x wmax
+    double *d = dyn + (int64_t)nb * wmax;      // wmax
+    int32_t *piv = (int32_t *)(d + wmax);      // wmax
+
+    for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
+        d[xl] = A[(x0 + xl) * lda + x0 + xl];
+        piv[xl] = 0;
+    }
+    __syncthreads();
+    local_argmax(d, piv, act, x0, nloc, &cand[0], wred);
+    cluster.sync();
+
+    const int tmax = (int)(nb < Lr ? nb : Lr);
+    int steps = 0;
+    bool done = false;
+    for (int t = 0; t < tmax; t++) {
+        if (threadIdx.x == 0) {
+            Cand best{-INFINITY, 0x7fffffff, -1};
+            for (int c = 0; c < CS; c++) {
+                Cand v = *cluster.map_shared_rank(&cand[t & 1], c);
+                if (better(v, best)) best = v;
+            }
+            s_best = best;
+        }
+        __syncthreads();
+        const Cand best = s_best;
+        if (!(best.val > tau)) {
+            done = true;
+            break;
+        }
+        const int64_t q = best.x;
+        const int owner = (int)(q / Wd);
+        const int64_t qloc = q - (int64_t)owner * Wd;
+        const double rkk = sqrt(best.val);
+        if (threadIdx.x < t) {
+            const double *ops = cluster.map_shared_rank(Ps, owner);
+            u[threadIdx.x] = ops[(int64_t)threadIdx.x * Wd + qloc];
+        }
+        __syncthreads();
+        const double *Aq = A + q * lda;
+        for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
+            const int64_t x = x0 + xl;
+            double v;
+            if (x == q) {
+                v = rkk;
+            } else if (piv[xl]) {
+                v = 0.0;
+            } else {
+                v = Aq[x];
+                for (int s = 0; s < t; s++) v = fma(-u[s], Ps[(int64_t)s * Wd + xl], v);
+                v = v / rkk;
+                d[xl] = fma(-v, v, d[xl]);
+            }
+            Ps[(int64_t)t * Wd + xl] = v;
+            P[(int64_t)t * ldp + x] = v;
+            Rrow[(k0 + t) * ldr + act[x]] = v;
+        }
+        __syncthreads();
+        if (owner == cr && threadIdx.x == 0) piv[qloc] = 1;
+        if (cr == 0 && threadIdx.x == 0) perm[k0 + t] = act[q];
+        __syncthreads();
+        local_argmax(d, piv, act, x0, nloc, &cand[(t + 1) & 1], wred);
+        cluster.sync();
+        steps = t + 1;
+    }
+
+    // Compaction: unpivoted active columns keep their relative order.
+    if (threadIdx.x < 32) {
+        int32_t cnt = 0;
+        for (int64_t b0 = 0; b0 < nloc; b0 += 32) {
+            int64_t xl = b0 + threadIdx.x;
+            bool f = xl < nloc && !piv[xl];
+            cnt += __popc(__ballot_sync(0xffffffffu, f));
+        }
+        if (threadIdx.x == 0) s_cnt = cnt;
+    }
+    cluster.sync();
+    if (threadIdx.x == 0) {
+        int64_t off = 0, tot = 0;
+        for (int c = 0; c < CS; c++) {
+            int32_t v = *cluster.map_shared_rank(&s_cnt, c);
+            if (c < cr) off += v;
+            tot += v;
+        }
+        s_off = off;
+        s_tot = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int64_t pos = s_off;
+        for (int64_t b0 = 0; b0 < nloc; b0 += 32) {
+            int64_t xl = b0 + threadIdx.x;
+            bool f = xl < nloc && !piv[xl];
+            unsigned mask = __ballot_sync(0xffffffffu, f);
+            if (f) {
+                int64_t p = pos + __popc(mask & ((1u << threadIdx.x) - 1u));
+                int32_t o = act[x0 + xl];
+                rem[p] = (int32_t)(x0 + xl);
+                act_next[p] = o;
+                if (done) perm[k0 + steps + p] = o;
+            }
+            pos += __popc(mask);
+        }
+    }
+    if (cr == 0 && threadIdx.x == 0) {
+        st->k = k0 + steps;
+        st->Lr = s_tot;
+        st->steps = steps;
+        if (done || k0 + steps >= L) {
+            st->done = 1;
+            st->rank = k0 + steps;
+        }
+    }
+    cluster.sync();  // keep shared memory alive until every peer has read it
+}
+
+// A_next[x', y'] = A[rem x', rem y'] - sum_t P[t, rem x'] P[t, rem y'] on
+// lower tiles, mirrored to the upper triangle.
+__global__ void __launch_bounds__(256)
+trailing_kernel(const double *__restrict__ A, double *__restrict__ An, int64_t lda,
+                const double *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
+                const FactorState *__restrict__ st) {
+    const FactorState s = *st;
+    if (s.done) return;
+    const int64_t Lr = s.Lr;
+    const int steps = (int)s.steps;
+    int64_t t = blockIdx.x;
+    int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (J * (J + 1) / 2 > t) J--;
+    while ((J + 1) * (J + 2) / 2 <= t) J++;
+    const int64_t I = t - J * (J + 1) / 2;
+    const int64_t r0 = J * 64, c0 = I * 64;
+    if (r0 >= Lr) return;
+    __shared__ double Pr[MAXNB][65];
+    __shared__ double Pc[MAXNB][65];
+    __shared__ int32_t rr_[64], rc_[64];
+    if (threadIdx.x < 64) {
+        int64_t x = r0 + threadIdx.x, y = c0 + threadIdx.x;
+        rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
+        rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < MAXNB * 64; e += 256) {
+        int tt = e / 64, k = e % 64;
+        Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : 0.0;
+        Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int a = rr_[ty + 16 * p], b = rc_[tx + 16 * q];
+            acc[p][q] = (a >= 0 && b >= 0) ? A[(int64_t)a * lda + b] : 0.0;
+        }
+    for (int tt = 0; tt < steps; tt++) {
+        double u[4], v[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            u[q] = Pr[tt][ty + 16 * q];
+            v[q] = Pc[tt][tx + 16 * q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[p][q] = fma(-u[p], v[q], acc[p][q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        int64_t x = r0 + ty + 16 * p;
+        if (x >= Lr) continue;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int64_t y = c0 + tx + 16 * q;
+            if (y >= Lr) continue;
+            An[x * lda + y] = acc[p][q];
+            if (J != I) An[y * lda + x] = acc[p][q];
+        }
+    }
+}
+
+// R[i, pos] = Rrow[i, perm pos] sqrt(dS[perm pos]) for i < rank, pos >= i;
+// Rt = R^T.  32 x 32 tiles transposed through shared memory.
+__global__ void finalize_kernel(const double *__restrict__ Rrow, int64_t ldrr,
+                                const int32_t *__restrict__ perm,
+                                const double *__restrict__ dS,
+                                const FactorState *__restrict__ st, int64_t L,
+                                double *__restrict__ R, double *__restrict__ Rt) {
+    __shared__ double tile[32][33];
+    const int64_t r = st->rank;
+    const int64_t i0 = (int64_t)blockIdx.y * 32, p0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int yy = ty; yy < 32; yy += 8) {
+        int64_t i = i0 + yy, pos = p0 + tx;
+        double v = 0.0;
+        if (i < r && pos < L && pos >= i) {
+            int32_t o = perm[pos];
+            double dd = dS[o];
+            v = Rrow[i * ldrr + o] * (dd > 0.0 ? sqrt(dd) : 0.0);
+        }
+        if (i < L && pos < L) R[i * L + pos] = v;
+        tile[yy][tx] = v;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        int64_t pos = p0 + yy, i = i0 + tx;
+        if (i < L && pos < L) Rt[pos * L + i] = tile[tx][yy];
+    }
+}
+
+// In-place triangular solves on CB right-hand-side columns per CTA, the
+// columns held in shared memory.  Forward: solves R11^T x = b reading rows
+// of R; backward: solves R11 x = b reading rows of Rt (columns of R).
+__global__ void __launch_bounds__(FT)
+trsm_fwd_kernel(const double *__restrict__ R, int64_t ldr, const int64_t *r_dev,
+                int64_t r_max, double *__restrict__ B, int64_t ldb, int64_t q, int CB) {
+    extern __shared__ double bs[];
+    __shared__ double xs[8];
+    const int64_t r = r_dev ? *r_dev : r_max;
+    const int64_t c0 = (int64_t)blockIdx.x * CB;
+    const int nc = (int)(q - c0 < CB ? q - c0 : CB);
+    if (nc <= 0) return;
+    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
+        int64_t i = e / nc, c = e % nc;
+        bs[c * r_max + i] = B[i * ldb + c0 + c];
+    }
+    __syncthreads();
+    for (int64_t i = 0; i < r; i++) {
+        if (threadIdx.x == 0) {
+            double rii = R[i * ldr + i];
+            for (int c = 0; c < nc; c++) {
+                double x = bs[c * r_max + i] / rii;
+                bs[c * r_max + i] = x;
+                xs[c] = x;
+            }
+        }
+        __syncthreads();
+        for (int64_t j = i + 1 + threadIdx.x; j < r; j += FT) {
+            double rij = R[i * ldr + j];
+            for (int c = 0; c < nc; c++) bs[c * r_max + j] = fma(-rij, xs[c], bs[c * r_max + j]);
+        }
+        __syncthreads();
+    }
+    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
+        int64_t i = e / nc, c = e % nc;
+        B[i * ldb + c0 + c] = bs[c * r_max + i];
+    }
+}
+
+__global__ void __launch_bounds__(FT)
+trsm_bwd_kernel(const double *__restrict__ Rt, int64_t ldr, const int64_t *r_dev,
+                int64_t r_max, double *__restrict__ B, int64_t ldb, int64_t q, int CB) {
+    extern __shared__ double bs[];
+    __shared__ double xs[8];
+    const int64_t r = r_dev ? *r_dev : r_max;
+    const int64_t c0 = (int64_t)blockIdx.x * CB;
+    const int nc = (int)(q - c0 < CB ? q - c0 : CB);
+    if (nc <= 0) return;
+    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
+        int64_t i = e / nc, c = e % nc;
+        bs[c * r_max + i] = B[i * ldb + c0 + c];
+    }
+    __syncthreads();
+    for (int64_t i = r - 1; i >= 0; i--) {
+        if (threadIdx.x == 0) {
+            double rii = Rt[i * ldr + i];
+            for (int c = 0; c < nc; c++) {
+                double x = bs[c * r_max + i] / rii;
+                bs[c * r_max + i] = x;
+                xs[c] = x;
+            }
+        }
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < i; j += FT) {
+            double rji = Rt[i * ldr + j];
+            for (int c = 0; c < nc; c++) bs[c * r_max + j] = fma(-rji, xs[c], bs[c * r_max + j]);
+        }
+        __syncthreads();
+    }
+    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
+        int64_t i = e / nc, c = e % nc;
+        B[i * ldb + c0 + c] = bs[c * r_max + i];
+    }
+}
+
+int g_cluster = 0;  // chosen cluster size (per process; devices are alike)
+
+int pick_cluster(size_t smem_for16, size_t smem_for8) {
+    if (g_cluster) return g_cluster;
+    cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int best = 8;
+    for (int cs : {16, 8}) {
+        size_t sm = cs == 16 ? smem_for16 : smem_for8;
+        cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(FT);
+        cfg.dynamicSmemBytes = sm;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, panel_kernel, &cfg) == cudaSuccess && n > 0) {
+            best = cs;
+            break;
+        }
+        cudaGetLastError();
+    }
+    g_cluster = best;
+    return best;
+}
+
+void panel_geometry(int64_t L, int cs, int *nb, int64_t *wmax, size_t *smem) {
+    *wmax = (L + cs - 1) / cs;
+    const size_t budget = 200 * 1024;
+    int64_t fit = (int64_t)((budget - (size_t)(*wmax) * 12) / ((size_t)(*wmax) * 8));
+    int b = (int)(fit < 16 ? fit : 16);
+    if (b < 1) b = 1;
+    *nb = b;
+    *smem = (size_t)b * (*wmax) * 8 + (size_t)(*wmax) * 12 + 64;
+}
+
+}  // namespace
+
+size_t factor_ws_bytes(int64_t L) {
+    Arena a;
+    factor_ws_carve(a, L);
+    return a.used;
+}
+
+FactorWs factor_ws_carve(Arena &ar, int64_t L) {
+    FactorWs w;
+    w.A0 = ar.take<double>(L * L);
+    w.A1 = ar.take<double>(L * L);
+    w.Rrow = ar.take<double>(L * L);
+    w.P = ar.take<double>((int64_t)MAXNB * L);
+    w.dS = ar.take<double>(L);
+    w.act0 = ar.take<int32_t>(L);
+    w.act1 = ar.take<int32_t>(L);
+    w.rem = ar.take<int32_t>(L);
+    w.perm = ar.take<int32_t>(L);
+    w.st = ar.take<FactorState>(1);
+    return w;
+}
+
+void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
+                    double tau, const FactorWs &w, double *R, double *Rt, int sms) {
+    if (L > ELM_MAX_L) throw ElmError(ELM_ERR_UNSUPPORTED, "L above ELM_MAX_L");
+    int nb16, nb8;
+    int64_t w16, w8;
+    size_t sm16, sm8;
+    panel_geometry(L, 16, &nb16, &w16, &sm16);
+    panel_geometry(L, 8, &nb8, &w8, &sm8);
+    const int cs = pick_cluster(sm16, sm8);
+    int nb;
+    int64_t wmax;
+    size_t smem;
+    panel_geometry(L, cs, &nb, &wmax, &smem);
+    ELM_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+
+    ELM_CUDA(cudaMemsetAsync(w.st, 0, sizeof(FactorState), s));
+    ELM_CUDA(cudaMemsetAsync(w.Rrow, 0, sizeof(double) * L * L, s));
+    {
+        int64_t blocks = (L * L + 255) / 256;
+        if (blocks > 8 * 1024) blocks = 8 * 1024;
+        equil_kernel<<<(unsigned)blocks, 256, 0, s>>>(S, lds, L, w.A0, L, w.dS, w.act0, w.st);
+        ELM_CHECK_LAUNCH();
+    }
+    const int64_t npanels = (L + nb - 1) / nb;
+    for (int64_t p = 0; p < npanels; p++) {
+        double *Ac = (p & 1) ? w.A1 : w.A0;
+        double *An = (p & 1) ? w.A0 : w.A1;
+        int32_t *ac = (p & 1) ? w.act1 : w.act0;
+        int32_t *an = (p & 1) ? w.act0 : w.act1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(FT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        ELM_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, (const double *)Ac, (int64_t)L,
+                                    (const int32_t *)ac, w.P, (int64_t)L, w.Rrow, (int64_t)L,
+                                    w.perm, w.rem, an, w.st, (int64_t)L, nb, wmax, tau));
+        ELM_CHECK_LAUNCH();
+        const int64_t Lup = L - (p + 1) * nb;
+        if (Lup > 0) {
+            int64_t T = (Lup + 63) / 64;
+            trailing_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(Ac, An, L, w.P, L,
+                                                                         w.rem, w.st);
+            ELM_CHECK_LAUNCH();
+        }
+    }
+    dim3 g((unsigned)((L + 31) / 32), (unsigned)((L + 31) / 32));
+    finalize_kernel<<<g, 256, 0, s>>>(w.Rrow, L, w.perm, w.dS, w.st, L, R, Rt);
+    ELM_CHECK_LAUNCH();
+}
+
+static int trsm_cb(int64_t r_max, int64_t q, int sms) {
+    int64_t fit = (int64_t)(200 * 1024) / (8 * (r_max > 0 ? r_max : 1));
+    int64_t want = (q + sms - 1) / sms;
+    int64_t cb = want < fit ? want : fit;
+    if (cb > 8) cb = 8;
+    if (cb < 1) cb = 1;
+    return (int)cb;
+}
+
+static int g_sms = 0;
+static int sms_now() {
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms;
+}
+
+void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
+              int64_t r_max, double *B, int64_t ldb, int64_t q) {
+    if (r_max <= 0 || q <= 0) return;
+    int cb = trsm_cb(r_max, q, sms_now());
+    size_t smem = (size_t)cb * r_max * 8;
+    if (smem > 220 * 1024) throw ElmError(ELM_ERR_UNSUPPORTED, "rank too large for trsm");
+    ELM_CUDA(cudaFuncSetAttribute(trsm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    trsm_fwd_kernel<<<(unsigned)((q + cb - 1) / cb), FT, smem, s>>>(R, ldr, r_dev, r_max, B,
+                                                                    ldb, q, cb);
+    ELM_CHECK_LAUNCH();
+}
+
+void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const int64_t *r_dev,
+              int64_t r_max, double *B, int64_t ldb, int64_t q) {
+    if (r_max <= 0 || q <= 0) return;
+    int cb = trsm_cb(r_max, q, sms_now());
+    size_t smem = (size_t)cb * r_max * 8;
+    if (smem > 220 * 1024) throw ElmError(ELM_ERR_UNSUPPORTED, "rank too large for trsm");
+    ELM_CUDA(cudaFuncSetAttribute(trsm_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    trsm_bwd_kernel<<<(unsigned)((q + cb - 1) / cb), FT, smem, s>>>(Rt, ldr, r_dev, r_max, B,
+                                                                    ldb, q, cb);
+    ELM_CHECK_LAUNCH();
+}
+
+}  // namespace elm
