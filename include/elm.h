@@ -117,7 +117,9 @@ typedef struct elm_problem {
 typedef struct elm_train_opts {
     int32_t precision;  /* ELM_PREC_FP64 or ELM_PREC_MIXED                   */
     int32_t max_refine; /* refinement steps (< 0: default 2 FP64, 4 mixed)   */
-    double tol_rank;    /* rank threshold on the unit-diagonal scale (<=0: L*2^-52) */
+    double tol_rank;    /* rank threshold on the unit-diagonal scale (<=0: L*2^-52
+                           for FP64, max(L*2^-52, 2^-32) for MIXED, whose Gram
+                           is exact up to dropped digit pairs below 2^-34)   */
     double refine_tol;  /* stop when ||dbeta||_F <= refine_tol ||beta||_F (<=0: 1e-12) */
     int32_t flags;      /* ELM_FLAG_* bits                                   */
     int32_t reserved;

@@ -217,8 +217,10 @@ struct Problem {
     double refine_tol;
 };
 
+void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res);
+
 void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
-    if (P.prec != ELM_PREC_FP64) throw ElmError(ELM_ERR_UNSUPPORTED, "precision not built");
+    if (P.prec == ELM_PREC_MIXED) return train_mixed(ctx, P, res);
     const elm_problem &pb = *P.p;
     cudaStream_t s = ctx->stream;
     const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
@@ -284,6 +286,108 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
         resid_f64(s, Ht, N, L, N, beta, m, Td, T.ld, Rres);
         htr_f64(s, Ht, N, L, N, Rres, m, G, hpart, hs);
         solve_beta(ctx, s, R, Rt, f.perm, r, L, G, m, m, dB, m);
+        axpy_norms(s, beta, dB, L * m, norms);
+        ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
+        ELM_CUDA(cudaStreamSynchronize(s));
+        res->refine_iters = it + 1;
+        res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        if (res->rel_update <= P.refine_tol) break;
+    }
+    mark(ctx, 5);
+    if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
+    const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyDeviceToHost;
+    ELM_CUDA(cudaMemcpy2DAsync(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
+                               m * sizeof(double), L, kind, s));
+    ELM_CUDA(cudaStreamSynchronize(s));
+    collect_phases(ctx);
+}
+
+// Mixed form: H, H^T H and H^T T from exact digit slices on the tensor
+// cores (Gram accurate to FP64 rounding of the 2^-31-grid H), rank decision,
+// factorisation and solves in FP64, then refinement steps on the normal
+// equations with the FP64 residual Z - S beta.
+void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
+    const elm_problem &pb = *P.p;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
+    const int64_t Lt = L + m, Lp = oz_pad(Lt, 128), Np = oz_pad(N, 64);
+    const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
+    const int hs_split = htr_f64_nsplit(L, L, ctx->sm_count);
+    In X, W, b, a, T;
+    double *zt, *hs, *G, *R, *Rt, *beta, *dB, *SB, *Gres, *hpart, *norms;
+    __nv_bfloat16 *planes;
+    int32_t *flag;
+    int *err;
+    OzHidWs hw;
+    FactorWs f;
+    with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+        X = stage(ar, s, pb.X, N, n, pb.ldx, xsz);
+        W = stage(ar, s, pb.W, n, L, pb.ldw, 8);
+        b = stage(ar, s, pb.b, 1, L, L, 8);
+        a = stage(ar, s, pb.a, 1, L, L, 8);
+        T = stage(ar, s, pb.T, N, m, pb.ldt, 8);
+        zt = ar.take<double>(Lp * Np);
+        planes = (__nv_bfloat16 *)ar.take<char>(oz_gram_planes_bytes(N, L, m));
+        hs = ar.take<double>(Lp);
+        G = ar.take<double>(Lt * Lt);
+        hw = oz_hid_carve(ar, N, n, L, m);
+        R = ar.take<double>(L * L);
+        Rt = ar.take<double>(L * L);
+        beta = ar.take<double>(L * m);
+        dB = ar.take<double>(L * m);
+        SB = ar.take<double>(L * m);
+        Gres = ar.take<double>(L * m);
+        hpart = ar.take<double>(htr_f64_ws(L, m, hs_split));
+        norms = ar.take<double>(2);
+        flag = ar.take<int32_t>(1);
+        err = ar.take<int>(1);
+        f = factor_ws_carve(ar, L);
+    });
+    ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    check_finite(s, X.p, pb.x_dtype, N, n, X.ld, flag);
+    const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
+                 *ad = (const double *)a.p, *Td = (const double *)T.p;
+    mark(ctx, 0);
+    // Algorithm 1 step 2 (Eq. 1, 3): pre-activation on the tensor cores,
+    // activation in FP64, digit planes of H
+    oz_preact(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, L, m, zt, err);
+    oz_activate(s, zt, L, N, m, bd, ad, pb.act, planes, hs, nullptr, 0);
+    mark(ctx, 1);
+    // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
+    oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
+    oz_gram(s, planes, hs, N, L, m, G, Lt, err);
+    mark(ctx, 2);
+    // Eq. 6, Algorithm 1 steps 3-4 (FP64)
+    factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, ctx->sm_count);
+    mark(ctx, 3);
+    int32_t fl = 0, xfl = 0;
+    int terr = 0;
+    const int64_t r = read_rank(s, f, &fl);
+    ELM_CUDA(cudaMemcpy(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost));
+    ELM_CUDA(cudaMemcpy(&terr, err, sizeof terr, cudaMemcpyDeviceToHost));
+    res->rank = r;
+    res->refine_iters = 0;
+    res->rel_update = 0.0;
+    res->status = ELM_OK;
+    if (terr) {
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if (fl || xfl) {
+        res->status = ELM_ERR_NUMERIC;
+        return;
+    }
+    const double *S = G, *Z = G + L;   // Z[l, c] = G[l, L + c]
+    // Eq. 5, Eq. 7 (FP64)
+    solve_beta(ctx, s, R, Rt, f.perm, r, L, Z, Lt, m, beta, m);
+    mark(ctx, 4);
+    double nrm[2] = {0.0, 0.0};
+    for (int it = 0; it < P.max_refine; it++) {
+        htr_f64(s, S, Lt, L, L, beta, m, SB, hpart, hs_split);   // S beta
+        sub_rows(s, Z, Lt, SB, L, m, Gres);                      // Z - S beta
+        solve_beta(ctx, s, R, Rt, f.perm, r, L, Gres, m, m, dB, m);
         axpy_norms(s, beta, dB, L * m, norms);
         ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
         ELM_CUDA(cudaStreamSynchronize(s));
@@ -370,7 +474,11 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
         cudaStream_t s = ctx->stream;
         const size_t xsz = x_dtype == ELM_F64 ? 8 : 4;
         In Xs, Ws, bs, as;
-        double *out = nullptr;
+        double *out = nullptr, *zt = nullptr, *hs = nullptr;
+        __nv_bfloat16 *planes = nullptr;
+        int *err = nullptr;
+        OzHidWs hw{};
+        const bool mixed = precision == ELM_PREC_MIXED;
         const bool dev_out = on_device(Ht);
         with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
             Xs = stage(ar, s, X, N, n, ldx, xsz);
@@ -378,10 +486,29 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
             bs = stage(ar, s, b, 1, L, L, 8);
             as = stage(ar, s, a, 1, L, L, 8);
             out = dev_out ? Ht : ar.take<double>(L * N);
+            if (mixed) {
+                zt = ar.take<double>(oz_pad(L, 128) * oz_pad(N, 64));
+                planes = (__nv_bfloat16 *)ar.take<char>(oz_gram_planes_bytes(N, L, 0));
+                hs = ar.take<double>(oz_pad(L, 128));
+                err = ar.take<int>(1);
+                hw = oz_hid_carve(ar, N, n, L, 0);
+            }
         });
         const int64_t ldo = dev_out ? ldh : N;
-        hidden_f64(s, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld,
-                   (const double *)bs.p, (const double *)as.p, L, act, out, ldo);
+        if (mixed) {
+            ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+            oz_preact(s, hw, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld, L, 0, zt,
+                      err);
+            oz_activate(s, zt, L, N, 0, (const double *)bs.p, (const double *)as.p, act, planes,
+                        hs, out, ldo);
+            int terr = 0;
+            ELM_CUDA(cudaMemcpyAsync(&terr, err, sizeof terr, cudaMemcpyDeviceToHost, s));
+            ELM_CUDA(cudaStreamSynchronize(s));
+            if (terr) throw ElmError(ELM_ERR_TIMEOUT, "tensor-core kernel wait expired");
+        } else {
+            hidden_f64(s, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld,
+                       (const double *)bs.p, (const double *)as.p, L, act, out, ldo);
+        }
         if (!dev_out) {
             ELM_CUDA(cudaMemcpy2DAsync(Ht, ldh * 8, out, N * 8, N * 8, L,
                                        cudaMemcpyDeviceToHost, s));
@@ -471,7 +598,13 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             P.prec = o.precision;
             P.max_refine = o.max_refine >= 0 ? o.max_refine
                                              : (o.precision == ELM_PREC_FP64 ? 2 : 4);
-            P.tau = o.tol_rank > 0.0 ? o.tol_rank : (double)probs[i].L * ldexp(1.0, -52);
+            // default rank threshold on the unit-diagonal scale: L 2^-52 for
+            // the FP64 Gram; the mixed Gram drops digit pairs below 2^-34 of
+            // the leading term, so its threshold sits above that level
+            const double tau64 = (double)probs[i].L * ldexp(1.0, -52);
+            P.tau = o.tol_rank > 0.0 ? o.tol_rank
+                                     : (o.precision == ELM_PREC_MIXED ? fmax(tau64, ldexp(1.0, -32))
+                                                                      : tau64);
             P.refine_tol = o.refine_tol > 0.0 ? o.refine_tol : 1e-12;
             elm_result r{};
             train_one(ctx, P, &r);

@@ -1,6 +1,7 @@
 // Internal declarations of libelm.so (not part of the public ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -156,5 +157,35 @@ void set_identity(cudaStream_t s, double *A, int64_t n);
 // Scan for non-finite entries; sets *flag = 1 if any.
 void check_finite(cudaStream_t s, const void *x, int xdt, int64_t rows, int64_t cols,
                   int64_t ld, int32_t *flag);
+
+// ------------------------------------------- tensor-core digit products
+int64_t oz_pad(int64_t v, int64_t q);
+struct OzHidWs {
+    __nv_bfloat16 *xp, *wp;  // digit planes of X and W
+    double *xs, *ws;         // their power-of-two row / column scales
+};
+// Scratch of oz_preact for an N x n input and L (+ m target) rows.
+OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m);
+// zt (Lp x Np FP64, Lp = pad(L+m, 128), Np = pad(N, 64)) = W^T X^T from
+// exact digit slices on the tensor cores.  *err set on a device-side timeout.
+void oz_preact(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
+               int64_t ldx, const double *W, int64_t ldw, int64_t L, int64_t m, double *zt,
+               int *err);
+// Bytes of the Gram digit planes (4 planes of Lp x Np bf16).
+size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m);
+// H = a g(zt + b) in FP64 -> Gram digit planes (rows < L, zero padding),
+// row scales hs, and FP64 Ht when Ht != NULL.
+void oz_activate(cudaStream_t s, const double *zt, int64_t L, int64_t N, int64_t m,
+                 const double *b, const double *a, int act, __nv_bfloat16 *planes, double *hs,
+                 double *Ht, int64_t ldh);
+// T -> digit plane rows L .. L+m-1.
+void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
+                 __nv_bfloat16 *planes, double *hs);
+// G (Lt x Lt, both triangles, Lt = L + m): Gram of [H^T; T^T] from the planes.
+void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
+             int64_t L, int64_t m, double *G, int64_t ldg, int *err);
+// out[i, c] = A[i * lda + c] - B[i * m + c]  (rows x m)
+void sub_rows(cudaStream_t s, const double *A, int64_t lda, const double *B, int64_t rows,
+              int64_t m, double *out);
 
 }  // namespace elm

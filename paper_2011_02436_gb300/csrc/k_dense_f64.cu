@@ -473,6 +473,16 @@ __global__ void set_identity_kernel(double *__restrict__ A, int64_t n) {
     for (; e < n * n; e += (int64_t)gridDim.x * blockDim.x) A[e] = (e / n == e % n) ? 1.0 : 0.0;
 }
 
+__global__ void sub_rows_kernel(const double *__restrict__ A, int64_t lda,
+                                const double *__restrict__ B, int64_t rows, int64_t m,
+                                double *__restrict__ out) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e < rows * m; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / m, c = e % m;
+        out[e] = A[i * lda + c] - B[e];
+    }
+}
+
 inline unsigned blocks_for(int64_t work, int per = 256, int64_t cap = 65535 * 8) {
     int64_t g = (work + per - 1) / per;
     if (g < 1) g = 1;
@@ -613,6 +623,12 @@ void scatter_rows(cudaStream_t s, const double *src, int64_t m, const int32_t *p
 
 void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, double *out) {
     axpy_norms_kernel<<<1, 256, 0, s>>>(beta, dB, count, out);
+    ELM_CHECK_LAUNCH();
+}
+
+void sub_rows(cudaStream_t s, const double *A, int64_t lda, const double *B, int64_t rows,
+              int64_t m, double *out) {
+    sub_rows_kernel<<<blocks_for(rows * m), 256, 0, s>>>(A, lda, B, rows, m, out);
     ELM_CHECK_LAUNCH();
 }
 

@@ -1,0 +1,698 @@
+// Mixed-precision dense products on the 5th-generation tensor cores.
+//
+// The hidden-layer pre-activation X W (Eq. 1, Eq. 3) and the Gram blocks
+// H^T H, H^T T (Eqs. 9-13) are computed from exact integer-digit slices:
+// every operand row is scaled by a power of two into [-1, 1] and split into
+// P signed digits of B bits,
+//     v = sum_p d_p 2^(-(B-1) - B(p-1)),   |d_p| <= 2^(B-1),
+// each digit an integer held exactly in bf16.  For a pair of digit planes
+// (p, q) the tcgen05 MMA (kind::f16, bf16 operands, FP32 accumulator in
+// tensor memory) sums products |d_p d_q| <= 2^(2B-2); over a K chunk of
+// 2^(24-2B+2) / 4 elements (256 for B = 8, 1024 for B = 7) the partial sums
+// stay below 2^24, so the FP32 accumulation is exact.  Pairs with the same
+// weight 2^(-B(p+q-2)) share one accumulator ("diagonal" t = p + q).  After
+// each chunk four drain warps fold the diagonals, as exact integers, into a
+// per-element int64 fixed-point running sum kept in tensor memory; the
+// epilogue converts it to FP64 once.  So the only roundings are the final
+// FP64 conversion and, for diagonals holding more than four pairs (weight
+// at most 2^(-4B) of the leading one), the FP32 accumulator itself.  Pairs
+// with p + q > TMAX are dropped.
+//
+// Kernel layout (one 128 x 64 output tile per CTA, 192 threads):
+//   warp 0      TMA producer: digit tiles of A (128 rows) and B (64 rows),
+//               32 K-elements per stage, 64-byte swizzle, STAGES-deep ring
+//   warp 1      TMEM allocation and the single MMA-issuing thread
+//   warps 2..5  drains and the FP64 epilogue (one TMEM lane each)
+// Every mbarrier wait is bounded by wall-clock time; on expiry the kernel
+// sets an error flag, stops issuing work and still frees its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include "elm_internal.cuh"
+
+namespace elm {
+
+namespace {
+
+constexpr int BM = 128;         // tile rows (A rows, TMEM lanes)
+constexpr int BN = 64;          // tile columns (B rows)
+constexpr int SK = 32;          // K elements per stage (64 bytes of bf16)
+
+// K stages per exact chunk for B-bit digits: products <= 2^(2B-2), and four
+// pairs of a diagonal over a chunk must stay <= 2^24.
+template <int DBITS>
+__host__ __device__ constexpr int chunk_slabs() {
+    return (1 << (24 - 2 * (DBITS - 1) - 2)) / SK;
+}
+constexpr int NTHREADS = 192;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on any single wait
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait.  Returns false when the bound expires or another warp has
+// already given up (abort flag in shared memory).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort) {
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = gtime();
+    for (;;) {
+        if (mbar_try(b, parity)) return true;
+        if (*abort) return false;
+        if (gtime() - t0 > WAIT_NS) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_2d(const CUtensorMap *tm, uint64_t *bar, void *dst, int x,
+                                       int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+        "l"((uint64_t)tm), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
+// 64 bytes, 8-row core groups 512 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                    // leading offset (unused when swizzled)
+    d |= (uint64_t)(512u >> 4) << 32;          // stride offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)4 << 61;                    // SWIZZLE_64B
+    return d;
+}
+// Instruction descriptor: kind::f16, bf16 x bf16 -> f32, both K-major.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct OzParams {
+    int64_t a_rows;     // rows per A digit plane
+    int64_t b_rows;     // rows per B digit plane
+    int64_t K;          // padded K (multiple of SK)
+    int64_t m_valid;    // output rows to write
+    int64_t n_valid;    // output columns to write
+    int64_t ntile_m;    // tiles along M
+    int gram;           // 1: lower-triangular tile set, mirrored writes
+    double out_scale;
+    const double *rscale;  // per output row (A row) power-of-two scale
+    const double *cscale;  // per output column (B row) scale
+    double *out;
+    int64_t ldo;
+    int *err;
+};
+
+template <int PA, int PB, int TMAX, int STAGES, int DBITS>
+__global__ void __launch_bounds__(NTHREADS, 1)
+ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             const OzParams P) {
+    constexpr int CHUNK_SLABS = chunk_slabs<DBITS>();
+    constexpr int ND = TMAX - 1;                 // diagonals t = 2..TMAX
+    constexpr uint32_t A_BYTES = BM * SK * 2;    // 8 KB per plane
+    constexpr uint32_t B_BYTES = BN * SK * 2;    // 4 KB per plane
+    constexpr uint32_t STAGE_BYTES = PA * A_BYTES + PB * B_BYTES;
+    // columns: ND accumulators, then the low and high 32-bit words of the
+    // int64 running sums
+    constexpr uint32_t LO_COL = ND * BN, HI_COL = ND * BN + BN;
+    constexpr uint32_t USED = ND * BN + 2 * BN;
+    constexpr uint32_t TMEM_COLS = USED <= 128 ? 128 : (USED <= 256 ? 256 : 512);
+    static_assert(USED <= 512, "too many diagonals for tensor memory");
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // tile coordinates
+    int64_t mt, nt;
+    if (P.gram) {
+        // lower tiles: row block J has 2(J+1) column blocks of 64
+        int64_t t = blockIdx.x;
+        int64_t J = (int64_t)((sqrt(4.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while (J * (J + 1) > t) J--;
+        while ((J + 1) * (J + 2) <= t) J++;
+        mt = J;
+        nt = t - J * (J + 1);
+    } else {
+        mt = blockIdx.x % P.ntile_m;
+        nt = blockIdx.x / P.ntile_m;
+    }
+    const int64_t m0 = mt * BM, n0 = nt * BN;
+    const int nslab = (int)(P.K / SK);
+    const int nchunk = (nslab + CHUNK_SLABS - 1) / CHUNK_SLABS;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        mbar_init(&acc_empty, 128);
+        mbar_init(&mma_done, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&tmem_base_sh)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    volatile int *abort = &abort_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------- producer
+            int issued = 0;
+            for (int s = 0; s < nslab; s++) {
+                const int st = s % STAGES;
+                if (s >= STAGES && !mbar_wait(&empty_bar[st], ((s / STAGES) - 1) & 1, abort))
+                    break;
+                uint8_t *base = smem + (size_t)st * STAGE_BYTES;
+                mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+#pragma unroll
+                for (int p = 0; p < PA; p++)
+                    tma_2d(&tmA, &full_bar[st], base + p * A_BYTES, s * SK,
+                           (int)(p * P.a_rows + m0));
+#pragma unroll
+                for (int q = 0; q < PB; q++)
+                    tma_2d(&tmB, &full_bar[st], base + PA * A_BYTES + q * B_BYTES, s * SK,
+                           (int)(q * P.b_rows + n0));
+                issued = s + 1;
+            }
+            if (*abort) {
+                // let copies already issued land before the CTA exits
+                for (int s = (issued > STAGES ? issued - STAGES : 0); s < issued; s++) {
+                    const int st = s % STAGES;
+                    const uint64_t t0 = gtime();
+                    while (!mbar_try(&full_bar[st], (s / STAGES) & 1) && gtime() - t0 < WAIT_NS) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issue
+            for (int s = 0; s < nslab && !*abort; s++) {
+                const int st = s % STAGES;
+                const int c = s / CHUNK_SLABS;
+                const bool first = (s % CHUNK_SLABS) == 0;
+                if (first && c > 0 && !mbar_wait(&acc_empty, (c - 1) & 1, abort)) break;
+                if (!mbar_wait(&full_bar[st], (s / STAGES) & 1, abort)) break;
+                tc_fence_after();
+                const uint32_t abase = su32(smem + (size_t)st * STAGE_BYTES);
+                const uint32_t bbase = abase + PA * A_BYTES;
+#pragma unroll
+                for (int t = 2; t <= TMAX; t++) {
+                    bool first_pair = true;
+#pragma unroll
+                    for (int p = 1; p <= PA; p++) {
+                        const int q = t - p;
+                        if (q < 1 || q > PB) continue;
+                        const uint64_t da = desc_sw64(abase + (p - 1) * A_BYTES);
+                        const uint64_t db = desc_sw64(bbase + (q - 1) * B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < SK / 16; kk++) {
+                            const uint32_t acc = (first && first_pair && kk == 0) ? 0u : 1u;
+                            mma_bf16(tmem + (uint32_t)((t - 2) * BN), da + 2 * kk, db + 2 * kk,
+                                     IDESC, acc);
+                        }
+                        first_pair = false;
+                    }
+                }
+                mma_commit(&empty_bar[st]);
+                if ((s % CHUNK_SLABS) == CHUNK_SLABS - 1 || s == nslab - 1) mma_commit(&acc_full);
+            }
+            // every MMA issued so far has completed once this barrier flips;
+            // tensor memory is freed only after that
+            mma_commit(&mma_done);
+            const uint64_t t0 = gtime();
+            while (!mbar_try(&mma_done, 0) && gtime() - t0 < WAIT_NS) {
+            }
+        }
+    } else {
+        // -------------------------------------------------------- drains
+        const int quarter = warp & 3;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        bool ok = true;
+        for (int c = 0; c < nchunk; c++) {
+            if (!mbar_wait(&acc_full, c & 1, abort)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll 1
+            for (int h = 0; h < BN / 16; h++) {
+                // V = sum_t acc_t 2^(B (TMAX - t)): exact integers in units of
+                // 2^(-B (TMAX - 2)) of the leading diagonal
+                long long run[16];
+                float v[16];
+                if (c == 0) {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) run[i] = 0;
+                } else {
+                    float w0[16], w1[16];
+                    tmem_ld16(lane_base + LO_COL + h * 16, w0);
+                    tmem_ld16(lane_base + HI_COL + h * 16, w1);
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        run[i] = (long long)(((unsigned long long)__float_as_uint(w1[i]) << 32) |
+                                             (unsigned long long)__float_as_uint(w0[i]));
+                }
+#pragma unroll
+                for (int t = 2; t <= TMAX; t++) {
+                    tmem_ld16(lane_base + (uint32_t)((t - 2) * BN + h * 16), v);
+                    const long long mult = 1ll << (DBITS * (TMAX - t));
+#pragma unroll
+                    for (int i = 0; i < 16; i++) run[i] += __float2ll_rn(v[i]) * mult;
+                }
+                uint32_t w[16];
+#pragma unroll
+                for (int i = 0; i < 16; i++) w[i] = (uint32_t)((unsigned long long)run[i]);
+                tmem_st16(lane_base + LO_COL + h * 16, w);
+#pragma unroll
+                for (int i = 0; i < 16; i++) w[i] = (uint32_t)((unsigned long long)run[i] >> 32);
+                tmem_st16(lane_base + HI_COL + h * 16, w);
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty);
+        }
+        if (ok && !*abort) {
+            // All stages have been consumed: reuse the ring as a 32 x 64 FP64
+            // staging tile per warp so that global writes are row-contiguous.
+            double *tile = (double *)smem + (size_t)quarter * 32 * (BN + 1);
+            const int64_t m = m0 + quarter * 32 + lane;
+            const double unit = ldexp(1.0, -DBITS * (TMAX - 2));
+            const double rs = m < P.m_valid ? P.out_scale * unit * P.rscale[m] : 0.0;
+#pragma unroll 1
+            for (int h = 0; h < BN / 16; h++) {
+                float w0[16], w1[16];
+                tmem_ld16(lane_base + LO_COL + h * 16, w0);
+                tmem_ld16(lane_base + HI_COL + h * 16, w1);
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const int64_t n = n0 + h * 16 + i;
+                    const double cs = n < P.n_valid ? P.cscale[n] : 0.0;
+                    const long long run =
+                        (long long)(((unsigned long long)__float_as_uint(w1[i]) << 32) |
+                                    (unsigned long long)__float_as_uint(w0[i]));
+                    const double v = (double)run * rs * cs;
+                    tile[lane * (BN + 1) + h * 16 + i] = v;
+                    if (P.gram && n < m && m < P.m_valid && n < P.n_valid)
+                        P.out[n * P.ldo + m] = v;    // mirror: lanes write consecutive m
+                }
+            }
+            __syncwarp();
+            for (int r = 0; r < 32; r++) {
+                const int64_t mr = m0 + quarter * 32 + r;
+                if (mr >= P.m_valid) break;
+#pragma unroll
+                for (int h = 0; h < BN / 32; h++) {
+                    const int64_t n = n0 + h * 32 + lane;
+                    if (n < P.n_valid && (!P.gram || n <= mr))
+                        P.out[mr * P.ldo + n] = tile[r * (BN + 1) + h * 32 + lane];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+    }
+    if (threadIdx.x == 0 && *abort) atomicExch(P.err, 1);
+}
+
+// ------------------------------------------------------------ digit slicing
+// v in [-1, 1] -> PD digits of B bits, v ~= sum_p d_p 2^(-(B-1) - B(p-1)),
+// |d_p| <= 2^(B-1); exact FP64 arithmetic, round-to-nearest digits.
+template <int PD, int DBITS>
+__device__ __forceinline__ void split_digits(double v, float *d) {
+    double x = v * (double)(1 << (DBITS - 1));
+#pragma unroll
+    for (int p = 0; p < PD; p++) {
+        double r = rint(x);
+        d[p] = (float)r;
+        x = (x - r) * (double)(1 << DBITS);
+    }
+}
+
+// Smallest power of two 2^e with |v| <= 2^e (1 for v == 0).
+__device__ __forceinline__ double pow2_ceil(double v) {
+    v = fabs(v);
+    if (!(v > 0.0) || !isfinite(v)) return 1.0;
+    int e;
+    double m = frexp(v, &e);  // v = m 2^e, m in [0.5, 1)
+    if (m == 0.5) e -= 1;
+    return ldexp(1.0, e);
+}
+
+// X (N x n, row stride ldx) -> PD planes of Np x nK bf16 (row i, col k),
+// rows scaled by xs[i] = pow2_ceil(max_k |X[i, k]|).  One warp per row.
+template <int PD, int DBITS, typename XT>
+__global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t n, int64_t ldx,
+                                   int64_t Np, int64_t nK, __nv_bfloat16 *__restrict__ planes,
+                                   double *__restrict__ xs) {
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= Np) return;
+    double mx = 0.0;
+    if (i < N)
+        for (int64_t k = lane; k < n; k += 32) mx = fmax(mx, fabs((double)X[i * ldx + k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double sc = pow2_ceil(mx);
+    if (lane == 0) xs[i] = sc;
+    const double inv = 1.0 / sc;  // exact: sc is a power of two
+    for (int64_t k = lane; k < nK; k += 32) {
+        float d[PD];
+        const double v = (i < N && k < n) ? (double)X[i * ldx + k] * inv : 0.0;
+        split_digits<PD, DBITS>(v, d);
+#pragma unroll
+        for (int p = 0; p < PD; p++)
+            planes[(int64_t)p * Np * nK + i * nK + k] = __float2bfloat16_rn(d[p]);
+    }
+}
+
+// W (n x L, row stride ldw) -> PD planes of Lp x nK bf16 (row j, col k),
+// columns scaled by ws[j] = pow2_ceil(max_k |W[k, j]|).  One thread per j.
+template <int PD, int DBITS>
+__global__ void digits_cols_kernel(const double *__restrict__ W, int64_t n, int64_t L,
+                                   int64_t ldw, int64_t Lp, int64_t nK,
+                                   __nv_bfloat16 *__restrict__ planes, double *__restrict__ ws) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Lp) return;
+    double mx = 0.0;
+    if (j < L)
+        for (int64_t k = 0; k < n; k++) mx = fmax(mx, fabs(W[k * ldw + j]));
+    const double sc = pow2_ceil(mx);
+    ws[j] = sc;
+    const double inv = 1.0 / sc;
+    for (int64_t k = 0; k < nK; k++) {
+        float d[PD];
+        const double v = (j < L && k < n) ? W[k * ldw + j] * inv : 0.0;
+        split_digits<PD, DBITS>(v, d);
+#pragma unroll
+        for (int p = 0; p < PD; p++)
+            planes[(int64_t)p * Lp * nK + j * nK + k] = __float2bfloat16_rn(d[p]);
+    }
+}
+
+__device__ __forceinline__ double act_f64(double z, int act) {
+    return act == ELM_ACT_TANH ? tanh(z) : 1.0 / (1.0 + exp(-z));
+}
+
+// H[j, i] = a_j g(z[j, i] + b_j) in FP64 from the tensor-core pre-activation;
+// written as PD digit planes (rows j < L of the Gram operand, scaled by
+// hs[j] = pow2_ceil(a_j)) and, if Ht != NULL, as FP64 Ht.  Also zeroes the
+// padding rows >= L + m and columns >= N.
+template <int PD, int DBITS>
+__global__ void act_digits_kernel(const double *__restrict__ zt, int64_t L, int64_t N,
+                                  int64_t m, const double *__restrict__ b,
+                                  const double *__restrict__ a, int act, int64_t Lp, int64_t Np,
+                                  __nv_bfloat16 *__restrict__ planes, double *__restrict__ hs,
+                                  double *__restrict__ Ht, int64_t ldh) {
+    const int64_t j = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Np) return;
+    if (j >= L && j < L + m) return;  // target rows: written by the target slicer
+    float d[PD];
+    if (j < L && i < N) {
+        const double aj = a ? a[j] : 1.0;
+        const double h = aj * act_f64(zt[j * Np + i] + b[j], act);
+        if (Ht) Ht[j * ldh + i] = h;
+        const double sc = pow2_ceil(aj);
+        if (i == 0) hs[j] = sc;
+        split_digits<PD, DBITS>(h / sc, d);
+    } else {
+#pragma unroll
+        for (int p = 0; p < PD; p++) d[p] = 0.f;
+        if (i == 0) hs[j] = 1.0;
+    }
+#pragma unroll
+    for (int p = 0; p < PD; p++)
+        planes[(int64_t)p * Lp * Np + j * Np + i] = __float2bfloat16_rn(d[p]);
+}
+
+// T (N x m) -> digit plane rows L + c (column c of T), scaled by
+// hs[L + c] = pow2_ceil(max_i |T[i, c]|).  One block per target column.
+template <int PD, int DBITS>
+__global__ void t_digits_kernel(const double *__restrict__ T, int64_t ldt, int64_t N, int64_t L,
+                                int64_t Lp, int64_t Np, __nv_bfloat16 *__restrict__ planes,
+                                double *__restrict__ hs) {
+    const int64_t c = blockIdx.x;
+    __shared__ double red[256];
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) mx = fmax(mx, fabs(T[i * ldt + c]));
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const double sc = pow2_ceil(red[0]);
+    if (threadIdx.x == 0) hs[L + c] = sc;
+    const double inv = 1.0 / sc;
+    for (int64_t i = threadIdx.x; i < Np; i += blockDim.x) {
+        float d[PD];
+        split_digits<PD, DBITS>(i < N ? T[i * ldt + c] * inv : 0.0, d);
+#pragma unroll
+        for (int p = 0; p < PD; p++)
+            planes[(int64_t)p * Lp * Np + (L + c) * Np + i] = __float2bfloat16_rn(d[p]);
+    }
+}
+
+// ------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        ELM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                  cudaEnableDefault, &q));
+        if (!p || q != cudaDriverEntryPointSuccess)
+            throw ElmError(ELM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D bf16 map over `rows` x `K` (row-major), box 32 x box_rows, 64-B swizzle.
+CUtensorMap make_map(const __nv_bfloat16 *base, int64_t rows, int64_t K, int box_rows) {
+    if (((uintptr_t)base & 15) || (K * 2) % 16)
+        throw ElmError(ELM_ERR_ARG, "digit planes misaligned for TMA");
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(K * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)SK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides,
+                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw ElmError(ELM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
+template <int PA, int PB, int TMAX, int STAGES, int DBITS>
+void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B, OzParams P,
+                  int64_t ntiles) {
+    constexpr size_t stage = (size_t)PA * BM * SK * 2 + (size_t)PB * BN * SK * 2;
+    const size_t smem = STAGES * stage + 1024;
+    auto k = ozaki_kernel<PA, PB, TMAX, STAGES, DBITS>;
+    static bool attr = false;
+    if (!attr) {
+        ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    CUtensorMap ma = make_map(A, PA * P.a_rows, P.K, BM);
+    CUtensorMap mb = make_map(B, PB * P.b_rows, P.K, BN);
+    k<<<(unsigned)ntiles, NTHREADS, smem, s>>>(ma, mb, P);
+    ELM_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+// Digit counts, digit widths and kept pairs (p + q <= TMAX) of the two
+// products.  Pre-activation: 5 digits of 8 bits (operand grid 2^-39, chunks
+// of 256 inputs).  Gram: 5 digits of 7 bits (H on a 2^-34 grid, chunks of
+// 1024 samples).
+constexpr int HID_PX = 5, HID_PW = 5, HID_TMAX = 6, HID_BITS = 8;
+constexpr int GRAM_PH = 5, GRAM_TMAX = 6, GRAM_BITS = 7;
+
+int64_t oz_pad(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
+
+OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m) {
+    const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
+    OzHidWs w;
+    w.xp = ar.take<__nv_bfloat16>(HID_PX * Np * nK);
+    w.wp = ar.take<__nv_bfloat16>(HID_PW * Lp * nK);
+    w.xs = ar.take<double>(Np);
+    w.ws = ar.take<double>(Lp);
+    return w;
+}
+
+size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m) {
+    return (size_t)GRAM_PH * oz_pad(L + m, BM) * oz_pad(N, BN) * 2;
+}
+
+// zt (Lp x Np FP64) = X W computed from exact digit slices on the tensor cores.
+void oz_preact(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
+               int64_t ldx, const double *W, int64_t ldw, int64_t L, int64_t m, double *zt,
+               int *err) {
+    const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
+    __nv_bfloat16 *xp = w.xp, *wp = w.wp;
+    double *xs = w.xs, *ws = w.ws;
+    if (xdt == ELM_F64)
+        digits_rows_kernel<HID_PX, HID_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
+            (const double *)X, N, n, ldx, Np, nK, xp, xs);
+    else
+        digits_rows_kernel<HID_PX, HID_BITS, float><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
+            (const float *)X, N, n, ldx, Np, nK, xp, xs);
+    ELM_CHECK_LAUNCH();
+    digits_cols_kernel<HID_PW, HID_BITS><<<(unsigned)((Lp + 127) / 128), 128, 0, s>>>(W, n, L, ldw, Lp, nK,
+                                                                             wp, ws);
+    ELM_CHECK_LAUNCH();
+    OzParams P{};
+    P.a_rows = Lp;
+    P.b_rows = Np;
+    P.K = nK;
+    P.m_valid = L;
+    P.n_valid = N;
+    P.ntile_m = Lp / BM;
+    P.gram = 0;
+    P.out_scale = ldexp(1.0, -2 * (HID_BITS - 1));
+    P.rscale = ws;
+    P.cscale = xs;
+    P.out = zt;
+    P.ldo = Np;
+    P.err = err;
+    launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS>(s, wp, xp, P, (Lp / BM) * (Np / BN));
+}
+
+// Activation + Gram digit planes (rows < L) from zt; optional FP64 Ht.
+void oz_activate(cudaStream_t s, const double *zt, int64_t L, int64_t N, int64_t m,
+                 const double *b, const double *a, int act, __nv_bfloat16 *planes, double *hs,
+                 double *Ht, int64_t ldh) {
+    const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
+    dim3 g((unsigned)((Np + 255) / 256), (unsigned)Lp);
+    act_digits_kernel<GRAM_PH, GRAM_BITS><<<g, 256, 0, s>>>(zt, L, N, m, b, a, act, Lp, Np, planes, hs, Ht,
+                                                 ldh);
+    ELM_CHECK_LAUNCH();
+}
+
+// Target rows L .. L+m-1 of the Gram digit planes.
+void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
+                 __nv_bfloat16 *planes, double *hs) {
+    if (m <= 0) return;
+    const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
+    t_digits_kernel<GRAM_PH, GRAM_BITS><<<(unsigned)m, 256, 0, s>>>(T, ldt, N, L, Lp, Np, planes, hs);
+    ELM_CHECK_LAUNCH();
+}
+
+// G (Lt x Lt FP64, both triangles, Lt = L + m) = Gram of the augmented rows
+// [H^T; T^T] from the digit planes.
+void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
+             int64_t L, int64_t m, double *G, int64_t ldg, int *err) {
+    const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
+    const int64_t nJ = Lp / BM;
+    OzParams P{};
+    P.a_rows = Lp;
+    P.b_rows = Lp;
+    P.K = Np;
+    P.m_valid = L + m;
+    P.n_valid = L + m;
+    P.ntile_m = nJ;
+    P.gram = 1;
+    P.out_scale = ldexp(1.0, -2 * (GRAM_BITS - 1));
+    P.rscale = hs;
+    P.cscale = hs;
+    P.out = G;
+    P.ldo = ldg;
+    P.err = err;
+    launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS>(s, planes, planes, P, nJ * (nJ + 1));
+}
+
+}  // namespace elm

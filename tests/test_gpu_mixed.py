@@ -1,0 +1,97 @@
+"""GPU parity of the mixed path (tensor-core digit products, FP64 rank
+decision, factorisation and refinement) against the CPU oracle.
+
+Bars: rank bit-exact; beta within 1e-6 relative Frobenius error; the
+tensor-core hidden layer within 1e-9 absolute of the FP64 definition.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import problem, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def elm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2011_02436_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(elm):
+    import torch
+    c = elm.elm_create(0, torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("N,n,L,xdt,act,kind", [
+    (1037, 13, 120, np.float32, 0, "normal"),
+    (300, 784, 333, np.float32, 0, "uniform01"),
+    (65, 5, 7, np.float64, 1, "uniform11"),
+])
+def test_hidden_tensor_core_matches_oracle(elm, ctx, N, n, L, xdt, act, kind):
+    p = synth.make_problem(N, n, L, 3, n_dup=min(7, L // 3), x_dtype=xdt, act=act, x_kind=kind,
+                           x_sparsity=0.8 if n == 784 else 0.0)
+    t = to_dev(p)
+    Lt = p["L"]
+    Ht = elm.elm_hidden(ctx, t["X"], t["W"], t["b"], t["a"], act,
+                        precision=elm.PREC_MIXED).cpu().numpy()
+    H = oracle.hidden(p["X"], p["W"], p["b"], p["a"], act)
+    assert Ht.shape == (Lt, N)
+    assert np.max(np.abs(Ht.T - H)) < 1e-9
+    src = p["src"]
+    for j in range(Lt):                                    # bitwise duplicates
+        k = int(np.nonzero(src == src[j])[0][0])
+        assert np.array_equal(Ht[j], Ht[k])
+
+
+def test_train_small_fp64_workload_mixed(elm, ctx):
+    p = synth.workload_small_fp64()
+    prob = problem(p)
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["rank"] == r == 180
+    assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("case", ["sparse_pixels", "rank_deficient", "tanh_wide_m", "scaled"])
+def test_train_reduced_workloads_mixed(elm, ctx, case):
+    if case == "sparse_pixels":
+        p = synth.workload_sparse_pixels(N=3000, L_unique=333)
+    elif case == "rank_deficient":
+        p = synth.workload_rank_deficient(N=4000, L_unique=250, n_dup=25, n_scaled=13)
+    elif case == "tanh_wide_m":
+        p = synth.make_problem(2500, 54, 301, 26, act=synth.ACT_TANH)
+    else:
+        p = synth.make_problem(1500, 20, 140, 5, n_dup=10, n_scaled=30, x_kind="uniform11")
+    prob = problem(p)
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["rank"] == r == p["rank"]
+    assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("N,n,L,m", [(50, 8, 80, 3), (1, 3, 5, 1), (7, 1, 1, 1), (129, 65, 64, 17),
+                                     (700, 33, 257, 2)])
+def test_train_edge_shapes_mixed(elm, ctx, N, n, L, m):
+    p = synth.make_problem(N, n, L, m, x_dtype=np.float64, x_kind="normal")
+    prob = problem(p)
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["rank"] == r
+    assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
+
+
+def test_train_host_buffers_mixed(elm, ctx):
+    p = synth.make_problem(700, 9, 60, 4, n_dup=5)
+    prob = dict(X=p["X"], W=p["W"], b=p["b"], a=p["a"], act=0, T=p["T"])
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], 0, p["T"])
+    assert res["rank"] == r
+    assert rel(prob["beta"], ref) <= 1e-6
