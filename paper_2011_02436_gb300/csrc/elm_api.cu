@@ -168,21 +168,21 @@ void solve_beta(elm_ctx *ctx, cudaStream_t s, const double *R, const double *Rt,
     double *yb = ab.yb;
     gather_rows(s, Z, ldz, perm, nullptr, r, m, yb, m);
     trsm_fwd(s, R, L, nullptr, r, yb, m, m);
-    trsm_bwd(s, Rt, L, nullptr, r, yb, m, m);
+    trsm_bwd(s, R, L, nullptr, r, yb, m, m);
     if (r < L) {
         const int64_t q = L - r;
         if (r > 0) {
             ELM_CUDA(cudaMemcpy2DAsync(ab.K, q * sizeof(double), R + r, L * sizeof(double),
                                        q * sizeof(double), r, cudaMemcpyDeviceToDevice, s));
-            trsm_bwd(s, Rt, L, nullptr, r, ab.K, q, q);
+            trsm_bwd(s, R, L, nullptr, r, ab.K, q, q);
             set_identity(s, ab.G2, q);
             gemm_f64(s, q, q, r, 1.0, ab.K, 1, q, ab.K, q, 1, 1.0, ab.G2, q);
             factor_pivoted(s, ab.G2, q, q, 0.0, ab.f2, ab.R2, ab.Rt2, ctx->sm_count);
             gemm_f64(s, q, m, r, 1.0, ab.K, 1, q, yb, m, 1, 0.0, ab.v, m);
             ELM_CUDA(cudaMemsetAsync(ab.w, 0, sizeof(double) * q * m, s));
             gather_rows(s, ab.v, m, ab.f2.perm, &ab.f2.st->rank, q, m, ab.w, m);
-            trsm_fwd(s, ab.R2, q, &ab.f2.st->rank, q, ab.w, m, m);
-            trsm_bwd(s, ab.Rt2, q, &ab.f2.st->rank, q, ab.w, m, m);
+            trsm_fwd(s, ab.R2, q, nullptr, q, ab.w, m, m);
+            trsm_bwd(s, ab.R2, q, nullptr, q, ab.w, m, m);
             scatter_rows(s, ab.w, m, ab.f2.perm, q, ab.v, m, 1.0, 0);
             gemm_f64(s, r, m, q, -1.0, ab.K, q, 1, ab.v, m, 1, 1.0, yb, m);
             gemm_f64(s, q, m, r, 1.0, ab.K, 1, q, yb, m, 1, 0.0, yb + r * m, m);
@@ -311,11 +311,11 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     const elm_problem &pb = *P.p;
     cudaStream_t s = ctx->stream;
     const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
-    const int64_t Lt = L + m, Lp = oz_pad(Lt, 128), Np = oz_pad(N, 64);
+    const int64_t Lt = L + m, Lp = oz_pad(Lt, 128);
     const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
     const int hs_split = htr_f64_nsplit(L, L, ctx->sm_count);
     In X, W, b, a, T;
-    double *zt, *hs, *G, *R, *Rt, *beta, *dB, *SB, *Gres, *hpart, *norms;
+    double *hs, *G, *R, *Rt, *beta, *dB, *SB, *Gres, *hpart, *norms;
     __nv_bfloat16 *planes;
     int32_t *flag;
     int *err;
@@ -327,7 +327,6 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         b = stage(ar, s, pb.b, 1, L, L, 8);
         a = stage(ar, s, pb.a, 1, L, L, 8);
         T = stage(ar, s, pb.T, N, m, pb.ldt, 8);
-        zt = ar.take<double>(Lp * Np);
         planes = (__nv_bfloat16 *)ar.take<char>(oz_gram_planes_bytes(N, L, m));
         hs = ar.take<double>(Lp);
         G = ar.take<double>(Lt * Lt);
@@ -351,9 +350,9 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
                  *ad = (const double *)a.p, *Td = (const double *)T.p;
     mark(ctx, 0);
     // Algorithm 1 step 2 (Eq. 1, 3): pre-activation on the tensor cores,
-    // activation in FP64, digit planes of H
-    oz_preact(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, L, m, zt, err);
-    oz_activate(s, zt, L, N, m, bd, ad, pb.act, planes, hs, nullptr, 0);
+    // activation in the epilogue, digit planes of H
+    oz_hidden(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, pb.act, L, m, planes, hs,
+              nullptr, 0, err);
     mark(ctx, 1);
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
@@ -474,7 +473,7 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
         cudaStream_t s = ctx->stream;
         const size_t xsz = x_dtype == ELM_F64 ? 8 : 4;
         In Xs, Ws, bs, as;
-        double *out = nullptr, *zt = nullptr, *hs = nullptr;
+        double *out = nullptr, *hs = nullptr;
         __nv_bfloat16 *planes = nullptr;
         int *err = nullptr;
         OzHidWs hw{};
@@ -487,7 +486,6 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
             as = stage(ar, s, a, 1, L, L, 8);
             out = dev_out ? Ht : ar.take<double>(L * N);
             if (mixed) {
-                zt = ar.take<double>(oz_pad(L, 128) * oz_pad(N, 64));
                 planes = (__nv_bfloat16 *)ar.take<char>(oz_gram_planes_bytes(N, L, 0));
                 hs = ar.take<double>(oz_pad(L, 128));
                 err = ar.take<int>(1);
@@ -497,10 +495,9 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
         const int64_t ldo = dev_out ? ldh : N;
         if (mixed) {
             ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-            oz_preact(s, hw, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld, L, 0, zt,
+            oz_hidden(s, hw, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld,
+                      (const double *)bs.p, (const double *)as.p, act, L, 0, planes, hs, out, ldo,
                       err);
-            oz_activate(s, zt, L, N, 0, (const double *)bs.p, (const double *)as.p, act, planes,
-                        hs, out, ldo);
             int terr = 0;
             ELM_CUDA(cudaMemcpyAsync(&terr, err, sizeof terr, cudaMemcpyDeviceToHost, s));
             ELM_CUDA(cudaStreamSynchronize(s));

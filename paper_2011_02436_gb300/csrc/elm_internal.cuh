@@ -133,11 +133,11 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     int sms);
 
 // X = R11^{-T} B (forward) and X = R11^{-1} B (backward), in place on B
-// (r x q, ld ldb).  R, Rt: pivot-order factor and transpose (ld L).
-// r and q may be read from device memory (r_dev / q_dev non-null).
+// (r x q, ld ldb), R the pivot-order upper factor (ld ldr), r = r_max (the
+// rank known on the host; r_dev is unused).
 void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
               int64_t r_max, double *B, int64_t ldb, int64_t q);
-void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const int64_t *r_dev,
+void trsm_bwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
               int64_t r_max, double *B, int64_t ldb, int64_t q);
 
 // Gather rows: dst[i, :] = src[perm[i], :] for i < r_dev.
@@ -163,21 +163,21 @@ int64_t oz_pad(int64_t v, int64_t q);
 struct OzHidWs {
     __nv_bfloat16 *xp, *wp;  // digit planes of X and W
     double *xs, *ws;         // their power-of-two row / column scales
+    float4 *tab;             // sigmoid table
 };
-// Scratch of oz_preact for an N x n input and L (+ m target) rows.
+// Scratch of oz_hidden for an N x n input and L (+ m target) rows.
 OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m);
-// zt (Lp x Np FP64, Lp = pad(L+m, 128), Np = pad(N, 64)) = W^T X^T from
-// exact digit slices on the tensor cores.  *err set on a device-side timeout.
-void oz_preact(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
-               int64_t ldx, const double *W, int64_t ldw, int64_t L, int64_t m, double *zt,
-               int *err);
-// Bytes of the Gram digit planes (4 planes of Lp x Np bf16).
+// Bytes of the Gram digit planes (5 planes of Lp x Np bf16,
+// Lp = pad(L + m, 128), Np = pad(N, 64)).
 size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m);
-// H = a g(zt + b) in FP64 -> Gram digit planes (rows < L, zero padding),
-// row scales hs, and FP64 Ht when Ht != NULL.
-void oz_activate(cudaStream_t s, const double *zt, int64_t L, int64_t N, int64_t m,
-                 const double *b, const double *a, int act, __nv_bfloat16 *planes, double *hs,
-                 double *Ht, int64_t ldh);
+// H = a g(X W + b): pre-activation from exact digit slices on the tensor
+// cores, activation in double-float in the epilogue, written straight into
+// the Gram digit planes (rows < L, zero padding) with row scales hs, and as
+// FP64 H^T when Ht != NULL.  *err set on a device-side timeout.
+void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
+               int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
+               int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
+               int64_t ldh, int *err);
 // T -> digit plane rows L .. L+m-1.
 void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
                  __nv_bfloat16 *planes, double *hs);

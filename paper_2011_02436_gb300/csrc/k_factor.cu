@@ -103,10 +103,49 @@ __global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t 
     }
 }
 
+// A pivot candidate as published to the cluster: the CTA's largest unpivoted
+// updated diagonal and that column's entries in the panel rows so far.
+struct Slot {
+    double val;
+    int32_t orig;
+    int32_t x;
+    double pcol[MAXNB];
+};
+constexpr int MAXCS = 16;
+
+// Local argmax of this CTA's slice, written as a Slot into every CTA of the
+// cluster (slot index `mine`), together with its panel column rows 0..t-1.
+__device__ void publish(cg::cluster_group &cluster, int CS, int cr, const double *d,
+                        const int32_t *piv, const int32_t *act, int64_t x0, int64_t nloc,
+                        const double *Ps, int64_t Wd, int t, Slot *slots, Cand *wred,
+                        Cand *s_mine) {
+    local_argmax(d, piv, act, x0, nloc, s_mine, wred);
+    const Cand me = *s_mine;
+    const int64_t xl = me.x >= 0 ? me.x - x0 : 0;
+    // warp w writes the slot into peers w, w + 8: lane 0 the header, lanes
+    // 1..31 (and 33..) the panel column rows 0..t-1
+    const int f0 = threadIdx.x & 31;
+    for (int peer = threadIdx.x >> 5; peer < CS; peer += FT / 32) {
+        Slot *dst = cluster.map_shared_rank(slots, peer) + cr;
+        for (int f = f0; f <= t; f += 32) {
+            if (f == 0) {
+                dst->val = me.val;
+                dst->orig = me.orig;
+                dst->x = me.x;
+            } else {
+                dst->pcol[f - 1] = me.x >= 0 ? Ps[(int64_t)(f - 1) * Wd + xl] : 0.0;
+            }
+        }
+    }
+}
+
 // One panel of up to nb pivots on a cluster.  A: active matrix (Lr x Lr,
 // full symmetric, lda), act: active -> original index.  Writes the panel
 // rows P (active index space, row stride ldp), the pivot rows Rrow (original
 // column order), perm, the compaction map rem / act_next and the state.
+// Per pivot there is exactly one cluster barrier: before it every CTA has
+// pushed its candidate into all peers' shared memory (double-buffered
+// slots), after it every CTA resolves the same pivot from local memory.
 __global__ void __launch_bounds__(FT)
 panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restrict__ act,
              double *__restrict__ P, int64_t ldp, double *__restrict__ Rrow, int64_t ldr,
@@ -116,9 +155,10 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks();
     const int cr = (int)cluster.block_rank();
-    __shared__ Cand cand[2];
+    __shared__ Slot slots[2][MAXCS];
     __shared__ Cand wred[FT / 32];
-    __shared__ Cand s_best;
+    __shared__ Cand s_mine, s_best;
+    __shared__ int s_bi;
     __shared__ double u[MAXNB];
     __shared__ int32_t s_cnt;
     __shared__ int64_t s_off, s_tot;
@@ -139,20 +179,33 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         piv[xl] = 0;
     }
     __syncthreads();
-    local_argmax(d, piv, act, x0, nloc, &cand[0], wred);
+    publish(cluster, CS, cr, d, piv, act, x0, nloc, Ps, Wd, 0, slots[0], wred, &s_mine);
     cluster.sync();
 
     const int tmax = (int)(nb < Lr ? nb : Lr);
     int steps = 0;
     bool done = false;
     for (int t = 0; t < tmax; t++) {
-        if (threadIdx.x == 0) {
-            Cand best{-INFINITY, 0x7fffffff, -1};
-            for (int c = 0; c < CS; c++) {
-                Cand v = *cluster.map_shared_rank(&cand[t & 1], c);
-                if (better(v, best)) best = v;
+        Slot *sl = slots[t & 1];
+        if (threadIdx.x < 32) {
+            Cand c{-INFINITY, 0x7fffffff, -1};
+            int bi = -1;
+            if (threadIdx.x < CS) {
+                c = Cand{sl[threadIdx.x].val, sl[threadIdx.x].orig, sl[threadIdx.x].x};
+                bi = threadIdx.x;
             }
-            s_best = best;
+            for (int o = 16; o > 0; o >>= 1) {
+                Cand c2 = shfl_cand(c, o);
+                int b2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (better(c2, c)) {
+                    c = c2;
+                    bi = b2;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_best = c;
+                s_bi = bi;
+            }
         }
         __syncthreads();
         const Cand best = s_best;
@@ -160,14 +213,11 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
             done = true;
             break;
         }
+        if (threadIdx.x < t) u[threadIdx.x] = sl[s_bi].pcol[threadIdx.x];
         const int64_t q = best.x;
         const int owner = (int)(q / Wd);
         const int64_t qloc = q - (int64_t)owner * Wd;
         const double rkk = sqrt(best.val);
-        if (threadIdx.x < t) {
-            const double *ops = cluster.map_shared_rank(Ps, owner);
-            u[threadIdx.x] = ops[(int64_t)threadIdx.x * Wd + qloc];
-        }
         __syncthreads();
         const double *Aq = A + q * lda;
         for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
@@ -191,7 +241,8 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         if (owner == cr && threadIdx.x == 0) piv[qloc] = 1;
         if (cr == 0 && threadIdx.x == 0) perm[k0 + t] = act[q];
         __syncthreads();
-        local_argmax(d, piv, act, x0, nloc, &cand[(t + 1) & 1], wred);
+        publish(cluster, CS, cr, d, piv, act, x0, nloc, Ps, Wd, t + 1, slots[(t + 1) & 1], wred,
+                &s_mine);
         cluster.sync();
         steps = t + 1;
     }
@@ -342,78 +393,106 @@ __global__ void finalize_kernel(const double *__restrict__ Rrow, int64_t ldrr,
     }
 }
 
-// In-place triangular solves on CB right-hand-side columns per CTA, the
-// columns held in shared memory.  Forward: solves R11^T x = b reading rows
-// of R; backward: solves R11 x = b reading rows of Rt (columns of R).
+// Blocked triangular solve on one thread-block cluster per group of CB
+// right-hand-side columns.  Rows are cut into diagonal blocks of TB_ rows,
+// dealt round-robin to the CTAs of the cluster; each CTA keeps its blocks of
+// B in shared memory.  Per diagonal block: its owner solves it against the
+// shared-memory copy of the diagonal block of R, one hardware cluster
+// barrier, then every CTA pulls the solved block through distributed shared
+// memory and updates its own remaining rows, one thread per row with the CB
+// right-hand sides in registers (R read once per element, coalesced).
+// FWD solves R^T x = b (R upper, top block first); otherwise R x = b
+// (bottom block first).
+constexpr int TB_ = 32;     // rows per diagonal block
+template <bool FWD, int CB>
 __global__ void __launch_bounds__(FT)
-trsm_fwd_kernel(const double *__restrict__ R, int64_t ldr, const int64_t *r_dev,
-                int64_t r_max, double *__restrict__ B, int64_t ldb, int64_t q, int CB) {
-    extern __shared__ double bs[];
-    __shared__ double xs[8];
-    const int64_t r = r_dev ? *r_dev : r_max;
-    const int64_t c0 = (int64_t)blockIdx.x * CB;
+trsm_cluster_kernel(const double *__restrict__ R, int64_t ldr, int64_t r,
+                    double *__restrict__ B, int64_t ldb, int64_t q, int nown) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CS = (int)cluster.num_blocks();
+    const int cr = (int)cluster.block_rank();
+    const int64_t c0 = (int64_t)(blockIdx.x / CS) * CB;
     const int nc = (int)(q - c0 < CB ? q - c0 : CB);
-    if (nc <= 0) return;
-    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
-        int64_t i = e / nc, c = e % nc;
-        bs[c * r_max + i] = B[i * ldb + c0 + c];
+    const int64_t nblk = (r + TB_ - 1) / TB_;
+    extern __shared__ double sm[];
+    double *bs = sm;                                   // nown x TB_ x CB
+    double *xb = bs + (size_t)nown * TB_ * CB;         // TB_ x CB pulled block
+    double *Rd = xb + TB_ * CB;                        // TB_ x (TB_ + 1) diagonal block
+    double *rinv = Rd + TB_ * (TB_ + 1);               // TB_ reciprocals of the diagonal
+    for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_ * CB; e += FT) {
+        const int kl = (int)(e / (TB_ * CB)), a = (int)((e / CB) % TB_), c = (int)(e % CB);
+        const int64_t k = (int64_t)kl * CS + cr, i = k * TB_ + a;
+        bs[e] = (k < nblk && i < r && c < nc) ? B[i * ldb + c0 + c] : 0.0;
     }
     __syncthreads();
-    for (int64_t i = 0; i < r; i++) {
-        if (threadIdx.x == 0) {
-            double rii = R[i * ldr + i];
-            for (int c = 0; c < nc; c++) {
-                double x = bs[c * r_max + i] / rii;
-                bs[c * r_max + i] = x;
-                xs[c] = x;
+    for (int64_t step = 0; step < nblk; step++) {
+        const int64_t k = FWD ? step : nblk - 1 - step;
+        const int owner = (int)(k % CS);
+        const int64_t i0 = k * TB_;
+        const int nb = (int)(r - i0 < TB_ ? r - i0 : TB_);
+        if (owner == cr) {
+            double *xk = bs + (size_t)(k / CS) * TB_ * CB;
+            for (int e = threadIdx.x; e < TB_ * TB_; e += FT) {
+                const int a = e / TB_, b2 = e % TB_;
+                Rd[a * (TB_ + 1) + b2] = (a < nb && b2 < nb) ? R[(i0 + a) * ldr + i0 + b2] : 0.0;
+            }
+            __syncthreads();
+            if (threadIdx.x < nb) rinv[threadIdx.x] = 1.0 / Rd[threadIdx.x * (TB_ + 1) + threadIdx.x];
+            __syncthreads();
+            for (int s2 = 0; s2 < nb; s2++) {
+                const int a = FWD ? s2 : nb - 1 - s2;
+                // thread (a2, c): row a2 of the block, column c
+                const int a2 = threadIdx.x / CB, c = threadIdx.x % CB;
+                const double xa = xk[a * CB + c] * rinv[a];
+                __syncthreads();
+                if (a2 == a) xk[a * CB + c] = xa;
+                else if (a2 < nb && (FWD ? a2 > a : a2 < a))
+                    xk[a2 * CB + c] -= (FWD ? Rd[a * (TB_ + 1) + a2] : Rd[a2 * (TB_ + 1) + a]) * xa;
+                __syncthreads();
             }
         }
-        __syncthreads();
-        for (int64_t j = i + 1 + threadIdx.x; j < r; j += FT) {
-            double rij = R[i * ldr + j];
-            for (int c = 0; c < nc; c++) bs[c * r_max + j] = fma(-rij, xs[c], bs[c * r_max + j]);
+        cluster.sync();
+        {
+            const double *src = cluster.map_shared_rank(bs, owner) + (size_t)(k / CS) * TB_ * CB;
+            for (int e = threadIdx.x; e < TB_ * CB; e += FT) xb[e] = src[e];
         }
         __syncthreads();
-    }
-    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
-        int64_t i = e / nc, c = e % nc;
-        B[i * ldb + c0 + c] = bs[c * r_max + i];
-    }
-}
-
-__global__ void __launch_bounds__(FT)
-trsm_bwd_kernel(const double *__restrict__ Rt, int64_t ldr, const int64_t *r_dev,
-                int64_t r_max, double *__restrict__ B, int64_t ldb, int64_t q, int CB) {
-    extern __shared__ double bs[];
-    __shared__ double xs[8];
-    const int64_t r = r_dev ? *r_dev : r_max;
-    const int64_t c0 = (int64_t)blockIdx.x * CB;
-    const int nc = (int)(q - c0 < CB ? q - c0 : CB);
-    if (nc <= 0) return;
-    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
-        int64_t i = e / nc, c = e % nc;
-        bs[c * r_max + i] = B[i * ldb + c0 + c];
-    }
-    __syncthreads();
-    for (int64_t i = r - 1; i >= 0; i--) {
-        if (threadIdx.x == 0) {
-            double rii = Rt[i * ldr + i];
-            for (int c = 0; c < nc; c++) {
-                double x = bs[c * r_max + i] / rii;
-                bs[c * r_max + i] = x;
-                xs[c] = x;
+        // update own blocks still to be solved: one thread per row
+        for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_; e += FT) {
+            const int kl = (int)(e / TB_), a2 = (int)(e % TB_);
+            const int64_t k2 = (int64_t)kl * CS + cr;
+            const int64_t j = k2 * TB_ + a2;
+            if (k2 >= nblk || j >= r || (FWD ? k2 <= k : k2 >= k)) continue;
+            double acc[CB];
+            double *bb = bs + (size_t)kl * TB_ * CB + (size_t)a2 * CB;
+#pragma unroll
+            for (int c = 0; c < CB; c++) acc[c] = bb[c];
+            if (FWD) {
+#pragma unroll 4
+                for (int a = 0; a < nb; a++) {
+                    const double rv = R[(i0 + a) * ldr + j];
+#pragma unroll
+                    for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xb[a * CB + c], acc[c]);
+                }
+            } else {
+                const double *Rj = R + j * ldr + i0;
+#pragma unroll 4
+                for (int a = 0; a < nb; a++) {
+                    const double rv = Rj[a];
+#pragma unroll
+                    for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xb[a * CB + c], acc[c]);
+                }
             }
-        }
-        __syncthreads();
-        for (int64_t j = threadIdx.x; j < i; j += FT) {
-            double rji = Rt[i * ldr + j];
-            for (int c = 0; c < nc; c++) bs[c * r_max + j] = fma(-rji, xs[c], bs[c * r_max + j]);
+#pragma unroll
+            for (int c = 0; c < CB; c++) bb[c] = acc[c];
         }
         __syncthreads();
     }
-    for (int64_t e = threadIdx.x; e < r * nc; e += FT) {
-        int64_t i = e / nc, c = e % nc;
-        B[i * ldb + c0 + c] = bs[c * r_max + i];
+    cluster.sync();  // peers may still read this CTA's blocks
+    for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_ * CB; e += FT) {
+        const int kl = (int)(e / (TB_ * CB)), a = (int)((e / CB) % TB_), c = (int)(e % CB);
+        const int64_t k = (int64_t)kl * CS + cr, i = k * TB_ + a;
+        if (k < nblk && i < r && c < nc) B[i * ldb + c0 + c] = bs[e];
     }
 }
 
@@ -452,7 +531,7 @@ void panel_geometry(int64_t L, int cs, int *nb, int64_t *wmax, size_t *smem) {
     *wmax = (L + cs - 1) / cs;
     const size_t budget = 200 * 1024;
     int64_t fit = (int64_t)((budget - (size_t)(*wmax) * 12) / ((size_t)(*wmax) * 8));
-    int b = (int)(fit < 16 ? fit : 16);
+    int b = (int)(fit < 24 ? fit : 24);
     if (b < 1) b = 1;
     *nb = b;
     *smem = (size_t)b * (*wmax) * 8 + (size_t)(*wmax) * 12 + 64;
@@ -540,50 +619,79 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     ELM_CHECK_LAUNCH();
 }
 
-static int trsm_cb(int64_t r_max, int64_t q, int sms) {
-    int64_t fit = (int64_t)(200 * 1024) / (8 * (r_max > 0 ? r_max : 1));
-    int64_t want = (q + sms - 1) / sms;
-    int64_t cb = want < fit ? want : fit;
-    if (cb > 8) cb = 8;
-    if (cb < 1) cb = 1;
-    return (int)cb;
+static int g_tcluster = 0;
+
+template <bool FWD, int CB>
+static void trsm_cluster_cb(cudaStream_t s, const double *R, int64_t ldr, int64_t r, double *B,
+                            int64_t ldb, int64_t q) {
+    auto k = trsm_cluster_kernel<FWD, CB>;
+    const int64_t nblk = (r + TB_ - 1) / TB_;
+    int cs = g_tcluster ? g_tcluster : 16;
+    for (;;) {
+        const int nown = (int)((nblk + cs - 1) / cs);
+        const size_t smem =
+            ((size_t)nown * TB_ * CB + TB_ * CB + TB_ * (TB_ + 1) + TB_) * sizeof(double);
+        if (smem > 200 * 1024) {
+            if (cs == 16) {
+                cs = 8;
+                continue;
+            }
+            throw ElmError(ELM_ERR_UNSUPPORTED, "rank too large for the cluster solve");
+        }
+        cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(cs * ((q + CB - 1) / CB)));
+        cfg.blockDim = dim3(FT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (!g_tcluster) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n == 0) {
+                cudaGetLastError();
+                if (cs == 16) {
+                    cs = 8;
+                    continue;
+                }
+                throw ElmError(ELM_ERR_CUDA, "no cluster configuration for the solve");
+            }
+            g_tcluster = cs;
+        }
+        ELM_CUDA(cudaLaunchKernelEx(&cfg, k, R, ldr, r, B, ldb, q, nown));
+        ELM_CHECK_LAUNCH();
+        return;
+    }
 }
 
-static int g_sms = 0;
-static int sms_now() {
-    if (!g_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sms <= 0) g_sms = 1;
-    }
-    return g_sms;
+// Right-hand sides per cluster: spread small counts over several clusters
+// (each cluster's 16 SMs issue few FP64 operations per clock).
+template <bool FWD>
+static void trsm_cluster(cudaStream_t s, const double *R, int64_t ldr, int64_t r, double *B,
+                         int64_t ldb, int64_t q) {
+    if (r <= 0 || q <= 0) return;
+    if (q <= 8) trsm_cluster_cb<FWD, 1>(s, R, ldr, r, B, ldb, q);
+    else if (q <= 16) trsm_cluster_cb<FWD, 2>(s, R, ldr, r, B, ldb, q);
+    else if (q <= 64) trsm_cluster_cb<FWD, 4>(s, R, ldr, r, B, ldb, q);
+    else trsm_cluster_cb<FWD, 8>(s, R, ldr, r, B, ldb, q);
 }
 
 void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
               int64_t r_max, double *B, int64_t ldb, int64_t q) {
-    if (r_max <= 0 || q <= 0) return;
-    int cb = trsm_cb(r_max, q, sms_now());
-    size_t smem = (size_t)cb * r_max * 8;
-    if (smem > 220 * 1024) throw ElmError(ELM_ERR_UNSUPPORTED, "rank too large for trsm");
-    ELM_CUDA(cudaFuncSetAttribute(trsm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    trsm_fwd_kernel<<<(unsigned)((q + cb - 1) / cb), FT, smem, s>>>(R, ldr, r_dev, r_max, B,
-                                                                    ldb, q, cb);
-    ELM_CHECK_LAUNCH();
+    (void)r_dev;
+    trsm_cluster<true>(s, R, ldr, r_max, B, ldb, q);
 }
 
-void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const int64_t *r_dev,
+void trsm_bwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
               int64_t r_max, double *B, int64_t ldb, int64_t q) {
-    if (r_max <= 0 || q <= 0) return;
-    int cb = trsm_cb(r_max, q, sms_now());
-    size_t smem = (size_t)cb * r_max * 8;
-    if (smem > 220 * 1024) throw ElmError(ELM_ERR_UNSUPPORTED, "rank too large for trsm");
-    ELM_CUDA(cudaFuncSetAttribute(trsm_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    trsm_bwd_kernel<<<(unsigned)((q + cb - 1) / cb), FT, smem, s>>>(Rt, ldr, r_dev, r_max, B,
-                                                                    ldb, q, cb);
-    ELM_CHECK_LAUNCH();
+    (void)r_dev;
+    trsm_cluster<false>(s, R, ldr, r_max, B, ldb, q);
 }
 
 }  // namespace elm

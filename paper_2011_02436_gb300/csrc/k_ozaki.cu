@@ -121,8 +121,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
             su32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
+// 16 consecutive 32-bit columns of this thread's TMEM lane; the caller
+// issues tmem_wait_ld() before using the registers.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -130,9 +131,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
     asm volatile(
@@ -159,6 +160,80 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
+// ---------------------------------------------------------------- double-float
+// Unevaluated sums hi + lo of two floats with the error-free transformations
+// of Knuth (TwoSum) and Dekker (FastTwoSum, TwoProduct via FMA): about 48
+// significant bits from FP32 instructions.
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+    dfl s = two_sum(x.h, y.h);
+    return fast_two_sum(s.h, s.l + x.l + y.l);
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+    const float p = x.h * y.h;
+    float e = fmaf(x.h, y.h, -p);
+    e = fmaf(x.h, y.l, fmaf(x.l, y.h, e));
+    return fast_two_sum(p, e);
+}
+
+// Logistic function of a double-float argument from a table of sigma and
+// sigma' (double-float) at z_k = -40 + k / 64, k = 0 .. 5120, and the Taylor
+// expansion to fourth order in delta = u - z_k (|delta| <= 2^-7):
+//   sigma(u) = s0 + s1 d + s2 d^2/2 + s3 d^3/6 + s4 d^4/24 + O(d^5),
+// with the derivatives of the logistic function written through s = sigma:
+//   s1 = s (1 - s), s2 = s1 (1 - 2 s), s3 = s1 (1 - 6 s + 6 s^2),
+//   s4 = s2 (1 - 12 s + 12 s^2).
+// The fifth-order remainder is below 1e-13; terms after the linear one are
+// at most 2^-15 and are evaluated in FP32.  Outside [-40, 40] sigma is 0 or
+// 1 to within 5e-18.
+constexpr int SIG_N = 5121;
+__device__ __forceinline__ dfl sigmoid_df(dfl u, const float4 *__restrict__ tab) {
+    if (u.h <= -40.f) return {0.f, 0.f};
+    if (u.h >= 40.f) return {1.f, 0.f};
+    int k = __float2int_rn((u.h + 40.f) * 64.f);
+    k = k < 0 ? 0 : (k > SIG_N - 1 ? SIG_N - 1 : k);
+    const float z0 = (float)k * 0.015625f - 40.f;   // exact
+    const dfl d = two_sum(u.h - z0, u.l);           // u.h - z0 is exact
+    const float4 t = __ldg(tab + k);
+    const dfl lin = df_mul({t.z, t.w}, d);
+    const float s = t.x, s1 = t.z;
+    const float a2 = s1 * fmaf(-2.f, s, 1.f);
+    const float q6 = fmaf(6.f * s, s - 1.f, 1.f);
+    const float q12 = fmaf(12.f * s, s - 1.f, 1.f);
+    const float a3 = s1 * q6, a4 = a2 * q12;
+    const float dh = d.h;
+    const float hot =
+        dh * dh * fmaf(dh, fmaf(dh, a4 * (1.f / 24.f), a3 * (1.f / 6.f)), 0.5f * a2);
+    const dfl h = df_add({t.x, t.y}, lin);
+    return fast_two_sum(h.h, h.l + hot);
+}
+
+// Epilogue of the fused hidden layer: H = a g(z + b) from the exact
+// pre-activation, written as Gram digit planes.
+struct ActParams {
+    const double *b, *a;    // bias and output scale (a may be NULL)
+    int act;                // ELM_ACT_*
+    int64_t L, m;           // hidden width; rows L .. L+m-1 belong to targets
+    __nv_bfloat16 *planes;  // Gram digit planes (GRAM_PH x Lp x Np)
+    int64_t plane_stride;   // Lp * Np
+    int64_t Np;
+    const double *hs;       // Gram row scales (pow2_ceil(a_j))
+    const float4 *tab;      // sigmoid table (s0 hi/lo, s1 hi/lo) on a 2^-6 grid
+    double *Ht;             // optional FP64 H^T (row j, column i)
+    int64_t ldh;
+};
+
 struct OzParams {
     int64_t a_rows;     // rows per A digit plane
     int64_t b_rows;     // rows per B digit plane
@@ -173,9 +248,98 @@ struct OzParams {
     double *out;
     int64_t ldo;
     int *err;
+    ActParams ap;       // used when the kernel's EPI == 1
 };
 
-template <int PA, int PB, int TMAX, int STAGES, int DBITS>
+// Fused hidden-layer epilogue for one TMEM lane (neuron j = m) and the 64
+// samples n0 .. n0+63: exact pre-activation V (int64) -> double-float z ->
+// h = a_j g(z + b_j) -> GRAM_PH digits of h / hs[j] on the 2^-34 grid.
+constexpr int GRAM_PH_ = 5, GRAM_BITS_ = 7;
+template <int DBITS, int TMAX>
+__device__ __forceinline__ void hidden_epilogue(const OzParams &P, int64_t m, int64_t n0,
+                                                uint32_t lo_addr, uint32_t hi_addr) {
+    const ActParams &A = P.ap;
+    // Every lane executes the warp-collective TMEM loads below; rows of the
+    // target block (written by the target slicer) only skip the stores.
+    const bool target_row = m >= A.L && m < A.L + A.m;
+    const bool live = m < A.L;
+    // per-row constants
+    int er = 0;
+    dfl bj{0.f, 0.f}, aj{1.f, 0.f};
+    float inv_hs = 1.f;
+    bool scaled = false;
+    if (live) {
+        const double scale = P.out_scale * P.rscale[m];   // power of two
+        er = ilogb(scale) - DBITS * (TMAX - 2);
+        const double b = A.b[m];
+        bj.h = (float)b;
+        bj.l = (float)(b - (double)bj.h);
+        if (A.a) {
+            const double av = A.a[m];
+            aj.h = (float)av;
+            aj.l = (float)(av - (double)aj.h);
+            scaled = true;
+        }
+        inv_hs = (float)(1.0 / A.hs[m]);
+    }
+    __nv_bfloat16 *row = A.planes + m * A.Np + n0;
+#pragma unroll 1
+    for (int h = 0; h < BN / 16; h++) {
+        uint32_t w0[16], w1[16];
+        tmem_ld16(lo_addr + h * 16, w0);
+        tmem_ld16(hi_addr + h * 16, w1);
+        tmem_wait_ld();
+        int dg[GRAM_PH_][16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int64_t n = n0 + h * 16 + i;
+            long long q = 0;
+            if (live && n < P.n_valid) {
+                const long long V = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
+                const int e = er + ilogb(P.cscale[n]);
+                const float vh = __ll2float_rn(V);
+                const long long Vh = __float2ll_rn(vh);            // exact: vh is an integer
+                dfl z{ldexpf(vh, e), ldexpf(__ll2float_rn(V - Vh), e)};
+                z = df_add(z, bj);
+                dfl hv;
+                if (A.act == ELM_ACT_TANH) {                        // tanh u = 2 sigma(2u) - 1
+                    dfl sg = sigmoid_df({2.f * z.h, 2.f * z.l}, A.tab);
+                    hv = df_add({2.f * sg.h, 2.f * sg.l}, {-1.f, 0.f});
+                } else {
+                    hv = sigmoid_df(z, A.tab);
+                }
+                if (scaled) hv = df_mul(hv, aj);
+                hv.h *= inv_hs;
+                hv.l *= inv_hs;
+                if (A.Ht) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
+                // q = round(h~ 2^34), from the two parts
+                const float Ah = hv.h * 17179869184.0f;
+                const float Ai = rintf(Ah);
+                q = (long long)Ai + (long long)rintf((Ah - Ai) + hv.l * 17179869184.0f);
+            }
+            // balanced base-2^7 digits, least significant first
+#pragma unroll
+            for (int p = GRAM_PH_ - 1; p >= 1; p--) {
+                const long long d = ((q + 64) & 127) - 64;
+                dg[p][i] = (int)d;
+                q = (q - d) >> 7;
+            }
+            dg[0][i] = (int)q;
+        }
+        if (target_row) continue;
+#pragma unroll
+        for (int p = 0; p < GRAM_PH_; p++) {
+            __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) v[i] = __float2bfloat16_rn((float)dg[p][i]);
+            uint4 *dst = (uint4 *)(row + (int64_t)p * A.plane_stride + h * 16);
+            dst[0] = *(const uint4 *)&v[0];
+            dst[1] = *(const uint4 *)&v[8];
+        }
+    }
+}
+
+template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
 ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const OzParams P) {
@@ -317,7 +481,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         bool ok = true;
         for (int c = 0; c < nchunk; c++) {
-            if (!mbar_wait(&acc_full, c & 1, abort)) {
+            // warp-uniform decision: TMEM loads below are warp-collective
+            const bool got = __all_sync(0xffffffffu, mbar_wait(&acc_full, c & 1, abort));
+            if (!got) {
                 ok = false;
                 break;
             }
@@ -327,72 +493,81 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 // V = sum_t acc_t 2^(B (TMAX - t)): exact integers in units of
                 // 2^(-B (TMAX - 2)) of the leading diagonal
                 long long run[16];
-                float v[16];
+                uint32_t w0[16], w1[16];
                 if (c == 0) {
 #pragma unroll
                     for (int i = 0; i < 16; i++) run[i] = 0;
                 } else {
-                    float w0[16], w1[16];
                     tmem_ld16(lane_base + LO_COL + h * 16, w0);
                     tmem_ld16(lane_base + HI_COL + h * 16, w1);
+                    tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 16; i++)
-                        run[i] = (long long)(((unsigned long long)__float_as_uint(w1[i]) << 32) |
-                                             (unsigned long long)__float_as_uint(w0[i]));
+                        run[i] = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
                 }
 #pragma unroll
-                for (int t = 2; t <= TMAX; t++) {
-                    tmem_ld16(lane_base + (uint32_t)((t - 2) * BN + h * 16), v);
+                for (int t = 2; t <= TMAX; t += 2) {
+                    tmem_ld16(lane_base + (uint32_t)((t - 2) * BN + h * 16), w0);
+                    if (t + 1 <= TMAX) tmem_ld16(lane_base + (uint32_t)((t - 1) * BN + h * 16), w1);
+                    tmem_wait_ld();
                     const long long mult = 1ll << (DBITS * (TMAX - t));
 #pragma unroll
-                    for (int i = 0; i < 16; i++) run[i] += __float2ll_rn(v[i]) * mult;
+                    for (int i = 0; i < 16; i++) run[i] += __float2ll_rn(__uint_as_float(w0[i])) * mult;
+                    if (t + 1 <= TMAX) {
+                        const long long mult1 = 1ll << (DBITS * (TMAX - t - 1));
+#pragma unroll
+                        for (int i = 0; i < 16; i++)
+                            run[i] += __float2ll_rn(__uint_as_float(w1[i])) * mult1;
+                    }
                 }
-                uint32_t w[16];
 #pragma unroll
-                for (int i = 0; i < 16; i++) w[i] = (uint32_t)((unsigned long long)run[i]);
-                tmem_st16(lane_base + LO_COL + h * 16, w);
+                for (int i = 0; i < 16; i++) w0[i] = (uint32_t)((unsigned long long)run[i]);
+                tmem_st16(lane_base + LO_COL + h * 16, w0);
 #pragma unroll
-                for (int i = 0; i < 16; i++) w[i] = (uint32_t)((unsigned long long)run[i] >> 32);
-                tmem_st16(lane_base + HI_COL + h * 16, w);
+                for (int i = 0; i < 16; i++) w0[i] = (uint32_t)((unsigned long long)run[i] >> 32);
+                tmem_st16(lane_base + HI_COL + h * 16, w0);
             }
             tc_fence_before();
             mbar_arrive(&acc_empty);
         }
-        if (ok && !*abort) {
-            // All stages have been consumed: reuse the ring as a 32 x 64 FP64
-            // staging tile per warp so that global writes are row-contiguous.
-            double *tile = (double *)smem + (size_t)quarter * 32 * (BN + 1);
+        if (__all_sync(0xffffffffu, ok && !*abort)) {
             const int64_t m = m0 + quarter * 32 + lane;
-            const double unit = ldexp(1.0, -DBITS * (TMAX - 2));
-            const double rs = m < P.m_valid ? P.out_scale * unit * P.rscale[m] : 0.0;
+            if (EPI == 0) {
+                // FP64 tile.  All stages have been consumed: reuse the ring as a
+                // 32 x 64 FP64 staging tile per warp for row-contiguous writes.
+                double *tile = (double *)smem + (size_t)quarter * 32 * (BN + 1);
+                const double unit = ldexp(1.0, -DBITS * (TMAX - 2));
+                const double rs = m < P.m_valid ? P.out_scale * unit * P.rscale[m] : 0.0;
 #pragma unroll 1
-            for (int h = 0; h < BN / 16; h++) {
-                float w0[16], w1[16];
-                tmem_ld16(lane_base + LO_COL + h * 16, w0);
-                tmem_ld16(lane_base + HI_COL + h * 16, w1);
+                for (int h = 0; h < BN / 16; h++) {
+                    uint32_t w0[16], w1[16];
+                    tmem_ld16(lane_base + LO_COL + h * 16, w0);
+                    tmem_ld16(lane_base + HI_COL + h * 16, w1);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const int64_t n = n0 + h * 16 + i;
-                    const double cs = n < P.n_valid ? P.cscale[n] : 0.0;
-                    const long long run =
-                        (long long)(((unsigned long long)__float_as_uint(w1[i]) << 32) |
-                                    (unsigned long long)__float_as_uint(w0[i]));
-                    const double v = (double)run * rs * cs;
-                    tile[lane * (BN + 1) + h * 16 + i] = v;
-                    if (P.gram && n < m && m < P.m_valid && n < P.n_valid)
-                        P.out[n * P.ldo + m] = v;    // mirror: lanes write consecutive m
+                    for (int i = 0; i < 16; i++) {
+                        const int64_t n = n0 + h * 16 + i;
+                        const double cs = n < P.n_valid ? P.cscale[n] : 0.0;
+                        const long long run = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
+                        const double v = (double)run * rs * cs;
+                        tile[lane * (BN + 1) + h * 16 + i] = v;
+                        if (P.gram && n < m && m < P.m_valid && n < P.n_valid)
+                            P.out[n * P.ldo + m] = v;    // mirror: lanes write consecutive m
+                    }
                 }
-            }
-            __syncwarp();
-            for (int r = 0; r < 32; r++) {
-                const int64_t mr = m0 + quarter * 32 + r;
-                if (mr >= P.m_valid) break;
+                __syncwarp();
+                for (int r = 0; r < 32; r++) {
+                    const int64_t mr = m0 + quarter * 32 + r;
+                    if (mr >= P.m_valid) break;
 #pragma unroll
-                for (int h = 0; h < BN / 32; h++) {
-                    const int64_t n = n0 + h * 32 + lane;
-                    if (n < P.n_valid && (!P.gram || n <= mr))
-                        P.out[mr * P.ldo + n] = tile[r * (BN + 1) + h * 32 + lane];
+                    for (int h = 0; h < BN / 32; h++) {
+                        const int64_t n = n0 + h * 32 + lane;
+                        if (n < P.n_valid && (!P.gram || n <= mr))
+                            P.out[mr * P.ldo + n] = tile[r * (BN + 1) + h * 32 + lane];
+                    }
                 }
+            } else {
+                hidden_epilogue<DBITS, TMAX>(P, m, n0, lane_base + LO_COL, lane_base + HI_COL);
             }
         }
     }
@@ -420,6 +595,21 @@ __device__ __forceinline__ void split_digits(double v, float *d) {
     }
 }
 
+// Balanced base-2^B digits of the integer q (|q| <= 2^(B-1+B(PD-1))),
+// most significant first: d[0] in [-2^(B-1), 2^(B-1)], the others in
+// [-2^(B-1), 2^(B-1)).
+template <int PD, int DBITS>
+__device__ __forceinline__ void int_digits(long long q, float *d) {
+    constexpr long long H = 1ll << (DBITS - 1), M = (1ll << DBITS) - 1;
+#pragma unroll
+    for (int p = PD - 1; p >= 1; p--) {
+        const long long r = ((q + H) & M) - H;
+        d[p] = (float)r;
+        q = (q - r) >> DBITS;
+    }
+    d[0] = (float)q;
+}
+
 // Smallest power of two 2^e with |v| <= 2^e (1 for v == 0).
 __device__ __forceinline__ double pow2_ceil(double v) {
     v = fabs(v);
@@ -436,6 +626,7 @@ template <int PD, int DBITS, typename XT>
 __global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t n, int64_t ldx,
                                    int64_t Np, int64_t nK, __nv_bfloat16 *__restrict__ planes,
                                    double *__restrict__ xs) {
+    constexpr int SH = (DBITS - 1) + DBITS * (PD - 1);
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= Np) return;
@@ -445,11 +636,11 @@ __global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t 
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const double sc = pow2_ceil(mx);
     if (lane == 0) xs[i] = sc;
-    const double inv = 1.0 / sc;  // exact: sc is a power of two
+    const double mul = ldexp(1.0 / sc, SH);  // exact: powers of two
     for (int64_t k = lane; k < nK; k += 32) {
         float d[PD];
-        const double v = (i < N && k < n) ? (double)X[i * ldx + k] * inv : 0.0;
-        split_digits<PD, DBITS>(v, d);
+        const long long q = (i < N && k < n) ? __double2ll_rn((double)X[i * ldx + k] * mul) : 0;
+        int_digits<PD, DBITS>(q, d);
 #pragma unroll
         for (int p = 0; p < PD; p++)
             planes[(int64_t)p * Np * nK + i * nK + k] = __float2bfloat16_rn(d[p]);
@@ -462,6 +653,7 @@ template <int PD, int DBITS>
 __global__ void digits_cols_kernel(const double *__restrict__ W, int64_t n, int64_t L,
                                    int64_t ldw, int64_t Lp, int64_t nK,
                                    __nv_bfloat16 *__restrict__ planes, double *__restrict__ ws) {
+    constexpr int SH = (DBITS - 1) + DBITS * (PD - 1);
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Lp) return;
     double mx = 0.0;
@@ -469,51 +661,35 @@ __global__ void digits_cols_kernel(const double *__restrict__ W, int64_t n, int6
         for (int64_t k = 0; k < n; k++) mx = fmax(mx, fabs(W[k * ldw + j]));
     const double sc = pow2_ceil(mx);
     ws[j] = sc;
-    const double inv = 1.0 / sc;
+    const double mul = ldexp(1.0 / sc, SH);
     for (int64_t k = 0; k < nK; k++) {
         float d[PD];
-        const double v = (j < L && k < n) ? W[k * ldw + j] * inv : 0.0;
-        split_digits<PD, DBITS>(v, d);
+        const long long q = (j < L && k < n) ? __double2ll_rn(W[k * ldw + j] * mul) : 0;
+        int_digits<PD, DBITS>(q, d);
 #pragma unroll
         for (int p = 0; p < PD; p++)
             planes[(int64_t)p * Lp * nK + j * nK + k] = __float2bfloat16_rn(d[p]);
     }
 }
 
-__device__ __forceinline__ double act_f64(double z, int act) {
-    return act == ELM_ACT_TANH ? tanh(z) : 1.0 / (1.0 + exp(-z));
+// Gram row scales: hs[j] = pow2_ceil(a_j) for hidden rows, 1 for padding
+// rows (target rows are set by the target slicer).
+__global__ void hs_kernel(const double *__restrict__ a, int64_t L, int64_t m, int64_t Lp,
+                          double *__restrict__ hs) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Lp || (j >= L && j < L + m)) return;
+    hs[j] = j < L ? (a ? pow2_ceil(a[j]) : 1.0) : 1.0;
 }
 
-// H[j, i] = a_j g(z[j, i] + b_j) in FP64 from the tensor-core pre-activation;
-// written as PD digit planes (rows j < L of the Gram operand, scaled by
-// hs[j] = pow2_ceil(a_j)) and, if Ht != NULL, as FP64 Ht.  Also zeroes the
-// padding rows >= L + m and columns >= N.
-template <int PD, int DBITS>
-__global__ void act_digits_kernel(const double *__restrict__ zt, int64_t L, int64_t N,
-                                  int64_t m, const double *__restrict__ b,
-                                  const double *__restrict__ a, int act, int64_t Lp, int64_t Np,
-                                  __nv_bfloat16 *__restrict__ planes, double *__restrict__ hs,
-                                  double *__restrict__ Ht, int64_t ldh) {
-    const int64_t j = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Np) return;
-    if (j >= L && j < L + m) return;  // target rows: written by the target slicer
-    float d[PD];
-    if (j < L && i < N) {
-        const double aj = a ? a[j] : 1.0;
-        const double h = aj * act_f64(zt[j * Np + i] + b[j], act);
-        if (Ht) Ht[j * ldh + i] = h;
-        const double sc = pow2_ceil(aj);
-        if (i == 0) hs[j] = sc;
-        split_digits<PD, DBITS>(h / sc, d);
-    } else {
-#pragma unroll
-        for (int p = 0; p < PD; p++) d[p] = 0.f;
-        if (i == 0) hs[j] = 1.0;
-    }
-#pragma unroll
-    for (int p = 0; p < PD; p++)
-        planes[(int64_t)p * Lp * Np + j * Np + i] = __float2bfloat16_rn(d[p]);
+// Sigmoid table: sigma(z_k) and sigma'(z_k) as double-float pairs.
+__global__ void sigmoid_table_kernel(float4 *__restrict__ tab) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= SIG_N) return;
+    const double z = -40.0 + (double)k / 64.0;
+    const double s0 = 1.0 / (1.0 + exp(-z));
+    const double s1 = s0 * (1.0 - s0);
+    const float s0h = (float)s0, s1h = (float)s1;
+    tab[k] = make_float4(s0h, (float)(s0 - (double)s0h), s1h, (float)(s1 - (double)s1h));
 }
 
 // T (N x m) -> digit plane rows L + c (column c of T), scaled by
@@ -576,12 +752,12 @@ CUtensorMap make_map(const __nv_bfloat16 *base, int64_t rows, int64_t K, int box
     return m;
 }
 
-template <int PA, int PB, int TMAX, int STAGES, int DBITS>
+template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI>
 void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B, OzParams P,
                   int64_t ntiles) {
     constexpr size_t stage = (size_t)PA * BM * SK * 2 + (size_t)PB * BN * SK * 2;
     const size_t smem = STAGES * stage + 1024;
-    auto k = ozaki_kernel<PA, PB, TMAX, STAGES, DBITS>;
+    auto k = ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI>;
     static bool attr = false;
     if (!attr) {
         ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -596,11 +772,11 @@ void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B
 }  // namespace
 
 // Digit counts, digit widths and kept pairs (p + q <= TMAX) of the two
-// products.  Pre-activation: 5 digits of 8 bits (operand grid 2^-39, chunks
-// of 256 inputs).  Gram: 5 digits of 7 bits (H on a 2^-34 grid, chunks of
-// 1024 samples).
-constexpr int HID_PX = 5, HID_PW = 5, HID_TMAX = 6, HID_BITS = 8;
-constexpr int GRAM_PH = 5, GRAM_TMAX = 6, GRAM_BITS = 7;
+// products.  Pre-activation: 6 digits of 7 bits (operand grid 2^-41; one
+// exact chunk for up to 1024 inputs).  Gram: 5 digits of 7 bits (H on a
+// 2^-34 grid, chunks of 1024 samples).
+constexpr int HID_PX = 6, HID_PW = 6, HID_TMAX = 7, HID_BITS = 7;
+constexpr int GRAM_PH = GRAM_PH_, GRAM_TMAX = 6, GRAM_BITS = GRAM_BITS_;
 
 int64_t oz_pad(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
 
@@ -611,6 +787,7 @@ OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m) {
     w.wp = ar.take<__nv_bfloat16>(HID_PW * Lp * nK);
     w.xs = ar.take<double>(Np);
     w.ws = ar.take<double>(Lp);
+    w.tab = ar.take<float4>(SIG_N);
     return w;
 }
 
@@ -618,22 +795,27 @@ size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m) {
     return (size_t)GRAM_PH * oz_pad(L + m, BM) * oz_pad(N, BN) * 2;
 }
 
-// zt (Lp x Np FP64) = X W computed from exact digit slices on the tensor cores.
-void oz_preact(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
-               int64_t ldx, const double *W, int64_t ldw, int64_t L, int64_t m, double *zt,
-               int *err) {
+// H = a g(X W + b) on the tensor cores, emitted directly as the Gram digit
+// planes (rows < L and padding rows; target rows are left to oz_t_digits),
+// with the row scales hs and, if Ht != NULL, FP64 H^T.
+void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
+               int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
+               int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
+               int64_t ldh, int *err) {
     const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
-    __nv_bfloat16 *xp = w.xp, *wp = w.wp;
-    double *xs = w.xs, *ws = w.ws;
     if (xdt == ELM_F64)
         digits_rows_kernel<HID_PX, HID_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const double *)X, N, n, ldx, Np, nK, xp, xs);
+            (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs);
     else
         digits_rows_kernel<HID_PX, HID_BITS, float><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const float *)X, N, n, ldx, Np, nK, xp, xs);
+            (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs);
     ELM_CHECK_LAUNCH();
-    digits_cols_kernel<HID_PW, HID_BITS><<<(unsigned)((Lp + 127) / 128), 128, 0, s>>>(W, n, L, ldw, Lp, nK,
-                                                                             wp, ws);
+    digits_cols_kernel<HID_PW, HID_BITS><<<(unsigned)((Lp + 127) / 128), 128, 0, s>>>(
+        W, n, L, ldw, Lp, nK, w.wp, w.ws);
+    ELM_CHECK_LAUNCH();
+    hs_kernel<<<(unsigned)((Lp + 255) / 256), 256, 0, s>>>(a, L, m, Lp, hs);
+    ELM_CHECK_LAUNCH();
+    sigmoid_table_kernel<<<(SIG_N + 255) / 256, 256, 0, s>>>(w.tab);
     ELM_CHECK_LAUNCH();
     OzParams P{};
     P.a_rows = Lp;
@@ -644,23 +826,25 @@ void oz_preact(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ntile_m = Lp / BM;
     P.gram = 0;
     P.out_scale = ldexp(1.0, -2 * (HID_BITS - 1));
-    P.rscale = ws;
-    P.cscale = xs;
-    P.out = zt;
-    P.ldo = Np;
+    P.rscale = w.ws;
+    P.cscale = w.xs;
+    P.out = nullptr;
+    P.ldo = 0;
     P.err = err;
-    launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS>(s, wp, xp, P, (Lp / BM) * (Np / BN));
-}
-
-// Activation + Gram digit planes (rows < L) from zt; optional FP64 Ht.
-void oz_activate(cudaStream_t s, const double *zt, int64_t L, int64_t N, int64_t m,
-                 const double *b, const double *a, int act, __nv_bfloat16 *planes, double *hs,
-                 double *Ht, int64_t ldh) {
-    const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
-    dim3 g((unsigned)((Np + 255) / 256), (unsigned)Lp);
-    act_digits_kernel<GRAM_PH, GRAM_BITS><<<g, 256, 0, s>>>(zt, L, N, m, b, a, act, Lp, Np, planes, hs, Ht,
-                                                 ldh);
-    ELM_CHECK_LAUNCH();
+    P.ap.b = b;
+    P.ap.a = a;
+    P.ap.act = act;
+    P.ap.L = L;
+    P.ap.m = m;
+    P.ap.planes = planes;
+    P.ap.plane_stride = Lp * Np;
+    P.ap.Np = Np;
+    P.ap.hs = hs;
+    P.ap.tab = w.tab;
+    P.ap.Ht = Ht;
+    P.ap.ldh = ldh;
+    launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P,
+                                                           (Lp / BM) * (Np / BN));
 }
 
 // Target rows L .. L+m-1 of the Gram digit planes.
@@ -668,7 +852,8 @@ void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_
                  __nv_bfloat16 *planes, double *hs) {
     if (m <= 0) return;
     const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
-    t_digits_kernel<GRAM_PH, GRAM_BITS><<<(unsigned)m, 256, 0, s>>>(T, ldt, N, L, Lp, Np, planes, hs);
+    t_digits_kernel<GRAM_PH, GRAM_BITS><<<(unsigned)m, 256, 0, s>>>(T, ldt, N, L, Lp, Np, planes,
+                                                                     hs);
     ELM_CHECK_LAUNCH();
 }
 
@@ -692,7 +877,8 @@ void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int6
     P.out = G;
     P.ldo = ldg;
     P.err = err;
-    launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS>(s, planes, planes, P, nJ * (nJ + 1));
+    launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS, 0>(s, planes, planes, P,
+                                                               nJ * (nJ + 1));
 }
 
 }  // namespace elm
