@@ -177,6 +177,39 @@ int elm_phase_times(elm_ctx *ctx, double *ms_out, int max_phases);
 const char *elm_phase_name(int phase);
 int64_t elm_launch_counter(void);
 
+/*
+ * elm_hidden_noalloc -- the mixed-precision hidden layer of elm_hidden
+ * (ELM_PREC_MIXED) for callers that may not allocate device memory, neither
+ * themselves nor through the library: for example a plugin inside a host
+ * framework that owns all device memory through its own pool, or a service
+ * that forbids allocator calls once it has started.  The paper has no
+ * counterpart; this is an interface variant, the arithmetic is that of
+ * elm_hidden.
+ *
+ * No context is needed and nothing is allocated: all scratch (the digit
+ * slices of X, W and H, their scales, the activation table and an error
+ * flag) lives in one fixed device array compiled into the library, of
+ * ELM_NOALLOC_SCRATCH_BYTES per device, held by every device that loads the
+ * library until the process exits.  elm_hidden_noalloc_bytes() reports how
+ * much of it a problem needs; larger problems get ELM_ERR_UNSUPPORTED.
+ * X, W, b, a and Ht must be device pointers (host pointers: ELM_ERR_ARG);
+ * the layouts are those of elm_hidden.  Work runs on `stream` (a
+ * cudaStream_t, NULL for the legacy default stream), and the call
+ * synchronises that stream before returning.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (once per device); call it once outside any
+ * latency-critical section first.  Every call on a device shares the same
+ * array and leaves its contents behind, so calls that overlap on the GPU
+ * (other threads or other streams) race and must be serialised by the
+ * caller.
+ */
+#define ELM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int elm_hidden_noalloc(const void *X, int x_dtype, int64_t N, int64_t n, int64_t ldx,
+                       const double *W, int64_t ldw, const double *b, const double *a,
+                       int64_t L, int act, double *Ht, int64_t ldh, void *stream);
+int elm_hidden_noalloc_bytes(int64_t N, int64_t n, int64_t L, int64_t *bytes);
+
 #ifdef __cplusplus
 }
 #endif

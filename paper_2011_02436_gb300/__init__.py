@@ -183,6 +183,32 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
 
 
 FLAG_PHASE_TIMING = 1
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def elm_hidden_noalloc(X, W, b, a=None, act=ACT_SIGMOID, Ht=None, stream=None):
+    """elm_hidden (mixed precision) without any device allocation by the
+    library: scratch comes from a fixed device array inside libelm.so.  All
+    arrays must be CUDA tensors; Ht is allocated here (by torch) when not
+    given."""
+    N, n = X.shape
+    L = W.shape[1]
+    if Ht is None:
+        Ht = _empty_like_device(X, (L, N))
+    st = _lib.load().elm_hidden_noalloc(_ptr(X), _xdtype(X), N, n, _ld(X), _ptr(W), _ld(W),
+                                        _ptr(b), _ptr(a), L, act, _ptr(Ht), _ld(Ht),
+                                        _stream_ptr(stream))
+    if st != OK:
+        raise ElmError(st, "elm_hidden_noalloc")
+    return Ht
+
+
+def elm_hidden_noalloc_bytes(N, n, L):
+    v = C.c_int64(0)
+    st = _lib.load().elm_hidden_noalloc_bytes(N, n, L, C.byref(v))
+    if st != OK:
+        raise ElmError(st, "elm_hidden_noalloc_bytes")
+    return int(v.value)
 
 
 def elm_phase_times(ctx):

@@ -43,6 +43,9 @@ SIGNATURES = [
     ("elm_phase_times", C.c_int, [vp, C.POINTER(dbl), C.c_int]),
     ("elm_phase_name", C.c_char_p, [C.c_int]),
     ("elm_launch_counter", i64, []),
+    ("elm_hidden_noalloc", C.c_int, [vp, C.c_int, i64, i64, i64, vp, i64, vp, vp, i64, C.c_int,
+                                     vp, i64, vp]),
+    ("elm_hidden_noalloc_bytes", C.c_int, [i64, i64, i64, C.POINTER(i64)]),
 ]
 
 _lib = None
