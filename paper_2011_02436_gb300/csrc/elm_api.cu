@@ -273,7 +273,11 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     res->refine_iters = 0;
     res->rel_update = 0.0;
     res->status = ELM_OK;
-    if (fl || xfl) {
+    if (fl & 2) {                       // a bounded wait in the factorisation expired
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if ((fl & 1) || xfl) {
         res->status = ELM_ERR_NUMERIC;
         return;
     }
@@ -370,11 +374,11 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     res->refine_iters = 0;
     res->rel_update = 0.0;
     res->status = ELM_OK;
-    if (terr) {
+    if (terr || (fl & 2)) {
         res->status = ELM_ERR_TIMEOUT;
         return;
     }
-    if (fl || xfl) {
+    if ((fl & 1) || xfl) {
         res->status = ELM_ERR_NUMERIC;
         return;
     }
@@ -548,7 +552,8 @@ int elm_pinv_rank(elm_ctx *ctx, const double *Ht, int64_t L, int64_t N, int64_t 
         factor_pivoted(s, S, L, L, tau, f, R, Rt, ctx->sm_count);
         int32_t fl = 0;
         const int64_t r = read_rank(s, f, &fl);
-        if (fl) throw ElmError(ELM_ERR_NUMERIC, "non-finite Gram matrix");
+        if (fl & 2) throw ElmError(ELM_ERR_TIMEOUT, "factorisation wait expired");
+        if (fl & 1) throw ElmError(ELM_ERR_NUMERIC, "non-finite Gram matrix");
         *rank_out = r;
         if (perm_out) {
             cudaMemcpyKind k = on_device(perm_out) ? cudaMemcpyDeviceToDevice

@@ -40,7 +40,7 @@ struct FactorState {
     int64_t Lr;       // active (not yet pivoted) columns
     int64_t rank;     // final rank (valid once done)
     int32_t done;     // 1 once the stopping rule fired or all columns pivoted
-    int32_t flags;    // bit 0: non-finite value met
+    int32_t flags;    // bit 0: non-finite value met; bit 1: a bounded wait expired
     int64_t steps;    // pivots taken by the last panel
 };
 
@@ -163,6 +163,7 @@ int64_t oz_pad(int64_t v, int64_t q);
 struct OzHidWs {
     __nv_bfloat16 *xp, *wp;  // digit planes of X and W
     double *xs, *ws;         // their power-of-two row / column scales
+    float *xsf;              // the row scales of X as floats
     float4 *tab;             // sigmoid table
 };
 // Scratch of oz_hidden for an N x n input and L (+ m target) rows.

@@ -30,47 +30,39 @@ namespace {
 constexpr int FT = 256;       // threads per CTA in the panel / solves
 constexpr int MAXNB = 32;     // largest panel width
 
+// Order key of a double as an unsigned integer (larger key = larger value,
+// NaN below everything): comparisons then use the integer pipes, not the
+// FP64 pipe, which issues about two lanes per clock per SM on GB300.
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) return 0ull;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 struct Cand {
+    unsigned long long key;
     double val;
     int32_t orig;
     int32_t x;
 };
 
+__device__ __forceinline__ Cand make_cand(double v, int32_t orig, int32_t x) {
+    return Cand{dkey(v), v, orig, x};
+}
+__device__ __forceinline__ Cand no_cand() { return Cand{0ull, -INFINITY, 0x7fffffff, -1}; }
+
+// larger value first; equal values: lower original index first
 __device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
-    return a.val > b.val || (a.val == b.val && a.orig < b.orig);
+    return a.key > b.key || (a.key == b.key && a.orig < b.orig);
 }
 
 __device__ __forceinline__ Cand shfl_cand(const Cand &c, int o) {
     Cand r;
-    r.val = __shfl_xor_sync(0xffffffffu, c.val, o);
+    r.key = __shfl_xor_sync(0xffffffffu, c.key, o);
+    r.val = __longlong_as_double(__shfl_xor_sync(0xffffffffu, __double_as_longlong(c.val), o));
     r.orig = __shfl_xor_sync(0xffffffffu, c.orig, o);
     r.x = __shfl_xor_sync(0xffffffffu, c.x, o);
     return r;
-}
-
-// Block-wide argmax of the unpivoted diagonal entries of this CTA's slice.
-__device__ void local_argmax(const double *d, const int32_t *piv, const int32_t *act,
-                             int64_t x0, int64_t nloc, Cand *out, Cand *wred) {
-    Cand best{-INFINITY, 0x7fffffff, -1};
-    for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
-        if (piv[xl]) continue;
-        Cand c{d[xl], act[x0 + xl], (int32_t)(x0 + xl)};
-        if (better(c, best)) best = c;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        Cand c = shfl_cand(best, o);
-        if (better(c, best)) best = c;
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) wred[warp] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Cand b = wred[0];
-        for (int w = 1; w < FT / 32; w++)
-            if (better(wred[w], b)) b = wred[w];
-        *out = b;
-    }
-    __syncthreads();
 }
 
 // S -> A = diag(s) S diag(s), s_j = 1/sqrt(S_jj) (0 if S_jj <= 0); dS = diag(S).
@@ -103,49 +95,93 @@ __global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t 
     }
 }
 
+// ------------------------------------------------------------ panel
 // A pivot candidate as published to the cluster: the CTA's largest unpivoted
-// updated diagonal and that column's entries in the panel rows so far.
+// updated diagonal, its original and active index, and that column's entries
+// in the panel rows so far.
 struct Slot {
     double val;
-    int32_t orig;
-    int32_t x;
+    long long idx;        // (orig << 32) | x, x = -1 when the CTA has none
     double pcol[MAXNB];
 };
 constexpr int MAXCS = 16;
+constexpr uint64_t PANEL_WAIT_NS = 2000000000ull;
 
-// Local argmax of this CTA's slice, written as a Slot into every CTA of the
-// cluster (slot index `mine`), together with its panel column rows 0..t-1.
-__device__ void publish(cg::cluster_group &cluster, int CS, int cr, const double *d,
-                        const int32_t *piv, const int32_t *act, int64_t x0, int64_t nloc,
-                        const double *Ps, int64_t Wd, int t, Slot *slots, Cand *wred,
-                        Cand *s_mine) {
-    local_argmax(d, piv, act, x0, nloc, s_mine, wred);
-    const Cand me = *s_mine;
-    const int64_t xl = me.x >= 0 ? me.x - x0 : 0;
-    // warp w writes the slot into peers w, w + 8: lane 0 the header, lanes
-    // 1..31 (and 33..) the panel column rows 0..t-1
-    const int f0 = threadIdx.x & 31;
-    for (int peer = threadIdx.x >> 5; peer < CS; peer += FT / 32) {
-        Slot *dst = cluster.map_shared_rank(slots, peer) + cr;
-        for (int f = f0; f <= t; f += 32) {
-            if (f == 0) {
-                dst->val = me.val;
-                dst->orig = me.orig;
-                dst->x = me.x;
-            } else {
-                dst->pcol[f - 1] = me.x >= 0 ? Ps[(int64_t)(f - 1) * Wd + xl] : 0.0;
-            }
-        }
+__device__ __forceinline__ uint32_t su32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t mapa(uint32_t a, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+// 8-byte store into a peer's shared memory, counted by that peer's mbarrier
+__device__ __forceinline__ void st_async64(uint32_t raddr, uint64_t v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(
+                     raddr),
+                 "l"(v), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = gtime();
+    for (;;) {
+        if (mbar_try(b, parity)) return true;
+        if (gtime() - t0 > PANEL_WAIT_NS) return false;
     }
+}
+
+__device__ __forceinline__ Cand slot_cand(const Slot &s) {
+    return make_cand(s.val, (int32_t)(s.idx >> 32), (int32_t)(s.idx & 0xffffffff));
+}
+
+// 1/sqrt(v) to FP64 accuracy: float seed, two Newton steps in FP64
+__device__ __forceinline__ double rsqrt64(double v) {
+    double y = (double)rsqrtf((float)v);
+    y = y * fma(-0.5 * v, y * y, 1.5);
+    y = y * fma(-0.5 * v, y * y, 1.5);
+    return y;
+}
+
+// Bytes a CTA receives for one exchange carrying `t` panel entries.
+__device__ __forceinline__ uint32_t exch_bytes(int CS, int t) {
+    return (uint32_t)CS * (16u + 8u * (uint32_t)t);
 }
 
 // One panel of up to nb pivots on a cluster.  A: active matrix (Lr x Lr,
 // full symmetric, lda), act: active -> original index.  Writes the panel
 // rows P (active index space, row stride ldp), the pivot rows Rrow (original
 // column order), perm, the compaction map rem / act_next and the state.
-// Per pivot there is exactly one cluster barrier: before it every CTA has
-// pushed its candidate into all peers' shared memory (double-buffered
-// slots), after it every CTA resolves the same pivot from local memory.
+// Per pivot every CTA sends its local candidate (with the candidate
+// column's panel entries) into every peer's shared memory with st.async;
+// each CTA waits on its own transaction-counted mbarrier (double-buffered
+// slots), so no cluster-wide barrier sits inside the pivot loop.  Waits are
+// bounded; on expiry the state's flag bit 1 is set.
 __global__ void __launch_bounds__(FT)
 panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restrict__ act,
              double *__restrict__ P, int64_t ldp, double *__restrict__ Rrow, int64_t ldr,
@@ -155,13 +191,12 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks();
     const int cr = (int)cluster.block_rank();
-    __shared__ Slot slots[2][MAXCS];
+    __shared__ __align__(16) Slot slots[2][MAXCS];
+    __shared__ __align__(8) uint64_t xbar[2];
     __shared__ Cand wred[FT / 32];
-    __shared__ Cand s_mine, s_best;
-    __shared__ int s_bi;
-    __shared__ double u[MAXNB];
     __shared__ int32_t s_cnt;
     __shared__ int64_t s_off, s_tot;
+    __shared__ int s_timeout;
     extern __shared__ double dyn[];
 
     const FactorState s0 = *st;
@@ -173,79 +208,131 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     double *Ps = dyn;                          // nb x wmax
     double *d = dyn + (int64_t)nb * wmax;      // wmax
     int32_t *piv = (int32_t *)(d + wmax);      // wmax
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    if (threadIdx.x == 0) {
+        mbar_init(&xbar[0], 1);
+        mbar_init(&xbar[1], 1);
+        s_timeout = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect(&xbar[0], exch_bytes(CS, 0));   // filled by the first exchange
+        mbar_expect(&xbar[1], exch_bytes(CS, 1));   // filled after pivot 0
+    }
     for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
         d[xl] = A[(x0 + xl) * lda + x0 + xl];
         piv[xl] = 0;
     }
-    __syncthreads();
-    publish(cluster, CS, cr, d, piv, act, x0, nloc, Ps, Wd, 0, slots[0], wred, &s_mine);
-    cluster.sync();
+    cluster.sync();   // every peer's barriers are initialised and armed
+
+    // local argmax over this CTA's unpivoted columns, then send it (and
+    // the column's first `t` panel entries) to every peer's slot `cr` of
+    // buffer `buf`
+    auto publish = [&](int t, int buf) {
+        Cand best = no_cand();
+        for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
+            if (piv[xl]) continue;
+            Cand c = make_cand(d[xl], act[x0 + xl], (int32_t)(x0 + xl));
+            if (better(c, best)) best = c;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            Cand c = shfl_cand(best, o);
+            if (better(c, best)) best = c;
+        }
+        if (lane == 0) wred[warp] = best;
+        __syncthreads();
+        Cand me = wred[0];
+        for (int w = 1; w < FT / 32; w++)
+            if (better(wred[w], me)) me = wred[w];
+        const int64_t xl = me.x >= 0 ? me.x - x0 : 0;
+        const uint32_t lslot = su32(&slots[buf][cr]);
+        const uint32_t lbar = su32(&xbar[buf]);
+        // thread (peer, f): f = 0 value, f = 1 index, f >= 2 panel entry f - 2
+        const int nf = 2 + t;
+        for (int e = threadIdx.x; e < CS * nf; e += FT) {
+            const int peer = e / nf, f = e % nf;
+            uint64_t v;
+            uint32_t off;
+            if (f == 0) {
+                v = (uint64_t)__double_as_longlong(me.val);
+                off = 0;
+            } else if (f == 1) {
+                v = ((uint64_t)(uint32_t)me.orig << 32) | (uint32_t)me.x;
+                off = 8;
+            } else {
+                const double pv = me.x >= 0 ? Ps[(int64_t)(f - 2) * Wd + xl] : 0.0;
+                v = (uint64_t)__double_as_longlong(pv);
+                off = 16 + 8 * (f - 2);
+            }
+            st_async64(mapa(lslot + off, peer), v, mapa(lbar, peer));
+        }
+    };
+
+    publish(0, 0);
 
     const int tmax = (int)(nb < Lr ? nb : Lr);
     int steps = 0;
     bool done = false;
     for (int t = 0; t < tmax; t++) {
-        Slot *sl = slots[t & 1];
-        if (threadIdx.x < 32) {
-            Cand c{-INFINITY, 0x7fffffff, -1};
-            int bi = -1;
-            if (threadIdx.x < CS) {
-                c = Cand{sl[threadIdx.x].val, sl[threadIdx.x].orig, sl[threadIdx.x].x};
-                bi = threadIdx.x;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                Cand c2 = shfl_cand(c, o);
-                int b2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (better(c2, c)) {
-                    c = c2;
-                    bi = b2;
-                }
-            }
-            if (threadIdx.x == 0) {
-                s_best = c;
-                s_bi = bi;
+        const int buf = t & 1;
+        if (!mbar_wait(&xbar[buf], (uint32_t)((t >> 1) & 1))) {
+            s_timeout = 1;
+            break;
+        }
+        // every warp reduces the CS candidates itself (no broadcast needed)
+        Cand best = no_cand();
+        int bi = -1;
+        if (lane < CS) {
+            best = slot_cand(slots[buf][lane]);
+            bi = lane;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            Cand c2 = shfl_cand(best, o);
+            int b2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (better(c2, best)) {
+                best = c2;
+                bi = b2;
             }
         }
-        __syncthreads();
-        const Cand best = s_best;
         if (!(best.val > tau)) {
             done = true;
             break;
         }
-        if (threadIdx.x < t) u[threadIdx.x] = sl[s_bi].pcol[threadIdx.x];
         const int64_t q = best.x;
-        const int owner = (int)(q / Wd);
-        const int64_t qloc = q - (int64_t)owner * Wd;
-        const double rkk = sqrt(best.val);
-        __syncthreads();
+        const double *ucol = slots[buf][bi].pcol;
         const double *Aq = A + q * lda;
+        // only warps that own columns spend FP64 issue slots
+        double rinv = 0.0, rkk = 0.0;
+        if ((int64_t)(warp * 32) < nloc) {
+            rinv = rsqrt64(best.val);
+            rkk = best.val * rinv;
+        }
         for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
             const int64_t x = x0 + xl;
             double v;
             if (x == q) {
                 v = rkk;
+                piv[xl] = 1;
             } else if (piv[xl]) {
                 v = 0.0;
             } else {
                 v = Aq[x];
-                for (int s = 0; s < t; s++) v = fma(-u[s], Ps[(int64_t)s * Wd + xl], v);
-                v = v / rkk;
+                for (int s = 0; s < t; s++) v = fma(-ucol[s], Ps[(int64_t)s * Wd + xl], v);
+                v = v * rinv;
                 d[xl] = fma(-v, v, d[xl]);
             }
             Ps[(int64_t)t * Wd + xl] = v;
             P[(int64_t)t * ldp + x] = v;
             Rrow[(k0 + t) * ldr + act[x]] = v;
         }
-        __syncthreads();
-        if (owner == cr && threadIdx.x == 0) piv[qloc] = 1;
         if (cr == 0 && threadIdx.x == 0) perm[k0 + t] = act[q];
-        __syncthreads();
-        publish(cluster, CS, cr, d, piv, act, x0, nloc, Ps, Wd, t + 1, slots[(t + 1) & 1], wred,
-                &s_mine);
-        cluster.sync();
+        __syncthreads();   // this CTA's slice updated; slots[buf] fully read
+        // re-arm this buffer for its next use (filled after pivot t + 1) before
+        // sending anything that lets a peer get there
+        if (threadIdx.x == 0 && t + 2 < tmax) mbar_expect(&xbar[buf], exch_bytes(CS, t + 2));
         steps = t + 1;
+        if (t + 1 < tmax) publish(t + 1, buf ^ 1);
     }
+    if (s_timeout && threadIdx.x == 0) atomicOr(&st->flags, 2);
 
     // Compaction: unpivoted active columns keep their relative order.
     if (threadIdx.x < 32) {

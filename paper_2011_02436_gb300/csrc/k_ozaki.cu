@@ -230,6 +230,7 @@ struct ActParams {
     int64_t Np;
     const double *hs;       // Gram row scales (pow2_ceil(a_j))
     const float4 *tab;      // sigmoid table (s0 hi/lo, s1 hi/lo) on a 2^-6 grid
+    const float *csf;       // per-sample scales as floats
     double *Ht;             // optional FP64 H^T (row j, column i)
     int64_t ldh;
 };
@@ -252,25 +253,29 @@ struct OzParams {
 };
 
 // Fused hidden-layer epilogue for one TMEM lane (neuron j = m) and the 64
-// samples n0 .. n0+63: exact pre-activation V (int64) -> double-float z ->
-// h = a_j g(z + b_j) -> GRAM_PH digits of h / hs[j] on the 2^-34 grid.
+// samples n0 .. n0+63: pre-activation (exact integer digit sums) ->
+// double-float z -> h = a_j g(z + b_j) -> GRAM_PH digits of h / hs[j] on the
+// 2^-34 grid.  All arithmetic per element is FP32 / double-float.
 constexpr int GRAM_PH_ = 5, GRAM_BITS_ = 7;
+__device__ __forceinline__ float pow2f_of(double v) {   // v a power of two in float range
+    return (float)v;
+}
 template <int DBITS, int TMAX>
 __device__ __forceinline__ void hidden_epilogue(const OzParams &P, int64_t m, int64_t n0,
-                                                uint32_t lo_addr, uint32_t hi_addr) {
+                                                uint32_t lane_base, uint32_t lo_col,
+                                                uint32_t hi_col, bool direct) {
     const ActParams &A = P.ap;
     // Every lane executes the warp-collective TMEM loads below; rows of the
     // target block (written by the target slicer) only skip the stores.
     const bool target_row = m >= A.L && m < A.L + A.m;
     const bool live = m < A.L;
-    // per-row constants
-    int er = 0;
+    // per-row constants: z = V * 2^(-2(B-1) - B(TMAX-2)) * ws[m] * xs[n]
+    float rowf = 0.f;
     dfl bj{0.f, 0.f}, aj{1.f, 0.f};
     float inv_hs = 1.f;
     bool scaled = false;
     if (live) {
-        const double scale = P.out_scale * P.rscale[m];   // power of two
-        er = ilogb(scale) - DBITS * (TMAX - 2);
+        rowf = pow2f_of(ldexp(P.out_scale * P.rscale[m], -DBITS * (TMAX - 2)));
         const double b = A.b[m];
         bj.h = (float)b;
         bj.l = (float)(b - (double)bj.h);
@@ -285,56 +290,79 @@ __device__ __forceinline__ void hidden_epilogue(const OzParams &P, int64_t m, in
     __nv_bfloat16 *row = A.planes + m * A.Np + n0;
 #pragma unroll 1
     for (int h = 0; h < BN / 16; h++) {
-        uint32_t w0[16], w1[16];
-        tmem_ld16(lo_addr + h * 16, w0);
-        tmem_ld16(hi_addr + h * 16, w1);
-        tmem_wait_ld();
-        int dg[GRAM_PH_][16];
+        dfl V[16];
+        if (direct) {
+            // V = sum_t acc_t 2^(B (TMAX - t)) in units of 2^(-B (TMAX - 2)):
+            // Horner from the leading diagonal (t = 2), in double-float
+            uint32_t w[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) V[i] = {0.f, 0.f};
+#pragma unroll
+            for (int t = 2; t <= TMAX; t++) {
+                tmem_ld16(lane_base + (uint32_t)((t - 2) * BN + h * 16), w);
+                tmem_wait_ld();
+                const float sc = (float)(1 << DBITS);
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const dfl x{V[i].h * sc, V[i].l * sc};
+                    V[i] = df_add(x, {__uint_as_float(w[i]), 0.f});
+                }
+            }
+        } else {
+            uint32_t w0[16], w1[16];
+            tmem_ld16(lane_base + lo_col + h * 16, w0);
+            tmem_ld16(lane_base + hi_col + h * 16, w1);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const long long run = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
+                const float vh = __ll2float_rn(run);
+                V[i] = {vh, __ll2float_rn(run - __float2ll_rn(vh))};
+            }
+        }
+        float dg[GRAM_PH_][16];
 #pragma unroll
         for (int i = 0; i < 16; i++) {
             const int64_t n = n0 + h * 16 + i;
-            long long q = 0;
-            if (live && n < P.n_valid) {
-                const long long V = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
-                const int e = er + ilogb(P.cscale[n]);
-                const float vh = __ll2float_rn(V);
-                const long long Vh = __float2ll_rn(vh);            // exact: vh is an integer
-                dfl z{ldexpf(vh, e), ldexpf(__ll2float_rn(V - Vh), e)};
-                z = df_add(z, bj);
-                dfl hv;
-                if (A.act == ELM_ACT_TANH) {                        // tanh u = 2 sigma(2u) - 1
-                    dfl sg = sigmoid_df({2.f * z.h, 2.f * z.l}, A.tab);
-                    hv = df_add({2.f * sg.h, 2.f * sg.l}, {-1.f, 0.f});
-                } else {
-                    hv = sigmoid_df(z, A.tab);
-                }
-                if (scaled) hv = df_mul(hv, aj);
-                hv.h *= inv_hs;
-                hv.l *= inv_hs;
-                if (A.Ht) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
-                // q = round(h~ 2^34), from the two parts
-                const float Ah = hv.h * 17179869184.0f;
-                const float Ai = rintf(Ah);
-                q = (long long)Ai + (long long)rintf((Ah - Ai) + hv.l * 17179869184.0f);
+            const bool on = live && n < P.n_valid;
+            // the unit of V is scaled into the argument with two exact
+            // power-of-two products
+            const float f = on ? rowf * A.csf[n] : 0.f;
+            dfl z{V[i].h * f, V[i].l * f};
+            z = df_add(z, bj);
+            dfl hv;
+            if (A.act == ELM_ACT_TANH) {                            // tanh u = 2 sigma(2u) - 1
+                dfl sg = sigmoid_df({2.f * z.h, 2.f * z.l}, A.tab);
+                hv = df_add({2.f * sg.h, 2.f * sg.l}, {-1.f, 0.f});
+            } else {
+                hv = sigmoid_df(z, A.tab);
             }
-            // balanced base-2^7 digits, least significant first
+            if (scaled) hv = df_mul(hv, aj);
+            hv.h = on ? hv.h * inv_hs : 0.f;
+            hv.l = on ? hv.l * inv_hs : 0.f;
+            if (on && A.Ht) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
+            // balanced digits of h~ on the 2^-34 grid, most significant first:
+            // d = rint(r 2^B), r <- r 2^B - d, carried in double-float
+            float rh = hv.h * (float)(1 << (GRAM_BITS_ - 1));
+            float rl = hv.l * (float)(1 << (GRAM_BITS_ - 1));
 #pragma unroll
-            for (int p = GRAM_PH_ - 1; p >= 1; p--) {
-                const long long d = ((q + 64) & 127) - 64;
-                dg[p][i] = (int)d;
-                q = (q - d) >> 7;
+            for (int p = 0; p < GRAM_PH_; p++) {
+                const float d = rintf(rh);
+                dg[p][i] = d;
+                const dfl r = two_sum(rh - d, rl);                  // rh - d is exact
+                rh = r.h * (float)(1 << GRAM_BITS_);
+                rl = r.l * (float)(1 << GRAM_BITS_);
             }
-            dg[0][i] = (int)q;
         }
         if (target_row) continue;
 #pragma unroll
         for (int p = 0; p < GRAM_PH_; p++) {
-            __align__(16) __nv_bfloat16 v[16];
+            __align__(16) __nv_bfloat162 v[8];
 #pragma unroll
-            for (int i = 0; i < 16; i++) v[i] = __float2bfloat16_rn((float)dg[p][i]);
+            for (int i = 0; i < 8; i++) v[i] = __floats2bfloat162_rn(dg[p][2 * i], dg[p][2 * i + 1]);
             uint4 *dst = (uint4 *)(row + (int64_t)p * A.plane_stride + h * 16);
             dst[0] = *(const uint4 *)&v[0];
-            dst[1] = *(const uint4 *)&v[8];
+            dst[1] = *(const uint4 *)&v[4];
         }
     }
 }
@@ -480,6 +508,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int quarter = warp & 3;
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         bool ok = true;
+        // the fused hidden-layer epilogue reads a single chunk's diagonals
+        // directly; otherwise every chunk is folded into the int64 sums
+        const bool direct = (EPI == 1) && nchunk == 1;
         for (int c = 0; c < nchunk; c++) {
             // warp-uniform decision: TMEM loads below are warp-collective
             const bool got = __all_sync(0xffffffffu, mbar_wait(&acc_full, c & 1, abort));
@@ -488,6 +519,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 break;
             }
             tc_fence_after();
+            if (direct) break;
 #pragma unroll 1
             for (int h = 0; h < BN / 16; h++) {
                 // V = sum_t acc_t 2^(B (TMAX - t)): exact integers in units of
@@ -510,14 +542,17 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     tmem_ld16(lane_base + (uint32_t)((t - 2) * BN + h * 16), w0);
                     if (t + 1 <= TMAX) tmem_ld16(lane_base + (uint32_t)((t - 1) * BN + h * 16), w1);
                     tmem_wait_ld();
+                    // accumulators are exact integers below 2^25: 32-bit
+                    // conversions and a widening multiply-add
                     const long long mult = 1ll << (DBITS * (TMAX - t));
 #pragma unroll
-                    for (int i = 0; i < 16; i++) run[i] += __float2ll_rn(__uint_as_float(w0[i])) * mult;
+                    for (int i = 0; i < 16; i++)
+                        run[i] += (long long)__float2int_rn(__uint_as_float(w0[i])) * mult;
                     if (t + 1 <= TMAX) {
                         const long long mult1 = 1ll << (DBITS * (TMAX - t - 1));
 #pragma unroll
                         for (int i = 0; i < 16; i++)
-                            run[i] += __float2ll_rn(__uint_as_float(w1[i])) * mult1;
+                            run[i] += (long long)__float2int_rn(__uint_as_float(w1[i])) * mult1;
                     }
                 }
 #pragma unroll
@@ -567,7 +602,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     }
                 }
             } else {
-                hidden_epilogue<DBITS, TMAX>(P, m, n0, lane_base + LO_COL, lane_base + HI_COL);
+                hidden_epilogue<DBITS, TMAX>(P, m, n0, lane_base, LO_COL, HI_COL, direct);
             }
         }
     }
@@ -625,7 +660,7 @@ __device__ __forceinline__ double pow2_ceil(double v) {
 template <int PD, int DBITS, typename XT>
 __global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t n, int64_t ldx,
                                    int64_t Np, int64_t nK, __nv_bfloat16 *__restrict__ planes,
-                                   double *__restrict__ xs) {
+                                   double *__restrict__ xs, float *__restrict__ xsf) {
     constexpr int SH = (DBITS - 1) + DBITS * (PD - 1);
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -635,7 +670,10 @@ __global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t 
         for (int64_t k = lane; k < n; k += 32) mx = fmax(mx, fabs((double)X[i * ldx + k]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const double sc = pow2_ceil(mx);
-    if (lane == 0) xs[i] = sc;
+    if (lane == 0) {
+        xs[i] = sc;
+        xsf[i] = (float)sc;
+    }
     const double mul = ldexp(1.0 / sc, SH);  // exact: powers of two
     for (int64_t k = lane; k < nK; k += 32) {
         float d[PD];
@@ -786,6 +824,7 @@ OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m) {
     w.xp = ar.take<__nv_bfloat16>(HID_PX * Np * nK);
     w.wp = ar.take<__nv_bfloat16>(HID_PW * Lp * nK);
     w.xs = ar.take<double>(Np);
+    w.xsf = ar.take<float>(Np);
     w.ws = ar.take<double>(Lp);
     w.tab = ar.take<float4>(SIG_N);
     return w;
@@ -805,10 +844,10 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
     if (xdt == ELM_F64)
         digits_rows_kernel<HID_PX, HID_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs);
+            (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf);
     else
         digits_rows_kernel<HID_PX, HID_BITS, float><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs);
+            (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf);
     ELM_CHECK_LAUNCH();
     digits_cols_kernel<HID_PW, HID_BITS><<<(unsigned)((Lp + 127) / 128), 128, 0, s>>>(
         W, n, L, ldw, Lp, nK, w.wp, w.ws);
@@ -841,6 +880,7 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ap.Np = Np;
     P.ap.hs = hs;
     P.ap.tab = w.tab;
+    P.ap.csf = w.xsf;
     P.ap.Ht = Ht;
     P.ap.ldh = ldh;
     launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P,
