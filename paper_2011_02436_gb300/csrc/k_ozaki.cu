@@ -46,7 +46,8 @@ template <int DBITS>
 __host__ __device__ constexpr int chunk_slabs() {
     return (1 << (24 - 2 * (DBITS - 1) - 2)) / SK;
 }
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 drains/epilogue
+constexpr int NEPI = 256;       // drain/epilogue threads: two warps per TMEM lane quarter
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on any single wait
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
@@ -249,124 +250,112 @@ struct OzParams {
     double *out;
     int64_t ldo;
     int *err;
+    int64_t ntiles;     // tiles in the tile set
     ActParams ap;       // used when the kernel's EPI == 1
 };
 
-// Fused hidden-layer epilogue for one TMEM lane (neuron j = m) and the 64
-// samples n0 .. n0+63: pre-activation (exact integer digit sums) ->
-// double-float z -> h = a_j g(z + b_j) -> GRAM_PH digits of h / hs[j] on the
-// 2^-34 grid.  All arithmetic per element is FP32 / double-float.
+// Fused hidden-layer epilogue for one row (neuron j = m) and 32 samples
+// n0 .. n0+31, from the pre-activation V (double-float, in units of
+// 2^(-2(B-1) - B(TMAX-2)) * ws[m] * xs[n]) held in registers: z -> h =
+// a_j g(z + b_j) -> GRAM_PH digits of h / hs[j] on the 2^-34 grid.  All
+// arithmetic per element is FP32 / double-float.
 constexpr int GRAM_PH_ = 5, GRAM_BITS_ = 7;
-__device__ __forceinline__ float pow2f_of(double v) {   // v a power of two in float range
-    return (float)v;
-}
+struct RowAct {
+    bool live, skip, scaled;
+    float rowf, inv_hs;
+    dfl bj, aj;
+};
 template <int DBITS, int TMAX>
-__device__ __forceinline__ void hidden_epilogue(const OzParams &P, int64_t m, int64_t n0,
-                                                uint32_t lane_base, uint32_t lo_col,
-                                                uint32_t hi_col, bool direct) {
+__device__ __forceinline__ RowAct row_setup(const OzParams &P, int64_t m) {
     const ActParams &A = P.ap;
-    // Every lane executes the warp-collective TMEM loads below; rows of the
-    // target block (written by the target slicer) only skip the stores.
-    const bool target_row = m >= A.L && m < A.L + A.m;
-    const bool live = m < A.L;
-    // per-row constants: z = V * 2^(-2(B-1) - B(TMAX-2)) * ws[m] * xs[n]
-    float rowf = 0.f;
-    dfl bj{0.f, 0.f}, aj{1.f, 0.f};
-    float inv_hs = 1.f;
-    bool scaled = false;
-    if (live) {
-        rowf = pow2f_of(ldexp(P.out_scale * P.rscale[m], -DBITS * (TMAX - 2)));
+    RowAct r{};
+    r.skip = m >= A.L && m < A.L + A.m;            // target rows: written by the slicer
+    r.live = m < A.L;
+    r.aj = {1.f, 0.f};
+    r.inv_hs = 1.f;
+    if (r.live) {
+        r.rowf = (float)ldexp(P.out_scale * P.rscale[m], -DBITS * (TMAX - 2));
         const double b = A.b[m];
-        bj.h = (float)b;
-        bj.l = (float)(b - (double)bj.h);
+        r.bj.h = (float)b;
+        r.bj.l = (float)(b - (double)r.bj.h);
         if (A.a) {
             const double av = A.a[m];
-            aj.h = (float)av;
-            aj.l = (float)(av - (double)aj.h);
-            scaled = true;
+            r.aj.h = (float)av;
+            r.aj.l = (float)(av - (double)r.aj.h);
+            r.scaled = true;
         }
-        inv_hs = (float)(1.0 / A.hs[m]);
+        r.inv_hs = (float)(1.0 / A.hs[m]);
     }
-    __nv_bfloat16 *row = A.planes + m * A.Np + n0;
-#pragma unroll 1
-    for (int h = 0; h < BN / 16; h++) {
-        dfl V[16];
-        if (direct) {
-            // V = sum_t acc_t 2^(B (TMAX - t)) in units of 2^(-B (TMAX - 2)):
-            // Horner from the leading diagonal (t = 2), in double-float
-            uint32_t w[16];
+    return r;
+}
+// 8 samples n0 .. n0+7 of one row
+__device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R, int64_t m,
+                                             int64_t n0, const dfl *V) {
+    const ActParams &A = P.ap;
+    if (R.skip) return;
+    float dg[GRAM_PH_][8];
 #pragma unroll
-            for (int i = 0; i < 16; i++) V[i] = {0.f, 0.f};
-#pragma unroll
-            for (int t = 2; t <= TMAX; t++) {
-                tmem_ld16(lane_base + (uint32_t)((t - 2) * BN + h * 16), w);
-                tmem_wait_ld();
-                const float sc = (float)(1 << DBITS);
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const dfl x{V[i].h * sc, V[i].l * sc};
-                    V[i] = df_add(x, {__uint_as_float(w[i]), 0.f});
-                }
-            }
+    for (int i = 0; i < 8; i++) {
+        const int64_t n = n0 + i;
+        const bool on = R.live && n < P.n_valid;
+        const float f = on ? R.rowf * A.csf[n] : 0.f;   // two exact power-of-two products
+        dfl z{V[i].h * f, V[i].l * f};
+        z = df_add(z, R.bj);
+        dfl hv;
+        if (A.act == ELM_ACT_TANH) {                    // tanh u = 2 sigma(2u) - 1
+            dfl sg = sigmoid_df({2.f * z.h, 2.f * z.l}, A.tab);
+            hv = df_add({2.f * sg.h, 2.f * sg.l}, {-1.f, 0.f});
         } else {
-            uint32_t w0[16], w1[16];
-            tmem_ld16(lane_base + lo_col + h * 16, w0);
-            tmem_ld16(lane_base + hi_col + h * 16, w1);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const long long run = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
-                const float vh = __ll2float_rn(run);
-                V[i] = {vh, __ll2float_rn(run - __float2ll_rn(vh))};
-            }
+            hv = sigmoid_df(z, A.tab);
         }
-        float dg[GRAM_PH_][16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const int64_t n = n0 + h * 16 + i;
-            const bool on = live && n < P.n_valid;
-            // the unit of V is scaled into the argument with two exact
-            // power-of-two products
-            const float f = on ? rowf * A.csf[n] : 0.f;
-            dfl z{V[i].h * f, V[i].l * f};
-            z = df_add(z, bj);
-            dfl hv;
-            if (A.act == ELM_ACT_TANH) {                            // tanh u = 2 sigma(2u) - 1
-                dfl sg = sigmoid_df({2.f * z.h, 2.f * z.l}, A.tab);
-                hv = df_add({2.f * sg.h, 2.f * sg.l}, {-1.f, 0.f});
-            } else {
-                hv = sigmoid_df(z, A.tab);
-            }
-            if (scaled) hv = df_mul(hv, aj);
-            hv.h = on ? hv.h * inv_hs : 0.f;
-            hv.l = on ? hv.l * inv_hs : 0.f;
-            if (on && A.Ht) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
-            // balanced digits of h~ on the 2^-34 grid, most significant first:
-            // d = rint(r 2^B), r <- r 2^B - d, carried in double-float
-            float rh = hv.h * (float)(1 << (GRAM_BITS_ - 1));
-            float rl = hv.l * (float)(1 << (GRAM_BITS_ - 1));
-#pragma unroll
-            for (int p = 0; p < GRAM_PH_; p++) {
-                const float d = rintf(rh);
-                dg[p][i] = d;
-                const dfl r = two_sum(rh - d, rl);                  // rh - d is exact
-                rh = r.h * (float)(1 << GRAM_BITS_);
-                rl = r.l * (float)(1 << GRAM_BITS_);
-            }
-        }
-        if (target_row) continue;
+        if (R.scaled) hv = df_mul(hv, R.aj);
+        hv.h = on ? hv.h * R.inv_hs : 0.f;
+        hv.l = on ? hv.l * R.inv_hs : 0.f;
+        if (on && A.Ht) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
+        // balanced digits of h~ on the 2^-34 grid, most significant first:
+        // d = rint(r 2^B), r <- r 2^B - d, carried in double-float
+        float rh = hv.h * (float)(1 << (GRAM_BITS_ - 1));
+        float rl = hv.l * (float)(1 << (GRAM_BITS_ - 1));
 #pragma unroll
         for (int p = 0; p < GRAM_PH_; p++) {
-            __align__(16) __nv_bfloat162 v[8];
-#pragma unroll
-            for (int i = 0; i < 8; i++) v[i] = __floats2bfloat162_rn(dg[p][2 * i], dg[p][2 * i + 1]);
-            uint4 *dst = (uint4 *)(row + (int64_t)p * A.plane_stride + h * 16);
-            dst[0] = *(const uint4 *)&v[0];
-            dst[1] = *(const uint4 *)&v[4];
+            const float d = rintf(rh);
+            dg[p][i] = d;
+            const dfl r = two_sum(rh - d, rl);            // rh - d is exact
+            rh = r.h * (float)(1 << GRAM_BITS_);
+            rl = r.l * (float)(1 << GRAM_BITS_);
         }
+    }
+    __nv_bfloat16 *row = A.planes + m * A.Np + n0;
+#pragma unroll
+    for (int p = 0; p < GRAM_PH_; p++) {
+        __align__(16) __nv_bfloat162 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) v[i] = __floats2bfloat162_rn(dg[p][2 * i], dg[p][2 * i + 1]);
+        *(uint4 *)(row + (int64_t)p * A.plane_stride) = *(const uint4 *)&v[0];
     }
 }
 
+__device__ __forceinline__ void tile_coords(const OzParams &P, int64_t t, int64_t &m0,
+                                            int64_t &n0) {
+    if (P.gram) {
+        // lower tiles: row block J has 2(J+1) column blocks of 64
+        int64_t J = (int64_t)((sqrt(4.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while (J * (J + 1) > t) J--;
+        while ((J + 1) * (J + 2) <= t) J++;
+        m0 = J * BM;
+        n0 = (t - J * (J + 1)) * BN;
+    } else {
+        m0 = (t % P.ntile_m) * BM;
+        n0 = (t / P.ntile_m) * BN;
+    }
+}
+
+// Persistent kernel: CTA b processes tiles b, b + G, b + 2G, ... (G = grid
+// size).  The TMA ring and all barrier phases run on across tiles, so the
+// producer prefetches the next tile while the epilogue of the last one runs;
+// the epilogue copies its final values out of tensor memory into registers
+// and releases it before doing the output arithmetic, so the next tile's
+// MMAs overlap that arithmetic.
 template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
 ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -377,7 +366,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     constexpr uint32_t B_BYTES = BN * SK * 2;    // 4 KB per plane
     constexpr uint32_t STAGE_BYTES = PA * A_BYTES + PB * B_BYTES;
     // columns: ND accumulators, then the low and high 32-bit words of the
-    // int64 running sums
+    // int64 running sums (used when K spans several chunks)
     constexpr uint32_t LO_COL = ND * BN, HI_COL = ND * BN + BN;
     constexpr uint32_t USED = ND * BN + 2 * BN;
     constexpr uint32_t TMEM_COLS = USED <= 128 ? 128 : (USED <= 256 ? 256 : 512);
@@ -391,24 +380,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     __shared__ int abort_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // tile coordinates
-    int64_t mt, nt;
-    if (P.gram) {
-        // lower tiles: row block J has 2(J+1) column blocks of 64
-        int64_t t = blockIdx.x;
-        int64_t J = (int64_t)((sqrt(4.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while (J * (J + 1) > t) J--;
-        while ((J + 1) * (J + 2) <= t) J++;
-        mt = J;
-        nt = t - J * (J + 1);
-    } else {
-        mt = blockIdx.x % P.ntile_m;
-        nt = blockIdx.x / P.ntile_m;
-    }
-    const int64_t m0 = mt * BM, n0 = nt * BN;
     const int nslab = (int)(P.K / SK);
     const int nchunk = (nslab + CHUNK_SLABS - 1) / CHUNK_SLABS;
+    const int64_t t_first = blockIdx.x, t_step = gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -416,7 +390,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, 128);
+        mbar_init(&acc_empty, NEPI);
         mbar_init(&mma_done, 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -436,29 +410,34 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (warp == 0) {
         if (lane == 0) {
             // ---------------------------------------------------- producer
-            int issued = 0;
-            for (int s = 0; s < nslab; s++) {
-                const int st = s % STAGES;
-                if (s >= STAGES && !mbar_wait(&empty_bar[st], ((s / STAGES) - 1) & 1, abort))
-                    break;
-                uint8_t *base = smem + (size_t)st * STAGE_BYTES;
-                mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+            int64_t g = 0, issued = 0;
+            for (int64_t t = t_first; t < P.ntiles && !*abort; t += t_step) {
+                int64_t m0, n0;
+                tile_coords(P, t, m0, n0);
+                for (int s = 0; s < nslab; s++, g++) {
+                    const int st = (int)(g % STAGES);
+                    if (g >= STAGES &&
+                        !mbar_wait(&empty_bar[st], (uint32_t)(((g / STAGES) - 1) & 1), abort))
+                        break;
+                    uint8_t *base = smem + (size_t)st * STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[st], STAGE_BYTES);
 #pragma unroll
-                for (int p = 0; p < PA; p++)
-                    tma_2d(&tmA, &full_bar[st], base + p * A_BYTES, s * SK,
-                           (int)(p * P.a_rows + m0));
+                    for (int p = 0; p < PA; p++)
+                        tma_2d(&tmA, &full_bar[st], base + p * A_BYTES, s * SK,
+                               (int)(p * P.a_rows + m0));
 #pragma unroll
-                for (int q = 0; q < PB; q++)
-                    tma_2d(&tmB, &full_bar[st], base + PA * A_BYTES + q * B_BYTES, s * SK,
-                           (int)(q * P.b_rows + n0));
-                issued = s + 1;
+                    for (int q = 0; q < PB; q++)
+                        tma_2d(&tmB, &full_bar[st], base + PA * A_BYTES + q * B_BYTES, s * SK,
+                               (int)(q * P.b_rows + n0));
+                    issued = g + 1;
+                }
             }
             if (*abort) {
                 // let copies already issued land before the CTA exits
-                for (int s = (issued > STAGES ? issued - STAGES : 0); s < issued; s++) {
-                    const int st = s % STAGES;
+                for (int64_t g2 = (issued > STAGES ? issued - STAGES : 0); g2 < issued; g2++) {
                     const uint64_t t0 = gtime();
-                    while (!mbar_try(&full_bar[st], (s / STAGES) & 1) && gtime() - t0 < WAIT_NS) {
+                    while (!mbar_try(&full_bar[g2 % STAGES], (uint32_t)((g2 / STAGES) & 1)) &&
+                           gtime() - t0 < WAIT_NS) {
                     }
                 }
             }
@@ -466,35 +445,42 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issue
-            for (int s = 0; s < nslab && !*abort; s++) {
-                const int st = s % STAGES;
-                const int c = s / CHUNK_SLABS;
-                const bool first = (s % CHUNK_SLABS) == 0;
-                if (first && c > 0 && !mbar_wait(&acc_empty, (c - 1) & 1, abort)) break;
-                if (!mbar_wait(&full_bar[st], (s / STAGES) & 1, abort)) break;
-                tc_fence_after();
-                const uint32_t abase = su32(smem + (size_t)st * STAGE_BYTES);
-                const uint32_t bbase = abase + PA * A_BYTES;
+            int64_t g = 0, gc = 0;
+            for (int64_t t = t_first; t < P.ntiles && !*abort; t += t_step) {
+                for (int s = 0; s < nslab && !*abort; s++, g++) {
+                    const int st = (int)(g % STAGES);
+                    const bool first = (s % CHUNK_SLABS) == 0;
+                    // accumulators free again once the previous chunk is read
+                    if (first && gc > 0 && !mbar_wait(&acc_empty, (uint32_t)((gc - 1) & 1), abort))
+                        break;
+                    if (!mbar_wait(&full_bar[st], (uint32_t)((g / STAGES) & 1), abort)) break;
+                    tc_fence_after();
+                    const uint32_t abase = su32(smem + (size_t)st * STAGE_BYTES);
+                    const uint32_t bbase = abase + PA * A_BYTES;
 #pragma unroll
-                for (int t = 2; t <= TMAX; t++) {
-                    bool first_pair = true;
+                    for (int td = 2; td <= TMAX; td++) {
+                        bool first_pair = true;
 #pragma unroll
-                    for (int p = 1; p <= PA; p++) {
-                        const int q = t - p;
-                        if (q < 1 || q > PB) continue;
-                        const uint64_t da = desc_sw64(abase + (p - 1) * A_BYTES);
-                        const uint64_t db = desc_sw64(bbase + (q - 1) * B_BYTES);
+                        for (int p = 1; p <= PA; p++) {
+                            const int q = td - p;
+                            if (q < 1 || q > PB) continue;
+                            const uint64_t da = desc_sw64(abase + (p - 1) * A_BYTES);
+                            const uint64_t db = desc_sw64(bbase + (q - 1) * B_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < SK / 16; kk++) {
-                            const uint32_t acc = (first && first_pair && kk == 0) ? 0u : 1u;
-                            mma_bf16(tmem + (uint32_t)((t - 2) * BN), da + 2 * kk, db + 2 * kk,
-                                     IDESC, acc);
+                            for (int kk = 0; kk < SK / 16; kk++) {
+                                const uint32_t acc = (first && first_pair && kk == 0) ? 0u : 1u;
+                                mma_bf16(tmem + (uint32_t)((td - 2) * BN), da + 2 * kk,
+                                         db + 2 * kk, IDESC, acc);
+                            }
+                            first_pair = false;
                         }
-                        first_pair = false;
+                    }
+                    mma_commit(&empty_bar[st]);
+                    if ((s % CHUNK_SLABS) == CHUNK_SLABS - 1 || s == nslab - 1) {
+                        mma_commit(&acc_full);
+                        gc++;
                     }
                 }
-                mma_commit(&empty_bar[st]);
-                if ((s % CHUNK_SLABS) == CHUNK_SLABS - 1 || s == nslab - 1) mma_commit(&acc_full);
             }
             // every MMA issued so far has completed once this barrier flips;
             // tensor memory is freed only after that
@@ -504,105 +490,127 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             }
         }
     } else {
-        // -------------------------------------------------------- drains
+        // ------------------------------------------------ drains and epilogue
         const int quarter = warp & 3;
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-        bool ok = true;
-        // the fused hidden-layer epilogue reads a single chunk's diagonals
-        // directly; otherwise every chunk is folded into the int64 sums
+        const int c0 = ((warp - 2) >> 2) * 32;       // this warp's 32 columns of the tile
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
         const bool direct = (EPI == 1) && nchunk == 1;
-        for (int c = 0; c < nchunk; c++) {
-            // warp-uniform decision: TMEM loads below are warp-collective
-            const bool got = __all_sync(0xffffffffu, mbar_wait(&acc_full, c & 1, abort));
-            if (!got) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            if (direct) break;
-#pragma unroll 1
-            for (int h = 0; h < BN / 16; h++) {
-                // V = sum_t acc_t 2^(B (TMAX - t)): exact integers in units of
-                // 2^(-B (TMAX - 2)) of the leading diagonal
-                long long run[16];
-                uint32_t w0[16], w1[16];
-                if (c == 0) {
+        int64_t gc = 0;
+        bool ok = true;
+        for (int64_t t = t_first; t < P.ntiles && ok; t += t_step) {
+            int64_t m0, n0;
+            tile_coords(P, t, m0, n0);
+            const int64_t m = m0 + quarter * 32 + lane;
+            long long run[32];     // EPI == 0: final sums of this warp's 32 columns
+            for (int c = 0; c < nchunk; c++, gc++) {
+                // warp-uniform decision: TMEM loads below are warp-collective
+                ok = __all_sync(0xffffffffu, mbar_wait(&acc_full, (uint32_t)(gc & 1), abort));
+                if (!ok) break;
+                tc_fence_after();
+                const bool last = c == nchunk - 1;
 #pragma unroll
-                    for (int i = 0; i < 16; i++) run[i] = 0;
-                } else {
-                    tmem_ld16(lane_base + LO_COL + h * 16, w0);
-                    tmem_ld16(lane_base + HI_COL + h * 16, w1);
-                    tmem_wait_ld();
+                for (int h = 0; h < 2; h++) {
+                    uint32_t w0[16], w1[16];
+                    if (direct) {
+                        // V = sum_t acc_t 2^(B (TMAX - t)): Horner from the leading
+                        // diagonal in double-float, parked in the (otherwise unused)
+                        // running-sum columns as (hi, lo) floats
+                        dfl V[16];
 #pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        run[i] = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
-                }
+                        for (int i = 0; i < 16; i++) V[i] = {0.f, 0.f};
 #pragma unroll
-                for (int t = 2; t <= TMAX; t += 2) {
-                    tmem_ld16(lane_base + (uint32_t)((t - 2) * BN + h * 16), w0);
-                    if (t + 1 <= TMAX) tmem_ld16(lane_base + (uint32_t)((t - 1) * BN + h * 16), w1);
-                    tmem_wait_ld();
-                    // accumulators are exact integers below 2^25: 32-bit
-                    // conversions and a widening multiply-add
-                    const long long mult = 1ll << (DBITS * (TMAX - t));
+                        for (int td = 2; td <= TMAX; td++) {
+                            tmem_ld16(lane_base + (uint32_t)((td - 2) * BN + h * 16), w0);
+                            tmem_wait_ld();
+                            const float sc = (float)(1 << DBITS);
 #pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        run[i] += (long long)__float2int_rn(__uint_as_float(w0[i])) * mult;
-                    if (t + 1 <= TMAX) {
-                        const long long mult1 = 1ll << (DBITS * (TMAX - t - 1));
+                            for (int i = 0; i < 16; i++)
+                                V[i] = df_add({V[i].h * sc, V[i].l * sc}, {__uint_as_float(w0[i]), 0.f});
+                        }
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            w0[i] = __float_as_uint(V[i].h);
+                            w1[i] = __float_as_uint(V[i].l);
+                        }
+                        tmem_st16(lane_base + LO_COL + h * 16, w0);
+                        tmem_st16(lane_base + HI_COL + h * 16, w1);
+                        continue;
+                    }
+                    long long *r = run + h * 16;
+                    if (c == 0) {
+#pragma unroll
+                        for (int i = 0; i < 16; i++) r[i] = 0;
+                    } else {
+                        tmem_ld16(lane_base + LO_COL + h * 16, w0);
+                        tmem_ld16(lane_base + HI_COL + h * 16, w1);
+                        tmem_wait_ld();
 #pragma unroll
                         for (int i = 0; i < 16; i++)
-                            run[i] += (long long)__float2int_rn(__uint_as_float(w1[i])) * mult1;
+                            r[i] = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
+                    }
+#pragma unroll
+                    for (int td = 2; td <= TMAX; td++) {
+                        tmem_ld16(lane_base + (uint32_t)((td - 2) * BN + h * 16), w0);
+                        tmem_wait_ld();
+                        // accumulators are exact integers below 2^25
+                        const long long mult = 1ll << (DBITS * (TMAX - td));
+#pragma unroll
+                        for (int i = 0; i < 16; i++)
+                            r[i] += (long long)__float2int_rn(__uint_as_float(w0[i])) * mult;
+                    }
+                    if (!last || EPI == 1) {
+                        if (last) {
+                            // EPI == 1 over several chunks: park V as (hi, lo) floats
+#pragma unroll
+                            for (int i = 0; i < 16; i++) {
+                                const float vh = __ll2float_rn(r[i]);
+                                w0[i] = __float_as_uint(vh);
+                                w1[i] = __float_as_uint(__ll2float_rn(r[i] - __float2ll_rn(vh)));
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; i++) {
+                                w0[i] = (uint32_t)((unsigned long long)r[i]);
+                                w1[i] = (uint32_t)((unsigned long long)r[i] >> 32);
+                            }
+                        }
+                        tmem_st16(lane_base + LO_COL + h * 16, w0);
+                        tmem_st16(lane_base + HI_COL + h * 16, w1);
                     }
                 }
-#pragma unroll
-                for (int i = 0; i < 16; i++) w0[i] = (uint32_t)((unsigned long long)run[i]);
-                tmem_st16(lane_base + LO_COL + h * 16, w0);
-#pragma unroll
-                for (int i = 0; i < 16; i++) w0[i] = (uint32_t)((unsigned long long)run[i] >> 32);
-                tmem_st16(lane_base + HI_COL + h * 16, w0);
+                tc_fence_before();
+                mbar_arrive(&acc_empty);   // MMAs may overwrite the accumulators now
             }
-            tc_fence_before();
-            mbar_arrive(&acc_empty);
-        }
-        if (__all_sync(0xffffffffu, ok && !*abort)) {
-            const int64_t m = m0 + quarter * 32 + lane;
+            if (!ok || *abort) break;
+            // ---------------------------------------------------- output
             if (EPI == 0) {
-                // FP64 tile.  All stages have been consumed: reuse the ring as a
-                // 32 x 64 FP64 staging tile per warp for row-contiguous writes.
-                double *tile = (double *)smem + (size_t)quarter * 32 * (BN + 1);
                 const double unit = ldexp(1.0, -DBITS * (TMAX - 2));
-                const double rs = m < P.m_valid ? P.out_scale * unit * P.rscale[m] : 0.0;
+                if (m < P.m_valid) {
+                    const double rs = P.out_scale * unit * P.rscale[m];
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const int64_t n = n0 + c0 + i;
+                        if (n >= P.n_valid || (P.gram && n > m)) continue;
+                        const double v = (double)run[i] * rs * P.cscale[n];
+                        P.out[m * P.ldo + n] = v;
+                        if (P.gram && n < m) P.out[n * P.ldo + m] = v;   // lanes: consecutive m
+                    }
+                }
+            } else {
+                // the running-sum columns are this warp's until its next drain
+                const RowAct ra = row_setup<DBITS, TMAX>(P, m);
 #pragma unroll 1
-                for (int h = 0; h < BN / 16; h++) {
+                for (int h = 0; h < 2; h++) {
                     uint32_t w0[16], w1[16];
                     tmem_ld16(lane_base + LO_COL + h * 16, w0);
                     tmem_ld16(lane_base + HI_COL + h * 16, w1);
                     tmem_wait_ld();
+                    dfl V[16];
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const int64_t n = n0 + h * 16 + i;
-                        const double cs = n < P.n_valid ? P.cscale[n] : 0.0;
-                        const long long run = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
-                        const double v = (double)run * rs * cs;
-                        tile[lane * (BN + 1) + h * 16 + i] = v;
-                        if (P.gram && n < m && m < P.m_valid && n < P.n_valid)
-                            P.out[n * P.ldo + m] = v;    // mirror: lanes write consecutive m
-                    }
+                    for (int i = 0; i < 16; i++) V[i] = {__uint_as_float(w0[i]), __uint_as_float(w1[i])};
+                    hidden_emit8(P, ra, m, n0 + c0 + h * 16, V);
+                    hidden_emit8(P, ra, m, n0 + c0 + h * 16 + 8, V + 8);
                 }
-                __syncwarp();
-                for (int r = 0; r < 32; r++) {
-                    const int64_t mr = m0 + quarter * 32 + r;
-                    if (mr >= P.m_valid) break;
-#pragma unroll
-                    for (int h = 0; h < BN / 32; h++) {
-                        const int64_t n = n0 + h * 32 + lane;
-                        if (n < P.n_valid && (!P.gram || n <= mr))
-                            P.out[mr * P.ldo + n] = tile[r * (BN + 1) + h * 32 + lane];
-                    }
-                }
-            } else {
-                hidden_epilogue<DBITS, TMAX>(P, m, n0, lane_base, LO_COL, HI_COL, direct);
             }
         }
     }
@@ -801,9 +809,17 @@ void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B
         ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        ELM_CUDA(cudaGetDevice(&dev));
+        ELM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     CUtensorMap ma = make_map(A, PA * P.a_rows, P.K, BM);
     CUtensorMap mb = make_map(B, PB * P.b_rows, P.K, BN);
-    k<<<(unsigned)ntiles, NTHREADS, smem, s>>>(ma, mb, P);
+    P.ntiles = ntiles;
+    const int64_t grid = ntiles < sms ? ntiles : sms;
+    k<<<(unsigned)grid, NTHREADS, smem, s>>>(ma, mb, P);
     ELM_CHECK_LAUNCH();
 }
 
