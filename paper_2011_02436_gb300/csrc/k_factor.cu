@@ -385,7 +385,9 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
 }
 
 // A_next[x', y'] = A[rem x', rem y'] - sum_t P[t, rem x'] P[t, rem y'] on
-// lower tiles, mirrored to the upper triangle.
+// lower 32 x 32 tiles, mirrored to the upper triangle.  Small tiles keep
+// the grid wide when the active matrix has shrunk to a few hundred rows.
+constexpr int TT = 32;
 __global__ void __launch_bounds__(256)
 trailing_kernel(const double *__restrict__ A, double *__restrict__ An, int64_t lda,
                 const double *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
@@ -399,50 +401,46 @@ trailing_kernel(const double *__restrict__ A, double *__restrict__ An, int64_t l
     while (J * (J + 1) / 2 > t) J--;
     while ((J + 1) * (J + 2) / 2 <= t) J++;
     const int64_t I = t - J * (J + 1) / 2;
-    const int64_t r0 = J * 64, c0 = I * 64;
+    const int64_t r0 = J * TT, c0 = I * TT;
     if (r0 >= Lr) return;
-    __shared__ double Pr[MAXNB][65];
-    __shared__ double Pc[MAXNB][65];
-    __shared__ int32_t rr_[64], rc_[64];
-    if (threadIdx.x < 64) {
+    __shared__ double Pr[MAXNB][TT + 1];
+    __shared__ double Pc[MAXNB][TT + 1];
+    __shared__ int32_t rr_[TT], rc_[TT];
+    if (threadIdx.x < TT) {
         int64_t x = r0 + threadIdx.x, y = c0 + threadIdx.x;
         rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
         rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < MAXNB * 64; e += 256) {
-        int tt = e / 64, k = e % 64;
+    for (int e = threadIdx.x; e < MAXNB * TT; e += 256) {
+        int tt = e / TT, k = e % TT;
         Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : 0.0;
         Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : 0.0;
     }
     __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4];
+    double acc[2][2];
 #pragma unroll
-    for (int p = 0; p < 4; p++)
+    for (int p = 0; p < 2; p++)
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < 2; q++) {
             int a = rr_[ty + 16 * p], b = rc_[tx + 16 * q];
             acc[p][q] = (a >= 0 && b >= 0) ? A[(int64_t)a * lda + b] : 0.0;
         }
     for (int tt = 0; tt < steps; tt++) {
-        double u[4], v[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            u[q] = Pr[tt][ty + 16 * q];
-            v[q] = Pc[tt][tx + 16 * q];
-        }
-#pragma unroll
-        for (int p = 0; p < 4; p++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) acc[p][q] = fma(-u[p], v[q], acc[p][q]);
+        const double u0 = Pr[tt][ty], u1 = Pr[tt][ty + 16];
+        const double v0 = Pc[tt][tx], v1 = Pc[tt][tx + 16];
+        acc[0][0] = fma(-u0, v0, acc[0][0]);
+        acc[0][1] = fma(-u0, v1, acc[0][1]);
+        acc[1][0] = fma(-u1, v0, acc[1][0]);
+        acc[1][1] = fma(-u1, v1, acc[1][1]);
     }
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
+    for (int p = 0; p < 2; p++) {
         int64_t x = r0 + ty + 16 * p;
         if (x >= Lr) continue;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < 2; q++) {
             int64_t y = c0 + tx + 16 * q;
             if (y >= Lr) continue;
             An[x * lda + y] = acc[p][q];
@@ -695,7 +693,7 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
         ELM_CHECK_LAUNCH();
         const int64_t Lup = L - (p + 1) * nb;
         if (Lup > 0) {
-            int64_t T = (Lup + 63) / 64;
+            int64_t T = (Lup + TT - 1) / TT;
             trailing_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(Ac, An, L, w.P, L,
                                                                          w.rem, w.st);
             ELM_CHECK_LAUNCH();

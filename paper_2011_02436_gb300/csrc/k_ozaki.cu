@@ -693,28 +693,104 @@ __global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t 
     }
 }
 
-// W (n x L, row stride ldw) -> PD planes of Lp x nK bf16 (row j, col k),
-// columns scaled by ws[j] = pow2_ceil(max_k |W[k, j]|).  One thread per j.
+// FP32 X: the same digits from FP32 arithmetic only.  x~ = x / xs[i] is
+// exact (power of two); d = rint(64 x~), r = 64 x~ - d is exact, then
+// d_p = rint(128 r), r <- 128 r - d_p: every step is exact in FP32 because
+// r keeps at most 24 significant bits.  8 consecutive k per thread, one
+// 16-byte store per plane.
 template <int PD, int DBITS>
-__global__ void digits_cols_kernel(const double *__restrict__ W, int64_t n, int64_t L,
-                                   int64_t ldw, int64_t Lp, int64_t nK,
-                                   __nv_bfloat16 *__restrict__ planes, double *__restrict__ ws) {
-    constexpr int SH = (DBITS - 1) + DBITS * (PD - 1);
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= Lp) return;
+__global__ void digits_rows_f32_kernel(const float *__restrict__ X, int64_t N, int64_t n,
+                                       int64_t ldx, int64_t Np, int64_t nK,
+                                       __nv_bfloat16 *__restrict__ planes,
+                                       double *__restrict__ xs, float *__restrict__ xsf) {
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= Np) return;
+    float mx = 0.f;
+    if (i < N)
+        for (int64_t k = lane; k < n; k += 32) mx = fmaxf(mx, fabsf(X[i * ldx + k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double sc = pow2_ceil((double)mx);
+    if (lane == 0) {
+        xs[i] = sc;
+        xsf[i] = (float)sc;
+    }
+    const float inv = (float)(1.0 / sc);
+    for (int64_t k0 = (int64_t)lane * 8; k0 < nK; k0 += 256) {
+        float d[PD][8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int64_t k = k0 + e;
+            float r = (i < N && k < n) ? X[i * ldx + k] * inv * (float)(1 << (DBITS - 1)) : 0.f;
+#pragma unroll
+            for (int p = 0; p < PD; p++) {
+                const float dp = rintf(r);
+                d[p][e] = dp;
+                r = (r - dp) * (float)(1 << DBITS);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < PD; p++) {
+            __align__(16) __nv_bfloat162 v[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) v[e] = __floats2bfloat162_rn(d[p][2 * e], d[p][2 * e + 1]);
+            *(uint4 *)(planes + (int64_t)p * Np * nK + i * nK + k0) = *(const uint4 *)&v[0];
+        }
+    }
+}
+
+// Column scales of W: ws[j] = pow2_ceil(max_k |W[k, j]|), 1 for padding.
+__global__ void col_scale_kernel(const double *__restrict__ W, int64_t n, int64_t L, int64_t ldw,
+                                 int64_t Lp, double *__restrict__ ws) {
+    // 32 columns per block, 8 row groups
+    __shared__ double red[8][33];
+    const int cj = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + cj;
     double mx = 0.0;
     if (j < L)
-        for (int64_t k = 0; k < n; k++) mx = fmax(mx, fabs(W[k * ldw + j]));
-    const double sc = pow2_ceil(mx);
-    ws[j] = sc;
-    const double mul = ldexp(1.0 / sc, SH);
-    for (int64_t k = 0; k < nK; k++) {
-        float d[PD];
-        const long long q = (j < L && k < n) ? __double2ll_rn(W[k * ldw + j] * mul) : 0;
-        int_digits<PD, DBITS>(q, d);
+        for (int64_t k = rg; k < n; k += 8) mx = fmax(mx, fabs(W[k * ldw + j]));
+    red[rg][cj] = mx;
+    __syncthreads();
+    if (rg == 0 && j < Lp) {
+        for (int r = 1; r < 8; r++) mx = fmax(mx, red[r][cj]);
+        ws[j] = j < L ? pow2_ceil(mx) : 1.0;
+    }
+}
+
+// W digits, one thread per (j, 8 consecutive k); FP64 value split into a
+// double-float pair once, digits from FP32 arithmetic.
+template <int PD, int DBITS>
+__global__ void digits_cols_par_kernel(const double *__restrict__ W, int64_t n, int64_t L,
+                                       int64_t ldw, int64_t Lp, int64_t nK,
+                                       __nv_bfloat16 *__restrict__ planes,
+                                       const double *__restrict__ ws) {
+    const int64_t kb = nK / 8;
+    const int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e0 >= Lp * kb) return;
+    const int64_t j = e0 / kb, k0 = (e0 % kb) * 8;
+    const double inv = 1.0 / ws[j];
+    float d[PD][8];
 #pragma unroll
-        for (int p = 0; p < PD; p++)
-            planes[(int64_t)p * Lp * nK + j * nK + k] = __float2bfloat16_rn(d[p]);
+    for (int e = 0; e < 8; e++) {
+        const int64_t k = k0 + e;
+        const double v = (j < L && k < n) ? W[k * ldw + j] * inv * (double)(1 << (DBITS - 1)) : 0.0;
+        float rh = (float)v;
+        float rl = (float)(v - (double)rh);
+#pragma unroll
+        for (int p = 0; p < PD; p++) {
+            const float dp = rintf(rh);
+            d[p][e] = dp;
+            const dfl r = two_sum(rh - dp, rl);   // rh - dp is exact
+            rh = r.h * (float)(1 << DBITS);
+            rl = r.l * (float)(1 << DBITS);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PD; p++) {
+        __align__(16) __nv_bfloat162 v[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) v[e] = __floats2bfloat162_rn(d[p][2 * e], d[p][2 * e + 1]);
+        *(uint4 *)(planes + (int64_t)p * Lp * nK + j * nK + k0) = *(const uint4 *)&v[0];
     }
 }
 
@@ -862,11 +938,13 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
         digits_rows_kernel<HID_PX, HID_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
             (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf);
     else
-        digits_rows_kernel<HID_PX, HID_BITS, float><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
+        digits_rows_f32_kernel<HID_PX, HID_BITS><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
             (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf);
     ELM_CHECK_LAUNCH();
-    digits_cols_kernel<HID_PW, HID_BITS><<<(unsigned)((Lp + 127) / 128), 128, 0, s>>>(
-        W, n, L, ldw, Lp, nK, w.wp, w.ws);
+    col_scale_kernel<<<(unsigned)((Lp + 31) / 32), 256, 0, s>>>(W, n, L, ldw, Lp, w.ws);
+    ELM_CHECK_LAUNCH();
+    digits_cols_par_kernel<HID_PW, HID_BITS>
+        <<<(unsigned)((Lp * (nK / 8) + 255) / 256), 256, 0, s>>>(W, n, L, ldw, Lp, nK, w.wp, w.ws);
     ELM_CHECK_LAUNCH();
     hs_kernel<<<(unsigned)((Lp + 255) / 256), 256, 0, s>>>(a, L, m, Lp, hs);
     ELM_CHECK_LAUNCH();
