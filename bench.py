@@ -125,6 +125,27 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """Largest `value` over all ranks (the slowest rank's time); `value`
+    itself when no process group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(count, rank, world):
+    """Indices of `count` independent problems handled by `rank` of `world`
+    (contiguous blocks, sizes differing by at most one; no collective)."""
+    base, extra = divmod(count, world)
+    start = rank * base + min(rank, extra)
+    return list(range(start, start + base + (1 if rank < extra else 0)))
+
+
 def cpu_baseline(full, sample_rows=2000, threads=None):
     """Time the oracle, as it stands, on the first `sample_rows` rows of the
     workload and scale its N-proportional phases to the full N."""
@@ -195,7 +216,7 @@ def run_native(args):
     dev = torch.device("cuda", local)
     prec = elm.PREC_MIXED if args.precision == "mixed" else elm.PREC_FP64
 
-    p = synth.workload_sparse_pixels()
+    p = synth.workload_sparse_pixels(N=args.rows)
     N, n, L, m = p["N"], p["n"], p["L"], p["m"]
     X = torch.from_numpy(p["X"]).to(dev)
     W = torch.from_numpy(p["W"]).to(dev)
@@ -216,7 +237,7 @@ def run_native(args):
     res = elm.elm_train(ctx, prob, precision=prec)[0]
     beta_run = beta.cpu().numpy()
     check = dict(rank=res["rank"], refine_iters=res["refine_iters"])
-    if prec != elm.PREC_FP64:
+    if prec != elm.PREC_FP64 and not args.no_fp64_check:
         prob64 = dict(prob, beta=torch.empty_like(beta))
         elm.elm_train(ctx, prob64, precision=elm.PREC_FP64)
         b64 = prob64["beta"].cpu().numpy()
@@ -238,11 +259,7 @@ def run_native(args):
     launches = elm.elm_launch_counter() - l0
     phases = elm.elm_phase_times(ctx)
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = ms
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(tt.item())
+    ms_max = max_over_ranks(ms, dev)
     value = ws * 1000.0 / ms_max
 
     # e2e through the C ABI with pinned host buffers
@@ -263,11 +280,7 @@ def run_native(args):
         elm.elm_train(ctx, hprob, precision=prec)
     f1.record(stream)
     barrier()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, dev)
     h2d = sum(t.numel() * t.element_size() for t in (hX, hW, hb, hT))
     d2h = hbeta.numel() * hbeta.element_size()
 
@@ -276,24 +289,33 @@ def run_native(args):
         pk = peaks()
         ph_ms = {k: v / args.steps for k, v in phases.items()}
         if prec == elm.PREC_FP64:
-            dom = "gram"
-            bound, peak, unit = "alu", pk["fp64"] * 1e3, "GFLOP/s"
-            achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e9
-            peak_note = "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 entry)"
-        else:
-            dom = "gram"
-            bound, peak, unit = "tensor", pk["bf16"], "TFLOP/s"
+            # Gram on the FP64 pipe (nominal rate; MEASURED_PEAKS.json has no FP64 entry)
             achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e12
-            peak_note = "%s bf16 dense burst" % pk["source"]
-        roof = dict(bound=bound, achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
-                    traffic=None, kernel=dom, peak_source=peak_note,
-                    phase_ms=ph_ms)
+            roof = dict(bound="alu", achieved=achieved, peak=pk["fp64"], unit="TFLOP/s",
+                        frac=achieved / pk["fp64"], traffic=None, kernel="gram_f64_kernel",
+                        peak_source="nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 entry)")
+        else:
+            # Gram on the tensor cores: algorithmic FLOPs (symmetric Gram counted
+            # once, as in the contract) over the phase time, against the measured
+            # bf16 burst peak; the digit emulation issues 15 digit-pair products
+            # of the lower-triangle tiles, reported beside it
+            Lp, Np = -(-(L + m) // 128) * 128, -(-N // 64) * 64
+            nJ = Lp // 128
+            issued = 15 * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
+            achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e12
+            roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16"], unit="TFLOP/s",
+                        frac=achieved / pk["bf16"], traffic=None,
+                        kernel="ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
+                        peak_source="%s bf16 dense burst" % pk["source"],
+                        issued_tflops=issued / (ph_ms["gram"] * 1e-3) / 1e12,
+                        issued_frac=issued / (ph_ms["gram"] * 1e-3) / 1e12 / pk["bf16"])
+        roof["phase_ms"] = ph_ms
         line = dict(metric=METRIC, value=value, unit="trainings/s", n_gpus=ws, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms_max, higher_is_better=True,
                     scaling="weak", vs_baseline=None,
                     dtype="f64" if prec == elm.PREC_FP64 else "bf16-slices+f64",
                     data="synthetic",
-                    config=dict(WORKLOAD, precision=args.precision,
+                    config=dict(WORKLOAD, N=N, precision=args.precision,
                                 parallelism="replicas" if ws > 1 else "single",
                                 l2="inputs larger than L2 (X 188 MB, H 0.96 GB): no flush"),
                     e2e=dict(value=ws * 1000.0 / e2e_ms, unit="trainings/s",
@@ -315,10 +337,14 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the cross-check of the mixed beta against the FP64 GPU path")
     ap.add_argument("--ref-rows", type=int, default=6000)
+    ap.add_argument("--rows", type=int, default=WORKLOAD["N"],
+                    help="rows of the workload (smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -481,8 +481,8 @@ __global__ void finalize_kernel(const double *__restrict__ Rrow, int64_t ldrr,
 // Blocked triangular solve on one thread-block cluster per group of CB
 // right-hand-side columns.  Rows are cut into diagonal blocks of TB_ rows,
 // dealt round-robin to the CTAs of the cluster; each CTA keeps its blocks of
-// B in shared memory.  Per diagonal block: its owner solves it against the
-// shared-memory copy of the diagonal block of R, one hardware cluster
+// B in shared memory.  Per diagonal block: one warp of its owner solves it
+// (lane = row, shuffles, no block barrier per row), one hardware cluster
 // barrier, then every CTA pulls the solved block through distributed shared
 // memory and updates its own remaining rows, one thread per row with the CB
 // right-hand sides in registers (R read once per element, coalesced).
@@ -502,8 +502,6 @@ trsm_cluster_kernel(const double *__restrict__ R, int64_t ldr, int64_t r,
     extern __shared__ double sm[];
     double *bs = sm;                                   // nown x TB_ x CB
     double *xb = bs + (size_t)nown * TB_ * CB;         // TB_ x CB pulled block
-    double *Rd = xb + TB_ * CB;                        // TB_ x (TB_ + 1) diagonal block
-    double *rinv = Rd + TB_ * (TB_ + 1);               // TB_ reciprocals of the diagonal
     for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_ * CB; e += FT) {
         const int kl = (int)(e / (TB_ * CB)), a = (int)((e / CB) % TB_), c = (int)(e % CB);
         const int64_t k = (int64_t)kl * CS + cr, i = k * TB_ + a;
@@ -517,24 +515,39 @@ trsm_cluster_kernel(const double *__restrict__ R, int64_t ldr, int64_t r,
         const int nb = (int)(r - i0 < TB_ ? r - i0 : TB_);
         if (owner == cr) {
             double *xk = bs + (size_t)(k / CS) * TB_ * CB;
-            for (int e = threadIdx.x; e < TB_ * TB_; e += FT) {
-                const int a = e / TB_, b2 = e % TB_;
-                Rd[a * (TB_ + 1) + b2] = (a < nb && b2 < nb) ? R[(i0 + a) * ldr + i0 + b2] : 0.0;
+            // one warp solves the 32 x 32 diagonal block: lane = row of the
+            // block, its CB right-hand sides in registers, the solved value
+            // broadcast by shuffle; no block-wide barrier per row
+            if (threadIdx.x < 32) {
+                const int a2 = threadIdx.x;
+                double xr[CB];
+                double rowR[TB_];   // FWD: column a2 of R (R[a][a2]); else row a2 (R[a2][a])
+#pragma unroll
+                for (int c = 0; c < CB; c++) xr[c] = a2 < nb ? xk[a2 * CB + c] : 0.0;
+#pragma unroll
+                for (int a = 0; a < TB_; a++)
+                    rowR[a] = (a2 < nb && a < nb)
+                                  ? (FWD ? R[(i0 + a) * ldr + i0 + a2] : R[(i0 + a2) * ldr + i0 + a])
+                                  : 0.0;
+                const double rinv_me = a2 < nb ? 1.0 / R[(i0 + a2) * ldr + i0 + a2] : 0.0;
+#pragma unroll
+                for (int s2 = 0; s2 < TB_; s2++) {
+                    const int a = FWD ? s2 : TB_ - 1 - s2;
+                    if (a >= nb) continue;                       // uniform over the warp
+                    if (a2 == a)
+#pragma unroll
+                        for (int c = 0; c < CB; c++) xr[c] *= rinv_me;
+#pragma unroll
+                    for (int c = 0; c < CB; c++) {
+                        const double xa = __shfl_sync(0xffffffffu, xr[c], a);
+                        if (FWD ? (a2 > a) : (a2 < a)) xr[c] = fma(-rowR[a], xa, xr[c]);
+                    }
+                }
+                if (a2 < nb)
+#pragma unroll
+                    for (int c = 0; c < CB; c++) xk[a2 * CB + c] = xr[c];
             }
             __syncthreads();
-            if (threadIdx.x < nb) rinv[threadIdx.x] = 1.0 / Rd[threadIdx.x * (TB_ + 1) + threadIdx.x];
-            __syncthreads();
-            for (int s2 = 0; s2 < nb; s2++) {
-                const int a = FWD ? s2 : nb - 1 - s2;
-                // thread (a2, c): row a2 of the block, column c
-                const int a2 = threadIdx.x / CB, c = threadIdx.x % CB;
-                const double xa = xk[a * CB + c] * rinv[a];
-                __syncthreads();
-                if (a2 == a) xk[a * CB + c] = xa;
-                else if (a2 < nb && (FWD ? a2 > a : a2 < a))
-                    xk[a2 * CB + c] -= (FWD ? Rd[a * (TB_ + 1) + a2] : Rd[a2 * (TB_ + 1) + a]) * xa;
-                __syncthreads();
-            }
         }
         cluster.sync();
         {
@@ -714,8 +727,7 @@ static void trsm_cluster_cb(cudaStream_t s, const double *R, int64_t ldr, int64_
     int cs = g_tcluster ? g_tcluster : 16;
     for (;;) {
         const int nown = (int)((nblk + cs - 1) / cs);
-        const size_t smem =
-            ((size_t)nown * TB_ * CB + TB_ * CB + TB_ * (TB_ + 1) + TB_) * sizeof(double);
+        const size_t smem = ((size_t)nown * TB_ * CB + TB_ * CB) * sizeof(double);
         if (smem > 200 * 1024) {
             if (cs == 16) {
                 cs = 8;
