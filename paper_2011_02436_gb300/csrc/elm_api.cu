@@ -134,63 +134,103 @@ In stage(Arena &ar, cudaStream_t s, const void *p, int64_t rows, int64_t cols, i
 }
 
 // ----------------------------------------------------------------- solves
-struct AuxBufs {
-    double *yb, *K, *G2, *v, *w, *R2, *Rt2;
-    FactorWs f2;
+// beta = H^+ Z through the full-rank factorisation H P = H1 [I K]
+// (Eq. 5, Eq. 7): out[perm[i], :] = ([y; K^T y])[i, :] with
+// y = (I + K K^T)^{-1} R11^{-1} R11^{-T} Z[perm[0..r-1], :] and
+// K = R11^{-1} R12.  The r x r system I + K K^T is solved through the
+// (L-r) x (L-r) system I + K^T K (Woodbury identity).  Everything that
+// depends only on the factor (inverse diagonal blocks, K, the factor of
+// I + K^T K) is prepared once and reused by every refinement step.
+struct Solver {
+    const double *R = nullptr, *Rt = nullptr;
+    int64_t ld = 0;
+    const int32_t *perm = nullptr;
+    int64_t r = 0, L = 0, m = 0;
+    double *DinvF = nullptr, *DinvB = nullptr;
+    // r < L
+    double *K = nullptr, *G2 = nullptr, *R2 = nullptr, *Rt2 = nullptr;
+    double *DinvF2 = nullptr, *DinvB2 = nullptr;
+    int64_t ld2 = 0;
+    FactorWs f2{};
+    // per-solve scratch
+    double *yb = nullptr, *v = nullptr, *w = nullptr;
+    int *tflag = nullptr;
 };
 
-AuxBufs carve_aux(Arena &ar, int64_t L, int64_t r, int64_t m) {
-    AuxBufs b{};
-    int64_t q = L - r;
-    b.yb = ar.take<double>(L * m);
-    if (q > 0) {
-        b.K = ar.take<double>(r * q);
-        b.G2 = ar.take<double>(q * q);
-        b.v = ar.take<double>(q * m);
-        b.w = ar.take<double>(q * m);
-        b.R2 = ar.take<double>(q * q);
-        b.Rt2 = ar.take<double>(q * q);
-        b.f2 = factor_ws_carve(ar, q);
+Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const double *Rt,
+                      int64_t ld, const int32_t *perm, int64_t r, int64_t L, int64_t m) {
+    Solver sv;
+    sv.R = R;
+    sv.Rt = Rt;
+    sv.ld = ld;
+    sv.perm = perm;
+    sv.r = r;
+    sv.L = L;
+    sv.m = m;
+    const int64_t q = L - r;
+    sv.ld2 = q > 0 ? tri_ld(q) : 0;
+    with_arena(&ctx->aux, &ctx->aux_size, s, [&](Arena &a) {
+        sv.yb = a.take<double>(L * m);
+        sv.DinvF = a.take<double>(trsm_dinv_doubles(r));
+        sv.DinvB = a.take<double>(trsm_dinv_doubles(r));
+        sv.tflag = a.take<int>(1);
+        if (q > 0 && r > 0) {
+            sv.K = a.take<double>(r * q);
+            sv.G2 = a.take<double>(q * q);
+            sv.v = a.take<double>(q * m);
+            sv.w = a.take<double>(q * m);
+            sv.R2 = a.take<double>(q * sv.ld2);
+            sv.Rt2 = a.take<double>(q * sv.ld2);
+            sv.DinvF2 = a.take<double>(trsm_dinv_doubles(q));
+            sv.DinvB2 = a.take<double>(trsm_dinv_doubles(q));
+            sv.f2 = factor_ws_carve(a, q);
+        }
+    });
+    ELM_CUDA(cudaMemsetAsync(sv.tflag, 0, sizeof(int), s));
+    trsm_prepare(s, R, ld, r, sv.DinvF, sv.DinvB);
+    if (q > 0 && r > 0) {
+        ELM_CUDA(cudaMemcpy2DAsync(sv.K, q * sizeof(double), R + r, ld * sizeof(double),
+                                   q * sizeof(double), r, cudaMemcpyDeviceToDevice, s));
+        trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag);
+        set_identity(s, sv.G2, q);
+        gemm_f64(s, q, q, r, 1.0, sv.K, 1, q, sv.K, q, 1, 1.0, sv.G2, q);
+        // I + K^T K is SPD with eigenvalues >= 1: full rank q
+        factor_pivoted(s, sv.G2, q, q, 0.0, sv.f2, sv.R2, sv.Rt2, sv.ld2, ctx->sm_count);
+        trsm_prepare(s, sv.R2, sv.ld2, q, sv.DinvF2, sv.DinvB2);
     }
-    return b;
+    return sv;
 }
 
-// out[perm[i], :] = ([y; K^T y])[i, :] with y = (I + K K^T)^{-1} R11^{-1}
-// R11^{-T} Z[perm[0..r-1], :] and K = R11^{-1} R12: beta = H^+ T through
-// the full-rank factorisation H P = H1 [I K] (Eq. 5, Eq. 7).  The r x r
-// system I + K K^T is solved through the (L-r) x (L-r) system I + K^T K
-// (Woodbury identity).
-void solve_beta(elm_ctx *ctx, cudaStream_t s, const double *R, const double *Rt,
-                const int32_t *perm, int64_t r, int64_t L, const double *Z, int64_t ldz,
-                int64_t m, double *out, int64_t ldo) {
-    AuxBufs ab{};
-    with_arena(&ctx->aux, &ctx->aux_size, s, [&](Arena &a) { ab = carve_aux(a, L, r, m); });
-    double *yb = ab.yb;
-    gather_rows(s, Z, ldz, perm, nullptr, r, m, yb, m);
-    trsm_fwd(s, R, L, nullptr, r, yb, m, m);
-    trsm_bwd(s, R, L, nullptr, r, yb, m, m);
-    if (r < L) {
-        const int64_t q = L - r;
+void solver_apply(cudaStream_t s, const Solver &sv, const double *Z, int64_t ldz, double *out,
+                  int64_t ldo) {
+    const int64_t r = sv.r, L = sv.L, m = sv.m, q = L - r;
+    double *yb = sv.yb;
+    gather_rows(s, Z, ldz, sv.perm, nullptr, r, m, yb, m);
+    trsm_fwd(s, sv.R, sv.ld, sv.DinvF, r, yb, m, m, sv.tflag);
+    trsm_bwd(s, sv.Rt, sv.ld, sv.DinvB, r, yb, m, m, sv.tflag);
+    if (q > 0) {
         if (r > 0) {
-            ELM_CUDA(cudaMemcpy2DAsync(ab.K, q * sizeof(double), R + r, L * sizeof(double),
-                                       q * sizeof(double), r, cudaMemcpyDeviceToDevice, s));
-            trsm_bwd(s, R, L, nullptr, r, ab.K, q, q);
-            set_identity(s, ab.G2, q);
-            gemm_f64(s, q, q, r, 1.0, ab.K, 1, q, ab.K, q, 1, 1.0, ab.G2, q);
-            factor_pivoted(s, ab.G2, q, q, 0.0, ab.f2, ab.R2, ab.Rt2, ctx->sm_count);
-            gemm_f64(s, q, m, r, 1.0, ab.K, 1, q, yb, m, 1, 0.0, ab.v, m);
-            ELM_CUDA(cudaMemsetAsync(ab.w, 0, sizeof(double) * q * m, s));
-            gather_rows(s, ab.v, m, ab.f2.perm, &ab.f2.st->rank, q, m, ab.w, m);
-            trsm_fwd(s, ab.R2, q, nullptr, q, ab.w, m, m);
-            trsm_bwd(s, ab.R2, q, nullptr, q, ab.w, m, m);
-            scatter_rows(s, ab.w, m, ab.f2.perm, q, ab.v, m, 1.0, 0);
-            gemm_f64(s, r, m, q, -1.0, ab.K, q, 1, ab.v, m, 1, 1.0, yb, m);
-            gemm_f64(s, q, m, r, 1.0, ab.K, 1, q, yb, m, 1, 0.0, yb + r * m, m);
+            gemm_f64(s, q, m, r, 1.0, sv.K, 1, q, yb, m, 1, 0.0, sv.v, m);
+            ELM_CUDA(cudaMemsetAsync(sv.w, 0, sizeof(double) * q * m, s));
+            gather_rows(s, sv.v, m, sv.f2.perm, &sv.f2.st->rank, q, m, sv.w, m);
+            trsm_fwd(s, sv.R2, sv.ld2, sv.DinvF2, q, sv.w, m, m, sv.tflag);
+            trsm_bwd(s, sv.Rt2, sv.ld2, sv.DinvB2, q, sv.w, m, m, sv.tflag);
+            scatter_rows(s, sv.w, m, sv.f2.perm, q, sv.v, m, 1.0, 0);
+            gemm_f64(s, r, m, q, -1.0, sv.K, q, 1, sv.v, m, 1, 1.0, yb, m);
+            gemm_f64(s, q, m, r, 1.0, sv.K, 1, q, yb, m, 1, 0.0, yb + r * m, m);
         } else {
             ELM_CUDA(cudaMemsetAsync(yb, 0, sizeof(double) * L * m, s));
         }
     }
-    scatter_rows(s, yb, m, perm, L, out, ldo, 1.0, 0);
+    scatter_rows(s, yb, m, sv.perm, L, out, ldo, 1.0, 0);
+}
+
+// Status of the solves so far (reads the device flag; synchronises s).
+bool solver_timed_out(cudaStream_t s, const Solver &sv) {
+    int f = 0;
+    ELM_CUDA(cudaMemcpyAsync(&f, sv.tflag, sizeof f, cudaMemcpyDeviceToHost, s));
+    ELM_CUDA(cudaStreamSynchronize(s));
+    return f != 0;
 }
 
 int64_t read_rank(cudaStream_t s, const FactorWs &f, int32_t *flags) {
@@ -241,8 +281,8 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
         S = ar.take<double>(L * L);
         Z = ar.take<double>(L * m);
         gpart = ar.take<double>(gram_f64_ws(L, m, ns));
-        R = ar.take<double>(L * L);
-        Rt = ar.take<double>(L * L);
+        R = ar.take<double>(L * tri_ld(L));
+        Rt = ar.take<double>(L * tri_ld(L));
         beta = ar.take<double>(L * m);
         dB = ar.take<double>(L * m);
         Rres = ar.take<double>(N * m);
@@ -264,7 +304,7 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     gram_f64(s, Ht, N, L, N, Td, T.ld, m, S, L, Z, m, gpart, ns);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4: permutation, rank, split
-    factor_pivoted(s, S, L, L, P.tau, f, R, Rt, ctx->sm_count);
+    factor_pivoted(s, S, L, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
     const int64_t r = read_rank(s, f, &fl);
@@ -282,14 +322,15 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
         return;
     }
     // Eq. 5, Eq. 7: beta = H^+ T
-    solve_beta(ctx, s, R, Rt, f.perm, r, L, Z, m, m, beta, m);
+    const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m);
+    solver_apply(s, sv, Z, m, beta, m);
     mark(ctx, 4);
     // refinement with the residual T - H beta
     double nrm[2] = {0.0, 0.0};
     for (int it = 0; it < P.max_refine; it++) {
         resid_f64(s, Ht, N, L, N, beta, m, Td, T.ld, Rres);
         htr_f64(s, Ht, N, L, N, Rres, m, G, hpart, hs);
-        solve_beta(ctx, s, R, Rt, f.perm, r, L, G, m, m, dB, m);
+        solver_apply(s, sv, G, m, dB, m);
         axpy_norms(s, beta, dB, L * m, norms);
         ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
         ELM_CUDA(cudaStreamSynchronize(s));
@@ -299,6 +340,7 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     }
     mark(ctx, 5);
     if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
+    if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
     const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyDeviceToHost;
     ELM_CUDA(cudaMemcpy2DAsync(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
@@ -335,8 +377,8 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         hs = ar.take<double>(Lp);
         G = ar.take<double>(Lt * Lt);
         hw = oz_hid_carve(ar, N, n, L, m);
-        R = ar.take<double>(L * L);
-        Rt = ar.take<double>(L * L);
+        R = ar.take<double>(L * tri_ld(L));
+        Rt = ar.take<double>(L * tri_ld(L));
         beta = ar.take<double>(L * m);
         dB = ar.take<double>(L * m);
         SB = ar.take<double>(L * m);
@@ -363,7 +405,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     oz_gram(s, planes, hs, N, L, m, G, Lt, err);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4 (FP64)
-    factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, ctx->sm_count);
+    factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
     int terr = 0;
@@ -384,13 +426,14 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     }
     const double *S = G, *Z = G + L;   // Z[l, c] = G[l, L + c]
     // Eq. 5, Eq. 7 (FP64)
-    solve_beta(ctx, s, R, Rt, f.perm, r, L, Z, Lt, m, beta, m);
+    const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m);
+    solver_apply(s, sv, Z, Lt, beta, m);
     mark(ctx, 4);
     double nrm[2] = {0.0, 0.0};
     for (int it = 0; it < P.max_refine; it++) {
         htr_f64(s, S, Lt, L, L, beta, m, SB, hpart, hs_split);   // S beta
         sub_rows(s, Z, Lt, SB, L, m, Gres);                      // Z - S beta
-        solve_beta(ctx, s, R, Rt, f.perm, r, L, Gres, m, m, dB, m);
+        solver_apply(s, sv, Gres, m, dB, m);
         axpy_norms(s, beta, dB, L * m, norms);
         ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
         ELM_CUDA(cudaStreamSynchronize(s));
@@ -400,6 +443,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     }
     mark(ctx, 5);
     if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
+    if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
     const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyDeviceToHost;
     ELM_CUDA(cudaMemcpy2DAsync(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
@@ -541,15 +585,15 @@ int elm_pinv_rank(elm_ctx *ctx, const double *Ht, int64_t L, int64_t N, int64_t 
             H = stage(ar, s, Ht, L, N, ldh, 8);
             S = ar.take<double>(L * L);
             gpart = ar.take<double>(gram_f64_ws(L, 0, ns));
-            R = ar.take<double>(L * L);
-            Rt = ar.take<double>(L * L);
+            R = ar.take<double>(L * tri_ld(L));
+            Rt = ar.take<double>(L * tri_ld(L));
             f = factor_ws_carve(ar, L);
             if (pinv_out && !dev_p) pv = ar.take<double>(L * N);
         });
         const double *Hd = (const double *)H.p;
         gram_f64(s, Hd, H.ld, L, N, nullptr, 0, 0, S, L, nullptr, 0, gpart, ns);
         const double tau = tol_rank > 0.0 ? tol_rank : (double)L * ldexp(1.0, -52);
-        factor_pivoted(s, S, L, L, tau, f, R, Rt, ctx->sm_count);
+        factor_pivoted(s, S, L, L, tau, f, R, Rt, tri_ld(L), ctx->sm_count);
         int32_t fl = 0;
         const int64_t r = read_rank(s, f, &fl);
         if (fl & 2) throw ElmError(ELM_ERR_TIMEOUT, "factorisation wait expired");
@@ -563,7 +607,9 @@ int elm_pinv_rank(elm_ctx *ctx, const double *Ht, int64_t L, int64_t N, int64_t 
         if (pinv_out) {
             double *dst = dev_p ? pinv_out : pv;
             const int64_t ldd = dev_p ? ldp : N;
-            solve_beta(ctx, s, R, Rt, f.perm, r, L, Hd, H.ld, N, dst, ldd);
+            const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, N);
+            solver_apply(s, sv, Hd, H.ld, dst, ldd);
+            if (solver_timed_out(s, sv)) throw ElmError(ELM_ERR_TIMEOUT, "solve wait expired");
             if (!dev_p)
                 ELM_CUDA(cudaMemcpy2DAsync(pinv_out, ldp * 8, pv, N * 8, N * 8, L,
                                            cudaMemcpyDeviceToHost, s));

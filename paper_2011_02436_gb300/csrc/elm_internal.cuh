@@ -125,20 +125,30 @@ struct FactorWs {
 };
 size_t factor_ws_bytes(int64_t L);
 FactorWs factor_ws_carve(Arena &ar, int64_t L);
-// Pivoted Cholesky of the L x L matrix S (lds).  Writes R (L x L, pivot
-// order, unscaled, rows >= rank zero) and Rt (its transpose), perm.
-// Returns nothing; rank lives in w.st->rank (device).
+// Row stride of the triangular factors: L rounded up to a multiple of 32,
+// so every 32-column row segment of a 32 x 32 block is 16-byte aligned and
+// inside the row (the solves fetch them with bulk copies).
+int64_t tri_ld(int64_t L);
+// Pivoted Cholesky of the L x L matrix S (lds).  Writes R (L rows, stride
+// ldr >= tri_ld(L), pivot order, unscaled, zero below the diagonal, in rows
+// >= rank and in the padding columns) and Rt = R^T (same shape), perm.
+// The rank lives in w.st->rank (device).
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
-                    double tau, const FactorWs &w, double *R, double *Rt,
+                    double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr,
                     int sms);
 
-// X = R11^{-T} B (forward) and X = R11^{-1} B (backward), in place on B
-// (r x q, ld ldb), R the pivot-order upper factor (ld ldr), r = r_max (the
-// rank known on the host; r_dev is unused).
-void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
-              int64_t r_max, double *B, int64_t ldb, int64_t q);
-void trsm_bwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
-              int64_t r_max, double *B, int64_t ldb, int64_t q);
+// Solves with the leading r x r block R11 of such a factor.  trsm_prepare
+// inverts its 32 x 32 diagonal blocks (DinvF, DinvB: trsm_dinv_doubles(r)
+// each); trsm_fwd then overwrites B (r x q, ldb) with R11^{-T} B reading R,
+// trsm_bwd with R11^{-1} B reading Rt.  *tflag |= 1 when a bounded
+// device-side wait gives up.
+int64_t trsm_dinv_doubles(int64_t r);
+void trsm_prepare(cudaStream_t s, const double *R, int64_t ldr, int64_t r, double *DinvF,
+                  double *DinvB);
+void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const double *DinvF, int64_t r,
+              double *B, int64_t ldb, int64_t q, int *tflag);
+void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const double *DinvB, int64_t r,
+              double *B, int64_t ldb, int64_t q, int *tflag);
 
 // Gather rows: dst[i, :] = src[perm[i], :] for i < r_dev.
 void gather_rows(cudaStream_t s, const double *src, int64_t lds, const int32_t *perm,

@@ -455,7 +455,7 @@ __global__ void finalize_kernel(const double *__restrict__ Rrow, int64_t ldrr,
                                 const int32_t *__restrict__ perm,
                                 const double *__restrict__ dS,
                                 const FactorState *__restrict__ st, int64_t L,
-                                double *__restrict__ R, double *__restrict__ Rt) {
+                                double *__restrict__ R, double *__restrict__ Rt, int64_t ld) {
     __shared__ double tile[32][33];
     const int64_t r = st->rank;
     const int64_t i0 = (int64_t)blockIdx.y * 32, p0 = (int64_t)blockIdx.x * 32;
@@ -468,125 +468,331 @@ __global__ void finalize_kernel(const double *__restrict__ Rrow, int64_t ldrr,
             double dd = dS[o];
             v = Rrow[i * ldrr + o] * (dd > 0.0 ? sqrt(dd) : 0.0);
         }
-        if (i < L && pos < L) R[i * L + pos] = v;
+        if (i < L) R[i * ld + pos] = v;   // columns L .. ld-1: zero padding
         tile[yy][tx] = v;
     }
     __syncthreads();
     for (int yy = ty; yy < 32; yy += 8) {
         int64_t pos = p0 + yy, i = i0 + tx;
-        if (i < L && pos < L) Rt[pos * L + i] = tile[tx][yy];
+        if (pos < L) Rt[pos * ld + i] = tile[tx][yy];
     }
 }
 
+// ------------------------------------------------------- triangular solves
+// Both directions are one kernel over a "coefficient" matrix C whose row i
+// holds the coefficients of x_i in every equation: C = R for R^T x = b
+// (top block first), C = R^T for R x = b (bottom block first).  Either way
+// the entries one step needs are contiguous row segments of C.
+constexpr int TB_ = 32;       // rows per diagonal block
+
+// Inverse U^{-1} of each TB_ x TB_ diagonal block U of the leading r x r
+// block of R, zero outside the block's nb x nb part (last block: nb < TB_).
+// Stored per block k as DinvF[k][a][c] = U^{-1}[a][c] (for R^T x = b the
+// block's equation matrix is U^T, so lane c of a solve reads column c of
+// (U^T)^{-1}, i.e. row-major entries [a][c] of U^{-1}) and DinvB[k][a][c] =
+// U^{-1}[c][a].  One warp per block; lane c solves U x = e_c by back
+// substitution with x in registers.
+__global__ void __launch_bounds__(32)
+diag_inv_kernel(const double *__restrict__ R, int64_t ldr, int64_t r,
+                double *__restrict__ DinvF, double *__restrict__ DinvB) {
+    __shared__ double U[TB_][TB_ + 1];
+    __shared__ double rd[TB_];
+    const int64_t k = blockIdx.x, i0 = k * TB_;
+    const int nb = (int)(r - i0 < TB_ ? r - i0 : TB_);
+    const int lane = threadIdx.x;
+    for (int a = 0; a < TB_; a++)
+        U[a][lane] = (a < nb && lane < nb) ? R[(i0 + a) * ldr + i0 + lane] : 0.0;
+    __syncwarp();
+    rd[lane] = lane < nb ? 1.0 / U[lane][lane] : 0.0;
+    __syncwarp();
+    double x[TB_];
+#pragma unroll
+    for (int i = TB_ - 1; i >= 0; i--) {
+        double v = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+        for (int l = i + 1; l < TB_; l++) v = fma(-U[i][l], x[l], v);
+        x[i] = (i < nb && lane < nb) ? v * rd[i] : 0.0;
+    }
+    double *F = DinvF + k * TB_ * TB_, *Bk = DinvB + k * TB_ * TB_;
+#pragma unroll
+    for (int i = 0; i < TB_; i++) F[i * TB_ + lane] = x[i];
+#pragma unroll
+    for (int i = 0; i < TB_; i++) Bk[lane * TB_ + i] = x[i];
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+}
+// shared memory of this CTA -> shared memory of a peer (cluster addresses
+// of the destination and of the peer's mbarrier)
+__device__ __forceinline__ void bulk_s2c(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "r"(su32(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+constexpr int NDG = 4;   // inverse-block buffers (fetched two steps ahead)
+
+constexpr int MAXSLOT = 2 * MAXCS;   // solution slots: two per cluster rank
+
+// shared memory of trsm_kernel in bytes: mbarriers (512 B), then the own
+// blocks of B, the solution slots, the partial sums of the split dot
+// products, the inverse diagonal blocks and the update slabs
+__host__ __device__ constexpr size_t trsm_smem_bytes(int nown, int nsl, int CB) {
+    return 512 + 8 * ((size_t)nown * TB_ * CB + (size_t)MAXSLOT * TB_ * CB + 8 * (size_t)TB_ * CB +
+                      (size_t)NDG * TB_ * TB_ + 2 * (size_t)nsl * TB_ * TB_);
+}
+
 // Blocked triangular solve on one thread-block cluster per group of CB
-// right-hand-side columns.  Rows are cut into diagonal blocks of TB_ rows,
-// dealt round-robin to the CTAs of the cluster; each CTA keeps its blocks of
-// B in shared memory.  Per diagonal block: one warp of its owner solves it
-// (lane = row, shuffles, no block barrier per row), one hardware cluster
-// barrier, then every CTA pulls the solved block through distributed shared
-// memory and updates its own remaining rows, one thread per row with the CB
-// right-hand sides in registers (R read once per element, coalesced).
-// FWD solves R^T x = b (R upper, top block first); otherwise R x = b
-// (bottom block first).
-constexpr int TB_ = 32;     // rows per diagonal block
-template <bool FWD, int CB>
+// right-hand-side columns (Algorithm 1 step 9 through the factor of Eq. 6).
+// Diagonal blocks of TB_ rows are dealt round-robin to the CTAs of the
+// cluster; each CTA keeps its blocks of B in shared memory.  Step s solves
+// block k_s: its owner applies the block's precomputed inverse (all eight
+// warps, the 32-term dot products split four ways per SM sub-partition)
+// and sends the solution with one bulk copy per peer into that peer's
+// slot s mod 2CS, completing on the peer's mbarrier; every CTA then updates
+// its remaining rows.  No cluster barrier sits in the loop: a CTA waits
+// only for the solution it needs, and the owner of step s+1 first updates
+// and solves its own block (look-ahead) before its other rows.  A slot is
+// rewritten 2CS steps later: every CTA owns a step among the CS before
+// that and sends its solution only after finishing step s, so the new
+// data cannot arrive before every receiver has consumed the old.
+// The inverse blocks and the slabs of C arrive by bulk copies issued ahead.
+// Waits are bounded; on expiry *tflag is set.
+template <bool REV, int CB>
 __global__ void __launch_bounds__(FT)
-trsm_cluster_kernel(const double *__restrict__ R, int64_t ldr, int64_t r,
-                    double *__restrict__ B, int64_t ldb, int64_t q, int nown) {
+trsm_kernel(const double *__restrict__ C, int64_t ldc, const double *__restrict__ Dinv,
+            int64_t r, double *__restrict__ B, int64_t ldb, int64_t q, int nown, int nsl,
+            int *tflag) {
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks();
     const int cr = (int)cluster.block_rank();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c0 = (int64_t)(blockIdx.x / CS) * CB;
     const int nc = (int)(q - c0 < CB ? q - c0 : CB);
     const int64_t nblk = (r + TB_ - 1) / TB_;
-    extern __shared__ double sm[];
-    double *bs = sm;                                   // nown x TB_ x CB
-    double *xb = bs + (size_t)nown * TB_ * CB;         // TB_ x CB pulled block
+    constexpr uint32_t XBYTES = TB_ * CB * 8;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    uint64_t *bar_sl = (uint64_t *)tsm;                 // 2: slab buffers
+    uint64_t *bar_dg = bar_sl + 2;                      // NDG: inverse-block buffers
+    uint64_t *bar_x = bar_dg + NDG;                     // MAXSLOT: solution slots
+    double *bs = (double *)(tsm + 512);                 // nown x TB_ x CB
+    double *xb = bs + (size_t)nown * TB_ * CB;          // MAXSLOT x TB_ x CB
+    double *part = xb + (size_t)MAXSLOT * TB_ * CB;     // 8 x TB_ x CB
+    const int NS = 2 * CS;                              // slots in use
+    double *dg = part + 8 * TB_ * CB;                   // NDG x TB_ x TB_
+    double *sl = dg + (size_t)NDG * TB_ * TB_;          // 2 x nsl x TB_ x TB_
+    __shared__ int s_abort;
+
+    auto blk = [&](int64_t s) { return REV ? nblk - 1 - s : s; };
+    auto owner_of = [&](int64_t s) { return (int)(blk(s) % CS); };
+    auto rows = [&](int64_t k) { return (int)(r - k * TB_ < TB_ ? r - k * TB_ : TB_); };
+    // own block k2 takes part in the update of step k
+    auto later = [&](int64_t k2, int64_t k) { return k2 < nblk && (REV ? k2 < k : k2 > k); };
+
+    // warp 1: inverse block of step s into dg[s % NDG] (if owned; else an
+    // empty phase, so every buffer's phase count follows the step count)
+    auto fill_diag = [&](int64_t s) {
+        if (s >= nblk) return;
+        const int64_t k = blk(s);
+        const int buf = (int)(s % NDG);
+        if (lane == 0) {
+            if ((int)(k % CS) == cr) {
+                mbar_expect(&bar_dg[buf], TB_ * TB_ * 8);
+                bulk_g2s(dg + (size_t)buf * TB_ * TB_, Dinv + k * TB_ * TB_, TB_ * TB_ * 8,
+                         &bar_dg[buf]);
+            } else {
+                mbar_arrive(&bar_dg[buf]);
+            }
+        }
+    };
+    // warp 1: rows of C coupling block k_s with the own blocks to update
+    // (those inside the window nsl) into sl[s & 1]
+    auto fill_slab = [&](int64_t s) {
+        if (s >= nblk) return;
+        const int64_t k = blk(s);
+        const int nb = rows(k);
+        const int buf = (int)(s & 1);
+        int cnt = 0;
+        for (int kl = 0; kl < nsl; kl++) cnt += later((int64_t)kl * CS + cr, k) ? 1 : 0;
+        if (lane == 0) {
+            if (cnt) mbar_expect(&bar_sl[buf], (uint32_t)cnt * (uint32_t)nb * TB_ * 8);
+            else mbar_arrive(&bar_sl[buf]);
+        }
+        __syncwarp();
+        for (int e = lane; e < nsl * TB_; e += 32) {
+            const int kl = e / TB_, a = e % TB_;
+            const int64_t k2 = (int64_t)kl * CS + cr;
+            if (a >= nb || !later(k2, k)) continue;
+            bulk_g2s(sl + (((size_t)buf * nsl + kl) * TB_ + a) * TB_,
+                     C + (k * TB_ + a) * ldc + k2 * TB_, TB_ * 8, &bar_sl[buf]);
+        }
+    };
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (!s_abort && !mbar_wait(bar, parity)) s_abort = 1;
+    };
+    // coefficient of x_{k_s*TB_+a} in equation k2*TB_+jj
+    auto coef = [&](int64_t s, int kl, int a, int jj) {
+        const int64_t k = blk(s), k2 = (int64_t)kl * CS + cr;
+        return kl < nsl ? sl[(((size_t)(s & 1) * nsl + kl) * TB_ + a) * TB_ + jj]
+                        : C[(k * TB_ + a) * ldc + k2 * TB_ + jj];
+    };
+
+    // owner of step s: x = Dinv_k b_k with all warps (warp: column warp %
+    // CB, a quarter warp / CB of the terms), then send to every peer
+    auto solve_send = [&](int64_t s) {
+        const int64_t k = blk(s);
+        const int slot = (int)(s % NS);
+        double *xs = xb + (size_t)slot * TB_ * CB;
+        double *xk = bs + (size_t)(k / CS) * TB_ * CB;
+        wait(&bar_dg[s % NDG], (uint32_t)((s / NDG) & 1));
+        {
+            constexpr int NQ = 8 / CB, AQ = TB_ / NQ;
+            const int c = warp % CB, qi = warp / CB;
+            const double *D = dg + (size_t)(s % NDG) * TB_ * TB_;
+            double p = 0.0;
+#pragma unroll
+            for (int a = qi * AQ; a < qi * AQ + AQ; a++) p = fma(D[a * TB_ + lane], xk[a * CB + c], p);
+            part[(qi * TB_ + lane) * CB + c] = p;
+        }
+        __syncthreads();
+        if (threadIdx.x < TB_ * CB) {
+            constexpr int NQ = 8 / CB;
+            double v = 0.0;
+#pragma unroll
+            for (int qi = 0; qi < NQ; qi++) v += part[qi * TB_ * CB + threadIdx.x];
+            xs[threadIdx.x] = v;
+            xk[threadIdx.x] = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (warp == 0 && lane < CS && lane != cr)
+            bulk_s2c(mapa(su32(xs), lane), xs, XBYTES, mapa(su32(&bar_x[slot]), lane));
+    };
+    // own block kl with the solution of step s, terms split over all warps
+    auto update_block = [&](int64_t s, const double *xs, int kl) {
+        const int nb = rows(blk(s));
+        const int64_t j = ((int64_t)kl * CS + cr) * TB_ + lane;
+        double acc[CB];
+#pragma unroll
+        for (int c = 0; c < CB; c++) acc[c] = 0.0;
+#pragma unroll
+        for (int a = warp * 4; a < warp * 4 + 4; a++) {
+            if (a >= nb) break;
+            const double rv = coef(s, kl, a, lane);
+#pragma unroll
+            for (int c = 0; c < CB; c++) acc[c] = fma(rv, xs[a * CB + c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CB; c++) part[(warp * TB_ + lane) * CB + c] = acc[c];
+        __syncthreads();
+        if (threadIdx.x < TB_ * CB && ((int64_t)kl * CS + cr) * TB_ + threadIdx.x / CB < r) {
+            double v = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) v += part[w * TB_ * CB + threadIdx.x];
+            bs[(size_t)kl * TB_ * CB + threadIdx.x] -= v;
+        }
+        (void)j;
+        __syncthreads();
+    };
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2 + NDG + MAXSLOT; i++) mbar_init(&bar_sl[i], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_ * CB; e += FT) {
         const int kl = (int)(e / (TB_ * CB)), a = (int)((e / CB) % TB_), c = (int)(e % CB);
         const int64_t k = (int64_t)kl * CS + cr, i = k * TB_ + a;
         bs[e] = (k < nblk && i < r && c < nc) ? B[i * ldb + c0 + c] : 0.0;
     }
     __syncthreads();
-    for (int64_t step = 0; step < nblk; step++) {
-        const int64_t k = FWD ? step : nblk - 1 - step;
-        const int owner = (int)(k % CS);
-        const int64_t i0 = k * TB_;
-        const int nb = (int)(r - i0 < TB_ ? r - i0 : TB_);
-        if (owner == cr) {
-            double *xk = bs + (size_t)(k / CS) * TB_ * CB;
-            // one warp solves the 32 x 32 diagonal block: lane = row of the
-            // block, its CB right-hand sides in registers, the solved value
-            // broadcast by shuffle; no block-wide barrier per row
-            if (threadIdx.x < 32) {
-                const int a2 = threadIdx.x;
-                double xr[CB];
-                double rowR[TB_];   // FWD: column a2 of R (R[a][a2]); else row a2 (R[a2][a])
+    // arm the receive slots for steps 0 .. 2CS-1, then let peers send
+    if (threadIdx.x < NS && threadIdx.x < nblk && owner_of(threadIdx.x) != cr)
+        mbar_expect(&bar_x[threadIdx.x], XBYTES);
+    cluster.sync();
+    if (warp == 1) {
+        for (int i = 0; i < NDG - 1; i++) fill_diag(i);
+        fill_slab(0);
+    }
+    if (nblk > 0 && owner_of(0) == cr) solve_send(0);
+
+    for (int64_t s = 0; s < nblk; s++) {
+        const int64_t k = blk(s);
+        const int slot = (int)(s % NS);
+        const bool mine = owner_of(s) == cr;
+        const double *xs = xb + (size_t)slot * TB_ * CB;
+        if (!mine) wait(&bar_x[slot], (uint32_t)((s / NS) & 1));
+        wait(&bar_sl[s & 1], (uint32_t)((s >> 1) & 1));
+        __syncthreads();
+        int skip = -1;
+        if (s + 1 < nblk && owner_of(s + 1) == cr) {   // look-ahead
+            skip = (int)(blk(s + 1) / CS);
+            update_block(s, xs, skip);
+            solve_send(s + 1);
+        }
+        if (!s_abort) {
+            const int nb = rows(k);
+            for (int e = threadIdx.x; e < nown * TB_; e += FT) {
+                const int kl = e / TB_, a2 = e % TB_;
+                const int64_t k2 = (int64_t)kl * CS + cr;
+                if (kl == skip || k2 * TB_ + a2 >= r || !later(k2, k)) continue;
+                double acc[CB];
+                double *bb = bs + (size_t)kl * TB_ * CB + (size_t)a2 * CB;
 #pragma unroll
-                for (int c = 0; c < CB; c++) xr[c] = a2 < nb ? xk[a2 * CB + c] : 0.0;
+                for (int c = 0; c < CB; c++) acc[c] = bb[c];
+                if (kl < nsl) {
+                    const double *sp = sl + (((size_t)(s & 1) * nsl + kl) * TB_) * TB_ + a2;
+#pragma unroll 8
+                    for (int a = 0; a < nb; a++) {
+                        const double rv = sp[a * TB_];
 #pragma unroll
-                for (int a = 0; a < TB_; a++)
-                    rowR[a] = (a2 < nb && a < nb)
-                                  ? (FWD ? R[(i0 + a) * ldr + i0 + a2] : R[(i0 + a2) * ldr + i0 + a])
-                                  : 0.0;
-                const double rinv_me = a2 < nb ? 1.0 / R[(i0 + a2) * ldr + i0 + a2] : 0.0;
+                        for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xs[a * CB + c], acc[c]);
+                    }
+                } else {
+                    const double *cp = C + k * TB_ * ldc + k2 * TB_ + a2;
+#pragma unroll 4
+                    for (int a = 0; a < nb; a++) {
+                        const double rv = cp[a * ldc];
 #pragma unroll
-                for (int s2 = 0; s2 < TB_; s2++) {
-                    const int a = FWD ? s2 : TB_ - 1 - s2;
-                    if (a >= nb) continue;                       // uniform over the warp
-                    if (a2 == a)
-#pragma unroll
-                        for (int c = 0; c < CB; c++) xr[c] *= rinv_me;
-#pragma unroll
-                    for (int c = 0; c < CB; c++) {
-                        const double xa = __shfl_sync(0xffffffffu, xr[c], a);
-                        if (FWD ? (a2 > a) : (a2 < a)) xr[c] = fma(-rowR[a], xa, xr[c]);
+                        for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xs[a * CB + c], acc[c]);
                     }
                 }
-                if (a2 < nb)
 #pragma unroll
-                    for (int c = 0; c < CB; c++) xk[a2 * CB + c] = xr[c];
+                for (int c = 0; c < CB; c++) bb[c] = acc[c];
             }
-            __syncthreads();
         }
-        cluster.sync();
-        {
-            const double *src = cluster.map_shared_rank(bs, owner) + (size_t)(k / CS) * TB_ * CB;
-            for (int e = threadIdx.x; e < TB_ * CB; e += FT) xb[e] = src[e];
+        __syncthreads();   // slot s, slab s read; bs updated
+        if (threadIdx.x == 0 && !mine && s + NS < nblk) mbar_expect(&bar_x[slot], XBYTES);
+        if (warp == 1 && !s_abort) {
+            fill_slab(s + 1);
+            fill_diag(s + NDG - 1);
         }
-        __syncthreads();
-        // update own blocks still to be solved: one thread per row
-        for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_; e += FT) {
-            const int kl = (int)(e / TB_), a2 = (int)(e % TB_);
-            const int64_t k2 = (int64_t)kl * CS + cr;
-            const int64_t j = k2 * TB_ + a2;
-            if (k2 >= nblk || j >= r || (FWD ? k2 <= k : k2 >= k)) continue;
-            double acc[CB];
-            double *bb = bs + (size_t)kl * TB_ * CB + (size_t)a2 * CB;
-#pragma unroll
-            for (int c = 0; c < CB; c++) acc[c] = bb[c];
-            if (FWD) {
-#pragma unroll 4
-                for (int a = 0; a < nb; a++) {
-                    const double rv = R[(i0 + a) * ldr + j];
-#pragma unroll
-                    for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xb[a * CB + c], acc[c]);
-                }
-            } else {
-                const double *Rj = R + j * ldr + i0;
-#pragma unroll 4
-                for (int a = 0; a < nb; a++) {
-                    const double rv = Rj[a];
-#pragma unroll
-                    for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xb[a * CB + c], acc[c]);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CB; c++) bb[c] = acc[c];
-        }
-        __syncthreads();
     }
-    cluster.sync();  // peers may still read this CTA's blocks
+    cluster.sync();   // every bulk copy between CTAs has landed
+    if (s_abort) {
+        // give copies from global memory already issued time to land
+        // before the shared memory is released
+        if (threadIdx.x == 0) {
+            atomicOr(tflag, 1);
+            const uint64_t t0 = gtime();
+            while (gtime() - t0 < 1000000ull) {
+            }
+        }
+        __syncthreads();
+        return;
+    }
     for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_ * CB; e += FT) {
         const int kl = (int)(e / (TB_ * CB)), a = (int)((e / CB) % TB_), c = (int)(e % CB);
         const int64_t k = (int64_t)kl * CS + cr, i = k * TB_ + a;
@@ -659,7 +865,8 @@ FactorWs factor_ws_carve(Arena &ar, int64_t L) {
 }
 
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
-                    double tau, const FactorWs &w, double *R, double *Rt, int sms) {
+                    double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr, int sms) {
+    if (ldr < tri_ld(L)) throw ElmError(ELM_ERR_ARG, "factor stride below tri_ld(L)");
     if (L > ELM_MAX_L) throw ElmError(ELM_ERR_UNSUPPORTED, "L above ELM_MAX_L");
     int nb16, nb8;
     int64_t w16, w8;
@@ -712,29 +919,35 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
             ELM_CHECK_LAUNCH();
         }
     }
-    dim3 g((unsigned)((L + 31) / 32), (unsigned)((L + 31) / 32));
-    finalize_kernel<<<g, 256, 0, s>>>(w.Rrow, L, w.perm, w.dS, w.st, L, R, Rt);
+    dim3 g((unsigned)(ldr / 32), (unsigned)((L + 31) / 32));
+    finalize_kernel<<<g, 256, 0, s>>>(w.Rrow, L, w.perm, w.dS, w.st, L, R, Rt, ldr);
     ELM_CHECK_LAUNCH();
 }
 
 static int g_tcluster = 0;
 
-template <bool FWD, int CB>
-static void trsm_cluster_cb(cudaStream_t s, const double *R, int64_t ldr, int64_t r, double *B,
-                            int64_t ldb, int64_t q) {
-    auto k = trsm_cluster_kernel<FWD, CB>;
+template <bool REV, int CB>
+static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const double *Dinv,
+                        int64_t r, double *B, int64_t ldb, int64_t q, int *tflag) {
+    auto k = trsm_kernel<REV, CB>;
     const int64_t nblk = (r + TB_ - 1) / TB_;
+    const size_t budget = 200 * 1024;
     int cs = g_tcluster ? g_tcluster : 16;
     for (;;) {
         const int nown = (int)((nblk + cs - 1) / cs);
-        const size_t smem = ((size_t)nown * TB_ * CB + TB_ * CB) * sizeof(double);
-        if (smem > 200 * 1024) {
+        // slab window: as many own blocks as fit (all of them up to r of
+        // about 10^4); blocks beyond it read C from global memory
+        const size_t fixed = trsm_smem_bytes(nown, 0, CB);
+        if (fixed > budget) {
             if (cs == 16) {
                 cs = 8;
                 continue;
             }
             throw ElmError(ELM_ERR_UNSUPPORTED, "rank too large for the cluster solve");
         }
+        int nsl = (int)((budget - fixed) / (2 * (size_t)TB_ * TB_ * 8));
+        if (nsl > nown) nsl = nown;
+        const size_t smem = trsm_smem_bytes(nown, nsl, CB);
         cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cudaLaunchConfig_t cfg = {};
@@ -761,7 +974,7 @@ static void trsm_cluster_cb(cudaStream_t s, const double *R, int64_t ldr, int64_
             }
             g_tcluster = cs;
         }
-        ELM_CUDA(cudaLaunchKernelEx(&cfg, k, R, ldr, r, B, ldb, q, nown));
+        ELM_CUDA(cudaLaunchKernelEx(&cfg, k, C, ldc, Dinv, r, B, ldb, q, nown, nsl, tflag));
         ELM_CHECK_LAUNCH();
         return;
     }
@@ -769,26 +982,37 @@ static void trsm_cluster_cb(cudaStream_t s, const double *R, int64_t ldr, int64_
 
 // Right-hand sides per cluster: spread small counts over several clusters
 // (each cluster's 16 SMs issue few FP64 operations per clock).
-template <bool FWD>
-static void trsm_cluster(cudaStream_t s, const double *R, int64_t ldr, int64_t r, double *B,
-                         int64_t ldb, int64_t q) {
+template <bool REV>
+static void trsm_any(cudaStream_t s, const double *C, int64_t ldc, const double *Dinv, int64_t r,
+                     double *B, int64_t ldb, int64_t q, int *tflag) {
     if (r <= 0 || q <= 0) return;
-    if (q <= 8) trsm_cluster_cb<FWD, 1>(s, R, ldr, r, B, ldb, q);
-    else if (q <= 16) trsm_cluster_cb<FWD, 2>(s, R, ldr, r, B, ldb, q);
-    else if (q <= 64) trsm_cluster_cb<FWD, 4>(s, R, ldr, r, B, ldb, q);
-    else trsm_cluster_cb<FWD, 8>(s, R, ldr, r, B, ldb, q);
+    if (ldc % TB_ != 0 || ldc < ((r + TB_ - 1) / TB_) * TB_)
+        throw ElmError(ELM_ERR_ARG, "triangular factor stride must be a multiple of 32");
+    if (q <= 8) trsm_launch<REV, 1>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
+    else if (q <= 16) trsm_launch<REV, 2>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
+    else if (q <= 64) trsm_launch<REV, 4>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
+    else trsm_launch<REV, 8>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
 }
 
-void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
-              int64_t r_max, double *B, int64_t ldb, int64_t q) {
-    (void)r_dev;
-    trsm_cluster<true>(s, R, ldr, r_max, B, ldb, q);
+int64_t tri_ld(int64_t L) { return ((L + TB_ - 1) / TB_) * TB_; }
+
+int64_t trsm_dinv_doubles(int64_t r) { return ((r + TB_ - 1) / TB_) * TB_ * TB_; }
+
+void trsm_prepare(cudaStream_t s, const double *R, int64_t ldr, int64_t r, double *DinvF,
+                  double *DinvB) {
+    if (r <= 0) return;
+    diag_inv_kernel<<<(unsigned)((r + TB_ - 1) / TB_), 32, 0, s>>>(R, ldr, r, DinvF, DinvB);
+    ELM_CHECK_LAUNCH();
 }
 
-void trsm_bwd(cudaStream_t s, const double *R, int64_t ldr, const int64_t *r_dev,
-              int64_t r_max, double *B, int64_t ldb, int64_t q) {
-    (void)r_dev;
-    trsm_cluster<false>(s, R, ldr, r_max, B, ldb, q);
+void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const double *DinvF, int64_t r,
+              double *B, int64_t ldb, int64_t q, int *tflag) {
+    trsm_any<false>(s, R, ldr, DinvF, r, B, ldb, q, tflag);
+}
+
+void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const double *DinvB, int64_t r,
+              double *B, int64_t ldb, int64_t q, int *tflag) {
+    trsm_any<true>(s, Rt, ldr, DinvB, r, B, ldb, q, tflag);
 }
 
 }  // namespace elm

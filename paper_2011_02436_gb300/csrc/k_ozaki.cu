@@ -168,6 +168,13 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
 struct dfl {
     float h, l;
 };
+
+// Two small integers (|d| <= 256, held in floats) as packed bf16: such a
+// float has at most 8 significant bits, so its bf16 encoding is exactly its
+// upper 16 bits -- integer operations, no conversion instruction.
+__device__ __forceinline__ uint32_t pack_bf16_int(float lo, float hi) {
+    return (__float_as_uint(lo) >> 16) | (__float_as_uint(hi) & 0xffff0000u);
+}
 __device__ __forceinline__ dfl two_sum(float a, float b) {
     const float s = a + b;
     const float bb = s - a;
@@ -328,10 +335,12 @@ __device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R,
     __nv_bfloat16 *row = A.planes + m * A.Np + n0;
 #pragma unroll
     for (int p = 0; p < GRAM_PH_; p++) {
-        __align__(16) __nv_bfloat162 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; i++) v[i] = __floats2bfloat162_rn(dg[p][2 * i], dg[p][2 * i + 1]);
-        *(uint4 *)(row + (int64_t)p * A.plane_stride) = *(const uint4 *)&v[0];
+        uint4 v;
+        v.x = pack_bf16_int(dg[p][0], dg[p][1]);
+        v.y = pack_bf16_int(dg[p][2], dg[p][3]);
+        v.z = pack_bf16_int(dg[p][4], dg[p][5]);
+        v.w = pack_bf16_int(dg[p][6], dg[p][7]);
+        *(uint4 *)(row + (int64_t)p * A.plane_stride) = v;
     }
 }
 
@@ -455,8 +464,10 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         break;
                     if (!mbar_wait(&full_bar[st], (uint32_t)((g / STAGES) & 1), abort)) break;
                     tc_fence_after();
-                    const uint32_t abase = su32(smem + (size_t)st * STAGE_BYTES);
-                    const uint32_t bbase = abase + PA * A_BYTES;
+                    // one descriptor per stage; planes and K steps are compile-time
+                    // offsets in its 16-byte start-address field (smem < 256 KB)
+                    const uint64_t da0 = desc_sw64(su32(smem + (size_t)st * STAGE_BYTES));
+                    const uint64_t db0 = da0 + (uint64_t)((PA * A_BYTES) >> 4);
 #pragma unroll
                     for (int td = 2; td <= TMAX; td++) {
                         bool first_pair = true;
@@ -464,8 +475,8 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         for (int p = 1; p <= PA; p++) {
                             const int q = td - p;
                             if (q < 1 || q > PB) continue;
-                            const uint64_t da = desc_sw64(abase + (p - 1) * A_BYTES);
-                            const uint64_t db = desc_sw64(bbase + (q - 1) * B_BYTES);
+                            const uint64_t da = da0 + (uint64_t)(((p - 1) * A_BYTES) >> 4);
+                            const uint64_t db = db0 + (uint64_t)(((q - 1) * B_BYTES) >> 4);
 #pragma unroll
                             for (int kk = 0; kk < SK / 16; kk++) {
                                 const uint32_t acc = (first && first_pair && kk == 0) ? 0u : 1u;
@@ -731,10 +742,12 @@ __global__ void digits_rows_f32_kernel(const float *__restrict__ X, int64_t N, i
         }
 #pragma unroll
         for (int p = 0; p < PD; p++) {
-            __align__(16) __nv_bfloat162 v[4];
-#pragma unroll
-            for (int e = 0; e < 4; e++) v[e] = __floats2bfloat162_rn(d[p][2 * e], d[p][2 * e + 1]);
-            *(uint4 *)(planes + (int64_t)p * Np * nK + i * nK + k0) = *(const uint4 *)&v[0];
+            uint4 v;
+            v.x = pack_bf16_int(d[p][0], d[p][1]);
+            v.y = pack_bf16_int(d[p][2], d[p][3]);
+            v.z = pack_bf16_int(d[p][4], d[p][5]);
+            v.w = pack_bf16_int(d[p][6], d[p][7]);
+            *(uint4 *)(planes + (int64_t)p * Np * nK + i * nK + k0) = v;
         }
     }
 }
@@ -787,10 +800,12 @@ __global__ void digits_cols_par_kernel(const double *__restrict__ W, int64_t n, 
     }
 #pragma unroll
     for (int p = 0; p < PD; p++) {
-        __align__(16) __nv_bfloat162 v[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) v[e] = __floats2bfloat162_rn(d[p][2 * e], d[p][2 * e + 1]);
-        *(uint4 *)(planes + (int64_t)p * Lp * nK + j * nK + k0) = *(const uint4 *)&v[0];
+        uint4 v;
+        v.x = pack_bf16_int(d[p][0], d[p][1]);
+        v.y = pack_bf16_int(d[p][2], d[p][3]);
+        v.z = pack_bf16_int(d[p][4], d[p][5]);
+        v.w = pack_bf16_int(d[p][6], d[p][7]);
+        *(uint4 *)(planes + (int64_t)p * Lp * nK + j * nK + k0) = v;
     }
 }
 
