@@ -28,7 +28,9 @@ namespace elm {
 namespace {
 
 constexpr int FT = 256;       // threads per CTA in the panel / solves
-constexpr int MAXNB = 32;     // largest panel width
+constexpr int MAXNB = 32;     // largest panel width of the data structures
+constexpr int PNB = 24;       // largest panel width the pivot kernel runs
+constexpr int MAXCPT = 8;     // panel columns per thread: wmax <= MAXCPT * FT
 
 // Order key of a double as an unsigned integer (larger key = larger value,
 // NaN below everything): comparisons then use the integer pipes, not the
@@ -37,32 +39,6 @@ __device__ __forceinline__ unsigned long long dkey(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     if ((b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull) return 0ull;
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-
-struct Cand {
-    unsigned long long key;
-    double val;
-    int32_t orig;
-    int32_t x;
-};
-
-__device__ __forceinline__ Cand make_cand(double v, int32_t orig, int32_t x) {
-    return Cand{dkey(v), v, orig, x};
-}
-__device__ __forceinline__ Cand no_cand() { return Cand{0ull, -INFINITY, 0x7fffffff, -1}; }
-
-// larger value first; equal values: lower original index first
-__device__ __forceinline__ bool better(const Cand &a, const Cand &b) {
-    return a.key > b.key || (a.key == b.key && a.orig < b.orig);
-}
-
-__device__ __forceinline__ Cand shfl_cand(const Cand &c, int o) {
-    Cand r;
-    r.key = __shfl_xor_sync(0xffffffffu, c.key, o);
-    r.val = __longlong_as_double(__shfl_xor_sync(0xffffffffu, __double_as_longlong(c.val), o));
-    r.orig = __shfl_xor_sync(0xffffffffu, c.orig, o);
-    r.x = __shfl_xor_sync(0xffffffffu, c.x, o);
-    return r;
 }
 
 // S -> A = diag(s) S diag(s), s_j = 1/sqrt(S_jj) (0 if S_jj <= 0); dS = diag(S).
@@ -99,7 +75,7 @@ __global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t 
 // A pivot candidate as published to the cluster: the CTA's largest unpivoted
 // updated diagonal, its original and active index, and that column's entries
 // in the panel rows so far.
-struct Slot {
+struct __align__(16) Slot {
     double val;
     long long idx;        // (orig << 32) | x, x = -1 when the CTA has none
     double pcol[MAXNB];
@@ -127,6 +103,28 @@ __device__ __forceinline__ void st_async64(uint32_t raddr, uint64_t v, uint32_t 
                  "l"(v), "r"(rbar)
                  : "memory");
 }
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+}
+// shared memory of this CTA -> shared memory of a peer (cluster addresses
+// of the destination and of the peer's mbarrier)
+__device__ __forceinline__ void bulk_s2c(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "r"(su32(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
 }
@@ -156,21 +154,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
     }
 }
 
-__device__ __forceinline__ Cand slot_cand(const Slot &s) {
-    return make_cand(s.val, (int32_t)(s.idx >> 32), (int32_t)(s.idx & 0xffffffff));
-}
 
-// 1/sqrt(v) to FP64 accuracy: float seed, two Newton steps in FP64
+// 1/sqrt(v) to FP64 accuracy for v > 0 within the float exponent range.
+// The seed y0 = rsqrtf(v) (about 22 bits) is formed with integer moves
+// instead of FP64 conversions (each FP64 instruction costs one 64-cycle
+// issue slot per SM sub-partition on GB300); then one third-order step of
+// the iteration for v^{-1/2}:  r = 1 - v y0^2 (exact product: y0 has 24
+// significant bits),  y1 = y0 + y0 r (1/2 + 3/8 r), whose truncation error
+// is about (5/16) r^3 < 2^-62 relative.
 __device__ __forceinline__ double rsqrt64(double v) {
-    double y = (double)rsqrtf((float)v);
-    y = y * fma(-0.5 * v, y * y, 1.5);
-    y = y * fma(-0.5 * v, y * y, 1.5);
-    return y;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)(b >> 52) - 1023;                       // v > 0
+    const uint32_t fb = ((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu);
+    const uint32_t yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+    const unsigned long long db =
+        ((unsigned long long)(((yb >> 23) & 0xffu) - 127 + 1023) << 52) |
+        ((unsigned long long)(yb & 0x7fffffu) << 29);
+    const double y0 = __longlong_as_double((long long)db);
+    const double r = fma(-v, y0 * y0, 1.0);
+    return fma(y0 * r, fma(0.375, r, 0.5), y0);
 }
 
-// Bytes a CTA receives for one exchange carrying `t` panel entries.
+// Bytes of one candidate message carrying `t` panel entries, and of one
+// exchange.
+__device__ __forceinline__ uint32_t msg_bytes(int t) {
+    return 16u + 8u * (uint32_t)t;
+}
 __device__ __forceinline__ uint32_t exch_bytes(int CS, int t) {
-    return (uint32_t)CS * (16u + 8u * (uint32_t)t);
+    return (uint32_t)CS * msg_bytes(t);
 }
 
 // One panel of up to nb pivots on a cluster.  A: active matrix (Lr x Lr,
@@ -182,6 +193,7 @@ __device__ __forceinline__ uint32_t exch_bytes(int CS, int t) {
 // each CTA waits on its own transaction-counted mbarrier (double-buffered
 // slots), so no cluster-wide barrier sits inside the pivot loop.  Waits are
 // bounded; on expiry the state's flag bit 1 is set.
+template <int CPT>
 __global__ void __launch_bounds__(FT)
 panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restrict__ act,
              double *__restrict__ P, int64_t ldp, double *__restrict__ Rrow, int64_t ldr,
@@ -191,9 +203,10 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks();
     const int cr = (int)cluster.block_rank();
-    __shared__ __align__(16) Slot slots[2][MAXCS];
+    __shared__ Slot slots[2][MAXCS];
     __shared__ __align__(8) uint64_t xbar[2];
-    __shared__ Cand wred[FT / 32];
+    __shared__ unsigned long long wred_k[FT / 32];
+    __shared__ uint32_t wred_o[FT / 32];
     __shared__ int32_t s_cnt;
     __shared__ int64_t s_off, s_tot;
     __shared__ int s_timeout;
@@ -208,6 +221,7 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     double *Ps = dyn;                          // nb x wmax
     double *d = dyn + (int64_t)nb * wmax;      // wmax
     int32_t *piv = (int32_t *)(d + wmax);      // wmax
+    int32_t *acts = piv + wmax;                // wmax: original index of own columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -218,57 +232,105 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         mbar_expect(&xbar[0], exch_bytes(CS, 0));   // filled by the first exchange
         mbar_expect(&xbar[1], exch_bytes(CS, 1));   // filled after pivot 0
     }
-    for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
-        d[xl] = A[(x0 + xl) * lda + x0 + xl];
-        piv[xl] = 0;
+    // this thread's peer (tid mod 16) for the sends: its slot cr and barrier
+    uint32_t rslot0[2], rbar0[2];
+    for (int b2 = 0; b2 < 2; b2++) {
+        const int peer = (int)(threadIdx.x & (MAXCS - 1)) < CS ? (int)(threadIdx.x & (MAXCS - 1)) : 0;
+        rslot0[b2] = mapa(su32(&slots[b2][cr]), peer);
+        rbar0[b2] = mapa(su32(&xbar[b2]), peer);
+    }
+    // this thread's columns xl = tid + i FT: diagonal, pivoted flag and
+    // original index live in registers (d is mirrored in shared memory for
+    // the message of the CTA's candidate)
+    double dreg[CPT];
+    int32_t areg[CPT];
+    bool preg[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; i++) {
+        const int64_t xl = threadIdx.x + (int64_t)i * FT;
+        dreg[i] = 0.0;
+        areg[i] = 0;
+        preg[i] = true;
+        if (xl < nloc) {
+            dreg[i] = A[(x0 + xl) * lda + x0 + xl];
+            areg[i] = act[x0 + xl];
+            preg[i] = false;
+            d[xl] = dreg[i];
+            piv[xl] = 0;
+        }
     }
     cluster.sync();   // every peer's barriers are initialised and armed
 
-    // local argmax over this CTA's unpivoted columns, then send it (and
-    // the column's first `t` panel entries) to every peer's slot `cr` of
-    // buffer `buf`
-    auto publish = [&](int t, int buf) {
-        Cand best = no_cand();
-        for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
-            if (piv[xl]) continue;
-            Cand c = make_cand(d[xl], act[x0 + xl], (int32_t)(x0 + xl));
-            if (better(c, best)) best = c;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            Cand c = shfl_cand(best, o);
-            if (better(c, best)) best = c;
-        }
-        if (lane == 0) wred[warp] = best;
-        __syncthreads();
-        Cand me = wred[0];
-        for (int w = 1; w < FT / 32; w++)
-            if (better(wred[w], me)) me = wred[w];
-        const int64_t xl = me.x >= 0 ? me.x - x0 : 0;
-        const uint32_t lslot = su32(&slots[buf][cr]);
-        const uint32_t lbar = su32(&xbar[buf]);
-        // thread (peer, f): f = 0 value, f = 1 index, f >= 2 panel entry f - 2
-        const int nf = 2 + t;
-        for (int e = threadIdx.x; e < CS * nf; e += FT) {
-            const int peer = e / nf, f = e % nf;
-            uint64_t v;
-            uint32_t off;
-            if (f == 0) {
-                v = (uint64_t)__double_as_longlong(me.val);
-                off = 0;
-            } else if (f == 1) {
-                v = ((uint64_t)(uint32_t)me.orig << 32) | (uint32_t)me.x;
-                off = 8;
-            } else {
-                const double pv = me.x >= 0 ? Ps[(int64_t)(f - 2) * Wd + xl] : 0.0;
-                v = (uint64_t)__double_as_longlong(pv);
-                off = 16 + 8 * (f - 2);
+    // Candidates travel as (order key of the diagonal, ord = orig << 14 |
+    // x): larger key first, equal keys to the lower original index.  Both
+    // fit integer registers, so a comparison costs no FP64 issue slot.
+    auto pbetter = [](unsigned long long ka, uint32_t oa, unsigned long long kb, uint32_t ob) {
+        return ka > kb || (ka == kb && oa < ob);
+    };
+    auto warp_best = [&](unsigned long long &k, uint32_t &o) {
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, off);
+            const uint32_t o2 = __shfl_xor_sync(0xffffffffu, o, off);
+            if (pbetter(k2, o2, k, o)) {
+                k = k2;
+                o = o2;
             }
-            st_async64(mapa(lslot + off, peer), v, mapa(lbar, peer));
+        }
+    };
+    // send this CTA's best (k, o) -- every thread passes its own -- with
+    // the column's first `t` panel entries to every peer's slot `cr` of
+    // buffer `buf`
+    // (all threads pass their own best)
+    auto publish = [&](int t, int buf, unsigned long long k, uint32_t o) {
+        warp_best(k, o);
+        if (lane == 0) {
+            wred_k[warp] = k;
+            wred_o[warp] = o;
+        }
+        __syncthreads();
+        k = wred_k[0];
+        o = wred_o[0];
+        for (int w = 1; w < FT / 32; w++)
+            if (pbetter(wred_k[w], wred_o[w], k, o)) {
+                k = wred_k[w];
+                o = wred_o[w];
+            }
+        const bool any = k != 0ull;
+        const int32_t bx = any ? (int32_t)(o & 0x3fffu) : -1;
+        const int64_t xl = any ? bx - x0 : 0;
+        // thread (peer = tid mod 16, f = tid / 16 + 16 j): f = 0 value, f = 1
+        // index, f >= 2 panel entry f - 2
+        const int nf = 2 + t;
+        const int peer = threadIdx.x & (MAXCS - 1);
+        if (peer >= CS) return;
+        const uint32_t rslot = buf ? rslot0[1] : rslot0[0], rbar = buf ? rbar0[1] : rbar0[0];
+        for (int f = threadIdx.x >> 4; f < nf; f += FT / MAXCS) {
+            uint64_t v;
+            if (f == 0) v = (uint64_t)__double_as_longlong(any ? d[xl] : -INFINITY);
+            else if (f == 1) v = any ? (((uint64_t)(o >> 14) << 32) | (uint32_t)bx) : ~0ull;
+            else v = (uint64_t)__double_as_longlong(any ? Ps[(int64_t)(f - 2) * Wd + xl] : 0.0);
+            st_async64(rslot + 8 * f, v, rbar);
         }
     };
 
-    publish(0, 0);
+    {
+        unsigned long long k = 0ull;
+        uint32_t o = 0xffffffffu;
+#pragma unroll
+        for (int i = 0; i < CPT; i++) {
+            const int64_t xl = threadIdx.x + (int64_t)i * FT;
+            if (preg[i]) continue;
+            const unsigned long long k2 = dkey(dreg[i]);
+            const uint32_t o2 = ((uint32_t)areg[i] << 14) | (uint32_t)(x0 + xl);
+            if (pbetter(k2, o2, k, o)) {
+                k = k2;
+                o = o2;
+            }
+        }
+        publish(0, 0, k, o);
+    }
 
+    const unsigned long long tau_key = dkey(tau);
     const int tmax = (int)(nb < Lr ? nb : Lr);
     int steps = 0;
     bool done = false;
@@ -279,58 +341,119 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
             break;
         }
         // every warp reduces the CS candidates itself (no broadcast needed)
-        Cand best = no_cand();
-        int bi = -1;
+        unsigned long long bk = 0ull;
+        uint32_t bo = 0xffffffffu;
         if (lane < CS) {
-            best = slot_cand(slots[buf][lane]);
-            bi = lane;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            Cand c2 = shfl_cand(best, o);
-            int b2 = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (better(c2, best)) {
-                best = c2;
-                bi = b2;
+            const Slot &sl = slots[buf][lane];
+            const int32_t sx = (int32_t)(sl.idx & 0xffffffff);
+            if (sx >= 0) {
+                bk = dkey(sl.val);
+                bo = ((uint32_t)(sl.idx >> 32) << 14) | (uint32_t)sx;
             }
         }
-        if (!(best.val > tau)) {
+        warp_best(bk, bo);
+        if (!(bk > tau_key)) {   // largest remaining diagonal <= tau (or none, or NaN)
             done = true;
             break;
         }
-        const int64_t q = best.x;
+        const int64_t q = bo & 0x3fffu;
+        const int bi = (int)(q / Wd);
+        const double bval = slots[buf][bi].val;
         const double *ucol = slots[buf][bi].pcol;
         const double *Aq = A + q * lda;
+        // this thread's entries of row q first: the load latency overlaps
+        // the reciprocal square root
+        double aq[CPT];
+#pragma unroll
+        for (int i = 0; i < CPT; i++) {
+            const int64_t xl = threadIdx.x + (int64_t)i * FT;
+            aq[i] = xl < nloc ? Aq[x0 + xl] : 0.0;
+        }
         // only warps that own columns spend FP64 issue slots
         double rinv = 0.0, rkk = 0.0;
         if ((int64_t)(warp * 32) < nloc) {
-            rinv = rsqrt64(best.val);
-            rkk = best.val * rinv;
+            rinv = rsqrt64(bval);
+            rkk = bval * rinv;
         }
-        for (int64_t xl = threadIdx.x; xl < nloc; xl += FT) {
+        // the pivot column's panel entries, the same for every thread
+        double uc[PNB];
+#pragma unroll
+        for (int s2 = 0; s2 < PNB; s2++) uc[s2] = s2 < t ? ucol[s2] : 0.0;
+        unsigned long long nk = 0ull;   // best candidate for the next pivot
+        uint32_t no = 0xffffffffu;
+#pragma unroll
+        for (int i = 0; i < CPT; i++) {
+            const int64_t xl = threadIdx.x + (int64_t)i * FT;
+            if (xl >= nloc) continue;
             const int64_t x = x0 + xl;
             double v;
             if (x == q) {
                 v = rkk;
+                preg[i] = true;
                 piv[xl] = 1;
-            } else if (piv[xl]) {
+                perm[k0 + t] = areg[i];
+            } else if (preg[i]) {
                 v = 0.0;
             } else {
-                v = Aq[x];
-                for (int s = 0; s < t; s++) v = fma(-ucol[s], Ps[(int64_t)s * Wd + xl], v);
-                v = v * rinv;
-                d[xl] = fma(-v, v, d[xl]);
+                // this column's panel entries, all loads issued before the chain
+                double pc[PNB];
+#pragma unroll
+                for (int s2 = 0; s2 < PNB; s2++)
+                    pc[s2] = s2 < t ? Ps[(int64_t)s2 * Wd + xl] : 0.0;
+                // keep the loads ahead of the chain (no sinking into the cases)
+#pragma unroll
+                for (int s2 = 0; s2 < PNB; s2++) asm volatile("" ::"d"(uc[s2]), "d"(pc[s2]));
+                // exactly t dependent FMAs, operands already in registers
+                // (jump into the unrolled chain: terms t-1 down to 0)
+                double acc = 0.0;
+                switch (t) {
+                case 24: acc = fma(uc[23], pc[23], acc); [[fallthrough]];
+                case 23: acc = fma(uc[22], pc[22], acc); [[fallthrough]];
+                case 22: acc = fma(uc[21], pc[21], acc); [[fallthrough]];
+                case 21: acc = fma(uc[20], pc[20], acc); [[fallthrough]];
+                case 20: acc = fma(uc[19], pc[19], acc); [[fallthrough]];
+                case 19: acc = fma(uc[18], pc[18], acc); [[fallthrough]];
+                case 18: acc = fma(uc[17], pc[17], acc); [[fallthrough]];
+                case 17: acc = fma(uc[16], pc[16], acc); [[fallthrough]];
+                case 16: acc = fma(uc[15], pc[15], acc); [[fallthrough]];
+                case 15: acc = fma(uc[14], pc[14], acc); [[fallthrough]];
+                case 14: acc = fma(uc[13], pc[13], acc); [[fallthrough]];
+                case 13: acc = fma(uc[12], pc[12], acc); [[fallthrough]];
+                case 12: acc = fma(uc[11], pc[11], acc); [[fallthrough]];
+                case 11: acc = fma(uc[10], pc[10], acc); [[fallthrough]];
+                case 10: acc = fma(uc[9], pc[9], acc); [[fallthrough]];
+                case 9: acc = fma(uc[8], pc[8], acc); [[fallthrough]];
+                case 8: acc = fma(uc[7], pc[7], acc); [[fallthrough]];
+                case 7: acc = fma(uc[6], pc[6], acc); [[fallthrough]];
+                case 6: acc = fma(uc[5], pc[5], acc); [[fallthrough]];
+                case 5: acc = fma(uc[4], pc[4], acc); [[fallthrough]];
+                case 4: acc = fma(uc[3], pc[3], acc); [[fallthrough]];
+                case 3: acc = fma(uc[2], pc[2], acc); [[fallthrough]];
+                case 2: acc = fma(uc[1], pc[1], acc); [[fallthrough]];
+                case 1: acc = fma(uc[0], pc[0], acc); [[fallthrough]];
+                default: break;
+                }
+                v = (aq[i] - acc) * rinv;
+                const double dn = fma(-v, v, dreg[i]);
+                dreg[i] = dn;
+                d[xl] = dn;
+                const unsigned long long k2 = dkey(dn);
+                const uint32_t o2 = ((uint32_t)areg[i] << 14) | (uint32_t)x;
+                if (pbetter(k2, o2, nk, no)) {
+                    nk = k2;
+                    no = o2;
+                }
             }
             Ps[(int64_t)t * Wd + xl] = v;
             P[(int64_t)t * ldp + x] = v;
-            Rrow[(k0 + t) * ldr + act[x]] = v;
+            Rrow[(k0 + t) * ldr + areg[i]] = v;
         }
-        if (cr == 0 && threadIdx.x == 0) perm[k0 + t] = act[q];
         __syncthreads();   // this CTA's slice updated; slots[buf] fully read
         // re-arm this buffer for its next use (filled after pivot t + 1) before
         // sending anything that lets a peer get there
         if (threadIdx.x == 0 && t + 2 < tmax) mbar_expect(&xbar[buf], exch_bytes(CS, t + 2));
         steps = t + 1;
-        if (t + 1 < tmax) publish(t + 1, buf ^ 1);
+        if (t + 1 < tmax) publish(t + 1, buf ^ 1, nk, no);
     }
     if (s_timeout && threadIdx.x == 0) atomicOr(&st->flags, 2);
 
@@ -518,28 +641,6 @@ diag_inv_kernel(const double *__restrict__ R, int64_t ldr, int64_t r,
     for (int i = 0; i < TB_; i++) F[i * TB_ + lane] = x[i];
 #pragma unroll
     for (int i = 0; i < TB_; i++) Bk[lane * TB_ + i] = x[i];
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(su32(dst)),
-        "l"(src), "r"(bytes), "r"(su32(bar))
-        : "memory");
-}
-// shared memory of this CTA -> shared memory of a peer (cluster addresses
-// of the destination and of the peer's mbarrier)
-__device__ __forceinline__ void bulk_s2c(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-        "[%3];" ::"r"(dst),
-        "r"(su32(src)), "r"(bytes), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
 constexpr int NDG = 4;   // inverse-block buffers (fetched two steps ahead)
@@ -804,11 +905,11 @@ int g_cluster = 0;  // chosen cluster size (per process; devices are alike)
 
 int pick_cluster(size_t smem_for16, size_t smem_for8) {
     if (g_cluster) return g_cluster;
-    cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(panel_kernel<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     int best = 8;
     for (int cs : {16, 8}) {
         size_t sm = cs == 16 ? smem_for16 : smem_for8;
-        cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(panel_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs);
         cfg.blockDim = dim3(FT);
@@ -821,7 +922,7 @@ int pick_cluster(size_t smem_for16, size_t smem_for8) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, panel_kernel, &cfg) == cudaSuccess && n > 0) {
+        if (cudaOccupancyMaxActiveClusters(&n, panel_kernel<1>, &cfg) == cudaSuccess && n > 0) {
             best = cs;
             break;
         }
@@ -834,11 +935,11 @@ int pick_cluster(size_t smem_for16, size_t smem_for8) {
 void panel_geometry(int64_t L, int cs, int *nb, int64_t *wmax, size_t *smem) {
     *wmax = (L + cs - 1) / cs;
     const size_t budget = 200 * 1024;
-    int64_t fit = (int64_t)((budget - (size_t)(*wmax) * 12) / ((size_t)(*wmax) * 8));
-    int b = (int)(fit < 24 ? fit : 24);
+    int64_t fit = (int64_t)((budget - (size_t)(*wmax) * 16) / ((size_t)(*wmax) * 8));
+    int b = (int)(fit < PNB ? fit : PNB);
     if (b < 1) b = 1;
     *nb = b;
-    *smem = (size_t)b * (*wmax) * 8 + (size_t)(*wmax) * 12 + 64;
+    *smem = (size_t)b * (*wmax) * 8 + (size_t)(*wmax) * 16 + 64;
 }
 
 }  // namespace
@@ -878,7 +979,13 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     int64_t wmax;
     size_t smem;
     panel_geometry(L, cs, &nb, &wmax, &smem);
-    ELM_CUDA(cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (wmax > (int64_t)MAXCPT * FT) throw ElmError(ELM_ERR_UNSUPPORTED, "L too large for the panel");
+    // columns per thread, as a compile-time count
+    auto kpanel = wmax <= FT ? panel_kernel<1>
+                  : wmax <= 2 * FT ? panel_kernel<2>
+                  : wmax <= 4 * FT ? panel_kernel<4> : panel_kernel<8>;
+    cudaFuncSetAttribute(kpanel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    ELM_CUDA(cudaFuncSetAttribute(kpanel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
 
     ELM_CUDA(cudaMemsetAsync(w.st, 0, sizeof(FactorState), s));
@@ -907,7 +1014,7 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        ELM_CUDA(cudaLaunchKernelEx(&cfg, panel_kernel, (const double *)Ac, (int64_t)L,
+        ELM_CUDA(cudaLaunchKernelEx(&cfg, kpanel, (const double *)Ac, (int64_t)L,
                                     (const int32_t *)ac, w.P, (int64_t)L, w.Rrow, (int64_t)L,
                                     w.perm, w.rem, an, w.st, (int64_t)L, nb, wmax, tau));
         ELM_CHECK_LAUNCH();
