@@ -120,7 +120,8 @@ typedef struct elm_train_opts {
     double tol_rank;    /* rank threshold on the unit-diagonal scale (<=0: L*2^-52
                            for FP64, max(L*2^-52, 2^-32) for MIXED, whose Gram
                            is exact up to dropped digit pairs below 2^-34)   */
-    double refine_tol;  /* stop when ||dbeta||_F <= refine_tol ||beta||_F (<=0: 1e-12) */
+    double refine_tol;  /* stop when ||dbeta||_F <= refine_tol ||beta||_F (<=0: 1e-12
+                           for FP64, 1e-9 for MIXED)                          */
     int32_t flags;      /* ELM_FLAG_* bits                                   */
     int32_t reserved;
 } elm_train_opts;

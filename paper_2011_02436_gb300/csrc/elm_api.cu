@@ -405,7 +405,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     oz_gram(s, planes, hs, N, L, m, G, Lt, err);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4 (FP64)
-    factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count);
+    factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
     int terr = 0;
@@ -653,7 +653,11 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             P.tau = o.tol_rank > 0.0 ? o.tol_rank
                                      : (o.precision == ELM_PREC_MIXED ? fmax(tau64, ldexp(1.0, -32))
                                                                       : tau64);
-            P.refine_tol = o.refine_tol > 0.0 ? o.refine_tol : 1e-12;
+            // mixed form: stop three orders below its 1e-6 accuracy target
+            // (its Gram matrix alone limits beta to about 1e-10); once an
+            // update is that small the remaining error is smaller still
+            P.refine_tol = o.refine_tol > 0.0 ? o.refine_tol
+                                              : (P.prec == ELM_PREC_MIXED ? 1e-9 : 1e-12);
             elm_result r{};
             train_one(ctx, P, &r);
             if (results) results[i] = r;

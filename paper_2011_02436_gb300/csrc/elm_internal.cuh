@@ -132,10 +132,13 @@ int64_t tri_ld(int64_t L);
 // Pivoted Cholesky of the L x L matrix S (lds).  Writes R (L rows, stride
 // ldr >= tri_ld(L), pivot order, unscaled, zero below the diagonal, in rows
 // >= rank and in the padding columns) and Rt = R^T (same shape), perm.
-// The rank lives in w.st->rank (device).
+// The rank lives in w.st->rank (device).  df: keep the active matrix as
+// double-float pairs and run the trailing updates on the FP32 pipes (about
+// 2^-44 relative per update; for the mixed form, whose Gram matrix is
+// itself accurate to about 2^-34), else FP64 throughout.
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr,
-                    int sms);
+                    int sms, bool df = false);
 
 // Solves with the leading r x r block R11 of such a factor.  trsm_prepare
 // inverts its 32 x 32 diagonal blocks (DinvF, DinvB: trsm_dinv_doubles(r)

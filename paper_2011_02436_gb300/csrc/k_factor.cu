@@ -41,7 +41,156 @@ __device__ __forceinline__ unsigned long long dkey(double v) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// ------------------------------------------------------------ double-float
+// Storage of the active matrix in the mixed form: v = h + l, two floats in
+// the eight bytes of a double.  The conversions use integer moves only (an
+// FP64 instruction costs a 64-cycle issue slot per SM sub-partition).
+struct F2 {
+    float h, l;
+};
+// h = v truncated to 24 significant bits, l = the remainder truncated to 24
+// bits: |v - h - l| < 2^-47 |v| for |v| >= 2^-70; magnitudes below 2^-126
+// (and the part of l below it) are dropped.
+__device__ __forceinline__ F2 d2df(double v) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const uint32_t sgn = (uint32_t)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    F2 r{0.f, 0.f};
+    if (e < -126) return r;
+    r.h = __uint_as_float(sgn | ((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffff));
+    const uint64_t m = b & 0x1fffffffull;   // the low 29 mantissa bits
+    if (m == 0) return r;
+    const int top = 63 - __clzll((long long)m);
+    const int el = e - 52 + top;
+    if (el < -126) return r;
+    const uint32_t mant = top >= 23 ? (uint32_t)(m >> (top - 23)) & 0x7fffff
+                                    : (uint32_t)(m << (23 - top)) & 0x7fffff;
+    r.l = __uint_as_float(sgn | ((uint32_t)(el + 127) << 23) | mant);
+    return r;
+}
+// exact value of a normal float (or zero) as a double
+__device__ __forceinline__ double f2d(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t ef = (b >> 23) & 0xff;
+    if (ef == 0) return 0.0;
+    return __longlong_as_double((long long)(((uint64_t)(b >> 31) << 63) |
+                                            ((uint64_t)(ef - 127 + 1023) << 52) |
+                                            ((uint64_t)(b & 0x7fffff) << 29)));
+}
+// 1/sqrt(v) to FP64 accuracy for v > 0 within the float exponent range.
+// The seed y0 = rsqrtf(v) (about 22 bits) is formed with integer moves
+// instead of FP64 conversions (each FP64 instruction costs one 64-cycle
+// issue slot per SM sub-partition on GB300); then one third-order step of
+// the iteration for v^{-1/2}:  r = 1 - v y0^2 (exact product: y0 has 24
+// significant bits),  y1 = y0 + y0 r (1/2 + 3/8 r), whose truncation error
+// is about (5/16) r^3 < 2^-62 relative.
+__device__ __forceinline__ double rsqrt64(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)(b >> 52) - 1023;                       // v > 0
+    const uint32_t fb = ((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu);
+    const uint32_t yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+    const unsigned long long db =
+        ((unsigned long long)(((yb >> 23) & 0xffu) - 127 + 1023) << 52) |
+        ((unsigned long long)(yb & 0x7fffffu) << 29);
+    const double y0 = __longlong_as_double((long long)db);
+    const double r = fma(-v, y0 * y0, 1.0);
+    return fma(y0 * r, fma(0.375, r, 0.5), y0);
+}
+
+// Double-float arithmetic (Knuth's TwoSum, Dekker's FastTwoSum, TwoProduct
+// by FMA): about 2^-44 relative, all on the FP32 pipes.
+__device__ __forceinline__ F2 df_renorm(float s, float e) {   // |s| >= |e|
+    const float h = s + e;
+    return F2{h, e - (h - s)};
+}
+__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = ((a.h - (s - bb)) + (b.h - bb)) + (a.l + b.l);
+    return df_renorm(s, e);
+}
+__device__ __forceinline__ F2 df_neg(F2 a) { return F2{-a.h, -a.l}; }
+__device__ __forceinline__ F2 df_mul(F2 a, F2 b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return df_renorm(p, e);
+}
+// (sh, sl) += a b, left unnormalised (renormalise after a run of terms)
+__device__ __forceinline__ void df_acc_prod(float &sh, float &sl, F2 a, F2 b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float s = sh + p;
+    const float bb = s - sh;
+    sl += ((sh - (s - bb)) + (p - bb)) + e;
+    sh = s;
+}
+// 1/sqrt(v), v > 0: float seed y0, then the third-order step
+// y0 + y0 r (1/2 + 3/8 r) with r = 1 - v y0^2 formed in double-float
+// (y0^2 is exact as a TwoProduct).
+__device__ __forceinline__ F2 df_rsqrt(F2 v) {
+    const float y0 = rsqrtf(v.h);
+    const float q = y0 * y0;
+    const float qe = fmaf(y0, y0, -q);
+    const F2 r = df_add(F2{1.f, 0.f}, df_neg(df_mul(v, F2{q, qe})));
+    const float rr = r.h + r.l;
+    return df_renorm(y0, y0 * rr * fmaf(0.375f, rr, 0.5f));
+}
+// order key of a normalised pair (lexicographic on the float keys of h, l)
+__device__ __forceinline__ uint32_t fkey(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long dfkey(F2 v) {
+    if (v.h != v.h) return 0ull;   // NaN below everything
+    return ((unsigned long long)fkey(v.h) << 32) | fkey(v.l);
+}
+
+// Arithmetic of the pivot panel: FP64, or double-float for the mixed form
+// (whose Gram matrix is itself accurate to about 2^-34).  Values travel in
+// eight bytes either way.
+template <bool DF>
+struct PanelArith;
+template <>
+struct PanelArith<false> {
+    using T = double;
+    static __device__ __forceinline__ T load(const double *A, int64_t i) { return A[i]; }
+    static __device__ __forceinline__ T of(double v) { return v; }
+    static __device__ __forceinline__ unsigned long long key(T v) { return dkey(v); }
+    static __device__ __forceinline__ T rsqrt(T v) { return rsqrt64(v); }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T scale_diff(T a, T acc, T r) { return (a - acc) * r; }
+    static __device__ __forceinline__ T sub_sq(T d, T v) { return fma(-v, v, d); }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ double to_double(T v) { return v; }
+};
+template <>
+struct PanelArith<true> {
+    using T = F2;
+    static __device__ __forceinline__ T load(const double *A, int64_t i) {
+        return reinterpret_cast<const F2 *>(A)[i];
+    }
+    static __device__ __forceinline__ T of(double v) { return d2df(v); }
+    static __device__ __forceinline__ unsigned long long key(T v) { return dfkey(v); }
+    static __device__ __forceinline__ T rsqrt(T v) { return df_rsqrt(v); }
+    static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+    static __device__ __forceinline__ T scale_diff(T a, T acc, T r) {
+        return df_mul(df_add(a, df_neg(acc)), r);
+    }
+    static __device__ __forceinline__ T sub_sq(T d, T v) {
+        float h = d.h, l = d.l;
+        df_acc_prod(h, l, v, df_neg(v));
+        return df_renorm(h, l);
+    }
+    static __device__ __forceinline__ T zero() { return F2{0.f, 0.f}; }
+    static __device__ __forceinline__ double to_double(T v) { return f2d(v.h) + f2d(v.l); }
+};
+
 // S -> A = diag(s) S diag(s), s_j = 1/sqrt(S_jj) (0 if S_jj <= 0); dS = diag(S).
+template <bool DF>
 __global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t L,
                              double *__restrict__ A, int64_t lda, double *__restrict__ dS,
                              int32_t *__restrict__ act, FactorState *st) {
@@ -55,7 +204,9 @@ __global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t 
         double sl = dl > 0.0 ? 1.0 / sqrt(dl) : 0.0;
         double v = S[j * lds + l];
         bad |= !isfinite(v);
-        A[j * lda + l] = (v * sj) * sl;
+        const double a = (v * sj) * sl;
+        if (DF) reinterpret_cast<F2 *>(A)[j * lda + l] = d2df(a);
+        else A[j * lda + l] = a;
         if (l == 0) {
             dS[j] = dj;
             act[j] = (int32_t)j;
@@ -155,25 +306,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
 }
 
 
-// 1/sqrt(v) to FP64 accuracy for v > 0 within the float exponent range.
-// The seed y0 = rsqrtf(v) (about 22 bits) is formed with integer moves
-// instead of FP64 conversions (each FP64 instruction costs one 64-cycle
-// issue slot per SM sub-partition on GB300); then one third-order step of
-// the iteration for v^{-1/2}:  r = 1 - v y0^2 (exact product: y0 has 24
-// significant bits),  y1 = y0 + y0 r (1/2 + 3/8 r), whose truncation error
-// is about (5/16) r^3 < 2^-62 relative.
-__device__ __forceinline__ double rsqrt64(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const int e = (int)(b >> 52) - 1023;                       // v > 0
-    const uint32_t fb = ((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu);
-    const uint32_t yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
-    const unsigned long long db =
-        ((unsigned long long)(((yb >> 23) & 0xffu) - 127 + 1023) << 52) |
-        ((unsigned long long)(yb & 0x7fffffu) << 29);
-    const double y0 = __longlong_as_double((long long)db);
-    const double r = fma(-v, y0 * y0, 1.0);
-    return fma(y0 * r, fma(0.375, r, 0.5), y0);
-}
 
 // Bytes of one candidate message carrying `t` panel entries, and of one
 // exchange.
@@ -193,7 +325,7 @@ __device__ __forceinline__ uint32_t exch_bytes(int CS, int t) {
 // each CTA waits on its own transaction-counted mbarrier (double-buffered
 // slots), so no cluster-wide barrier sits inside the pivot loop.  Waits are
 // bounded; on expiry the state's flag bit 1 is set.
-template <int CPT>
+template <int CPT, bool DF>
 __global__ void __launch_bounds__(FT)
 panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restrict__ act,
              double *__restrict__ P, int64_t ldp, double *__restrict__ Rrow, int64_t ldr,
@@ -218,8 +350,12 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     const int64_t Wd = (Lr + CS - 1) / CS;
     const int64_t x0 = (int64_t)cr * Wd;
     const int64_t nloc = x0 < Lr ? (Lr - x0 < Wd ? Lr - x0 : Wd) : 0;
-    double *Ps = dyn;                          // nb x wmax
-    double *d = dyn + (int64_t)nb * wmax;      // wmax
+    using AR = PanelArith<DF>;
+    using T = typename AR::T;
+    T *Ps = reinterpret_cast<T *>(dyn);        // nb x wmax
+    T *d = Ps + (int64_t)nb * wmax;            // wmax
+    T *Pg = reinterpret_cast<T *>(P);          // panel rows (global)
+    T *Rg = reinterpret_cast<T *>(Rrow);       // pivot rows (global)
     int32_t *piv = (int32_t *)(d + wmax);      // wmax
     int32_t *acts = piv + wmax;                // wmax: original index of own columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -242,17 +378,17 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     // this thread's columns xl = tid + i FT: diagonal, pivoted flag and
     // original index live in registers (d is mirrored in shared memory for
     // the message of the CTA's candidate)
-    double dreg[CPT];
+    T dreg[CPT];
     int32_t areg[CPT];
     bool preg[CPT];
 #pragma unroll
     for (int i = 0; i < CPT; i++) {
         const int64_t xl = threadIdx.x + (int64_t)i * FT;
-        dreg[i] = 0.0;
+        dreg[i] = AR::zero();
         areg[i] = 0;
         preg[i] = true;
         if (xl < nloc) {
-            dreg[i] = A[(x0 + xl) * lda + x0 + xl];
+            dreg[i] = AR::load(A, (x0 + xl) * lda + x0 + xl);
             areg[i] = act[x0 + xl];
             preg[i] = false;
             d[xl] = dreg[i];
@@ -306,9 +442,9 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         const uint32_t rslot = buf ? rslot0[1] : rslot0[0], rbar = buf ? rbar0[1] : rbar0[0];
         for (int f = threadIdx.x >> 4; f < nf; f += FT / MAXCS) {
             uint64_t v;
-            if (f == 0) v = (uint64_t)__double_as_longlong(any ? d[xl] : -INFINITY);
+            if (f == 0) v = any ? *reinterpret_cast<const uint64_t *>(&d[xl]) : 0ull;
             else if (f == 1) v = any ? (((uint64_t)(o >> 14) << 32) | (uint32_t)bx) : ~0ull;
-            else v = (uint64_t)__double_as_longlong(any ? Ps[(int64_t)(f - 2) * Wd + xl] : 0.0);
+            else v = any ? *reinterpret_cast<const uint64_t *>(&Ps[(int64_t)(f - 2) * Wd + xl]) : 0ull;
             st_async64(rslot + 8 * f, v, rbar);
         }
     };
@@ -320,7 +456,7 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         for (int i = 0; i < CPT; i++) {
             const int64_t xl = threadIdx.x + (int64_t)i * FT;
             if (preg[i]) continue;
-            const unsigned long long k2 = dkey(dreg[i]);
+            const unsigned long long k2 = AR::key(dreg[i]);
             const uint32_t o2 = ((uint32_t)areg[i] << 14) | (uint32_t)(x0 + xl);
             if (pbetter(k2, o2, k, o)) {
                 k = k2;
@@ -330,7 +466,7 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         publish(0, 0, k, o);
     }
 
-    const unsigned long long tau_key = dkey(tau);
+    const unsigned long long tau_key = AR::key(AR::of(tau));
     const int tmax = (int)(nb < Lr ? nb : Lr);
     int steps = 0;
     bool done = false;
@@ -347,7 +483,7 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
             const Slot &sl = slots[buf][lane];
             const int32_t sx = (int32_t)(sl.idx & 0xffffffff);
             if (sx >= 0) {
-                bk = dkey(sl.val);
+                bk = AR::key(*reinterpret_cast<const T *>(&sl.val));
                 bo = ((uint32_t)(sl.idx >> 32) << 14) | (uint32_t)sx;
             }
         }
@@ -358,27 +494,27 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         }
         const int64_t q = bo & 0x3fffu;
         const int bi = (int)(q / Wd);
-        const double bval = slots[buf][bi].val;
-        const double *ucol = slots[buf][bi].pcol;
-        const double *Aq = A + q * lda;
+        const T bval = *reinterpret_cast<const T *>(&slots[buf][bi].val);
+        const T *ucol = reinterpret_cast<const T *>(slots[buf][bi].pcol);
+        const int64_t aq0 = q * lda + x0;
         // this thread's entries of row q first: the load latency overlaps
         // the reciprocal square root
-        double aq[CPT];
+        T aq[CPT];
 #pragma unroll
         for (int i = 0; i < CPT; i++) {
             const int64_t xl = threadIdx.x + (int64_t)i * FT;
-            aq[i] = xl < nloc ? Aq[x0 + xl] : 0.0;
+            aq[i] = xl < nloc ? AR::load(A, aq0 + xl) : AR::zero();
         }
         // only warps that own columns spend FP64 issue slots
-        double rinv = 0.0, rkk = 0.0;
+        T rinv = AR::zero(), rkk = AR::zero();
         if ((int64_t)(warp * 32) < nloc) {
-            rinv = rsqrt64(bval);
-            rkk = bval * rinv;
+            rinv = AR::rsqrt(bval);
+            rkk = AR::mul(bval, rinv);
         }
         // the pivot column's panel entries, the same for every thread
-        double uc[PNB];
+        T uc[PNB];
 #pragma unroll
-        for (int s2 = 0; s2 < PNB; s2++) uc[s2] = s2 < t ? ucol[s2] : 0.0;
+        for (int s2 = 0; s2 < PNB; s2++) uc[s2] = s2 < t ? ucol[s2] : AR::zero();
         unsigned long long nk = 0ull;   // best candidate for the next pivot
         uint32_t no = 0xffffffffu;
 #pragma unroll
@@ -386,58 +522,91 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
             const int64_t xl = threadIdx.x + (int64_t)i * FT;
             if (xl >= nloc) continue;
             const int64_t x = x0 + xl;
-            double v;
+            T v;
             if (x == q) {
                 v = rkk;
                 preg[i] = true;
                 piv[xl] = 1;
                 perm[k0 + t] = areg[i];
             } else if (preg[i]) {
-                v = 0.0;
+                v = AR::zero();
             } else {
                 // this column's panel entries, all loads issued before the chain
-                double pc[PNB];
+                T pc[PNB];
 #pragma unroll
                 for (int s2 = 0; s2 < PNB; s2++)
-                    pc[s2] = s2 < t ? Ps[(int64_t)s2 * Wd + xl] : 0.0;
-                // keep the loads ahead of the chain (no sinking into the cases)
-#pragma unroll
-                for (int s2 = 0; s2 < PNB; s2++) asm volatile("" ::"d"(uc[s2]), "d"(pc[s2]));
-                // exactly t dependent FMAs, operands already in registers
+                    pc[s2] = s2 < t ? Ps[(int64_t)s2 * Wd + xl] : AR::zero();
+                // exactly t chained terms, operands already in registers
                 // (jump into the unrolled chain: terms t-1 down to 0)
-                double acc = 0.0;
-                switch (t) {
-                case 24: acc = fma(uc[23], pc[23], acc); [[fallthrough]];
-                case 23: acc = fma(uc[22], pc[22], acc); [[fallthrough]];
-                case 22: acc = fma(uc[21], pc[21], acc); [[fallthrough]];
-                case 21: acc = fma(uc[20], pc[20], acc); [[fallthrough]];
-                case 20: acc = fma(uc[19], pc[19], acc); [[fallthrough]];
-                case 19: acc = fma(uc[18], pc[18], acc); [[fallthrough]];
-                case 18: acc = fma(uc[17], pc[17], acc); [[fallthrough]];
-                case 17: acc = fma(uc[16], pc[16], acc); [[fallthrough]];
-                case 16: acc = fma(uc[15], pc[15], acc); [[fallthrough]];
-                case 15: acc = fma(uc[14], pc[14], acc); [[fallthrough]];
-                case 14: acc = fma(uc[13], pc[13], acc); [[fallthrough]];
-                case 13: acc = fma(uc[12], pc[12], acc); [[fallthrough]];
-                case 12: acc = fma(uc[11], pc[11], acc); [[fallthrough]];
-                case 11: acc = fma(uc[10], pc[10], acc); [[fallthrough]];
-                case 10: acc = fma(uc[9], pc[9], acc); [[fallthrough]];
-                case 9: acc = fma(uc[8], pc[8], acc); [[fallthrough]];
-                case 8: acc = fma(uc[7], pc[7], acc); [[fallthrough]];
-                case 7: acc = fma(uc[6], pc[6], acc); [[fallthrough]];
-                case 6: acc = fma(uc[5], pc[5], acc); [[fallthrough]];
-                case 5: acc = fma(uc[4], pc[4], acc); [[fallthrough]];
-                case 4: acc = fma(uc[3], pc[3], acc); [[fallthrough]];
-                case 3: acc = fma(uc[2], pc[2], acc); [[fallthrough]];
-                case 2: acc = fma(uc[1], pc[1], acc); [[fallthrough]];
-                case 1: acc = fma(uc[0], pc[0], acc); [[fallthrough]];
-                default: break;
+                T acc;
+                if constexpr (DF) {
+                    float ah = 0.f, al = 0.f;
+                    auto term = [&](F2 a2, F2 b2) { df_acc_prod(ah, al, a2, b2); };
+                    switch (t) {
+                    case 24: term(uc[23], pc[23]); [[fallthrough]];
+                    case 23: term(uc[22], pc[22]); [[fallthrough]];
+                    case 22: term(uc[21], pc[21]); [[fallthrough]];
+                    case 21: term(uc[20], pc[20]); [[fallthrough]];
+                    case 20: term(uc[19], pc[19]); [[fallthrough]];
+                    case 19: term(uc[18], pc[18]); [[fallthrough]];
+                    case 18: term(uc[17], pc[17]); [[fallthrough]];
+                    case 17: term(uc[16], pc[16]); [[fallthrough]];
+                    case 16: term(uc[15], pc[15]); [[fallthrough]];
+                    case 15: term(uc[14], pc[14]); [[fallthrough]];
+                    case 14: term(uc[13], pc[13]); [[fallthrough]];
+                    case 13: term(uc[12], pc[12]); [[fallthrough]];
+                    case 12: term(uc[11], pc[11]); [[fallthrough]];
+                    case 11: term(uc[10], pc[10]); [[fallthrough]];
+                    case 10: term(uc[9], pc[9]); [[fallthrough]];
+                    case 9: term(uc[8], pc[8]); [[fallthrough]];
+                    case 8: term(uc[7], pc[7]); [[fallthrough]];
+                    case 7: term(uc[6], pc[6]); [[fallthrough]];
+                    case 6: term(uc[5], pc[5]); [[fallthrough]];
+                    case 5: term(uc[4], pc[4]); [[fallthrough]];
+                    case 4: term(uc[3], pc[3]); [[fallthrough]];
+                    case 3: term(uc[2], pc[2]); [[fallthrough]];
+                    case 2: term(uc[1], pc[1]); [[fallthrough]];
+                    case 1: term(uc[0], pc[0]); [[fallthrough]];
+                    default: break;
+                    }
+                    acc = df_renorm(ah, al);
+                } else {
+                    double a1 = 0.0;
+                    auto term = [&](double a2, double b2) { a1 = fma(a2, b2, a1); };
+                    switch (t) {
+                    case 24: term(uc[23], pc[23]); [[fallthrough]];
+                    case 23: term(uc[22], pc[22]); [[fallthrough]];
+                    case 22: term(uc[21], pc[21]); [[fallthrough]];
+                    case 21: term(uc[20], pc[20]); [[fallthrough]];
+                    case 20: term(uc[19], pc[19]); [[fallthrough]];
+                    case 19: term(uc[18], pc[18]); [[fallthrough]];
+                    case 18: term(uc[17], pc[17]); [[fallthrough]];
+                    case 17: term(uc[16], pc[16]); [[fallthrough]];
+                    case 16: term(uc[15], pc[15]); [[fallthrough]];
+                    case 15: term(uc[14], pc[14]); [[fallthrough]];
+                    case 14: term(uc[13], pc[13]); [[fallthrough]];
+                    case 13: term(uc[12], pc[12]); [[fallthrough]];
+                    case 12: term(uc[11], pc[11]); [[fallthrough]];
+                    case 11: term(uc[10], pc[10]); [[fallthrough]];
+                    case 10: term(uc[9], pc[9]); [[fallthrough]];
+                    case 9: term(uc[8], pc[8]); [[fallthrough]];
+                    case 8: term(uc[7], pc[7]); [[fallthrough]];
+                    case 7: term(uc[6], pc[6]); [[fallthrough]];
+                    case 6: term(uc[5], pc[5]); [[fallthrough]];
+                    case 5: term(uc[4], pc[4]); [[fallthrough]];
+                    case 4: term(uc[3], pc[3]); [[fallthrough]];
+                    case 3: term(uc[2], pc[2]); [[fallthrough]];
+                    case 2: term(uc[1], pc[1]); [[fallthrough]];
+                    case 1: term(uc[0], pc[0]); [[fallthrough]];
+                    default: break;
+                    }
+                    acc = a1;
                 }
-                v = (aq[i] - acc) * rinv;
-                const double dn = fma(-v, v, dreg[i]);
+                v = AR::scale_diff(aq[i], acc, rinv);
+                const T dn = AR::sub_sq(dreg[i], v);
                 dreg[i] = dn;
                 d[xl] = dn;
-                const unsigned long long k2 = dkey(dn);
+                const unsigned long long k2 = AR::key(dn);
                 const uint32_t o2 = ((uint32_t)areg[i] << 14) | (uint32_t)x;
                 if (pbetter(k2, o2, nk, no)) {
                     nk = k2;
@@ -445,8 +614,8 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
                 }
             }
             Ps[(int64_t)t * Wd + xl] = v;
-            P[(int64_t)t * ldp + x] = v;
-            Rrow[(k0 + t) * ldr + areg[i]] = v;
+            Pg[(int64_t)t * ldp + x] = v;
+            Rg[(k0 + t) * ldr + areg[i]] = v;
         }
         __syncthreads();   // this CTA's slice updated; slots[buf] fully read
         // re-arm this buffer for its next use (filled after pivot t + 1) before
@@ -572,8 +741,90 @@ trailing_kernel(const double *__restrict__ A, double *__restrict__ An, int64_t l
     }
 }
 
+// The same update in the mixed form, on the FP32 pipes: A, An and the
+// panel rows hold double-float pairs, and each product P[t, x] P[t, y]
+// (TwoProduct by FMA, cross terms included) is subtracted with TwoSum:
+// about 2^-44 relative per element, against 24 FP64 FMAs that each take a
+// 64-cycle issue slot.
+__device__ __forceinline__ void df_sub_prod(float &sh, float &sl, const F2 a, const F2 b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float s = sh - p;
+    const float bb = s - sh;
+    const float err = (sh - (s - bb)) + (-p - bb);
+    sl = sl + (err - e);
+    sh = s;
+}
+__global__ void __launch_bounds__(256)
+trailing_df_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
+                   const F2 *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
+                   const FactorState *__restrict__ st) {
+    const FactorState s = *st;
+    if (s.done) return;
+    const int64_t Lr = s.Lr;
+    const int steps = (int)s.steps;
+    int64_t t = blockIdx.x;
+    int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (J * (J + 1) / 2 > t) J--;
+    while ((J + 1) * (J + 2) / 2 <= t) J++;
+    const int64_t I = t - J * (J + 1) / 2;
+    const int64_t r0 = J * TT, c0 = I * TT;
+    if (r0 >= Lr) return;
+    __shared__ F2 Pr[MAXNB][TT + 1];
+    __shared__ F2 Pc[MAXNB][TT + 1];
+    __shared__ int32_t rr_[TT], rc_[TT];
+    if (threadIdx.x < TT) {
+        int64_t x = r0 + threadIdx.x, y = c0 + threadIdx.x;
+        rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
+        rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < MAXNB * TT; e += 256) {
+        int tt = e / TT, k = e % TT;
+        Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : F2{0.f, 0.f};
+        Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : F2{0.f, 0.f};
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float ah[2][2], al[2][2];
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            int a = rr_[ty + 16 * p], b = rc_[tx + 16 * q];
+            const F2 v = (a >= 0 && b >= 0) ? A[(int64_t)a * lda + b] : F2{0.f, 0.f};
+            ah[p][q] = v.h;
+            al[p][q] = v.l;
+        }
+    for (int tt = 0; tt < steps; tt++) {
+        const F2 u0 = Pr[tt][ty], u1 = Pr[tt][ty + 16];
+        const F2 v0 = Pc[tt][tx], v1 = Pc[tt][tx + 16];
+        df_sub_prod(ah[0][0], al[0][0], u0, v0);
+        df_sub_prod(ah[0][1], al[0][1], u0, v1);
+        df_sub_prod(ah[1][0], al[1][0], u1, v0);
+        df_sub_prod(ah[1][1], al[1][1], u1, v1);
+    }
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        int64_t x = r0 + ty + 16 * p;
+        if (x >= Lr) continue;
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            int64_t y = c0 + tx + 16 * q;
+            if (y >= Lr) continue;
+            const float sh = ah[p][q] + al[p][q];
+            const F2 v{sh, al[p][q] - (sh - ah[p][q])};
+            An[x * lda + y] = v;
+            if (J != I) An[y * lda + x] = v;
+        }
+    }
+}
+
 // R[i, pos] = Rrow[i, perm pos] sqrt(dS[perm pos]) for i < rank, pos >= i;
 // Rt = R^T.  32 x 32 tiles transposed through shared memory.
+template <bool DF>
 __global__ void finalize_kernel(const double *__restrict__ Rrow, int64_t ldrr,
                                 const int32_t *__restrict__ perm,
                                 const double *__restrict__ dS,
@@ -589,7 +840,9 @@ __global__ void finalize_kernel(const double *__restrict__ Rrow, int64_t ldrr,
         if (i < r && pos < L && pos >= i) {
             int32_t o = perm[pos];
             double dd = dS[o];
-            v = Rrow[i * ldrr + o] * (dd > 0.0 ? sqrt(dd) : 0.0);
+            const double rv = PanelArith<DF>::to_double(
+                reinterpret_cast<const typename PanelArith<DF>::T *>(Rrow)[i * ldrr + o]);
+            v = rv * (dd > 0.0 ? sqrt(dd) : 0.0);
         }
         if (i < L) R[i * ld + pos] = v;   // columns L .. ld-1: zero padding
         tile[yy][tx] = v;
@@ -905,11 +1158,11 @@ int g_cluster = 0;  // chosen cluster size (per process; devices are alike)
 
 int pick_cluster(size_t smem_for16, size_t smem_for8) {
     if (g_cluster) return g_cluster;
-    cudaFuncSetAttribute(panel_kernel<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(panel_kernel<1, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     int best = 8;
     for (int cs : {16, 8}) {
         size_t sm = cs == 16 ? smem_for16 : smem_for8;
-        cudaFuncSetAttribute(panel_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(panel_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs);
         cfg.blockDim = dim3(FT);
@@ -922,7 +1175,7 @@ int pick_cluster(size_t smem_for16, size_t smem_for8) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, panel_kernel<1>, &cfg) == cudaSuccess && n > 0) {
+        if (cudaOccupancyMaxActiveClusters(&n, panel_kernel<1, false>, &cfg) == cudaSuccess && n > 0) {
             best = cs;
             break;
         }
@@ -966,7 +1219,8 @@ FactorWs factor_ws_carve(Arena &ar, int64_t L) {
 }
 
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
-                    double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr, int sms) {
+                    double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr, int sms,
+                    bool df) {
     if (ldr < tri_ld(L)) throw ElmError(ELM_ERR_ARG, "factor stride below tri_ld(L)");
     if (L > ELM_MAX_L) throw ElmError(ELM_ERR_UNSUPPORTED, "L above ELM_MAX_L");
     int nb16, nb8;
@@ -981,9 +1235,12 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     panel_geometry(L, cs, &nb, &wmax, &smem);
     if (wmax > (int64_t)MAXCPT * FT) throw ElmError(ELM_ERR_UNSUPPORTED, "L too large for the panel");
     // columns per thread, as a compile-time count
-    auto kpanel = wmax <= FT ? panel_kernel<1>
-                  : wmax <= 2 * FT ? panel_kernel<2>
-                  : wmax <= 4 * FT ? panel_kernel<4> : panel_kernel<8>;
+    auto kpanel = df ? (wmax <= FT ? panel_kernel<1, true>
+                        : wmax <= 2 * FT ? panel_kernel<2, true>
+                        : wmax <= 4 * FT ? panel_kernel<4, true> : panel_kernel<8, true>)
+                     : (wmax <= FT ? panel_kernel<1, false>
+                        : wmax <= 2 * FT ? panel_kernel<2, false>
+                        : wmax <= 4 * FT ? panel_kernel<4, false> : panel_kernel<8, false>);
     cudaFuncSetAttribute(kpanel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     ELM_CUDA(cudaFuncSetAttribute(kpanel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
@@ -993,7 +1250,8 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     {
         int64_t blocks = (L * L + 255) / 256;
         if (blocks > 8 * 1024) blocks = 8 * 1024;
-        equil_kernel<<<(unsigned)blocks, 256, 0, s>>>(S, lds, L, w.A0, L, w.dS, w.act0, w.st);
+        if (df) equil_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(S, lds, L, w.A0, L, w.dS, w.act0, w.st);
+        else equil_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(S, lds, L, w.A0, L, w.dS, w.act0, w.st);
         ELM_CHECK_LAUNCH();
     }
     const int64_t npanels = (L + nb - 1) / nb;
@@ -1021,13 +1279,18 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
         const int64_t Lup = L - (p + 1) * nb;
         if (Lup > 0) {
             int64_t T = (Lup + TT - 1) / TT;
-            trailing_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(Ac, An, L, w.P, L,
-                                                                         w.rem, w.st);
+            if (df)
+                trailing_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
+                    (const F2 *)Ac, (F2 *)An, L, (const F2 *)w.P, L, w.rem, w.st);
+            else
+                trailing_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(Ac, An, L, w.P, L,
+                                                                             w.rem, w.st);
             ELM_CHECK_LAUNCH();
         }
     }
     dim3 g((unsigned)(ldr / 32), (unsigned)((L + 31) / 32));
-    finalize_kernel<<<g, 256, 0, s>>>(w.Rrow, L, w.perm, w.dS, w.st, L, R, Rt, ldr);
+    if (df) finalize_kernel<true><<<g, 256, 0, s>>>(w.Rrow, L, w.perm, w.dS, w.st, L, R, Rt, ldr);
+    else finalize_kernel<false><<<g, 256, 0, s>>>(w.Rrow, L, w.perm, w.dS, w.st, L, R, Rt, ldr);
     ELM_CHECK_LAUNCH();
 }
 
