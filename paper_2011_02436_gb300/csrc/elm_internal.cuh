@@ -178,6 +178,7 @@ struct OzHidWs {
     double *xs, *ws;         // their power-of-two row / column scales
     float *xsf;              // the row scales of X as floats
     float4 *tab;             // sigmoid table
+    float4 *rowc;            // per hidden row: epilogue constants (two float4)
 };
 // Scratch of oz_hidden for an N x n input and L (+ m target) rows.
 OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m);

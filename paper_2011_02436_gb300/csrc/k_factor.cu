@@ -689,7 +689,8 @@ trailing_kernel(const double *__restrict__ A, double *__restrict__ An, int64_t l
     const int64_t Lr = s.Lr;
     const int steps = (int)s.steps;
     int64_t t = blockIdx.x;
-    int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    // lower-triangle tile (J, I) of block t: float estimate, exact integer fix
+    int64_t J = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while (J * (J + 1) / 2 > t) J--;
     while ((J + 1) * (J + 2) / 2 <= t) J++;
     const int64_t I = t - J * (J + 1) / 2;
@@ -766,7 +767,8 @@ trailing_df_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     const int64_t Lr = s.Lr;
     const int steps = (int)s.steps;
     int64_t t = blockIdx.x;
-    int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    // lower-triangle tile (J, I) of block t: float estimate, exact integer fix
+    int64_t J = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while (J * (J + 1) / 2 > t) J--;
     while ((J + 1) * (J + 2) / 2 <= t) J++;
     const int64_t I = t - J * (J + 1) / 2;

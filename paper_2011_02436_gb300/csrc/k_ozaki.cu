@@ -239,6 +239,7 @@ struct ActParams {
     const double *hs;       // Gram row scales (pow2_ceil(a_j))
     const float4 *tab;      // sigmoid table (s0 hi/lo, s1 hi/lo) on a 2^-6 grid
     const float *csf;       // per-sample scales as floats
+    const float4 *rowc;     // per hidden row: {rowf, 1/hs, b hi, b lo}, {a hi, a lo, scaled, 0}
     double *Ht;             // optional FP64 H^T (row j, column i)
     int64_t ldh;
 };
@@ -272,7 +273,33 @@ struct RowAct {
     float rowf, inv_hs;
     dfl bj, aj;
 };
+// Per-row constants of the epilogue, formed once per hidden row (FP64
+// work, so not once per tile): rowf = out_scale rscale 2^(-B (TMAX - 2)),
+// 1 / hs, the bias b and the output scale a as double-float pairs.
 template <int DBITS, int TMAX>
+__global__ void rowconst_kernel(double out_scale, const double *__restrict__ rscale,
+                                const double *__restrict__ b, const double *__restrict__ a,
+                                const double *__restrict__ hs, int64_t L, int64_t Lp,
+                                float4 *__restrict__ rowc) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Lp) return;
+    float4 c0 = make_float4(0.f, 1.f, 0.f, 0.f), c1 = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (m < L) {
+        c0.x = (float)ldexp(out_scale * rscale[m], -DBITS * (TMAX - 2));
+        c0.y = (float)(1.0 / hs[m]);
+        const double bv = b[m];
+        c0.z = (float)bv;
+        c0.w = (float)(bv - (double)c0.z);
+        if (a) {
+            const double av = a[m];
+            c1.x = (float)av;
+            c1.y = (float)(av - (double)c1.x);
+            c1.z = 1.f;
+        }
+    }
+    rowc[2 * m] = c0;
+    rowc[2 * m + 1] = c1;
+}
 __device__ __forceinline__ RowAct row_setup(const OzParams &P, int64_t m) {
     const ActParams &A = P.ap;
     RowAct r{};
@@ -281,17 +308,12 @@ __device__ __forceinline__ RowAct row_setup(const OzParams &P, int64_t m) {
     r.aj = {1.f, 0.f};
     r.inv_hs = 1.f;
     if (r.live) {
-        r.rowf = (float)ldexp(P.out_scale * P.rscale[m], -DBITS * (TMAX - 2));
-        const double b = A.b[m];
-        r.bj.h = (float)b;
-        r.bj.l = (float)(b - (double)r.bj.h);
-        if (A.a) {
-            const double av = A.a[m];
-            r.aj.h = (float)av;
-            r.aj.l = (float)(av - (double)r.aj.h);
-            r.scaled = true;
-        }
-        r.inv_hs = (float)(1.0 / A.hs[m]);
+        const float4 c0 = A.rowc[2 * m], c1 = A.rowc[2 * m + 1];
+        r.rowf = c0.x;
+        r.inv_hs = c0.y;
+        r.bj = {c0.z, c0.w};
+        r.aj = {c1.x, c1.y};
+        r.scaled = c1.z != 0.f;
     }
     return r;
 }
@@ -609,7 +631,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 }
             } else {
                 // the running-sum columns are this warp's until its next drain
-                const RowAct ra = row_setup<DBITS, TMAX>(P, m);
+                const RowAct ra = row_setup(P, m);
 #pragma unroll 1
                 for (int h = 0; h < 2; h++) {
                     uint32_t w0[16], w1[16];
@@ -934,6 +956,7 @@ OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m) {
     w.xsf = ar.take<float>(Np);
     w.ws = ar.take<double>(Lp);
     w.tab = ar.take<float4>(SIG_N);
+    w.rowc = ar.take<float4>(2 * Lp);
     return w;
 }
 
@@ -965,6 +988,9 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     ELM_CHECK_LAUNCH();
     sigmoid_table_kernel<<<(SIG_N + 255) / 256, 256, 0, s>>>(w.tab);
     ELM_CHECK_LAUNCH();
+    rowconst_kernel<HID_BITS, HID_TMAX><<<(unsigned)((Lp + 255) / 256), 256, 0, s>>>(
+        ldexp(1.0, -2 * (HID_BITS - 1)), w.ws, b, a, hs, L, Lp, w.rowc);
+    ELM_CHECK_LAUNCH();
     OzParams P{};
     P.a_rows = Lp;
     P.b_rows = Np;
@@ -990,6 +1016,7 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ap.hs = hs;
     P.ap.tab = w.tab;
     P.ap.csf = w.xsf;
+    P.ap.rowc = w.rowc;
     P.ap.Ht = Ht;
     P.ap.ldh = ldh;
     launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P,
