@@ -63,6 +63,12 @@ def peaks():
                 fp64=1.25)
 
 
+# DRAM bytes (read + write) of one Gram tensor-kernel launch per sample row:
+# 741.0 MB at 20000 rows in profiles/tensor_panel_trailing_sparse_pixels_20000rows_full.md
+# (the launch streams the digit planes, whose size is proportional to the rows).
+GRAM_DRAM_BYTES_PER_ROW = (718.989568e6 + 21.957120e6) / 20000
+
+
 class Clocks:
     """nvidia-smi sampling in the background during the timed region."""
 
@@ -304,7 +310,7 @@ def run_native(args):
             issued = 15 * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
             achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e12
             roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16"], unit="TFLOP/s",
-                        frac=achieved / pk["bf16"], traffic=None,
+                        frac=achieved / pk["bf16"], traffic=GRAM_DRAM_BYTES_PER_ROW * N,
                         kernel="ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
                         peak_source="%s bf16 dense burst" % pk["source"],
                         issued_tflops=issued / (ph_ms["gram"] * 1e-3) / 1e12,

@@ -165,7 +165,8 @@ int elm_predict(elm_ctx *ctx, const void *X, int x_dtype, int64_t N,
  * elm_phase_times: milliseconds spent in each training phase, summed over
  * the elm_train calls made with ELM_FLAG_PHASE_TIMING since the previous
  * elm_phase_times call (which resets the sums).  Phases, in order:
- *   0 hidden layer   1 Gram H^T H, H^T T   2 pivoted factorisation
+ *   0 hidden layer (mixed form: with the digit rows of T)
+ *   1 Gram H^T H, H^T T   2 pivoted factorisation
  *   3 first solve    4 refinement
  * Writes min(max_phases, ELM_NUM_PHASES) values to ms_out (host) and
  * returns ELM_NUM_PHASES, or a negative elm_status on error.

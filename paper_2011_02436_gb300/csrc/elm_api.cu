@@ -399,9 +399,11 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     // activation in the epilogue, digit planes of H
     oz_hidden(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, pb.act, L, m, planes, hs,
               nullptr, 0, err);
+    // digit rows of the targets beside those of H (part of the hidden phase,
+    // so the Gram phase times the Gram kernel alone)
+    oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
     mark(ctx, 1);
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
-    oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
     oz_gram(s, planes, hs, N, L, m, G, Lt, err);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4 (FP64)
