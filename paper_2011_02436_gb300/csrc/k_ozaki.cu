@@ -157,9 +157,9 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
     d |= (uint64_t)4 << 61;                    // SWIZZLE_64B
     return d;
 }
-// Instruction descriptor: kind::f16, bf16 x bf16 -> f32, both K-major.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: kind::f16, bf16 x bf16 -> f32, both K-major,
+// M = 128; the N field (bits 17-22, N / 8) is set per MMA.
+constexpr uint32_t IDESC_M = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BM >> 4) << 24);
 
 // ---------------------------------------------------------------- double-float
 // Unevaluated sums hi + lo of two floats with the error-free transformations
@@ -457,9 +457,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         tma_2d(&tmA, &full_bar[st], base + p * A_BYTES, s * SK,
                                (int)(p * P.a_rows + m0));
 #pragma unroll
-                    for (int q = 0; q < PB; q++)
-                        tma_2d(&tmB, &full_bar[st], base + PA * A_BYTES + q * B_BYTES, s * SK,
-                               (int)(q * P.b_rows + n0));
+                    for (int q = 0; q < PB; q++)   // digit q + 1, stored in descending order
+                        tma_2d(&tmB, &full_bar[st], base + PA * A_BYTES + (PB - 1 - q) * B_BYTES,
+                               s * SK, (int)(q * P.b_rows + n0));
                     issued = g + 1;
                 }
             }
@@ -490,22 +490,33 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     // offsets in its 16-byte start-address field (smem < 256 KB)
                     const uint64_t da0 = desc_sw64(su32(smem + (size_t)st * STAGE_BYTES));
                     const uint64_t db0 = da0 + (uint64_t)((PA * A_BYTES) >> 4);
+                    // A plane p against the B planes q = TMAX-p .. 1 (diagonals
+                    // t = TMAX .. p+1) in MMAs of width up to 256: B planes are
+                    // stored in descending order and diagonal t's accumulator sits
+                    // at column (TMAX - t) BN, so the group starts at column 0 (and,
+                    // past four planes, continues at column 256 with width 64 or
+                    // 128): A is read once per group instead of once per pair, and
+                    // every accumulator address is a multiple of its MMA width.
+                    // p = 1 reaches every diagonal and comes first, so it alone
+                    // starts the chunk's accumulators.
+                    static_assert(PB >= TMAX - 1, "plane 1 must reach every diagonal");
+                    static_assert(TMAX - 1 <= 8, "at most two MMA groups per plane");
 #pragma unroll
-                    for (int td = 2; td <= TMAX; td++) {
-                        bool first_pair = true;
+                    for (int p = 1; p <= PA && p < TMAX; p++) {
+                        const int nall = TMAX - p;        // planes q = nall .. 1
 #pragma unroll
-                        for (int p = 1; p <= PA; p++) {
-                            const int q = td - p;
-                            if (q < 1 || q > PB) continue;
+                        for (int g = 0; g * 4 < nall; g++) {
+                            const int q_hi = nall - 4 * g;
+                            const int nq = q_hi < 4 ? q_hi : 4;
+                            const uint32_t idesc = IDESC_M | ((uint32_t)((BN * nq) >> 3) << 17);
                             const uint64_t da = da0 + (uint64_t)(((p - 1) * A_BYTES) >> 4);
-                            const uint64_t db = db0 + (uint64_t)(((q - 1) * B_BYTES) >> 4);
+                            const uint64_t db = db0 + (uint64_t)(((PB - q_hi) * B_BYTES) >> 4);
 #pragma unroll
                             for (int kk = 0; kk < SK / 16; kk++) {
-                                const uint32_t acc = (first && first_pair && kk == 0) ? 0u : 1u;
-                                mma_bf16(tmem + (uint32_t)((td - 2) * BN), da + 2 * kk,
-                                         db + 2 * kk, IDESC, acc);
+                                const uint32_t acc = (first && p == 1 && kk == 0) ? 0u : 1u;
+                                mma_bf16(tmem + (uint32_t)(4 * g * BN), da + 2 * kk, db + 2 * kk,
+                                         idesc, acc);
                             }
-                            first_pair = false;
                         }
                     }
                     mma_commit(&empty_bar[st]);
@@ -553,7 +564,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         for (int i = 0; i < 16; i++) V[i] = {0.f, 0.f};
 #pragma unroll
                         for (int td = 2; td <= TMAX; td++) {
-                            tmem_ld16(lane_base + (uint32_t)((td - 2) * BN + h * 16), w0);
+                            tmem_ld16(lane_base + (uint32_t)((TMAX - td) * BN + h * 16), w0);
                             tmem_wait_ld();
                             const float sc = (float)(1 << DBITS);
 #pragma unroll
@@ -583,7 +594,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     }
 #pragma unroll
                     for (int td = 2; td <= TMAX; td++) {
-                        tmem_ld16(lane_base + (uint32_t)((td - 2) * BN + h * 16), w0);
+                        tmem_ld16(lane_base + (uint32_t)((TMAX - td) * BN + h * 16), w0);
                         tmem_wait_ld();
                         // accumulators are exact integers below 2^25
                         const long long mult = 1ll << (DBITS * (TMAX - td));
