@@ -513,8 +513,10 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         }
         // the pivot column's panel entries, the same for every thread
         T uc[PNB];
+        if constexpr (!DF) {
 #pragma unroll
-        for (int s2 = 0; s2 < PNB; s2++) uc[s2] = s2 < t ? ucol[s2] : AR::zero();
+            for (int s2 = 0; s2 < PNB; s2++) uc[s2] = s2 < t ? ucol[s2] : AR::zero();
+        }
         unsigned long long nk = 0ull;   // best candidate for the next pivot
         uint32_t no = 0xffffffffu;
 #pragma unroll
@@ -531,46 +533,32 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
             } else if (preg[i]) {
                 v = AR::zero();
             } else {
-                // this column's panel entries, all loads issued before the chain
-                T pc[PNB];
-#pragma unroll
-                for (int s2 = 0; s2 < PNB; s2++)
-                    pc[s2] = s2 < t ? Ps[(int64_t)s2 * Wd + xl] : AR::zero();
-                // exactly t chained terms, operands already in registers
-                // (jump into the unrolled chain: terms t-1 down to 0)
                 T acc;
                 if constexpr (DF) {
+                    // double-float: short dependent steps, so a plain loop with
+                    // its loads unrolled four ahead keeps the FP32 pipe busy
                     float ah = 0.f, al = 0.f;
-                    auto term = [&](F2 a2, F2 b2) { df_acc_prod(ah, al, a2, b2); };
-                    switch (t) {
-                    case 24: term(uc[23], pc[23]); [[fallthrough]];
-                    case 23: term(uc[22], pc[22]); [[fallthrough]];
-                    case 22: term(uc[21], pc[21]); [[fallthrough]];
-                    case 21: term(uc[20], pc[20]); [[fallthrough]];
-                    case 20: term(uc[19], pc[19]); [[fallthrough]];
-                    case 19: term(uc[18], pc[18]); [[fallthrough]];
-                    case 18: term(uc[17], pc[17]); [[fallthrough]];
-                    case 17: term(uc[16], pc[16]); [[fallthrough]];
-                    case 16: term(uc[15], pc[15]); [[fallthrough]];
-                    case 15: term(uc[14], pc[14]); [[fallthrough]];
-                    case 14: term(uc[13], pc[13]); [[fallthrough]];
-                    case 13: term(uc[12], pc[12]); [[fallthrough]];
-                    case 12: term(uc[11], pc[11]); [[fallthrough]];
-                    case 11: term(uc[10], pc[10]); [[fallthrough]];
-                    case 10: term(uc[9], pc[9]); [[fallthrough]];
-                    case 9: term(uc[8], pc[8]); [[fallthrough]];
-                    case 8: term(uc[7], pc[7]); [[fallthrough]];
-                    case 7: term(uc[6], pc[6]); [[fallthrough]];
-                    case 6: term(uc[5], pc[5]); [[fallthrough]];
-                    case 5: term(uc[4], pc[4]); [[fallthrough]];
-                    case 4: term(uc[3], pc[3]); [[fallthrough]];
-                    case 3: term(uc[2], pc[2]); [[fallthrough]];
-                    case 2: term(uc[1], pc[1]); [[fallthrough]];
-                    case 1: term(uc[0], pc[0]); [[fallthrough]];
-                    default: break;
+                    const T *pcol = Ps + xl;
+                    int s2 = 0;
+                    for (; s2 + 4 <= t; s2 += 4) {
+                        const F2 u0 = ucol[s2], u1 = ucol[s2 + 1], u2 = ucol[s2 + 2], u3 = ucol[s2 + 3];
+                        const F2 p0 = pcol[(int64_t)s2 * Wd], p1 = pcol[(int64_t)(s2 + 1) * Wd];
+                        const F2 p2 = pcol[(int64_t)(s2 + 2) * Wd], p3 = pcol[(int64_t)(s2 + 3) * Wd];
+                        df_acc_prod(ah, al, u0, p0);
+                        df_acc_prod(ah, al, u1, p1);
+                        df_acc_prod(ah, al, u2, p2);
+                        df_acc_prod(ah, al, u3, p3);
                     }
+                    for (; s2 < t; s2++) df_acc_prod(ah, al, ucol[s2], pcol[(int64_t)s2 * Wd]);
                     acc = df_renorm(ah, al);
                 } else {
+                    // FP64: each step is a 64-cycle issue slot; load the column's
+                    // panel entries first, then run exactly t chained FMAs
+                    // (a jump into an unrolled chain: terms t-1 down to 0)
+                    T pc[PNB];
+#pragma unroll
+                    for (int s2 = 0; s2 < PNB; s2++)
+                        pc[s2] = s2 < t ? Ps[(int64_t)s2 * Wd + xl] : AR::zero();
                     double a1 = 0.0;
                     auto term = [&](double a2, double b2) { a1 = fma(a2, b2, a1); };
                     switch (t) {
@@ -815,6 +803,82 @@ trailing_df_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             int64_t y = c0 + tx + 16 * q;
+            if (y >= Lr) continue;
+            const float sh = ah[p][q] + al[p][q];
+            const F2 v{sh, al[p][q] - (sh - ah[p][q])};
+            An[x * lda + y] = v;
+            if (J != I) An[y * lda + x] = v;
+        }
+    }
+}
+
+// 64 x 64 lower tiles for large active matrices: each thread keeps a 4 x 4
+// block (16 independent double-float chains) and the panel rows of the
+// tile are staged once in shared memory.
+constexpr int TT2 = 64;
+__global__ void __launch_bounds__(256)
+trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
+                     const F2 *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
+                     const FactorState *__restrict__ st) {
+    const FactorState s = *st;
+    if (s.done) return;
+    const int64_t Lr = s.Lr;
+    const int steps = (int)s.steps;
+    const int64_t t = blockIdx.x;
+    int64_t J = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (J * (J + 1) / 2 > t) J--;
+    while ((J + 1) * (J + 2) / 2 <= t) J++;
+    const int64_t I = t - J * (J + 1) / 2;
+    const int64_t r0 = J * TT2, c0 = I * TT2;
+    if (r0 >= Lr) return;
+    __shared__ F2 Pr[PNB][TT2];
+    __shared__ F2 Pc[PNB][TT2];
+    __shared__ int32_t rr_[TT2], rc_[TT2];
+    if (threadIdx.x < TT2) {
+        const int64_t x = r0 + threadIdx.x;
+        rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
+    } else if (threadIdx.x < 2 * TT2) {
+        const int64_t y = c0 + threadIdx.x - TT2;
+        rc_[threadIdx.x - TT2] = y < Lr ? rem[y] : -1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PNB * TT2; e += 256) {
+        const int tt = e / TT2, k = e % TT2;
+        Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : F2{0.f, 0.f};
+        Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : F2{0.f, 0.f};
+    }
+    __syncthreads();
+    // thread (ty, tx) owns rows ty + 16 p and columns tx + 16 q, p, q < 4
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float ah[4][4], al[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int a = rr_[ty + 16 * p], b = rc_[tx + 16 * q];
+            const F2 v = (a >= 0 && b >= 0) ? A[(int64_t)a * lda + b] : F2{0.f, 0.f};
+            ah[p][q] = v.h;
+            al[p][q] = v.l;
+        }
+    for (int tt = 0; tt < steps; tt++) {
+        F2 u[4], w[4];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            u[p] = Pr[tt][ty + 16 * p];
+            w[p] = Pc[tt][tx + 16 * p];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) df_sub_prod(ah[p][q], al[p][q], u[p], w[q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        const int64_t x = r0 + ty + 16 * p;
+        if (x >= Lr) continue;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int64_t y = c0 + tx + 16 * q;
             if (y >= Lr) continue;
             const float sh = ah[p][q] + al[p][q];
             const F2 v{sh, al[p][q] - (sh - ah[p][q])};
@@ -1281,7 +1345,11 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
         const int64_t Lup = L - (p + 1) * nb;
         if (Lup > 0) {
             int64_t T = (Lup + TT - 1) / TT;
-            if (df)
+            if (df && Lup > 768) {
+                const int64_t T2 = (Lup + TT2 - 1) / TT2;
+                trailing_df64_kernel<<<(unsigned)(T2 * (T2 + 1) / 2), 256, 0, s>>>(
+                    (const F2 *)Ac, (F2 *)An, L, (const F2 *)w.P, L, w.rem, w.st);
+            } else if (df)
                 trailing_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
                     (const F2 *)Ac, (F2 *)An, L, (const F2 *)w.P, L, w.rem, w.st);
             else
