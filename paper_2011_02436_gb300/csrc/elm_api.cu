@@ -69,6 +69,18 @@ void require(bool ok, const char *what) {
     if (!ok) throw ElmError(ELM_ERR_ARG, what);
 }
 
+// Strided copy of `rows` rows of `width` bytes; one linear copy when both
+// sides are contiguous (the 2-D copy path moves pinned host memory at well
+// under half the rate of a linear copy on GB300).
+void copy2d(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t rows,
+            cudaMemcpyKind kind, cudaStream_t s) {
+    if (rows == 0 || width == 0) return;
+    if ((dpitch == width && spitch == width) || rows == 1)
+        ELM_CUDA(cudaMemcpyAsync(dst, src, width * rows, kind, s));
+    else
+        ELM_CUDA(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, kind, s));
+}
+
 bool on_device(const void *p) {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -128,8 +140,8 @@ In stage(Arena &ar, cudaStream_t s, const void *p, int64_t rows, int64_t cols, i
     r.ld = cols;
     r.host = true;
     if (d)
-        ELM_CUDA(cudaMemcpy2DAsync(d, cols * esz, p, ld * esz, cols * esz, rows,
-                                   cudaMemcpyHostToDevice, s));
+        copy2d(d, cols * esz, p, ld * esz, cols * esz, rows,
+                                   cudaMemcpyHostToDevice, s);
     return r;
 }
 
@@ -189,8 +201,8 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
     ELM_CUDA(cudaMemsetAsync(sv.tflag, 0, sizeof(int), s));
     trsm_prepare(s, R, ld, r, sv.DinvF, sv.DinvB);
     if (q > 0 && r > 0) {
-        ELM_CUDA(cudaMemcpy2DAsync(sv.K, q * sizeof(double), R + r, ld * sizeof(double),
-                                   q * sizeof(double), r, cudaMemcpyDeviceToDevice, s));
+        copy2d(sv.K, q * sizeof(double), R + r, ld * sizeof(double),
+                                   q * sizeof(double), r, cudaMemcpyDeviceToDevice, s);
         trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag);
         set_identity(s, sv.G2, q);
         gemm_f64(s, q, q, r, 1.0, sv.K, 1, q, sv.K, q, 1, 1.0, sv.G2, q);
@@ -343,8 +355,8 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
     const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyDeviceToHost;
-    ELM_CUDA(cudaMemcpy2DAsync(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
-                               m * sizeof(double), L, kind, s));
+    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
+                               m * sizeof(double), L, kind, s);
     ELM_CUDA(cudaStreamSynchronize(s));
     collect_phases(ctx);
 }
@@ -448,8 +460,8 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
     const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyDeviceToHost;
-    ELM_CUDA(cudaMemcpy2DAsync(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
-                               m * sizeof(double), L, kind, s));
+    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
+                               m * sizeof(double), L, kind, s);
     ELM_CUDA(cudaStreamSynchronize(s));
     collect_phases(ctx);
 }
@@ -557,8 +569,8 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
                        (const double *)bs.p, (const double *)as.p, L, act, out, ldo);
         }
         if (!dev_out) {
-            ELM_CUDA(cudaMemcpy2DAsync(Ht, ldh * 8, out, N * 8, N * 8, L,
-                                       cudaMemcpyDeviceToHost, s));
+            copy2d(Ht, ldh * 8, out, N * 8, N * 8, L,
+                                       cudaMemcpyDeviceToHost, s);
             ELM_CUDA(cudaStreamSynchronize(s));
         } else if (Xs.host || Ws.host || bs.host || as.host) {
             ELM_CUDA(cudaStreamSynchronize(s));
@@ -613,8 +625,8 @@ int elm_pinv_rank(elm_ctx *ctx, const double *Ht, int64_t L, int64_t N, int64_t 
             solver_apply(s, sv, Hd, H.ld, dst, ldd);
             if (solver_timed_out(s, sv)) throw ElmError(ELM_ERR_TIMEOUT, "solve wait expired");
             if (!dev_p)
-                ELM_CUDA(cudaMemcpy2DAsync(pinv_out, ldp * 8, pv, N * 8, N * 8, L,
-                                           cudaMemcpyDeviceToHost, s));
+                copy2d(pinv_out, ldp * 8, pv, N * 8, N * 8, L,
+                                           cudaMemcpyDeviceToHost, s);
         }
         ELM_CUDA(cudaStreamSynchronize(s));
     });
@@ -713,8 +725,8 @@ int elm_predict(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, 
                     (const double *)bs.p, (const double *)as.p, L, act,
                     (const double *)Bs.p, Bs.ld, m, out, ldo);
         if (!dev_out) {
-            ELM_CUDA(cudaMemcpy2DAsync(Y, ldy * 8, out, m * 8, m * 8, N,
-                                       cudaMemcpyDeviceToHost, s));
+            copy2d(Y, ldy * 8, out, m * 8, m * 8, N,
+                                       cudaMemcpyDeviceToHost, s);
             ELM_CUDA(cudaStreamSynchronize(s));
         } else if (Xs.host || Ws.host || bs.host || as.host || Bs.host) {
             ELM_CUDA(cudaStreamSynchronize(s));
