@@ -1,6 +1,7 @@
 // Internal declarations of libelm.so (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -170,6 +171,12 @@ void set_identity(cudaStream_t s, double *A, int64_t n);
 // Scan for non-finite entries; sets *flag = 1 if any.
 void check_finite(cudaStream_t s, const void *x, int xdt, int64_t rows, int64_t cols,
                   int64_t ld, int32_t *flag);
+
+// 2-D TMA map over a row-major FP64 matrix of `rows` x `cols` (row pitch
+// ld elements, 16-byte aligned base and pitch), box bx x by elements, no
+// swizzle; out-of-range rows and columns read as zero.
+CUtensorMap make_map_f64(const double *base, int64_t rows, int64_t cols, int64_t ld, int bx,
+                         int by);
 
 // ------------------------------------------- tensor-core digit products
 int64_t oz_pad(int64_t v, int64_t q);

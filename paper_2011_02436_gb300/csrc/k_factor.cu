@@ -272,6 +272,15 @@ __device__ __forceinline__ void bulk_s2c(uint32_t dst, const void *src, uint32_t
         "r"(su32(src)), "r"(bytes), "r"(bar)
         : "memory");
 }
+// one tile of a 2-D tensor map into this CTA's shared memory
+__device__ __forceinline__ void tma2d_g2s(const CUtensorMap *tm, uint64_t *bar, void *dst, int x,
+                                          int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+        "l"((uint64_t)tm), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
@@ -992,9 +1001,9 @@ __host__ __device__ constexpr size_t trsm_smem_bytes(int nown, int nsl, int CB) 
 // Waits are bounded; on expiry *tflag is set.
 template <bool REV, int CB>
 __global__ void __launch_bounds__(FT)
-trsm_kernel(const double *__restrict__ C, int64_t ldc, const double *__restrict__ Dinv,
-            int64_t r, double *__restrict__ B, int64_t ldb, int64_t q, int nown, int nsl,
-            int *tflag) {
+trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ C, int64_t ldc,
+            const double *__restrict__ Dinv, int64_t r, double *__restrict__ B, int64_t ldb,
+            int64_t q, int nown, int nsl, int *tflag) {
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks();
     const int cr = (int)cluster.block_rank();
@@ -1037,26 +1046,25 @@ trsm_kernel(const double *__restrict__ C, int64_t ldc, const double *__restrict_
             }
         }
     };
-    // warp 1: rows of C coupling block k_s with the own blocks to update
-    // (those inside the window nsl) into sl[s & 1]
+    // thread 0: the 32 x 32 tiles of C coupling block k_s with the own
+    // blocks to update (those inside the window nsl) into sl[s & 1], one
+    // tensor-map copy per tile (rows past r read as zero)
     auto fill_slab = [&](int64_t s) {
-        if (s >= nblk) return;
+        if (s >= nblk || threadIdx.x != 0) return;
         const int64_t k = blk(s);
-        const int nb = rows(k);
         const int buf = (int)(s & 1);
         int cnt = 0;
         for (int kl = 0; kl < nsl; kl++) cnt += later((int64_t)kl * CS + cr, k) ? 1 : 0;
-        if (lane == 0) {
-            if (cnt) mbar_expect(&bar_sl[buf], (uint32_t)cnt * (uint32_t)nb * TB_ * 8);
-            else mbar_arrive(&bar_sl[buf]);
+        if (!cnt) {
+            mbar_arrive(&bar_sl[buf]);
+            return;
         }
-        __syncwarp();
-        for (int e = lane; e < nsl * TB_; e += 32) {
-            const int kl = e / TB_, a = e % TB_;
+        mbar_expect(&bar_sl[buf], (uint32_t)cnt * TB_ * TB_ * 8);
+        for (int kl = 0; kl < nsl; kl++) {
             const int64_t k2 = (int64_t)kl * CS + cr;
-            if (a >= nb || !later(k2, k)) continue;
-            bulk_g2s(sl + (((size_t)buf * nsl + kl) * TB_ + a) * TB_,
-                     C + (k * TB_ + a) * ldc + k2 * TB_, TB_ * 8, &bar_sl[buf]);
+            if (!later(k2, k)) continue;
+            tma2d_g2s(&tmC, &bar_sl[buf], sl + ((size_t)buf * nsl + kl) * TB_ * TB_,
+                      (int)(k2 * TB_), (int)(k * TB_));
         }
     };
     auto wait = [&](uint64_t *bar, uint32_t parity) {
@@ -1142,10 +1150,9 @@ trsm_kernel(const double *__restrict__ C, int64_t ldc, const double *__restrict_
     if (threadIdx.x < NS && threadIdx.x < nblk && owner_of(threadIdx.x) != cr)
         mbar_expect(&bar_x[threadIdx.x], XBYTES);
     cluster.sync();
-    if (warp == 1) {
+    if (warp == 1)
         for (int i = 0; i < NDG - 1; i++) fill_diag(i);
-        fill_slab(0);
-    }
+    fill_slab(0);
     if (nblk > 0 && owner_of(0) == cr) solve_send(0);
 
     for (int64_t s = 0; s < nblk; s++) {
@@ -1195,9 +1202,9 @@ trsm_kernel(const double *__restrict__ C, int64_t ldc, const double *__restrict_
         }
         __syncthreads();   // slot s, slab s read; bs updated
         if (threadIdx.x == 0 && !mine && s + NS < nblk) mbar_expect(&bar_x[slot], XBYTES);
-        if (warp == 1 && !s_abort) {
+        if (!s_abort) {
             fill_slab(s + 1);
-            fill_diag(s + NDG - 1);
+            if (warp == 1) fill_diag(s + NDG - 1);
         }
     }
     cluster.sync();   // every bulk copy between CTAs has landed
@@ -1414,7 +1421,8 @@ static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const doub
             }
             g_tcluster = cs;
         }
-        ELM_CUDA(cudaLaunchKernelEx(&cfg, k, C, ldc, Dinv, r, B, ldb, q, nown, nsl, tflag));
+        const CUtensorMap tmC = make_map_f64(C, r, ldc, ldc, TB_, TB_);
+        ELM_CUDA(cudaLaunchKernelEx(&cfg, k, tmC, C, ldc, Dinv, r, B, ldb, q, nown, nsl, tflag));
         ELM_CHECK_LAUNCH();
         return;
     }

@@ -949,6 +949,23 @@ void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B
 
 }  // namespace
 
+CUtensorMap make_map_f64(const double *base, int64_t rows, int64_t cols, int64_t ld, int bx,
+                         int by) {
+    if (((uintptr_t)base & 15) || (ld * 8) % 16)
+        throw ElmError(ELM_ERR_ARG, "matrix misaligned for TMA");
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 8)};
+    cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void *)base, dims, strides,
+                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw ElmError(ELM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return m;
+}
+
 // Digit counts, digit widths and kept pairs (p + q <= TMAX) of the two
 // products.  Pre-activation: 6 digits of 7 bits (operand grid 2^-41; one
 // exact chunk for up to 1024 inputs).  Gram: 5 digits of 7 bits (H on a
