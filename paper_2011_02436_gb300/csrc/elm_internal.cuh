@@ -119,6 +119,7 @@ struct FactorWs {
     double *Rrow;          // L x L pivot rows in original column order
     double *P;             // nb x L panel rows (active index space)
     double *dS;            // L diagonal of S
+    double *sc;            // L equilibration scales 1/sqrt(S_jj)
     int32_t *act0, *act1;  // active -> original index maps
     int32_t *rem;          // compaction map of the last panel
     int32_t *perm;         // pivot order

@@ -190,36 +190,42 @@ struct PanelArith<true> {
 };
 
 // S -> A = diag(s) S diag(s), s_j = 1/sqrt(S_jj) (0 if S_jj <= 0); dS = diag(S).
-template <bool DF>
-__global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t L,
-                             double *__restrict__ A, int64_t lda, double *__restrict__ dS,
-                             int32_t *__restrict__ act, FactorState *st) {
-    int64_t total = L * L;
-    int bad = 0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = e / L, l = e % L;
-        double dj = S[j * lds + j], dl = S[l * lds + l];
-        double sj = dj > 0.0 ? 1.0 / sqrt(dj) : 0.0;
-        double sl = dl > 0.0 ? 1.0 / sqrt(dl) : 0.0;
-        double v = S[j * lds + l];
-        bad |= !isfinite(v);
-        const double a = (v * sj) * sl;
-        if (DF) reinterpret_cast<F2 *>(A)[j * lda + l] = d2df(a);
-        else A[j * lda + l] = a;
-        if (l == 0) {
-            dS[j] = dj;
-            act[j] = (int32_t)j;
-        }
+// s_j = 1/sqrt(S_jj) (0 if S_jj <= 0), dS = diag(S), act = identity, and
+// the factorisation state; one thread per column.
+__global__ void equil_scale_kernel(const double *__restrict__ S, int64_t lds, int64_t L,
+                                   double *__restrict__ sc, double *__restrict__ dS,
+                                   int32_t *__restrict__ act, FactorState *st) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < L) {
+        const double dj = S[j * lds + j];
+        sc[j] = dj > 0.0 ? 1.0 / sqrt(dj) : 0.0;
+        dS[j] = dj;
+        act[j] = (int32_t)j;
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, 1);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (j == 0) {
         st->k = 0;
         st->Lr = L;
         st->rank = L;
         st->done = 0;
         st->steps = 0;
+        st->flags = 0;
     }
+}
+// S -> A = diag(s) S diag(s) (row j = blockIdx.y), as FP64 or double-float
+template <bool DF>
+__global__ void equil_kernel(const double *__restrict__ S, int64_t lds, int64_t L,
+                             const double *__restrict__ sc, double *__restrict__ A, int64_t lda,
+                             FactorState *st) {
+    const int64_t j = blockIdx.y, l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int bad = 0;
+    if (l < L) {
+        const double v = S[j * lds + l];
+        bad = !isfinite(v);
+        const double a = (v * sc[j]) * sc[l];
+        if (DF) reinterpret_cast<F2 *>(A)[j * lda + l] = d2df(a);
+        else A[j * lda + l] = a;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, 1);
 }
 
 // ------------------------------------------------------------ panel
@@ -1283,6 +1289,7 @@ FactorWs factor_ws_carve(Arena &ar, int64_t L) {
     w.Rrow = ar.take<double>(L * L);
     w.P = ar.take<double>((int64_t)MAXNB * L);
     w.dS = ar.take<double>(L);
+    w.sc = ar.take<double>(L);
     w.act0 = ar.take<int32_t>(L);
     w.act1 = ar.take<int32_t>(L);
     w.rem = ar.take<int32_t>(L);
@@ -1321,10 +1328,12 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     ELM_CUDA(cudaMemsetAsync(w.st, 0, sizeof(FactorState), s));
     ELM_CUDA(cudaMemsetAsync(w.Rrow, 0, sizeof(double) * L * L, s));
     {
-        int64_t blocks = (L * L + 255) / 256;
-        if (blocks > 8 * 1024) blocks = 8 * 1024;
-        if (df) equil_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(S, lds, L, w.A0, L, w.dS, w.act0, w.st);
-        else equil_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(S, lds, L, w.A0, L, w.dS, w.act0, w.st);
+        equil_scale_kernel<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(S, lds, L, w.sc, w.dS,
+                                                                       w.act0, w.st);
+        ELM_CHECK_LAUNCH();
+        const dim3 g((unsigned)((L + 255) / 256), (unsigned)L);
+        if (df) equil_kernel<true><<<g, 256, 0, s>>>(S, lds, L, w.sc, w.A0, L, w.st);
+        else equil_kernel<false><<<g, 256, 0, s>>>(S, lds, L, w.sc, w.A0, L, w.st);
         ELM_CHECK_LAUNCH();
     }
     const int64_t npanels = (L + nb - 1) / nb;
