@@ -116,7 +116,7 @@ typedef struct elm_problem {
 
 typedef struct elm_train_opts {
     int32_t precision;  /* ELM_PREC_FP64 or ELM_PREC_MIXED                   */
-    int32_t max_refine; /* refinement steps (< 0: default 2 FP64, 4 mixed)   */
+    int32_t max_refine; /* refinement steps (< 0: default 2 FP64, 6 mixed)   */
     double tol_rank;    /* rank threshold on the unit-diagonal scale (<=0: L*2^-52
                            for FP64, max(L*2^-52, 2^-32) for MIXED, whose Gram
                            is exact up to dropped digit pairs below 2^-34)   */
@@ -142,8 +142,11 @@ typedef struct elm_result {
  * H^T H and H^T T, pivoted rank decision, beta = H^+ T through the
  * full-rank factorisation H P = H1 [I K] (beta = P [I; K^T] (I + K K^T)^{-1}
  * (H1^T H1)^{-1} H1^T T), then refinement steps with the residual
- * T - H beta.  opts may be NULL (FP64 defaults).  results: host array of
- * `count` entries, or NULL.  Returns ELM_OK or the first failing status.
+ * H^T (T - H beta).  opts may be NULL (FP64 defaults).  results: host array
+ * of `count` entries, or NULL.  Returns ELM_OK or the first failing status.
+ * ELM_PREC_MIXED trains a problem in the FP64 form instead when its
+ * tensor-core Gram cannot settle it: a rejected pivot above the FP64 rank
+ * threshold, or refinement that does not reach refine_tol.
  */
 int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
               const elm_train_opts *opts, elm_result *results);

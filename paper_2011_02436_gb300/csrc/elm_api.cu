@@ -245,11 +245,12 @@ bool solver_timed_out(cudaStream_t s, const Solver &sv) {
     return f != 0;
 }
 
-int64_t read_rank(cudaStream_t s, const FactorWs &f, int32_t *flags) {
+int64_t read_rank(cudaStream_t s, const FactorWs &f, int32_t *flags, double *stop_val = nullptr) {
     FactorState st;
     ELM_CUDA(cudaMemcpyAsync(&st, f.st, sizeof st, cudaMemcpyDeviceToHost, s));
     ELM_CUDA(cudaStreamSynchronize(s));
     if (flags) *flags = st.flags;
+    if (stop_val) *stop_val = st.stop_val;
     return st.rank;
 }
 
@@ -266,6 +267,7 @@ struct Problem {
     int prec;
     int max_refine;
     double tau;
+    double tau64;      // the FP64 form's rank threshold L 2^-52 (unit-diagonal scale)
     double refine_tol;
 };
 
@@ -365,15 +367,25 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
 // cores (Gram accurate to FP64 rounding of the 2^-31-grid H), rank decision,
 // factorisation and solves in FP64, then refinement steps on the normal
 // equations with the FP64 residual Z - S beta.
+// Mixed form: H, H^T H and H^T T from exact digit slices on the tensor
+// cores (the Gram is that of H on a 2^-34 grid), rank decision and
+// factorisation in double-float, FP64 solves, then refinement steps whose
+// residual G = H^T (T - H beta) reads H itself, kept in double-float
+// (about 2^-43), so the steps converge to the least-squares solution of
+// the accurate H, not of the grid H.  Two cases the grid Gram cannot
+// settle fall back to the FP64 form for that problem: a rejected pivot
+// above the FP64 threshold L 2^-52 (the FP64 rank rule might keep it), and
+// refinement that does not reach refine_tol (H too ill-conditioned for a
+// Gram accurate to 2^-34 to precondition the steps).
 void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     const elm_problem &pb = *P.p;
     cudaStream_t s = ctx->stream;
     const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
     const int64_t Lt = L + m, Lp = oz_pad(Lt, 128);
     const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
-    const int hs_split = htr_f64_nsplit(L, L, ctx->sm_count);
+    const int hs_split = htr_df_nsplit(L, N, ctx->sm_count);
     In X, W, b, a, T;
-    double *hs, *G, *R, *Rt, *beta, *dB, *SB, *Gres, *hpart, *norms;
+    double *hs, *G, *R, *Rt, *beta, *dB, *Rres, *Gres, *hpart, *norms, *Hdf, *betaT;
     __nv_bfloat16 *planes;
     int32_t *flag;
     int *err;
@@ -389,13 +401,15 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         hs = ar.take<double>(Lp);
         G = ar.take<double>(Lt * Lt);
         hw = oz_hid_carve(ar, N, n, L, m);
+        Hdf = ar.take<double>(N * L);    // H as double-float pairs, eight bytes each
         R = ar.take<double>(L * tri_ld(L));
         Rt = ar.take<double>(L * tri_ld(L));
         beta = ar.take<double>(L * m);
         dB = ar.take<double>(L * m);
-        SB = ar.take<double>(L * m);
+        Rres = ar.take<double>(N * m);
         Gres = ar.take<double>(L * m);
-        hpart = ar.take<double>(htr_f64_ws(L, m, hs_split));
+        hpart = ar.take<double>((int64_t)hs_split * L * m);
+        betaT = ar.take<double>(L * (m < 32 ? m : 32));
         norms = ar.take<double>(2);
         flag = ar.take<int32_t>(1);
         err = ar.take<int>(1);
@@ -408,9 +422,9 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
                  *ad = (const double *)a.p, *Td = (const double *)T.p;
     mark(ctx, 0);
     // Algorithm 1 step 2 (Eq. 1, 3): pre-activation on the tensor cores,
-    // activation in the epilogue, digit planes of H
+    // activation in the epilogue, digit planes of H and H itself
     oz_hidden(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, pb.act, L, m, planes, hs,
-              nullptr, 0, err);
+              nullptr, 0, err, Hdf);
     // digit rows of the targets beside those of H (part of the hidden phase,
     // so the Gram phase times the Gram kernel alone)
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
@@ -418,12 +432,13 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
     oz_gram(s, planes, hs, N, L, m, G, Lt, err);
     mark(ctx, 2);
-    // Eq. 6, Algorithm 1 steps 3-4 (FP64)
+    // Eq. 6, Algorithm 1 steps 3-4 (double-float)
     factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
     int terr = 0;
-    const int64_t r = read_rank(s, f, &fl);
+    double stop_val = 0.0;
+    const int64_t r = read_rank(s, f, &fl, &stop_val);
     ELM_CUDA(cudaMemcpy(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost));
     ELM_CUDA(cudaMemcpy(&terr, err, sizeof terr, cudaMemcpyDeviceToHost));
     res->rank = r;
@@ -438,30 +453,47 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         res->status = ELM_ERR_NUMERIC;
         return;
     }
-    const double *S = G, *Z = G + L;   // Z[l, c] = G[l, L + c]
+    auto fallback = [&]() {
+        Problem P64 = P;
+        P64.prec = ELM_PREC_FP64;
+        P64.max_refine = 2;
+        P64.tau = P.tau64;
+        P64.refine_tol = 1e-12;
+        train_one(ctx, P64, res);
+    };
+    if (r < L && stop_val > P.tau64) return fallback();
+    const double *Z = G + L;   // Z[l, c] = G[l, L + c]
     // Eq. 5, Eq. 7 (FP64)
     const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m);
     solver_apply(s, sv, Z, Lt, beta, m);
     mark(ctx, 4);
     double nrm[2] = {0.0, 0.0};
+    bool converged = P.max_refine == 0;
     for (int it = 0; it < P.max_refine; it++) {
-        htr_f64(s, S, Lt, L, L, beta, m, SB, hpart, hs_split);   // S beta
-        sub_rows(s, Z, Lt, SB, L, m, Gres);                      // Z - S beta
+        resid_df(s, Hdf, L, N, beta, m, Td, T.ld, Rres, betaT);        // T - H beta (pairs)
+        htr_df(s, Hdf, L, N, Rres, m, Gres, hpart, hs_split);           // H^T (T - H beta)
         solver_apply(s, sv, Gres, m, dB, m);
         axpy_norms(s, beta, dB, L * m, norms);
         ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
         ELM_CUDA(cudaStreamSynchronize(s));
         res->refine_iters = it + 1;
         res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
-        if (res->rel_update <= P.refine_tol) break;
+        if (res->rel_update <= P.refine_tol) {
+            converged = true;
+            break;
+        }
     }
     mark(ctx, 5);
+    if (solver_timed_out(s, sv)) {
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if (!converged) return fallback();
     if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
-    if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
     const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyDeviceToHost;
-    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
-                               m * sizeof(double), L, kind, s);
+    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double), m * sizeof(double), L,
+           kind, s);
     ELM_CUDA(cudaStreamSynchronize(s));
     collect_phases(ctx);
 }
@@ -659,11 +691,12 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             P.p = &probs[i];
             P.prec = o.precision;
             P.max_refine = o.max_refine >= 0 ? o.max_refine
-                                             : (o.precision == ELM_PREC_FP64 ? 2 : 4);
+                                             : (o.precision == ELM_PREC_FP64 ? 2 : 6);
             // default rank threshold on the unit-diagonal scale: L 2^-52 for
             // the FP64 Gram; the mixed Gram drops digit pairs below 2^-34 of
             // the leading term, so its threshold sits above that level
             const double tau64 = (double)probs[i].L * ldexp(1.0, -52);
+            P.tau64 = o.tol_rank > 0.0 ? o.tol_rank : tau64;
             P.tau = o.tol_rank > 0.0 ? o.tol_rank
                                      : (o.precision == ELM_PREC_MIXED ? fmax(tau64, ldexp(1.0, -32))
                                                                       : tau64);

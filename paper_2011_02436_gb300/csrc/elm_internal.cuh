@@ -43,6 +43,7 @@ struct FactorState {
     int32_t done;     // 1 once the stopping rule fired or all columns pivoted
     int32_t flags;    // bit 0: non-finite value met; bit 1: a bounded wait expired
     int64_t steps;    // pivots taken by the last panel
+    double stop_val;  // largest rejected diagonal (unit-diagonal scale), 0 if none
 };
 
 // Bump allocator over the context's device workspace.  With base == nullptr
@@ -106,6 +107,17 @@ int htr_f64_nsplit(int64_t L, int64_t N, int sms);
 void htr_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
              int64_t N, const double *R, int64_t m, double *G, double *part,
              int nsplit);
+
+// The refinement products of the mixed form with H (N x L, sample-major)
+// held as double-float pairs: Rd = T - H beta (N x m pairs; betaT scratch of
+// L x min(m, 32) pairs) and G = H^T Rd (L x m) through
+// htr_df_nsplit(L, N, sms) x L x m doubles of partial sums; double-float
+// arithmetic, targets in passes of up to 32.
+void resid_df(cudaStream_t s, const void *H, int64_t L, int64_t N, const double *beta,
+              int64_t m, const double *T, int64_t ldt, void *Rd, void *betaT);
+int htr_df_nsplit(int64_t L, int64_t N, int sms);
+void htr_df(cudaStream_t s, const void *H, int64_t L, int64_t N, const void *Rd, int64_t m,
+            double *G, double *part, int nsplit);
 
 // Fused prediction Y = g(X W + b) beta (FP64).
 void predict_f64(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n,
@@ -195,12 +207,14 @@ OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m);
 size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m);
 // H = a g(X W + b): pre-activation from exact digit slices on the tensor
 // cores, activation in double-float in the epilogue, written straight into
-// the Gram digit planes (rows < L, zero padding) with row scales hs, and as
-// FP64 H^T when Ht != NULL.  *err set on a device-side timeout.
+// the Gram digit planes (rows < L, zero padding) with row scales hs, as
+// FP64 H^T (row stride ldh) when Ht != NULL, and as double-float H (N x L,
+// sample-major, eight bytes per element, about 2^-43 relative) when
+// Hdf != NULL.  *err set on a device-side timeout.
 void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
-               int64_t ldh, int *err);
+               int64_t ldh, int *err, void *Hdf = nullptr);
 // T -> digit plane rows L .. L+m-1.
 void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
                  __nv_bfloat16 *planes, double *hs);

@@ -10,6 +10,9 @@
 // outputs.
 #include <math.h>
 
+#include <type_traits>
+
+#include "df_arith.cuh"
 #include "elm_internal.cuh"
 
 namespace elm {
@@ -291,6 +294,110 @@ htr_f64_kernel(const double *__restrict__ Ht, int64_t ldh, int64_t L,
             if (c0 + c < m) part[((int64_t)blockIdx.y * L + j) * m + c0 + c] = acc[c];
 }
 
+// The refinement products of the mixed form with H (N x L, sample-major)
+// held as double-float pairs: Rd = T - H beta (pairs) and G = H^T Rd, every
+// product a TwoProduct and every sum a TwoSum on the FP32 pipes (about
+// 2^-44 relative), so the residual is as accurate as the H it reads.  RC
+// (a compile-time count >= the targets) keeps the accumulators in
+// registers.
+
+// betaT[c, j] = beta[j, c0 + c] as pairs (c < mc)
+__global__ void beta_pairs_kernel(const double *__restrict__ beta, int64_t L, int64_t m,
+                                  int64_t c0, int64_t mc, df::F2 *__restrict__ betaT) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= L * mc) return;
+    const int64_t c = e / L, j = e % L;
+    betaT[e] = df::d2df(beta[j * m + c0 + c]);
+}
+
+// Rd[i, :] = T[i, :] - H[i, :] beta: one warp per SPW samples, lanes over
+// the neurons (coalesced rows of H and of betaT, each betaT value reused by
+// the warp's SPW samples from registers), warp reductions
+template <int RC>
+constexpr int spw_for() { return RC <= 10 ? 4 : (RC <= 16 ? 2 : 1); }   // register budget
+template <int RC, int SPW = spw_for<RC>()>
+__global__ void __launch_bounds__(256)
+resid_df_kernel(const df::F2 *__restrict__ H, int64_t L, int64_t N,
+                const df::F2 *__restrict__ betaT, int64_t m, int64_t c0, int mc,
+                const double *__restrict__ T, int64_t ldt, df::F2 *__restrict__ Rd) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = ((int64_t)blockIdx.x * 8 + warp) * SPW;
+    if (i0 >= N) return;   // warp-uniform
+    float ah[SPW][RC], al[SPW][RC];
+#pragma unroll
+    for (int q = 0; q < SPW; q++)
+#pragma unroll
+        for (int c = 0; c < RC; c++) ah[q][c] = al[q][c] = 0.f;
+    for (int64_t j = lane; j < L; j += 32) {
+        df::F2 bv[RC];
+#pragma unroll
+        for (int c = 0; c < RC; c++) bv[c] = c < mc ? betaT[c * L + j] : df::F2{0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < SPW; q++) {
+            const int64_t i = i0 + q;
+            const df::F2 h = i < N ? H[i * L + j] : df::F2{0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < RC; c++) df::df_acc_prod(ah[q][c], al[q][c], h, bv[c]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < SPW; q++) {
+        const int64_t i = i0 + q;
+#pragma unroll
+        for (int c = 0; c < RC; c++) {
+            if (c >= mc) break;
+            df::F2 v = df::df_renorm(ah[q][c], al[q][c]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const df::F2 w{__shfl_xor_sync(0xffffffffu, v.h, o),
+                               __shfl_xor_sync(0xffffffffu, v.l, o)};
+                v = df::df_add(v, w);
+            }
+            if (lane == 0 && i < N)
+                Rd[i * m + c0 + c] = df::df_add(df::d2df(T[i * ldt + c0 + c]), df::df_neg(v));
+        }
+    }
+}
+
+// part[p, j, :] = sum over the samples of split p of H[i, j] Rd[i, :]: one
+// thread per neuron (coalesced rows of H), the split's Rd rows staged in
+// shared memory (broadcast reads)
+constexpr int HT_ROWS = 64;
+template <int RC>
+__global__ void __launch_bounds__(256)
+htr_df_kernel(const df::F2 *__restrict__ H, int64_t L, int64_t N, const df::F2 *__restrict__ Rd,
+              int64_t m, int64_t c0, int mc, double *__restrict__ part, int64_t chunk) {
+    __shared__ df::F2 Rs[HT_ROWS][RC];
+    const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t ib = (int64_t)blockIdx.y * chunk, ie = min(N, ib + chunk);
+    float ah[RC], al[RC];
+#pragma unroll
+    for (int c = 0; c < RC; c++) ah[c] = al[c] = 0.f;
+    for (int64_t i0 = ib; i0 < ie; i0 += HT_ROWS) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < HT_ROWS * RC; e += 256) {
+            const int ii = e / RC, cc = e % RC;
+            const int64_t i = i0 + ii;
+            Rs[ii][cc] = (i < ie && cc < mc) ? Rd[i * m + c0 + cc] : df::F2{0.f, 0.f};
+        }
+        __syncthreads();
+        if (j < L) {
+            const int in = (int)min((int64_t)HT_ROWS, ie - i0);
+#pragma unroll 2
+            for (int ii = 0; ii < in; ii++) {
+                const df::F2 h = H[(i0 + ii) * L + j];
+#pragma unroll
+                for (int c = 0; c < RC; c++) df::df_acc_prod(ah[c], al[c], h, Rs[ii][c]);
+            }
+        }
+    }
+    if (j < L)
+#pragma unroll
+        for (int c = 0; c < RC; c++)
+            if (c < mc)
+                part[((int64_t)blockIdx.y * L + j) * m + c0 + c] = df::f2d(ah[c]) + df::f2d(al[c]);
+}
+
 __global__ void split_sum_kernel(const double *__restrict__ part, int nsplit,
                                  int64_t count, double *__restrict__ out) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,6 +674,63 @@ void htr_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
     dim3 grid((unsigned)((L + 7) / 8), (unsigned)nsplit, (unsigned)((m + RC - 1) / RC));
     htr_f64_kernel<<<grid, 256, 0, s>>>(Ht, ldh, L, N, R, m, part, chunk);
     ELM_CHECK_LAUNCH();
+    split_sum_kernel<<<blocks_for(L * m), 256, 0, s>>>(part, nsplit, L * m, G);
+    ELM_CHECK_LAUNCH();
+}
+
+// targets per pass: the smallest compile-time count covering m (32 above)
+template <class F>
+static void with_rc(int64_t m, F &&f) {
+    if (m <= 2) f(std::integral_constant<int, 2>());
+    else if (m <= 4) f(std::integral_constant<int, 4>());
+    else if (m <= 6) f(std::integral_constant<int, 6>());
+    else if (m <= 8) f(std::integral_constant<int, 8>());
+    else if (m <= 10) f(std::integral_constant<int, 10>());
+    else if (m <= 12) f(std::integral_constant<int, 12>());
+    else if (m <= 16) f(std::integral_constant<int, 16>());
+    else if (m <= 20) f(std::integral_constant<int, 20>());
+    else if (m <= 26) f(std::integral_constant<int, 26>());
+    else f(std::integral_constant<int, 32>());
+}
+
+void resid_df(cudaStream_t s, const void *H, int64_t L, int64_t N, const double *beta,
+              int64_t m, const double *T, int64_t ldt, void *Rd, void *betaT) {
+    for (int64_t c0 = 0; c0 < m; c0 += 32) {   // targets in passes of up to 32
+        const int64_t mc = m - c0 < 32 ? m - c0 : 32;
+        beta_pairs_kernel<<<blocks_for(L * mc), 256, 0, s>>>(beta, L, m, c0, mc, (df::F2 *)betaT);
+        ELM_CHECK_LAUNCH();
+        with_rc(mc, [&](auto rc) {
+            constexpr int RC = decltype(rc)::value;
+            constexpr int SPW = spw_for<RC>();
+            resid_df_kernel<RC><<<(unsigned)((N + 8 * SPW - 1) / (8 * SPW)), 256, 0, s>>>(
+                (const df::F2 *)H, L, N, (const df::F2 *)betaT, m, c0, (int)mc, T, ldt,
+                (df::F2 *)Rd);
+        });
+        ELM_CHECK_LAUNCH();
+    }
+}
+
+int htr_df_nsplit(int64_t L, int64_t N, int sms) {
+    const int64_t blocks = (L + 255) / 256;
+    int64_t ns = (8 * (int64_t)sms + blocks - 1) / blocks;
+    const int64_t cap = (N + HT_ROWS - 1) / HT_ROWS;
+    if (ns > cap) ns = cap;
+    return (int)(ns < 1 ? 1 : ns);
+}
+
+void htr_df(cudaStream_t s, const void *H, int64_t L, int64_t N, const void *Rd, int64_t m,
+            double *G, double *part, int nsplit) {
+    const int64_t chunk = ((N + nsplit - 1) / nsplit + HT_ROWS - 1) / HT_ROWS * HT_ROWS;
+    for (int64_t c0 = 0; c0 < m; c0 += 32) {
+        const int64_t mc = m - c0 < 32 ? m - c0 : 32;
+        with_rc(mc, [&](auto rc) {
+            constexpr int RC = decltype(rc)::value;
+            dim3 grid((unsigned)((L + 255) / 256), (unsigned)nsplit);
+            htr_df_kernel<RC><<<grid, 256, 0, s>>>((const df::F2 *)H, L, N, (const df::F2 *)Rd,
+                                                   m, c0, (int)mc, part, chunk);
+        });
+        ELM_CHECK_LAUNCH();
+    }
     split_sum_kernel<<<blocks_for(L * m), 256, 0, s>>>(part, nsplit, L * m, G);
     ELM_CHECK_LAUNCH();
 }

@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include "df_arith.cuh"
 #include "elm_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -26,6 +27,7 @@ namespace cg = cooperative_groups;
 namespace elm {
 
 namespace {
+using namespace df;
 
 constexpr int FT = 256;       // threads per CTA in the panel / solves
 constexpr int MAXNB = 32;     // largest panel width of the data structures
@@ -41,42 +43,6 @@ __device__ __forceinline__ unsigned long long dkey(double v) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
-// ------------------------------------------------------------ double-float
-// Storage of the active matrix in the mixed form: v = h + l, two floats in
-// the eight bytes of a double.  The conversions use integer moves only (an
-// FP64 instruction costs a 64-cycle issue slot per SM sub-partition).
-struct F2 {
-    float h, l;
-};
-// h = v truncated to 24 significant bits, l = the remainder truncated to 24
-// bits: |v - h - l| < 2^-47 |v| for |v| >= 2^-70; magnitudes below 2^-126
-// (and the part of l below it) are dropped.
-__device__ __forceinline__ F2 d2df(double v) {
-    const uint64_t b = (uint64_t)__double_as_longlong(v);
-    const uint32_t sgn = (uint32_t)(b >> 63) << 31;
-    const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    F2 r{0.f, 0.f};
-    if (e < -126) return r;
-    r.h = __uint_as_float(sgn | ((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffff));
-    const uint64_t m = b & 0x1fffffffull;   // the low 29 mantissa bits
-    if (m == 0) return r;
-    const int top = 63 - __clzll((long long)m);
-    const int el = e - 52 + top;
-    if (el < -126) return r;
-    const uint32_t mant = top >= 23 ? (uint32_t)(m >> (top - 23)) & 0x7fffff
-                                    : (uint32_t)(m << (23 - top)) & 0x7fffff;
-    r.l = __uint_as_float(sgn | ((uint32_t)(el + 127) << 23) | mant);
-    return r;
-}
-// exact value of a normal float (or zero) as a double
-__device__ __forceinline__ double f2d(float x) {
-    const uint32_t b = __float_as_uint(x);
-    const uint32_t ef = (b >> 23) & 0xff;
-    if (ef == 0) return 0.0;
-    return __longlong_as_double((long long)(((uint64_t)(b >> 31) << 63) |
-                                            ((uint64_t)(ef - 127 + 1023) << 52) |
-                                            ((uint64_t)(b & 0x7fffff) << 29)));
-}
 // 1/sqrt(v) to FP64 accuracy for v > 0 within the float exponent range.
 // The seed y0 = rsqrtf(v) (about 22 bits) is formed with integer moves
 // instead of FP64 conversions (each FP64 instruction costs one 64-cycle
@@ -97,37 +63,6 @@ __device__ __forceinline__ double rsqrt64(double v) {
     return fma(y0 * r, fma(0.375, r, 0.5), y0);
 }
 
-// Double-float arithmetic (Knuth's TwoSum, Dekker's FastTwoSum, TwoProduct
-// by FMA): about 2^-44 relative, all on the FP32 pipes.
-__device__ __forceinline__ F2 df_renorm(float s, float e) {   // |s| >= |e|
-    const float h = s + e;
-    return F2{h, e - (h - s)};
-}
-__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
-    const float s = a.h + b.h;
-    const float bb = s - a.h;
-    const float e = ((a.h - (s - bb)) + (b.h - bb)) + (a.l + b.l);
-    return df_renorm(s, e);
-}
-__device__ __forceinline__ F2 df_neg(F2 a) { return F2{-a.h, -a.l}; }
-__device__ __forceinline__ F2 df_mul(F2 a, F2 b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    return df_renorm(p, e);
-}
-// (sh, sl) += a b, left unnormalised (renormalise after a run of terms)
-__device__ __forceinline__ void df_acc_prod(float &sh, float &sl, F2 a, F2 b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    const float s = sh + p;
-    const float bb = s - sh;
-    sl += ((sh - (s - bb)) + (p - bb)) + e;
-    sh = s;
-}
 // 1/sqrt(v), v > 0: float seed y0, then the third-order step
 // y0 + y0 r (1/2 + 3/8 r) with r = 1 - v y0^2 formed in double-float
 // (y0^2 is exact as a TwoProduct).
@@ -209,6 +144,7 @@ __global__ void equil_scale_kernel(const double *__restrict__ S, int64_t lds, in
         st->done = 0;
         st->steps = 0;
         st->flags = 0;
+        st->stop_val = 0.0;
     }
 }
 // S -> A = diag(s) S diag(s) (row j = blockIdx.y), as FP64 or double-float
@@ -504,6 +440,13 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
         }
         warp_best(bk, bo);
         if (!(bk > tau_key)) {   // largest remaining diagonal <= tau (or none, or NaN)
+            if (cr == 0 && threadIdx.x == 0) {
+                double sv = 0.0;
+                if (bk != 0ull)
+                    sv = AR::to_double(*reinterpret_cast<const T *>(
+                        &slots[buf][(int)((int64_t)(bo & 0x3fffu) / Wd)].val));
+                st->stop_val = sv;
+            }
             done = true;
             break;
         }

@@ -241,6 +241,8 @@ struct ActParams {
     const float *csf;       // per-sample scales as floats
     const float4 *rowc;     // per hidden row: {rowf, 1/hs, b hi, b lo}, {a hi, a lo, scaled, 0}
     double *Ht;             // optional FP64 H^T (row j, column i)
+    float2 *Hdf;            // optional H as double-float pairs, sample-major: [n * ldhd + m]
+    int64_t ldhd;
     int64_t ldh;
 };
 
@@ -338,9 +340,10 @@ __device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R,
             hv = sigmoid_df(z, A.tab);
         }
         if (R.scaled) hv = df_mul(hv, R.aj);
-        hv.h = on ? hv.h * R.inv_hs : 0.f;
-        hv.l = on ? hv.l * R.inv_hs : 0.f;
         if (on && A.Ht) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
+        if (on && A.Hdf) A.Hdf[n * A.ldhd + m] = make_float2(hv.h, hv.l);   // lanes: consecutive m
+        hv.h = on ? hv.h * R.inv_hs : 0.f;   // the digit planes hold H / hs
+        hv.l = on ? hv.l * R.inv_hs : 0.f;
         // balanced digits of h~ on the 2^-34 grid, most significant first:
         // d = rint(r 2^B), r <- r 2^B - d, carried in double-float
         float rh = hv.h * (float)(1 << (GRAM_BITS_ - 1));
@@ -998,7 +1001,7 @@ size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m) {
 void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
-               int64_t ldh, int *err) {
+               int64_t ldh, int *err, void *Hdf) {
     const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
     if (xdt == ELM_F64)
         digits_rows_kernel<HID_PX, HID_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
@@ -1046,6 +1049,8 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ap.csf = w.xsf;
     P.ap.rowc = w.rowc;
     P.ap.Ht = Ht;
+    P.ap.Hdf = (float2 *)Hdf;
+    P.ap.ldhd = L;
     P.ap.ldh = ldh;
     launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P,
                                                            (Lp / BM) * (Np / BN));

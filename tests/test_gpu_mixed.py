@@ -30,14 +30,15 @@ def ctx(elm):
     c.close()
 
 
-@pytest.mark.parametrize("N,n,L,xdt,act,kind", [
-    (1037, 13, 120, np.float32, 0, "normal"),
-    (300, 784, 333, np.float32, 0, "uniform01"),
-    (65, 5, 7, np.float64, 1, "uniform11"),
+@pytest.mark.parametrize("N,n,L,xdt,act,kind,n_scaled", [
+    (1037, 13, 120, np.float32, 0, "normal", 0),
+    (300, 784, 333, np.float32, 0, "uniform01", 0),
+    (65, 5, 7, np.float64, 1, "uniform11", 0),
+    (777, 21, 90, np.float32, 1, "normal", 9),      # power-of-two output scales a_j
 ])
-def test_hidden_tensor_core_matches_oracle(elm, ctx, N, n, L, xdt, act, kind):
-    p = synth.make_problem(N, n, L, 3, n_dup=min(7, L // 3), x_dtype=xdt, act=act, x_kind=kind,
-                           x_sparsity=0.8 if n == 784 else 0.0)
+def test_hidden_tensor_core_matches_oracle(elm, ctx, N, n, L, xdt, act, kind, n_scaled):
+    p = synth.make_problem(N, n, L, 3, n_dup=min(7, L // 3), n_scaled=n_scaled, x_dtype=xdt,
+                           act=act, x_kind=kind, x_sparsity=0.8 if n == 784 else 0.0)
     t = to_dev(p)
     Lt = p["L"]
     Ht = elm.elm_hidden(ctx, t["X"], t["W"], t["b"], t["a"], act,
@@ -45,10 +46,10 @@ def test_hidden_tensor_core_matches_oracle(elm, ctx, N, n, L, xdt, act, kind):
     H = oracle.hidden(p["X"], p["W"], p["b"], p["a"], act)
     assert Ht.shape == (Lt, N)
     assert np.max(np.abs(Ht.T - H)) < 1e-9
-    src = p["src"]
+    src, sc = p["src"], p["scale"]
     for j in range(Lt):                                    # bitwise duplicates
-        k = int(np.nonzero(src == src[j])[0][0])
-        assert np.array_equal(Ht[j], Ht[k])
+        k = int(np.nonzero((src == src[j]) & (sc == 1.0))[0][0])
+        assert np.array_equal(Ht[j], sc[j] * Ht[k])
 
 
 def test_train_small_fp64_workload_mixed(elm, ctx):
