@@ -208,6 +208,22 @@ def run_reference(args):
     return 0
 
 
+WORKLOADS = {
+    "sparse_pixels": (lambda rows: [synth.workload_sparse_pixels(N=rows)], WORKLOAD["workload"]),
+    "small": (lambda rows: [synth.workload_small_fp64()],
+              "small ELM: X 2000x16 U[0,1] FP64, L=200 sigmoid (180 unique + 20 duplicates, "
+              "rank 180), 4 one-hot classes"),
+    "rank_deficient": (lambda rows: [synth.workload_rank_deficient()],
+                       "rank-deficient ELM: X 100000x64 N(0,1) FP32, L=6000 sigmoid (5100 unique "
+                       "+ 600 duplicates + 300 scaled copies, rank 5100), 3 regression targets"),
+    "batched": (lambda rows: synth.workload_batched(),
+                "batched uneven ELMs: 128 problems, N in [5000,50000], d in {16,54,128}, "
+                "L in [100,3000], sigmoid/tanh, 2-26 one-hot classes"),
+    "large": (lambda rows: [synth.workload_large()],
+              "large ELM: X 500000x128 U[-1,1] FP32, L=8000 sigmoid, 20 one-hot classes"),
+}
+
+
 def run_native(args):
     import torch
     import __graft_entry__
@@ -222,35 +238,42 @@ def run_native(args):
     dev = torch.device("cuda", local)
     prec = elm.PREC_MIXED if args.precision == "mixed" else elm.PREC_FP64
 
-    p = synth.workload_sparse_pixels(N=args.rows)
-    N, n, L, m = p["N"], p["n"], p["L"], p["m"]
-    X = torch.from_numpy(p["X"]).to(dev)
-    W = torch.from_numpy(p["W"]).to(dev)
-    b = torch.from_numpy(p["b"]).to(dev)
-    T = torch.from_numpy(p["T"]).to(dev)
-    beta = torch.empty((L, m), dtype=torch.float64, device=dev)
+    gen, desc = WORKLOADS[args.workload]
+    plist = gen(args.rows)
+    probs, hosts = [], []
+    for p in plist:
+        L, m = p["W"].shape[1], p["T"].shape[1]
+        probs.append(dict(X=torch.from_numpy(p["X"]).to(dev), W=torch.from_numpy(p["W"]).to(dev),
+                          b=torch.from_numpy(p["b"]).to(dev),
+                          a=None if p.get("a") is None else torch.from_numpy(p["a"]).to(dev),
+                          act=int(p.get("act", 0)), T=torch.from_numpy(p["T"]).to(dev),
+                          beta=torch.empty((L, m), dtype=torch.float64, device=dev)))
+        hosts.append(p)
+    count = len(probs)
     stream = torch.cuda.current_stream(dev)
     ctx = elm.elm_create(local, stream)
-    prob = dict(X=X, W=W, b=b, a=None, act=0, T=T, beta=beta)
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # verified run: rank and accuracy against the oracle's bar (beta vs the
-    # FP64 GPU path, whose own parity with the oracle is tested in tests/)
-    res = elm.elm_train(ctx, prob, precision=prec)[0]
-    beta_run = beta.cpu().numpy()
-    check = dict(rank=res["rank"], refine_iters=res["refine_iters"])
+    # verified run: rank and accuracy (beta against the FP64 GPU path, whose
+    # own parity with the oracle is tested in tests/)
+    res = elm.elm_train(ctx, probs, precision=prec)
+    check = dict(rank=[r["rank"] for r in res] if count > 1 else res[0]["rank"],
+                 refine_iters=max(r["refine_iters"] for r in res))
     if prec != elm.PREC_FP64 and not args.no_fp64_check:
-        prob64 = dict(prob, beta=torch.empty_like(beta))
-        elm.elm_train(ctx, prob64, precision=elm.PREC_FP64)
-        b64 = prob64["beta"].cpu().numpy()
-        check["rel_err_vs_fp64_path"] = float(np.linalg.norm(beta_run - b64) / np.linalg.norm(b64))
+        errs = []
+        for pr in probs:
+            p64 = dict(pr, beta=torch.empty_like(pr["beta"]))
+            elm.elm_train(ctx, p64, precision=elm.PREC_FP64)
+            b64, bm = p64["beta"].cpu().numpy(), pr["beta"].cpu().numpy()
+            errs.append(float(np.linalg.norm(bm - b64) / np.linalg.norm(b64)))
+        check["rel_err_vs_fp64_path"] = max(errs)
 
     for _ in range(args.warmup):
-        elm.elm_train(ctx, prob, precision=prec)
+        elm.elm_train(ctx, probs, precision=prec)
     elm.elm_phase_times(ctx)                       # reset
     barrier()
     l0 = elm.elm_launch_counter()
@@ -259,75 +282,90 @@ def run_native(args):
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            elm.elm_train(ctx, prob, precision=prec, flags=elm.FLAG_PHASE_TIMING)
+            elm.elm_train(ctx, probs, precision=prec, flags=elm.FLAG_PHASE_TIMING)
         e1.record(stream)
         barrier()
     launches = elm.elm_launch_counter() - l0
     phases = elm.elm_phase_times(ctx)
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ms, dev)
-    value = ws * 1000.0 / ms_max
+    value = ws * count * 1000.0 / ms_max
 
     # e2e through the C ABI with pinned host buffers
-    hX = torch.from_numpy(p["X"]).pin_memory()
-    hW = torch.from_numpy(p["W"]).pin_memory()
-    hb = torch.from_numpy(p["b"]).pin_memory()
-    hT = torch.from_numpy(p["T"]).pin_memory()
-    hbeta = torch.empty((L, m), dtype=torch.float64).pin_memory()
-    hprob = dict(X=hX, W=hW, b=hb, a=None, act=0, T=hT, beta=hbeta)
-    elm.elm_train(ctx, hprob, precision=prec)
+    hprobs = []
+    h2d = 0
+    for p in hosts:
+        hp = dict(X=torch.from_numpy(p["X"]).pin_memory(), W=torch.from_numpy(p["W"]).pin_memory(),
+                  b=torch.from_numpy(p["b"]).pin_memory(),
+                  a=None if p.get("a") is None else torch.from_numpy(p["a"]).pin_memory(),
+                  act=int(p.get("act", 0)), T=torch.from_numpy(p["T"]).pin_memory(),
+                  beta=torch.empty((p["W"].shape[1], p["T"].shape[1]),
+                                   dtype=torch.float64).pin_memory())
+        h2d += sum(hp[k].numel() * hp[k].element_size() for k in ("X", "W", "b", "a", "T")
+                   if hp[k] is not None)
+        hprobs.append(hp)
+    d2h = sum(hp["beta"].numel() * 8 for hp in hprobs)
+    elm.elm_train(ctx, hprobs, precision=prec)
     barrier()
-    t0 = time.perf_counter()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     e2e_steps = max(1, min(args.steps, 5))
     for _ in range(e2e_steps):
-        elm.elm_train(ctx, hprob, precision=prec)
+        elm.elm_train(ctx, hprobs, precision=prec)
     f1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, dev)
-    h2d = sum(t.numel() * t.element_size() for t in (hX, hW, hb, hT))
-    d2h = hbeta.numel() * hbeta.element_size()
 
     if rank == 0:
-        fl = flops_model(N, n, L, m)
         pk = peaks()
         ph_ms = {k: v / args.steps for k, v in phases.items()}
+        gram_fl, issued = 0.0, 0.0
+        for p in hosts:
+            N, n = p["X"].shape
+            L, m = p["W"].shape[1], p["T"].shape[1]
+            gram_fl += flops_model(N, n, L, m)["gram"]
+            Lp, Np = -(-(L + m) // 128) * 128, -(-N // 64) * 64
+            nJ = Lp // 128
+            issued += 15 * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
+        N_all = sum(p["X"].shape[0] for p in hosts)
         if prec == elm.PREC_FP64:
             # Gram on the FP64 pipe (nominal rate; MEASURED_PEAKS.json has no FP64 entry)
-            achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e12
+            achieved = gram_fl / (ph_ms["gram"] * 1e-3) / 1e12
             roof = dict(bound="alu", achieved=achieved, peak=pk["fp64"], unit="TFLOP/s",
                         frac=achieved / pk["fp64"], traffic=None, kernel="gram_f64_kernel",
                         peak_source="nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 entry)")
         else:
             # Gram on the tensor cores: algorithmic FLOPs (symmetric Gram counted
-            # once, as in the contract) over the phase time, against the measured
-            # bf16 burst peak; the digit emulation issues 15 digit-pair products
-            # of the lower-triangle tiles, reported beside it
-            Lp, Np = -(-(L + m) // 128) * 128, -(-N // 64) * 64
-            nJ = Lp // 128
-            issued = 15 * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
-            achieved = fl["gram"] / (ph_ms["gram"] * 1e-3) / 1e12
+            # once, as in the contract) over the Gram phase (that kernel alone),
+            # against the measured bf16 burst peak; the digit emulation issues 15
+            # digit-pair products of the lower-triangle tiles, reported beside it
+            achieved = gram_fl / (ph_ms["gram"] * 1e-3) / 1e12
             roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16"], unit="TFLOP/s",
-                        frac=achieved / pk["bf16"], traffic=GRAM_DRAM_BYTES_PER_ROW * N,
+                        frac=achieved / pk["bf16"], traffic=GRAM_DRAM_BYTES_PER_ROW * N_all,
                         kernel="ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
                         peak_source="%s bf16 dense burst" % pk["source"],
                         issued_tflops=issued / (ph_ms["gram"] * 1e-3) / 1e12,
                         issued_frac=issued / (ph_ms["gram"] * 1e-3) / 1e12 / pk["bf16"])
         roof["phase_ms"] = ph_ms
+        first = hosts[0]
+        cfg = dict(workload=desc, precision=args.precision,
+                   parallelism="replicas" if ws > 1 else "single",
+                   l2="inputs larger than L2 (X and the digit planes stream from HBM): no flush")
+        if count == 1:
+            cfg.update(N=first["X"].shape[0], n=first["X"].shape[1], L=first["W"].shape[1],
+                       m=first["T"].shape[1])
+        else:
+            cfg.update(problems=count)
         line = dict(metric=METRIC, value=value, unit="trainings/s", n_gpus=ws, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms_max, higher_is_better=True,
                     scaling="weak", vs_baseline=None,
                     dtype="f64" if prec == elm.PREC_FP64 else "bf16-slices+f64",
-                    data="synthetic",
-                    config=dict(WORKLOAD, N=N, precision=args.precision,
-                                parallelism="replicas" if ws > 1 else "single",
-                                l2="inputs larger than L2 (X 188 MB, H 0.96 GB): no flush"),
-                    e2e=dict(value=ws * 1000.0 / e2e_ms, unit="trainings/s",
+                    data="synthetic", config=cfg,
+                    e2e=dict(value=ws * count * 1000.0 / e2e_ms, unit="trainings/s",
                              h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches, roofline=roof, clocks=clk.summary(), check=check)
-        if not args.no_cpu_baseline:
+        if args.workload == "sparse_pixels" and not args.no_cpu_baseline:
             cb = cpu_baseline(WORKLOAD, sample_rows=args.ref_rows)
             cb.pop("projected_s_per_training", None)
             line["cpu_baseline"] = cb
@@ -350,7 +388,9 @@ def main():
                     help="skip the cross-check of the mixed beta against the FP64 GPU path")
     ap.add_argument("--ref-rows", type=int, default=6000)
     ap.add_argument("--rows", type=int, default=WORKLOAD["N"],
-                    help="rows of the workload (smaller only for profiling captures)")
+                    help="rows of the sparse-pixel workload (smaller only for profiling captures)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sparse_pixels",
+                    help="the timed workload (the default is the headline configuration)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

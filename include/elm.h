@@ -116,7 +116,8 @@ typedef struct elm_problem {
 
 typedef struct elm_train_opts {
     int32_t precision;  /* ELM_PREC_FP64 or ELM_PREC_MIXED                   */
-    int32_t max_refine; /* refinement steps (< 0: default 2 FP64, 6 mixed)   */
+    int32_t max_refine; /* refinement steps (< 0: default 2 FP64, 12 mixed;
+                           mixed steps stop early once they stop contracting) */
     double tol_rank;    /* rank threshold on the unit-diagonal scale (<=0: L*2^-52
                            for FP64, max(L*2^-52, 2^-32) for MIXED, whose Gram
                            is exact up to dropped digit pairs below 2^-34)   */

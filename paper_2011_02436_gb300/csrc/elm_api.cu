@@ -469,6 +469,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     mark(ctx, 4);
     double nrm[2] = {0.0, 0.0};
     bool converged = P.max_refine == 0;
+    double prev = INFINITY;
     for (int it = 0; it < P.max_refine; it++) {
         resid_df(s, Hdf, L, N, beta, m, Td, T.ld, Rres, betaT);        // T - H beta (pairs)
         htr_df(s, Hdf, L, N, Rres, m, Gres, hpart, hs_split);           // H^T (T - H beta)
@@ -482,6 +483,10 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
             converged = true;
             break;
         }
+        // the steps must contract; once they stop doing so the grid Gram
+        // is too coarse a preconditioner for this H
+        if (it >= 1 && !(res->rel_update < 0.5 * prev)) break;
+        prev = res->rel_update;
     }
     mark(ctx, 5);
     if (solver_timed_out(s, sv)) {
@@ -691,7 +696,7 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             P.p = &probs[i];
             P.prec = o.precision;
             P.max_refine = o.max_refine >= 0 ? o.max_refine
-                                             : (o.precision == ELM_PREC_FP64 ? 2 : 6);
+                                             : (o.precision == ELM_PREC_FP64 ? 2 : 12);
             // default rank threshold on the unit-diagonal scale: L 2^-52 for
             // the FP64 Gram; the mixed Gram drops digit pairs below 2^-34 of
             // the leading term, so its threshold sits above that level

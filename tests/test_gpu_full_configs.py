@@ -1,0 +1,129 @@
+"""Parity at the full sizes of the workload configurations, in the launch
+configuration bench.py times (mixed form, device-resident inputs).
+
+The oracle cannot train these sizes in test time, so it checks what holds at
+any size and recomputes H itself (plain FP64, row chunks):
+  * the planted rank (full, or unique neurons only);
+  * least-squares optimality of beta (Eq. 5): ||H^T (T - H beta)|| small
+    against ||H||^2 ||beta|| + ||H|| ||T|| (rounding of the check itself is
+    about 1e-13 of that scale; the bar is 1e-9);
+  * the minimum-norm split over planted copies (Moore-Penrose, Eq. 5):
+    exact duplicates share equally, a copy scaled by s gets s times the
+    original's weight;
+  * for the smallest batched problems, the oracle's own beta within 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def elm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2011_02436_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(elm):
+    import torch
+    c = elm.elm_create(0, torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+def train_mixed(elm, ctx, p):
+    import torch
+    dev = torch.device("cuda", 0)
+    L, m = p["W"].shape[1], p["T"].shape[1]
+    prob = dict(X=torch.from_numpy(p["X"]).to(dev), W=torch.from_numpy(p["W"]).to(dev),
+                b=torch.from_numpy(p["b"]).to(dev),
+                a=None if p.get("a") is None else torch.from_numpy(p["a"]).to(dev),
+                act=int(p.get("act", 0)), T=torch.from_numpy(p["T"]).to(dev),
+                beta=torch.empty((L, m), dtype=torch.float64, device=dev))
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    return res, prob["beta"].cpu().numpy()
+
+
+def optimality(p, beta, rows=20000):
+    """||H^T (T - H beta)||_F over (||H||_F^2 ||beta||_F + ||H||_F ||T||_F),
+    H from the oracle in row chunks."""
+    X, W, b, T = p["X"], p["W"], p["b"], p["T"]
+    a, act = p.get("a"), int(p.get("act", 0))
+    G = np.zeros((W.shape[1], T.shape[1]))
+    h2 = 0.0
+    for r0 in range(0, X.shape[0], rows):
+        H = oracle.hidden(X[r0:r0 + rows], W, b, a, act)
+        G += H.T @ (T[r0:r0 + rows] - H @ beta)
+        h2 += float(np.sum(H * H))
+    scale = h2 * np.linalg.norm(beta) + np.sqrt(h2) * np.linalg.norm(T)
+    return float(np.linalg.norm(G) / scale)
+
+
+def copies_share(p, beta):
+    """Largest relative deviation from the minimum-norm split over copies."""
+    src, sc = p["src"], p["scale"]
+    worst = 0.0
+    for j in range(len(src)):
+        k = int(np.nonzero((src == src[j]) & (sc == 1.0))[0][0])
+        if k == j:
+            continue
+        want = sc[j] * beta[k]   # duplicate: sc = 1; scaled copy: s times the original
+        worst = max(worst, float(np.max(np.abs(beta[j] - want)) /
+                                 max(np.max(np.abs(beta[k])), 1e-300)))
+    return worst
+
+
+def test_sparse_pixels_full(elm, ctx):
+    p = synth.workload_sparse_pixels()
+    res, beta = train_mixed(elm, ctx, p)
+    assert res["status"] == 0 and res["rank"] == 2000
+    assert optimality(p, beta) < 1e-9
+
+
+def test_rank_deficient_full(elm, ctx):
+    p = synth.workload_rank_deficient()
+    res, beta = train_mixed(elm, ctx, p)
+    assert res["status"] == 0 and res["rank"] == p["rank"] == 5100
+    assert copies_share(p, beta) < 1e-9
+    assert optimality(p, beta) < 1e-9
+
+
+def test_batched_full(elm, ctx):
+    ps = synth.workload_batched()
+    import torch
+    dev = torch.device("cuda", 0)
+    probs = []
+    for p in ps:
+        L, m = p["W"].shape[1], p["T"].shape[1]
+        probs.append(dict(X=torch.from_numpy(p["X"]).to(dev), W=torch.from_numpy(p["W"]).to(dev),
+                          b=torch.from_numpy(p["b"]).to(dev), a=None, act=int(p["act"]),
+                          T=torch.from_numpy(p["T"]).to(dev),
+                          beta=torch.empty((L, m), dtype=torch.float64, device=dev)))
+    res = elm.elm_train(ctx, probs, precision=elm.PREC_MIXED)
+    for p, r in zip(ps, res):
+        assert r["status"] == 0 and r["rank"] == p["W"].shape[1]      # planted full rank
+    # the oracle end to end on the smallest problems (by N L^2)
+    order = sorted(range(len(ps)), key=lambda i: ps[i]["X"].shape[0] * ps[i]["W"].shape[1] ** 2)
+    for i in order[:3]:
+        p = ps[i]
+        bo, ro, _ = oracle.train(p["X"], p["W"], p["b"], None, int(p["act"]), p["T"])
+        bg = probs[i]["beta"].cpu().numpy()
+        assert ro == res[i]["rank"]
+        assert np.linalg.norm(bg - bo) / np.linalg.norm(bo) < 1e-6
+    # least-squares optimality on a spread of the others
+    for i in order[3::16]:
+        assert optimality(ps[i], probs[i]["beta"].cpu().numpy()) < 1e-9
+
+
+@pytest.mark.slow
+def test_large_full(elm, ctx):
+    p = synth.workload_large()
+    res, beta = train_mixed(elm, ctx, p)
+    assert res["status"] == 0 and res["rank"] == 8000
+    assert optimality(p, beta, rows=25000) < 1e-9
