@@ -311,35 +311,54 @@ __global__ void beta_pairs_kernel(const double *__restrict__ beta, int64_t L, in
 }
 
 // Rd[i, :] = T[i, :] - H[i, :] beta: one warp per SPW samples, lanes over
-// the neurons (coalesced rows of H and of betaT, each betaT value reused by
-// the warp's SPW samples from registers), warp reductions
+// the neurons (coalesced rows of H), warp reductions.  The CTA stages betaT
+// in tiles of JT neurons in shared memory, so each value is fetched from L2
+// once per CTA and reused by its 8 SPW samples; at most 128 registers keep
+// two CTAs per SM.
 template <int RC>
-constexpr int spw_for() { return RC <= 10 ? 4 : (RC <= 16 ? 2 : 1); }   // register budget
+constexpr int spw_for() { return RC <= 10 ? 4 : (RC <= 20 ? 2 : 1); }   // register budget
+template <int RC>
+__host__ __device__ constexpr int rjt_for() { return RC <= 16 ? 256 : 128; }                // <= 32 KB of tile
 template <int RC, int SPW = spw_for<RC>()>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 resid_df_kernel(const df::F2 *__restrict__ H, int64_t L, int64_t N,
                 const df::F2 *__restrict__ betaT, int64_t m, int64_t c0, int mc,
                 const double *__restrict__ T, int64_t ldt, df::F2 *__restrict__ Rd) {
+    constexpr int JT = rjt_for<RC>();
+    __shared__ df::F2 bs[RC][JT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i0 = ((int64_t)blockIdx.x * 8 + warp) * SPW;
-    if (i0 >= N) return;   // warp-uniform
     float ah[SPW][RC], al[SPW][RC];
 #pragma unroll
     for (int q = 0; q < SPW; q++)
 #pragma unroll
         for (int c = 0; c < RC; c++) ah[q][c] = al[q][c] = 0.f;
-    for (int64_t j = lane; j < L; j += 32) {
-        df::F2 bv[RC];
+    for (int64_t j0 = 0; j0 < L; j0 += JT) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < RC * JT; e += 256) {
+            const int c = e / JT, jj = e % JT;
+            const int64_t j = j0 + jj;
+            bs[c][jj] = (c < mc && j < L) ? betaT[c * L + j] : df::F2{0.f, 0.f};
+        }
+        __syncthreads();
+        if (i0 >= N) continue;   // warp-uniform; the barriers above stay collective
+#pragma unroll 1
+        for (int st = 0; st < JT / 32; st++) {
+            if (j0 + st * 32 >= L) break;   // warp-uniform
+            const int64_t j = j0 + st * 32 + lane;
+            df::F2 h[SPW];
 #pragma unroll
-        for (int c = 0; c < RC; c++) bv[c] = c < mc ? betaT[c * L + j] : df::F2{0.f, 0.f};
+            for (int q = 0; q < SPW; q++)
+                h[q] = (i0 + q < N && j < L) ? H[(i0 + q) * L + j] : df::F2{0.f, 0.f};
 #pragma unroll
-        for (int q = 0; q < SPW; q++) {
-            const int64_t i = i0 + q;
-            const df::F2 h = i < N ? H[i * L + j] : df::F2{0.f, 0.f};
+            for (int c = 0; c < RC; c++) {
+                const df::F2 bv = bs[c][st * 32 + lane];
 #pragma unroll
-            for (int c = 0; c < RC; c++) df::df_acc_prod(ah[q][c], al[q][c], h, bv[c]);
+                for (int q = 0; q < SPW; q++) df::df_acc_prod(ah[q][c], al[q][c], h[q], bv);
+            }
         }
     }
+    if (i0 >= N) return;
 #pragma unroll
     for (int q = 0; q < SPW; q++) {
         const int64_t i = i0 + q;

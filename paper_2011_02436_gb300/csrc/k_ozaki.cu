@@ -18,11 +18,12 @@
 // at most 2^(-4B) of the leading one), the FP32 accumulator itself.  Pairs
 // with p + q > TMAX are dropped.
 //
-// Kernel layout (one 128 x 64 output tile per CTA, 192 threads):
+// Kernel layout (persistent, 128 x 64 output tiles, 320 threads):
 //   warp 0      TMA producer: digit tiles of A (128 rows) and B (64 rows),
 //               32 K-elements per stage, 64-byte swizzle, STAGES-deep ring
 //   warp 1      TMEM allocation and the single MMA-issuing thread
-//   warps 2..5  drains and the FP64 epilogue (one TMEM lane each)
+//   warps 2..9  drains and the epilogue (two warps per TMEM lane quarter,
+//               32 columns each)
 // Every mbarrier wait is bounded by wall-clock time; on expiry the kernel
 // sets an error flag, stops issuing work and still frees its TMEM.
 #include <cuda.h>
@@ -136,7 +137,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+// Ties 16 registers written by an earlier tmem_ld16 to this point, so that no
+// use of them is scheduled above the preceding tmem_wait_ld.
+__device__ __forceinline__ void reg_fence16(uint32_t *r) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+// Stores without the completion wait; tmem_wait_st() before the columns are
+// handed over (barrier arrive) or read back.
+__device__ __forceinline__ void tmem_st16_async(uint32_t taddr, const uint32_t *r) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
         "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
@@ -144,6 +155,8 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
         "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
         "r"(r[15])
         : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
@@ -174,6 +187,13 @@ struct dfl {
 // upper 16 bits -- integer operations, no conversion instruction.
 __device__ __forceinline__ uint32_t pack_bf16_int(float lo, float hi) {
     return (__float_as_uint(lo) >> 16) | (__float_as_uint(hi) & 0xffff0000u);
+}
+// Nearest integer, ties to even, of |x| < 2^22 on the FP32 add pipe: in
+// x + 1.5 2^23 the unit is the last mantissa bit, so the add rounds x to an
+// integer and the subtraction is exact.  Same result as rintf, which issues
+// on the narrower conversion (XU) pipe.
+__device__ __forceinline__ float rint_digit(float x) {
+    return __fadd_rn(__fadd_rn(x, 12582912.f), -12582912.f);
 }
 __device__ __forceinline__ dfl two_sum(float a, float b) {
     const float s = a + b;
@@ -261,7 +281,7 @@ struct OzParams {
     int64_t ldo;
     int *err;
     int64_t ntiles;     // tiles in the tile set
-    ActParams ap;       // used when the kernel's EPI == 1
+    ActParams ap;       // used when the kernel's EPI != 0
 };
 
 // Fused hidden-layer epilogue for one row (neuron j = m) and 32 samples
@@ -319,7 +339,9 @@ __device__ __forceinline__ RowAct row_setup(const OzParams &P, int64_t m) {
     }
     return r;
 }
-// 8 samples n0 .. n0+7 of one row
+// 8 samples n0 .. n0+7 of one row; HT: also write FP64 H^T (a compile-time
+// switch, so the training form issues no FP64 conversion for it)
+template <bool HT>
 __device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R, int64_t m,
                                              int64_t n0, const dfl *V) {
     const ActParams &A = P.ap;
@@ -340,7 +362,7 @@ __device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R,
             hv = sigmoid_df(z, A.tab);
         }
         if (R.scaled) hv = df_mul(hv, R.aj);
-        if (on && A.Ht) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
+        if (HT && on) A.Ht[m * A.ldh + n] = (double)hv.h + (double)hv.l;
         if (on && A.Hdf) A.Hdf[n * A.ldhd + m] = make_float2(hv.h, hv.l);   // lanes: consecutive m
         hv.h = on ? hv.h * R.inv_hs : 0.f;   // the digit planes hold H / hs
         hv.l = on ? hv.l * R.inv_hs : 0.f;
@@ -350,7 +372,7 @@ __device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R,
         float rl = hv.l * (float)(1 << (GRAM_BITS_ - 1));
 #pragma unroll
         for (int p = 0; p < GRAM_PH_; p++) {
-            const float d = rintf(rh);
+            const float d = rint_digit(rh);
             dg[p][i] = d;
             const dfl r = two_sum(rh - d, rl);            // rh - d is exact
             rh = r.h * (float)(1 << GRAM_BITS_);
@@ -541,7 +563,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int quarter = warp & 3;
         const int c0 = ((warp - 2) >> 2) * 32;       // this warp's 32 columns of the tile
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-        const bool direct = (EPI == 1) && nchunk == 1;
+        const bool direct = (EPI != 0) && nchunk == 1;
         int64_t gc = 0;
         bool ok = true;
         for (int64_t t = t_first; t < P.ntiles && ok; t += t_step) {
@@ -555,75 +577,109 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 if (!ok) break;
                 tc_fence_after();
                 const bool last = c == nchunk - 1;
+                // Each TMEM load is issued before the arithmetic on the previous
+                // one (two register buffers), so its latency overlaps that work.
+                const auto diag_addr = [&](int k) {   // k = h ND + (t - 2)
+                    return lane_base + (uint32_t)((TMAX - 2 - k % ND) * BN + (k / ND) * 16);
+                };
+                uint32_t wb[2][16];
+                if (direct) {
+                    // V = sum_t acc_t 2^(B (TMAX - t)): Horner from the leading
+                    // diagonal in double-float, parked in the (otherwise unused)
+                    // running-sum columns as (hi, lo) floats
+                    dfl V[16];
+                    tmem_ld16(diag_addr(0), wb[0]);
+                    tmem_wait_ld();
+                    reg_fence16(wb[0]);
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    uint32_t w0[16], w1[16];
-                    if (direct) {
-                        // V = sum_t acc_t 2^(B (TMAX - t)): Horner from the leading
-                        // diagonal in double-float, parked in the (otherwise unused)
-                        // running-sum columns as (hi, lo) floats
-                        dfl V[16];
+                    for (int k = 0; k < 2 * ND; k++) {
+                        if (k + 1 < 2 * ND) tmem_ld16(diag_addr(k + 1), wb[(k + 1) & 1]);
+                        const uint32_t *w = wb[k & 1];
+                        const float sc = (float)(1 << DBITS);
+                        if (k % ND == 0) {
 #pragma unroll
-                        for (int i = 0; i < 16; i++) V[i] = {0.f, 0.f};
-#pragma unroll
-                        for (int td = 2; td <= TMAX; td++) {
-                            tmem_ld16(lane_base + (uint32_t)((TMAX - td) * BN + h * 16), w0);
-                            tmem_wait_ld();
-                            const float sc = (float)(1 << DBITS);
-#pragma unroll
-                            for (int i = 0; i < 16; i++)
-                                V[i] = df_add({V[i].h * sc, V[i].l * sc}, {__uint_as_float(w0[i]), 0.f});
-                        }
-#pragma unroll
-                        for (int i = 0; i < 16; i++) {
-                            w0[i] = __float_as_uint(V[i].h);
-                            w1[i] = __float_as_uint(V[i].l);
-                        }
-                        tmem_st16(lane_base + LO_COL + h * 16, w0);
-                        tmem_st16(lane_base + HI_COL + h * 16, w1);
-                        continue;
-                    }
-                    long long *r = run + h * 16;
-                    if (c == 0) {
-#pragma unroll
-                        for (int i = 0; i < 16; i++) r[i] = 0;
-                    } else {
-                        tmem_ld16(lane_base + LO_COL + h * 16, w0);
-                        tmem_ld16(lane_base + HI_COL + h * 16, w1);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int i = 0; i < 16; i++)
-                            r[i] = (long long)(((unsigned long long)w1[i] << 32) | w0[i]);
-                    }
-#pragma unroll
-                    for (int td = 2; td <= TMAX; td++) {
-                        tmem_ld16(lane_base + (uint32_t)((TMAX - td) * BN + h * 16), w0);
-                        tmem_wait_ld();
-                        // accumulators are exact integers below 2^25
-                        const long long mult = 1ll << (DBITS * (TMAX - td));
-#pragma unroll
-                        for (int i = 0; i < 16; i++)
-                            r[i] += (long long)__float2int_rn(__uint_as_float(w0[i])) * mult;
-                    }
-                    if (!last || EPI == 1) {
-                        if (last) {
-                            // EPI == 1 over several chunks: park V as (hi, lo) floats
-#pragma unroll
-                            for (int i = 0; i < 16; i++) {
-                                const float vh = __ll2float_rn(r[i]);
-                                w0[i] = __float_as_uint(vh);
-                                w1[i] = __float_as_uint(__ll2float_rn(r[i] - __float2ll_rn(vh)));
-                            }
+                            for (int i = 0; i < 16; i++) V[i] = {__uint_as_float(w[i]), 0.f};
                         } else {
 #pragma unroll
+                            for (int i = 0; i < 16; i++)
+                                V[i] = df_add({V[i].h * sc, V[i].l * sc}, {__uint_as_float(w[i]), 0.f});
+                        }
+                        if (k % ND == ND - 1) {
+                            const int h = k / ND;
+                            uint32_t s0[16], s1[16];
+#pragma unroll
                             for (int i = 0; i < 16; i++) {
-                                w0[i] = (uint32_t)((unsigned long long)r[i]);
-                                w1[i] = (uint32_t)((unsigned long long)r[i] >> 32);
+                                s0[i] = __float_as_uint(V[i].h);
+                                s1[i] = __float_as_uint(V[i].l);
+                            }
+                            tmem_st16_async(lane_base + LO_COL + h * 16, s0);
+                            tmem_st16_async(lane_base + HI_COL + h * 16, s1);
+                        }
+                        if (k + 1 < 2 * ND) {
+                            tmem_wait_ld();
+                            reg_fence16(wb[(k + 1) & 1]);
+                        }
+                    }
+                    tmem_wait_st();
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        long long *r = run + h * 16;
+                        if (c == 0) {
+#pragma unroll
+                            for (int i = 0; i < 16; i++) r[i] = 0;
+                        } else {
+                            tmem_ld16(lane_base + LO_COL + h * 16, wb[0]);
+                            tmem_ld16(lane_base + HI_COL + h * 16, wb[1]);
+                            tmem_wait_ld();
+                            reg_fence16(wb[0]);
+                            reg_fence16(wb[1]);
+#pragma unroll
+                            for (int i = 0; i < 16; i++)
+                                r[i] = (long long)(((unsigned long long)wb[1][i] << 32) | wb[0][i]);
+                        }
+                        tmem_ld16(diag_addr(h * ND), wb[0]);
+                        tmem_wait_ld();
+                        reg_fence16(wb[0]);
+#pragma unroll
+                        for (int td = 2; td <= TMAX; td++) {
+                            const int k = td - 2;
+                            if (td < TMAX) tmem_ld16(diag_addr(h * ND + k + 1), wb[(k + 1) & 1]);
+                            const uint32_t *w = wb[k & 1];
+                            // accumulators are exact integers below 2^25
+                            const long long mult = 1ll << (DBITS * (TMAX - td));
+#pragma unroll
+                            for (int i = 0; i < 16; i++)
+                                r[i] += (long long)__float2int_rn(__uint_as_float(w[i])) * mult;
+                            if (td < TMAX) {
+                                tmem_wait_ld();
+                                reg_fence16(wb[(k + 1) & 1]);
                             }
                         }
-                        tmem_st16(lane_base + LO_COL + h * 16, w0);
-                        tmem_st16(lane_base + HI_COL + h * 16, w1);
+                        if (!last || EPI != 0) {
+                            // the previous stores from these registers have completed
+                            tmem_wait_st();
+                            uint32_t *w0 = wb[0], *w1 = wb[1];
+                            if (last) {
+                                // EPI != 0 over several chunks: park V as (hi, lo) floats
+#pragma unroll
+                                for (int i = 0; i < 16; i++) {
+                                    const float vh = __ll2float_rn(r[i]);
+                                    w0[i] = __float_as_uint(vh);
+                                    w1[i] = __float_as_uint(__ll2float_rn(r[i] - __float2ll_rn(vh)));
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; i++) {
+                                    w0[i] = (uint32_t)((unsigned long long)r[i]);
+                                    w1[i] = (uint32_t)((unsigned long long)r[i] >> 32);
+                                }
+                            }
+                            tmem_st16_async(lane_base + LO_COL + h * 16, w0);
+                            tmem_st16_async(lane_base + HI_COL + h * 16, w1);
+                        }
                     }
+                    tmem_wait_st();
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty);   // MMAs may overwrite the accumulators now
@@ -655,8 +711,8 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     dfl V[16];
 #pragma unroll
                     for (int i = 0; i < 16; i++) V[i] = {__uint_as_float(w0[i]), __uint_as_float(w1[i])};
-                    hidden_emit8(P, ra, m, n0 + c0 + h * 16, V);
-                    hidden_emit8(P, ra, m, n0 + c0 + h * 16 + 8, V + 8);
+                    hidden_emit8<EPI == 2>(P, ra, m, n0 + c0 + h * 16, V);
+                    hidden_emit8<EPI == 2>(P, ra, m, n0 + c0 + h * 16 + 8, V + 8);
                 }
             }
         }
@@ -771,7 +827,7 @@ __global__ void digits_rows_f32_kernel(const float *__restrict__ X, int64_t N, i
             float r = (i < N && k < n) ? X[i * ldx + k] * inv * (float)(1 << (DBITS - 1)) : 0.f;
 #pragma unroll
             for (int p = 0; p < PD; p++) {
-                const float dp = rintf(r);
+                const float dp = rint_digit(r);
                 d[p][e] = dp;
                 r = (r - dp) * (float)(1 << DBITS);
             }
@@ -827,7 +883,7 @@ __global__ void digits_cols_par_kernel(const double *__restrict__ W, int64_t n, 
         float rl = (float)(v - (double)rh);
 #pragma unroll
         for (int p = 0; p < PD; p++) {
-            const float dp = rintf(rh);
+            const float dp = rint_digit(rh);
             d[p][e] = dp;
             const dfl r = two_sum(rh - dp, rl);   // rh - dp is exact
             rh = r.h * (float)(1 << DBITS);
@@ -1052,8 +1108,12 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ap.Hdf = (float2 *)Hdf;
     P.ap.ldhd = L;
     P.ap.ldh = ldh;
-    launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P,
-                                                           (Lp / BM) * (Np / BN));
+    if (Ht)
+        launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 2>(s, w.wp, w.xp, P,
+                                                               (Lp / BM) * (Np / BN));
+    else
+        launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P,
+                                                               (Lp / BM) * (Np / BN));
 }
 
 // Target rows L .. L+m-1 of the Gram digit planes.
