@@ -417,14 +417,13 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     });
     ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
     ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    check_finite(s, X.p, pb.x_dtype, N, n, X.ld, flag);
     const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
                  *ad = (const double *)a.p, *Td = (const double *)T.p;
     mark(ctx, 0);
     // Algorithm 1 step 2 (Eq. 1, 3): pre-activation on the tensor cores,
     // activation in the epilogue, digit planes of H and H itself
     oz_hidden(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, pb.act, L, m, planes, hs,
-              nullptr, 0, err, Hdf);
+              nullptr, 0, err, Hdf, /*nonfinite=*/flag);
     // digit rows of the targets beside those of H (part of the hidden phase,
     // so the Gram phase times the Gram kernel alone)
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);

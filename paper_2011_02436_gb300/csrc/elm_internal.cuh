@@ -210,11 +210,13 @@ size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m);
 // the Gram digit planes (rows < L, zero padding) with row scales hs, as
 // FP64 H^T (row stride ldh) when Ht != NULL, and as double-float H (N x L,
 // sample-major, eight bytes per element, about 2^-43 relative) when
-// Hdf != NULL.  *err set on a device-side timeout.
+// Hdf != NULL.  *err set on a device-side timeout; *nonfinite (if given)
+// |= 1 when X holds a NaN or an infinity.
 void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
-               int64_t ldh, int *err, void *Hdf = nullptr);
+               int64_t ldh, int *err, void *Hdf = nullptr,
+               int32_t *nonfinite = nullptr);
 // T -> digit plane rows L .. L+m-1.
 void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
                  __nv_bfloat16 *planes, double *hs);

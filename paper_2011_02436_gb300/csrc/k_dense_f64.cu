@@ -527,16 +527,15 @@ __global__ void sumsq_kernel(const double *__restrict__ x, int64_t rows,
     if (threadIdx.x == 0) out[0] = red[0];
 }
 
+// a warp per row (grid-strided), lanes over the columns
 template <typename XT>
 __global__ void check_finite_kernel(const XT *__restrict__ x, int64_t rows,
                                     int64_t cols, int64_t ld, int32_t *flag) {
-    int64_t total = rows * cols;
+    const int lane = threadIdx.x & 31;
     int bad = 0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double v = (double)x[(e / cols) * ld + e % cols];
-        bad |= !isfinite(v);
-    }
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < rows;
+         i += (int64_t)gridDim.x * (blockDim.x >> 5))
+        for (int64_t k = lane; k < cols; k += 32) bad |= !isfinite((double)x[i * ld + k]);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
@@ -782,7 +781,7 @@ void sumsq(cudaStream_t s, const double *x, int64_t rows, int64_t cols, int64_t 
 
 void check_finite(cudaStream_t s, const void *x, int xdt, int64_t rows, int64_t cols,
                   int64_t ld, int32_t *flag) {
-    unsigned g = blocks_for(rows * cols, 256, 4096);
+    unsigned g = blocks_for(rows * 32, 256, 4096);
     if (xdt == ELM_F64)
         check_finite_kernel<double><<<g, 256, 0, s>>>((const double *)x, rows, cols, ld, flag);
     else

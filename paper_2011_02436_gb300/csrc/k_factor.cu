@@ -354,15 +354,16 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     auto pbetter = [](unsigned long long ka, uint32_t oa, unsigned long long kb, uint32_t ob) {
         return ka > kb || (ka == kb && oa < ob);
     };
+    // warp-wide best by three hardware reductions: the largest key (high
+    // word, then low word among the lanes holding that high word), then
+    // the smallest ord among the lanes holding that key
     auto warp_best = [&](unsigned long long &k, uint32_t &o) {
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, off);
-            const uint32_t o2 = __shfl_xor_sync(0xffffffffu, o, off);
-            if (pbetter(k2, o2, k, o)) {
-                k = k2;
-                o = o2;
-            }
-        }
+        const uint32_t kh = (uint32_t)(k >> 32), kl = (uint32_t)k;
+        const uint32_t mh = __reduce_max_sync(0xffffffffu, kh);
+        const uint32_t ml = __reduce_max_sync(0xffffffffu, kh == mh ? kl : 0u);
+        const unsigned long long mk = ((unsigned long long)mh << 32) | ml;
+        o = __reduce_min_sync(0xffffffffu, k == mk ? o : 0xffffffffu);
+        k = mk;
     };
     // send this CTA's best (k, o) -- every thread passes its own -- with
     // the column's first `t` panel entries to every peer's slot `cr` of
@@ -375,13 +376,9 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
             wred_o[warp] = o;
         }
         __syncthreads();
-        k = wred_k[0];
-        o = wred_o[0];
-        for (int w = 1; w < FT / 32; w++)
-            if (pbetter(wred_k[w], wred_o[w], k, o)) {
-                k = wred_k[w];
-                o = wred_o[w];
-            }
+        k = lane < FT / 32 ? wred_k[lane] : 0ull;
+        o = lane < FT / 32 ? wred_o[lane] : 0xffffffffu;
+        warp_best(k, o);
         const bool any = k != 0ull;
         const int32_t bx = any ? (int32_t)(o & 0x3fffu) : -1;
         const int64_t xl = any ? bx - x0 : 0;

@@ -771,14 +771,21 @@ __device__ __forceinline__ double pow2_ceil(double v) {
 template <int PD, int DBITS, typename XT>
 __global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t n, int64_t ldx,
                                    int64_t Np, int64_t nK, __nv_bfloat16 *__restrict__ planes,
-                                   double *__restrict__ xs, float *__restrict__ xsf) {
+                                   double *__restrict__ xs, float *__restrict__ xsf,
+                                   int32_t *__restrict__ nonfinite) {
     constexpr int SH = (DBITS - 1) + DBITS * (PD - 1);
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= Np) return;
     double mx = 0.0;
+    bool bad = false;
     if (i < N)
-        for (int64_t k = lane; k < n; k += 32) mx = fmax(mx, fabs((double)X[i * ldx + k]));
+        for (int64_t k = lane; k < n; k += 32) {
+            const double v = (double)X[i * ldx + k];
+            bad |= !isfinite(v);
+            mx = fmax(mx, fabs(v));
+        }
+    if (__any_sync(0xffffffffu, bad) && lane == 0 && nonfinite) atomicOr(nonfinite, 1);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const double sc = pow2_ceil(mx);
     if (lane == 0) {
@@ -805,13 +812,20 @@ template <int PD, int DBITS>
 __global__ void digits_rows_f32_kernel(const float *__restrict__ X, int64_t N, int64_t n,
                                        int64_t ldx, int64_t Np, int64_t nK,
                                        __nv_bfloat16 *__restrict__ planes,
-                                       double *__restrict__ xs, float *__restrict__ xsf) {
+                                       double *__restrict__ xs, float *__restrict__ xsf,
+                                       int32_t *__restrict__ nonfinite) {
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= Np) return;
     float mx = 0.f;
+    bool bad = false;
     if (i < N)
-        for (int64_t k = lane; k < n; k += 32) mx = fmaxf(mx, fabsf(X[i * ldx + k]));
+        for (int64_t k = lane; k < n; k += 32) {
+            const float v = X[i * ldx + k];
+            bad |= !isfinite(v);
+            mx = fmaxf(mx, fabsf(v));
+        }
+    if (__any_sync(0xffffffffu, bad) && lane == 0 && nonfinite) atomicOr(nonfinite, 1);
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const double sc = pow2_ceil((double)mx);
     if (lane == 0) {
@@ -902,12 +916,12 @@ __global__ void digits_cols_par_kernel(const double *__restrict__ W, int64_t n, 
 }
 
 // Gram row scales: hs[j] = pow2_ceil(a_j) for hidden rows, 1 for padding
-// rows (target rows are set by the target slicer).
+// rows, 0 for target rows (filled in by the target slicer).
 __global__ void hs_kernel(const double *__restrict__ a, int64_t L, int64_t m, int64_t Lp,
                           double *__restrict__ hs) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= Lp || (j >= L && j < L + m)) return;
-    hs[j] = j < L ? (a ? pow2_ceil(a[j]) : 1.0) : 1.0;
+    if (j >= Lp) return;
+    hs[j] = j < L ? (a ? pow2_ceil(a[j]) : 1.0) : (j < L + m ? 0.0 : 1.0);
 }
 
 // Sigmoid table: sigma(z_k) and sigma'(z_k) as double-float pairs.
@@ -921,32 +935,45 @@ __global__ void sigmoid_table_kernel(float4 *__restrict__ tab) {
     tab[k] = make_float4(s0h, (float)(s0 - (double)s0h), s1h, (float)(s1 - (double)s1h));
 }
 
+// max_i |T[i, c]| into hs[L + c] (set to 0 by hs_kernel): non-negative
+// doubles order like their 64-bit patterns, so an integer atomicMax keeps
+// the largest.  Blocks of 32 columns x 8 row phases, grid-strided rows.
+__global__ void t_colmax_kernel(const double *__restrict__ T, int64_t ldt, int64_t N, int64_t m,
+                                int64_t L, double *__restrict__ hs) {
+    __shared__ double red[8][33];
+    const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    double mx = 0.0;
+    if (c < m)
+        for (int64_t i = (int64_t)blockIdx.y * 8 + threadIdx.y; i < N; i += (int64_t)gridDim.y * 8)
+            mx = fmax(mx, fabs(T[i * ldt + c]));
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < m) {
+        for (int y = 1; y < 8; y++) mx = fmax(mx, red[y][threadIdx.x]);
+        if (mx > 0.0)
+            atomicMax(reinterpret_cast<unsigned long long *>(hs + L + c),
+                      (unsigned long long)__double_as_longlong(mx));
+    }
+}
 // T (N x m) -> digit plane rows L + c (column c of T), scaled by
-// hs[L + c] = pow2_ceil(max_i |T[i, c]|).  One block per target column.
+// hs[L + c] = pow2_ceil(max_i |T[i, c]|); thread per sample, grid.y = c.
+// Block (0, c) writes the scale back over the maximum; a block that reads
+// it afterwards gets the same scale (pow2_ceil is idempotent).
 template <int PD, int DBITS>
 __global__ void t_digits_kernel(const double *__restrict__ T, int64_t ldt, int64_t N, int64_t L,
                                 int64_t Lp, int64_t Np, __nv_bfloat16 *__restrict__ planes,
                                 double *__restrict__ hs) {
-    const int64_t c = blockIdx.x;
-    __shared__ double red[256];
-    double mx = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) mx = fmax(mx, fabs(T[i * ldt + c]));
-    red[threadIdx.x] = mx;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-        __syncthreads();
-    }
-    const double sc = pow2_ceil(red[0]);
-    if (threadIdx.x == 0) hs[L + c] = sc;
-    const double inv = 1.0 / sc;
-    for (int64_t i = threadIdx.x; i < Np; i += blockDim.x) {
-        float d[PD];
-        split_digits<PD, DBITS>(i < N ? T[i * ldt + c] * inv : 0.0, d);
+    const int64_t c = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double sc = pow2_ceil(hs[L + c]);
+    __syncthreads();   // every thread of block (0, c) has read before the write-back
+    if (blockIdx.x == 0 && threadIdx.x == 0) hs[L + c] = sc;
+    if (i >= Np) return;
+    float d[PD];
+    split_digits<PD, DBITS>(i < N ? T[i * ldt + c] * (1.0 / sc) : 0.0, d);
 #pragma unroll
-        for (int p = 0; p < PD; p++)
-            planes[(int64_t)p * Lp * Np + (L + c) * Np + i] = __float2bfloat16_rn(d[p]);
-    }
+    for (int p = 0; p < PD; p++)
+        planes[(int64_t)p * Lp * Np + (L + c) * Np + i] = __float2bfloat16_rn(d[p]);
 }
 
 // ------------------------------------------------------------ host side
@@ -1053,18 +1080,19 @@ size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m) {
 
 // H = a g(X W + b) on the tensor cores, emitted directly as the Gram digit
 // planes (rows < L and padding rows; target rows are left to oz_t_digits),
-// with the row scales hs and, if Ht != NULL, FP64 H^T.
+// with the row scales hs and, if Ht != NULL, FP64 H^T; the digit slicer of X
+// also records a non-finite X in *nonfinite (when given).
 void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
-               int64_t ldh, int *err, void *Hdf) {
+               int64_t ldh, int *err, void *Hdf, int32_t *nonfinite) {
     const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
     if (xdt == ELM_F64)
         digits_rows_kernel<HID_PX, HID_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf);
+            (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf, nonfinite);
     else
         digits_rows_f32_kernel<HID_PX, HID_BITS><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf);
+            (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf, nonfinite);
     ELM_CHECK_LAUNCH();
     col_scale_kernel<<<(unsigned)((Lp + 31) / 32), 256, 0, s>>>(W, n, L, ldw, Lp, w.ws);
     ELM_CHECK_LAUNCH();
@@ -1121,8 +1149,12 @@ void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_
                  __nv_bfloat16 *planes, double *hs) {
     if (m <= 0) return;
     const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
-    t_digits_kernel<GRAM_PH, GRAM_BITS><<<(unsigned)m, 256, 0, s>>>(T, ldt, N, L, Lp, Np, planes,
-                                                                     hs);
+    const int64_t ry = (N + 7) / 8 < 512 ? (N + 7) / 8 : 512;
+    t_colmax_kernel<<<dim3((unsigned)((m + 31) / 32), (unsigned)(ry > 0 ? ry : 1)), dim3(32, 8), 0,
+                      s>>>(T, ldt, N, m, L, hs);
+    ELM_CHECK_LAUNCH();
+    t_digits_kernel<GRAM_PH, GRAM_BITS><<<dim3((unsigned)((Np + 255) / 256), (unsigned)m), 256, 0,
+                                          s>>>(T, ldt, N, L, Lp, Np, planes, hs);
     ELM_CHECK_LAUNCH();
 }
 

@@ -96,3 +96,13 @@ def test_train_host_buffers_mixed(elm, ctx):
     ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], 0, p["T"])
     assert res["rank"] == r
     assert rel(prob["beta"], ref) <= 1e-6
+
+
+@pytest.mark.parametrize("xdt,bad", [(np.float32, np.nan), (np.float64, np.inf),
+                                     (np.float32, -np.inf)])
+def test_nonfinite_input_is_reported_mixed(elm, ctx, xdt, bad):
+    # the digit slicer of X records the non-finite entry (no separate pass)
+    p = synth.make_problem(300, 9, 40, 2, x_dtype=xdt)
+    p["X"][117, 4] = bad
+    res = elm.elm_train(ctx, problem(p), precision=elm.PREC_MIXED, check=False)[0]
+    assert res["status"] == 4                                # ELM_ERR_NUMERIC
