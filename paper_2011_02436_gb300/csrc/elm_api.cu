@@ -386,6 +386,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     const int hs_split = htr_df_nsplit(L, N, ctx->sm_count);
     In X, W, b, a, T;
     double *hs, *G, *R, *Rt, *beta, *dB, *Rres, *Gres, *hpart, *norms, *Hdf, *betaT;
+    long long *gpart;
     __nv_bfloat16 *planes;
     int32_t *flag;
     int *err;
@@ -409,6 +410,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         Rres = ar.take<double>(N * m);
         Gres = ar.take<double>(L * m);
         hpart = ar.take<double>((int64_t)hs_split * L * m);
+        gpart = (long long *)ar.take<char>(oz_gram_part_bytes());
         betaT = ar.take<double>(L * (m < 32 ? m : 32));
         norms = ar.take<double>(2);
         flag = ar.take<int32_t>(1);
@@ -429,7 +431,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
     mark(ctx, 1);
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
-    oz_gram(s, planes, hs, N, L, m, G, Lt, err);
+    oz_gram(s, planes, hs, N, L, m, G, Lt, err, gpart);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4 (double-float)
     factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true);

@@ -281,6 +281,8 @@ struct OzParams {
     int64_t ldo;
     int *err;
     int64_t ntiles;     // tiles in the tile set
+    int64_t whole;      // tiles below this run over the whole K range, one CTA each
+    long long *part;    // EPI == 0: int64 partial sums of the tiles from `whole` on
     ActParams ap;       // used when the kernel's EPI != 0
 };
 
@@ -406,6 +408,40 @@ __device__ __forceinline__ void tile_coords(const OzParams &P, int64_t t, int64_
     }
 }
 
+// Work of one CTA: the tiles b, b + G, ... below P.whole over their whole K
+// range, then a contiguous share of the remaining tiles' K chunks (tile
+// after tile), so the last, partial wave of tiles is spread over every CTA.
+// Chunk boundaries keep each piece's running sums exact; the pieces of a
+// split tile are added as int64 (order-independent) into P.part.
+struct WorkIter {
+    int64_t t_next, pos, pos_end;
+};
+__device__ __forceinline__ WorkIter work_begin(const OzParams &P, int nchunk) {
+    WorkIter w;
+    const int64_t G = gridDim.x, R = (P.ntiles - P.whole) * nchunk;
+    w.t_next = blockIdx.x;
+    w.pos = R * (int64_t)blockIdx.x / G;
+    w.pos_end = R * ((int64_t)blockIdx.x + 1) / G;
+    return w;
+}
+__device__ __forceinline__ bool work_next(const OzParams &P, int nchunk, WorkIter &w,
+                                          int64_t &t, int &c_lo, int &c_hi) {
+    if (w.t_next < P.whole) {
+        t = w.t_next;
+        c_lo = 0;
+        c_hi = nchunk;
+        w.t_next += gridDim.x;
+        return true;
+    }
+    if (w.pos >= w.pos_end) return false;
+    t = P.whole + w.pos / nchunk;
+    c_lo = (int)(w.pos % nchunk);
+    const int64_t left = w.pos_end - w.pos;
+    c_hi = left < nchunk - c_lo ? c_lo + (int)left : nchunk;
+    w.pos += c_hi - c_lo;
+    return true;
+}
+
 // Persistent kernel: CTA b processes tiles b, b + G, b + 2G, ... (G = grid
 // size).  The TMA ring and all barrier phases run on across tiles, so the
 // producer prefetches the next tile while the epilogue of the last one runs;
@@ -438,7 +474,6 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nslab = (int)(P.K / SK);
     const int nchunk = (nslab + CHUNK_SLABS - 1) / CHUNK_SLABS;
-    const int64_t t_first = blockIdx.x, t_step = gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -466,11 +501,14 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (warp == 0) {
         if (lane == 0) {
             // ---------------------------------------------------- producer
-            int64_t g = 0, issued = 0;
-            for (int64_t t = t_first; t < P.ntiles && !*abort; t += t_step) {
+            int64_t g = 0, issued = 0, t;
+            int c_lo, c_hi;
+            WorkIter wi = work_begin(P, nchunk);
+            while (!*abort && work_next(P, nchunk, wi, t, c_lo, c_hi)) {
                 int64_t m0, n0;
                 tile_coords(P, t, m0, n0);
-                for (int s = 0; s < nslab; s++, g++) {
+                const int s_hi = c_hi * CHUNK_SLABS < nslab ? c_hi * CHUNK_SLABS : nslab;
+                for (int s = c_lo * CHUNK_SLABS; s < s_hi; s++, g++) {
                     const int st = (int)(g % STAGES);
                     if (g >= STAGES &&
                         !mbar_wait(&empty_bar[st], (uint32_t)(((g / STAGES) - 1) & 1), abort))
@@ -501,9 +539,12 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issue
-            int64_t g = 0, gc = 0;
-            for (int64_t t = t_first; t < P.ntiles && !*abort; t += t_step) {
-                for (int s = 0; s < nslab && !*abort; s++, g++) {
+            int64_t g = 0, gc = 0, t;
+            int c_lo, c_hi;
+            WorkIter wi = work_begin(P, nchunk);
+            while (!*abort && work_next(P, nchunk, wi, t, c_lo, c_hi)) {
+                const int s_hi = c_hi * CHUNK_SLABS < nslab ? c_hi * CHUNK_SLABS : nslab;
+                for (int s = c_lo * CHUNK_SLABS; s < s_hi && !*abort; s++, g++) {
                     const int st = (int)(g % STAGES);
                     const bool first = (s % CHUNK_SLABS) == 0;
                     // accumulators free again once the previous chunk is read
@@ -545,7 +586,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         }
                     }
                     mma_commit(&empty_bar[st]);
-                    if ((s % CHUNK_SLABS) == CHUNK_SLABS - 1 || s == nslab - 1) {
+                    if ((s % CHUNK_SLABS) == CHUNK_SLABS - 1 || s == s_hi - 1) {
                         mma_commit(&acc_full);
                         gc++;
                     }
@@ -564,19 +605,21 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int c0 = ((warp - 2) >> 2) * 32;       // this warp's 32 columns of the tile
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
         const bool direct = (EPI != 0) && nchunk == 1;
-        int64_t gc = 0;
+        int64_t gc = 0, t;
+        int c_lo, c_hi;
         bool ok = true;
-        for (int64_t t = t_first; t < P.ntiles && ok; t += t_step) {
+        WorkIter wi = work_begin(P, nchunk);
+        while (ok && work_next(P, nchunk, wi, t, c_lo, c_hi)) {
             int64_t m0, n0;
             tile_coords(P, t, m0, n0);
             const int64_t m = m0 + quarter * 32 + lane;
             long long run[32];     // EPI == 0: final sums of this warp's 32 columns
-            for (int c = 0; c < nchunk; c++, gc++) {
+            for (int c = c_lo; c < c_hi; c++, gc++) {
                 // warp-uniform decision: TMEM loads below are warp-collective
                 ok = __all_sync(0xffffffffu, mbar_wait(&acc_full, (uint32_t)(gc & 1), abort));
                 if (!ok) break;
                 tc_fence_after();
-                const bool last = c == nchunk - 1;
+                const bool last = c == c_hi - 1;
                 // Each TMEM load is issued before the arithmetic on the previous
                 // one (two register buffers), so its latency overlaps that work.
                 const auto diag_addr = [&](int k) {   // k = h ND + (t - 2)
@@ -625,7 +668,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         long long *r = run + h * 16;
-                        if (c == 0) {
+                        if (c == c_lo) {
 #pragma unroll
                             for (int i = 0; i < 16; i++) r[i] = 0;
                         } else {
@@ -686,7 +729,17 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             }
             if (!ok || *abort) break;
             // ---------------------------------------------------- output
-            if (EPI == 0) {
+            if (EPI == 0 && t >= P.whole) {
+                // a piece of a split tile (all of it, possibly): exact int64 adds,
+                // column-major in the tile so a warp's 32 lanes (rows) hit
+                // consecutive addresses; gram_tail_kernel writes the tile
+                long long *pt = P.part + (t - P.whole) * (BM * BN) + (int64_t)c0 * BM +
+                                quarter * 32 + lane;
+#pragma unroll
+                for (int i = 0; i < 32; i++)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(pt + i * BM),
+                              (unsigned long long)run[i]);
+            } else if (EPI == 0) {
                 const double unit = ldexp(1.0, -DBITS * (TMAX - 2));
                 if (m < P.m_valid) {
                     const double rs = P.out_scale * unit * P.rscale[m];
@@ -725,6 +778,24 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                      "r"(TMEM_COLS));
     }
     if (threadIdx.x == 0 && *abort) atomicExch(P.err, 1);
+}
+
+// Split tiles of the Gram: FP64 values from the int64 sums of their pieces,
+// with the same expression as the whole-tile epilogue (bitwise the same
+// result).  grid = (BM BN / 256, split tiles); element e is column-major.
+template <int DBITS, int TMAX>
+__global__ void gram_tail_kernel(const OzParams P) {
+    const int64_t k = blockIdx.y;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    int64_t m0, n0;
+    tile_coords(P, P.whole + k, m0, n0);
+    const int64_t m = m0 + e % BM, n = n0 + e / BM;
+    if (m >= P.m_valid || n >= P.n_valid || (P.gram && n > m)) return;
+    const double unit = ldexp(1.0, -DBITS * (TMAX - 2));
+    const double rs = P.out_scale * unit * P.rscale[m];
+    const double v = (double)P.part[k * (BM * BN) + e] * rs * P.cscale[n];
+    P.out[m * P.ldo + n] = v;
+    if (P.gram && n < m) P.out[n * P.ldo + m] = v;
 }
 
 // ------------------------------------------------------------ digit slicing
@@ -1008,6 +1079,16 @@ CUtensorMap make_map(const __nv_bfloat16 *base, int64_t rows, int64_t K, int box
     return m;
 }
 
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        ELM_CUDA(cudaGetDevice(&dev));
+        ELM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
 template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI>
 void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B, OzParams P,
                   int64_t ntiles) {
@@ -1019,16 +1100,14 @@ void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B
         ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        ELM_CUDA(cudaGetDevice(&dev));
-        ELM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    }
+    const int sms = sm_count();
     CUtensorMap ma = make_map(A, PA * P.a_rows, P.K, BM);
     CUtensorMap mb = make_map(B, PB * P.b_rows, P.K, BN);
     P.ntiles = ntiles;
-    const int64_t grid = ntiles < sms ? ntiles : sms;
+    // only the Gram epilogue handles split tiles
+    if (EPI != 0 || !P.part || P.whole > ntiles || P.whole < 0) P.whole = ntiles;
+    // split tiles spread over every SM; otherwise one CTA per tile at most
+    const int64_t grid = (ntiles < sms && P.whole == ntiles) ? ntiles : sms;
     k<<<(unsigned)grid, NTHREADS, smem, s>>>(ma, mb, P);
     ELM_CHECK_LAUNCH();
 }
@@ -1136,6 +1215,7 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ap.Hdf = (float2 *)Hdf;
     P.ap.ldhd = L;
     P.ap.ldh = ldh;
+    P.whole = (Lp / BM) * (Np / BN);   // no split tiles
     if (Ht)
         launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 2>(s, w.wp, w.xp, P,
                                                                (Lp / BM) * (Np / BN));
@@ -1160,11 +1240,17 @@ void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_
 
 // G (Lt x Lt FP64, both triangles, Lt = L + m) = Gram of the augmented rows
 // [H^T; T^T] from the digit planes.
+size_t oz_gram_part_bytes() { return (size_t)sm_count() * BM * BN * sizeof(long long); }
+
 void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
-             int64_t L, int64_t m, double *G, int64_t ldg, int *err) {
+             int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part) {
     const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
-    const int64_t nJ = Lp / BM;
+    const int64_t nJ = Lp / BM, ntiles = nJ * (nJ + 1);
+    const int64_t sms = sm_count();
     OzParams P{};
+    // the last, partial wave of tiles is split by K chunks over every CTA
+    P.whole = (part && ntiles % sms != 0) ? ntiles / sms * sms : ntiles;
+    P.part = part;
     P.a_rows = Lp;
     P.b_rows = Lp;
     P.K = Np;
@@ -1178,8 +1264,16 @@ void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int6
     P.out = G;
     P.ldo = ldg;
     P.err = err;
-    launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS, 0>(s, planes, planes, P,
-                                                               nJ * (nJ + 1));
+    if (P.whole < ntiles)
+        ELM_CUDA(cudaMemsetAsync(part, 0, (size_t)(ntiles - P.whole) * BM * BN * sizeof(long long),
+                                 s));
+    launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS, 0>(s, planes, planes, P, ntiles);
+    if (P.whole < ntiles) {
+        P.ntiles = ntiles;
+        gram_tail_kernel<GRAM_BITS, GRAM_TMAX>
+            <<<dim3(BM * BN / 256, (unsigned)(ntiles - P.whole)), 256, 0, s>>>(P);
+        ELM_CHECK_LAUNCH();
+    }
 }
 
 }  // namespace elm
