@@ -131,11 +131,18 @@ typedef struct elm_train_opts {
  * the context's stream (read them with elm_phase_times). */
 #define ELM_FLAG_PHASE_TIMING 1
 
+/* elm_result.form: the route that produced beta */
+#define ELM_FORM_FP64 0          /* FP64 form (ELM_PREC_FP64)                   */
+#define ELM_FORM_MIXED 1         /* mixed form                                  */
+#define ELM_FORM_MIXED_TO_FP64 2 /* mixed form handed over to the FP64 form     */
+
 typedef struct elm_result {
     int64_t rank;         /* r                                              */
     int32_t refine_iters; /* refinement steps taken                         */
     int32_t status;       /* elm_status of this problem                     */
     double rel_update;    /* ||dbeta||_F / ||beta||_F of the last step      */
+    int32_t form;         /* ELM_FORM_*                                     */
+    int32_t reserved;     /* 0                                              */
 } elm_result;
 
 /*
@@ -147,7 +154,8 @@ typedef struct elm_result {
  * of `count` entries, or NULL.  Returns ELM_OK or the first failing status.
  * ELM_PREC_MIXED trains a problem in the FP64 form instead when its
  * tensor-core Gram cannot settle it: a rejected pivot above the FP64 rank
- * threshold, or refinement that does not reach refine_tol.
+ * threshold, or refinement that does not reach refine_tol (results[i].form
+ * tells which route produced beta).
  */
 int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
               const elm_train_opts *opts, elm_result *results);

@@ -168,7 +168,7 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
               refine_tol=0.0, check=True, flags=0):
     """Train each problem (dict with X, W, b, a, act, T and optional beta
     output).  Returns a list of dicts (rank, refine_iters, status,
-    rel_update); beta is written into problem['beta']."""
+    rel_update, form: FORM_*); beta is written into problem['beta']."""
     if isinstance(problems, dict):
         problems = [problems]
     arr = (_lib.elm_problem * len(problems))(*[_problem(p) for p in problems])
@@ -179,7 +179,10 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
     if check:
         _check(ctx, st)
     return [dict(rank=r.rank, refine_iters=r.refine_iters, status=r.status,
-                 rel_update=r.rel_update) for r in res]
+                 rel_update=r.rel_update, form=r.form) for r in res]
+
+
+FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64 = 0, 1, 2
 
 
 FLAG_PHASE_TIMING = 1

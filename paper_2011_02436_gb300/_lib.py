@@ -23,7 +23,8 @@ class elm_train_opts(C.Structure):
 
 
 class elm_result(C.Structure):
-    _fields_ = [("rank", i64), ("refine_iters", i32), ("status", i32), ("rel_update", dbl)]
+    _fields_ = [("rank", i64), ("refine_iters", i32), ("status", i32), ("rel_update", dbl),
+                ("form", i32), ("reserved", i32)]
 
 
 # (name, restype, argtypes) for every entry point declared in include/elm.h

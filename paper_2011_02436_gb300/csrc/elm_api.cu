@@ -275,6 +275,8 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res);
 
 void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     if (P.prec == ELM_PREC_MIXED) return train_mixed(ctx, P, res);
+    res->form = ELM_FORM_FP64;
+    res->reserved = 0;
     const elm_problem &pb = *P.p;
     cudaStream_t s = ctx->stream;
     const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
@@ -364,10 +366,6 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
 }
 
 // Mixed form: H, H^T H and H^T T from exact digit slices on the tensor
-// cores (Gram accurate to FP64 rounding of the 2^-31-grid H), rank decision,
-// factorisation and solves in FP64, then refinement steps on the normal
-// equations with the FP64 residual Z - S beta.
-// Mixed form: H, H^T H and H^T T from exact digit slices on the tensor
 // cores (the Gram is that of H on a 2^-34 grid), rank decision and
 // factorisation in double-float, FP64 solves, then refinement steps whose
 // residual G = H^T (T - H beta) reads H itself, kept in double-float
@@ -430,6 +428,15 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     // so the Gram phase times the Gram kernel alone)
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
     mark(ctx, 1);
+    auto fallback = [&]() {
+        Problem P64 = P;
+        P64.prec = ELM_PREC_FP64;
+        P64.max_refine = 2;
+        P64.tau = P.tau64;
+        P64.refine_tol = 1e-12;
+        train_one(ctx, P64, res);
+        res->form = ELM_FORM_MIXED_TO_FP64;
+    };
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
     oz_gram(s, planes, hs, N, L, m, G, Lt, err, gpart);
     mark(ctx, 2);
@@ -446,6 +453,8 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     res->refine_iters = 0;
     res->rel_update = 0.0;
     res->status = ELM_OK;
+    res->form = ELM_FORM_MIXED;
+    res->reserved = 0;
     if (terr || (fl & 2)) {
         res->status = ELM_ERR_TIMEOUT;
         return;
@@ -454,14 +463,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         res->status = ELM_ERR_NUMERIC;
         return;
     }
-    auto fallback = [&]() {
-        Problem P64 = P;
-        P64.prec = ELM_PREC_FP64;
-        P64.max_refine = 2;
-        P64.tau = P.tau64;
-        P64.refine_tol = 1e-12;
-        train_one(ctx, P64, res);
-    };
+    // a rank decision the mixed Gram cannot settle goes to the FP64 form
     if (r < L && stop_val > P.tau64) return fallback();
     const double *Z = G + L;   // Z[l, c] = G[l, L + c]
     // Eq. 5, Eq. 7 (FP64)

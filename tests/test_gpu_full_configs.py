@@ -10,7 +10,10 @@ any size and recomputes H itself (plain FP64, row chunks):
   * the minimum-norm split over planted copies (Moore-Penrose, Eq. 5):
     exact duplicates share equally, a copy scaled by s gets s times the
     original's weight;
-  * for the smallest batched problems, the oracle's own beta within 1e-6.
+  * for the smallest batched problems, the oracle's own beta within 1e-6;
+  * every batched problem the mixed form keeps (form FORM_MIXED) within 1e-6
+    of the FP64 form's beta (whose own parity with the oracle is tested
+    elsewhere); the others were handed to the FP64 form whole.
 """
 import numpy as np
 import pytest
@@ -83,6 +86,7 @@ def test_sparse_pixels_full(elm, ctx):
     p = synth.workload_sparse_pixels()
     res, beta = train_mixed(elm, ctx, p)
     assert res["status"] == 0 and res["rank"] == 2000
+    assert res["form"] == elm.FORM_MIXED
     assert optimality(p, beta) < 1e-9
 
 
@@ -90,6 +94,7 @@ def test_rank_deficient_full(elm, ctx):
     p = synth.workload_rank_deficient()
     res, beta = train_mixed(elm, ctx, p)
     assert res["status"] == 0 and res["rank"] == p["rank"] == 5100
+    assert res["form"] == elm.FORM_MIXED
     assert copies_share(p, beta) < 1e-9
     assert optimality(p, beta) < 1e-9
 
@@ -119,6 +124,17 @@ def test_batched_full(elm, ctx):
     # least-squares optimality on a spread of the others
     for i in order[3::16]:
         assert optimality(ps[i], probs[i]["beta"].cpu().numpy()) < 1e-9
+    # the mixed form's own results against the FP64 form
+    assert all(r["form"] in (elm.FORM_MIXED, elm.FORM_MIXED_TO_FP64) for r in res)
+    assert sum(r["form"] == elm.FORM_MIXED for r in res) >= 100
+    for p, pr, r in zip(ps, probs, res):
+        if r["form"] != elm.FORM_MIXED:
+            continue
+        p64 = dict(pr, beta=torch.empty_like(pr["beta"]))
+        r64 = elm.elm_train(ctx, p64, precision=elm.PREC_FP64)[0]
+        assert r64["form"] == elm.FORM_FP64 and r64["rank"] == r["rank"]
+        b64 = p64["beta"].cpu().numpy()
+        assert np.linalg.norm(pr["beta"].cpu().numpy() - b64) / np.linalg.norm(b64) < 1e-6
 
 
 @pytest.mark.slow
@@ -126,4 +142,5 @@ def test_large_full(elm, ctx):
     p = synth.workload_large()
     res, beta = train_mixed(elm, ctx, p)
     assert res["status"] == 0 and res["rank"] == 8000
+    assert res["form"] == elm.FORM_MIXED
     assert optimality(p, beta, rows=25000) < 1e-9

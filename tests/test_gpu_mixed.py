@@ -58,6 +58,7 @@ def test_train_small_fp64_workload_mixed(elm, ctx):
     res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
     ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
     assert res["rank"] == r == 180
+    assert res["form"] == elm.FORM_MIXED                   # no hand-over to FP64
     assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
 
 
