@@ -221,8 +221,9 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
 void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
                  __nv_bfloat16 *planes, double *hs);
 // G (Lt x Lt, both triangles, Lt = L + m): Gram of [H^T; T^T] from the planes.
-// part (oz_gram_part_bytes()): int64 partial sums of the tiles of the last,
-// partial wave, which are split over every SM by K chunks (NULL: no split).
+// part (oz_gram_part_bytes()): int64 partial sums of the tiles of a last,
+// partial wave of at most half the SM count, which are split over every SM
+// by K chunks (NULL: no split).
 size_t oz_gram_part_bytes();
 void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
              int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part);
