@@ -767,11 +767,13 @@ trailing_df_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     }
 }
 
-// 64 x 64 lower tiles for large active matrices: each thread keeps a 4 x 4
-// block (16 independent double-float chains) and the panel rows of the
-// tile are staged once in shared memory.
-constexpr int TT2 = 64;
-__global__ void __launch_bounds__(256)
+// 64 x 64 lower tiles for large active matrices, each split into two CTAs
+// of 32 rows x 64 columns (128 threads, 4 x 4 independent double-float
+// chains per thread): the finer units balance the single wave over the SMs
+// (up to 8 resident per SM instead of 4).  The tile's panel rows are
+// staged once per CTA in shared memory.
+constexpr int TT2 = 64, TR2 = 32;
+__global__ void __launch_bounds__(128, 8)
 trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
                      const F2 *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
                      const FactorState *__restrict__ st) {
@@ -784,33 +786,35 @@ trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     while (J * (J + 1) / 2 > t) J--;
     while ((J + 1) * (J + 2) / 2 <= t) J++;
     const int64_t I = t - J * (J + 1) / 2;
-    const int64_t r0 = J * TT2, c0 = I * TT2;
+    const int64_t r0 = J * TT2 + (int64_t)blockIdx.y * TR2, c0 = I * TT2;
     if (r0 >= Lr) return;
-    __shared__ F2 Pr[PNB][TT2];
+    __shared__ F2 Pr[PNB][TR2];
     __shared__ F2 Pc[PNB][TT2];
-    __shared__ int32_t rr_[TT2], rc_[TT2];
-    if (threadIdx.x < TT2) {
+    __shared__ int32_t rr_[TR2], rc_[TT2];
+    if (threadIdx.x < TR2) {
         const int64_t x = r0 + threadIdx.x;
         rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
-    } else if (threadIdx.x < 2 * TT2) {
-        const int64_t y = c0 + threadIdx.x - TT2;
-        rc_[threadIdx.x - TT2] = y < Lr ? rem[y] : -1;
+    }
+    if (threadIdx.x < TT2) {
+        const int64_t y = c0 + threadIdx.x;
+        rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < PNB * TT2; e += 256) {
+    for (int e = threadIdx.x; e < PNB * TT2; e += 128) {
         const int tt = e / TT2, k = e % TT2;
-        Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : F2{0.f, 0.f};
         Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : F2{0.f, 0.f};
+        if (k < TR2)
+            Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : F2{0.f, 0.f};
     }
     __syncthreads();
-    // thread (ty, tx) owns rows ty + 16 p and columns tx + 16 q, p, q < 4
+    // thread (ty, tx) owns rows ty + 8 p and columns tx + 16 q, p, q < 4
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     float ah[4][4], al[4][4];
 #pragma unroll
     for (int p = 0; p < 4; p++)
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const int a = rr_[ty + 16 * p], b = rc_[tx + 16 * q];
+            const int a = rr_[ty + 8 * p], b = rc_[tx + 16 * q];
             const F2 v = (a >= 0 && b >= 0) ? A[(int64_t)a * lda + b] : F2{0.f, 0.f};
             ah[p][q] = v.h;
             al[p][q] = v.l;
@@ -819,7 +823,7 @@ trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
         F2 u[4], w[4];
 #pragma unroll
         for (int p = 0; p < 4; p++) {
-            u[p] = Pr[tt][ty + 16 * p];
+            u[p] = Pr[tt][ty + 8 * p];
             w[p] = Pc[tt][tx + 16 * p];
         }
 #pragma unroll
@@ -829,7 +833,7 @@ trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     }
 #pragma unroll
     for (int p = 0; p < 4; p++) {
-        const int64_t x = r0 + ty + 16 * p;
+        const int64_t x = r0 + ty + 8 * p;
         if (x >= Lr) continue;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
@@ -1303,7 +1307,7 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
             int64_t T = (Lup + TT - 1) / TT;
             if (df && Lup > 768) {
                 const int64_t T2 = (Lup + TT2 - 1) / TT2;
-                trailing_df64_kernel<<<(unsigned)(T2 * (T2 + 1) / 2), 256, 0, s>>>(
+                trailing_df64_kernel<<<dim3((unsigned)(T2 * (T2 + 1) / 2), TT2 / TR2), 128, 0, s>>>(
                     (const F2 *)Ac, (F2 *)An, L, (const F2 *)w.P, L, w.rem, w.st);
             } else if (df)
                 trailing_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
