@@ -221,7 +221,12 @@ WORKLOADS = {
                 "L in [100,3000], sigmoid/tanh, 2-26 one-hot classes"),
     "large": (lambda rows: [synth.workload_large()],
               "large ELM: X 500000x128 U[-1,1] FP32, L=8000 sigmoid, 20 one-hot classes"),
+    # the shape of the paper's Table 1 experiment; L from --hidden
+    "gina_shaped": (lambda rows: [synth.workload_gina_shaped(L=ARGS_HIDDEN[0])],
+                    "Table-1-shaped ELM: X 3468x971 (80% zeros, U[0,1], FP32), L={L} sigmoid, "
+                    "2 one-hot classes"),
 }
+ARGS_HIDDEN = [2000]
 
 
 def run_native(args):
@@ -239,6 +244,7 @@ def run_native(args):
     prec = elm.PREC_MIXED if args.precision == "mixed" else elm.PREC_FP64
 
     gen, desc = WORKLOADS[args.workload]
+    desc = desc.replace("{L}", str(args.hidden))
     plist = gen(args.rows)
     probs, hosts = [], []
     for p in plist:
@@ -391,7 +397,11 @@ def main():
                     help="rows of the sparse-pixel workload (smaller only for profiling captures)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sparse_pixels",
                     help="the timed workload (the default is the headline configuration)")
+    ap.add_argument("--hidden", type=int, default=2000,
+                    help="hidden width L of the gina_shaped workload (the paper's Table 1 "
+                         "uses 500, 1000, 1500, 2000)")
     args = ap.parse_args()
+    ARGS_HIDDEN[0] = args.hidden
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

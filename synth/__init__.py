@@ -200,6 +200,16 @@ def workload_batched(count: int = 128, N_range=(5000, 50000),
             for i in range(count)]
 
 
+def workload_gina_shaped(L: int = 2000, **kw):
+    """The shape of the paper's Table 1 experiment (3468 samples x 971
+    features, L in {500, 1000, 1500, 2000}, sigmoid, two classes) on
+    synthetic inputs: entries 0 w.p. 0.8 else U[0,1] (FP32)."""
+    args = dict(N=3468, n=971, L_unique=L, m=2, x_kind="uniform01", x_sparsity=0.8,
+                x_dtype=np.float32, seed=SEED_BASE + 1000 * 6 + L)
+    args.update(kw)
+    return make_problem(**args)
+
+
 def workload_large(**kw):
     """500000x128 U[-1,1] FP32, L=8000 sigmoid, 20 one-hot classes."""
     args = dict(N=500000, n=128, L_unique=8000, m=20, x_kind="uniform11",

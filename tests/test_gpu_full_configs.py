@@ -40,7 +40,7 @@ def ctx(elm):
     c.close()
 
 
-def train_mixed(elm, ctx, p):
+def train_mixed(elm, ctx, p, precision=None):
     import torch
     dev = torch.device("cuda", 0)
     L, m = p["W"].shape[1], p["T"].shape[1]
@@ -49,7 +49,7 @@ def train_mixed(elm, ctx, p):
                 a=None if p.get("a") is None else torch.from_numpy(p["a"]).to(dev),
                 act=int(p.get("act", 0)), T=torch.from_numpy(p["T"]).to(dev),
                 beta=torch.empty((L, m), dtype=torch.float64, device=dev))
-    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED if precision is None else precision)[0]
     return res, prob["beta"].cpu().numpy()
 
 
@@ -144,3 +144,16 @@ def test_large_full(elm, ctx):
     assert res["status"] == 0 and res["rank"] == 8000
     assert res["form"] == elm.FORM_MIXED
     assert optimality(p, beta, rows=25000) < 1e-9
+
+
+@pytest.mark.parametrize("L", [500, 2000])
+def test_gina_shaped_matches_oracle(elm, ctx, L):
+    """The shape of the paper's Table 1 experiment (3468 x 971, L = 500 and
+    2000): the oracle end to end, both forms."""
+    p = synth.workload_gina_shaped(L=L)
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], None, int(p["act"]), p["T"])
+    assert r == L
+    for prec, tol in ((elm.PREC_MIXED, 1e-6), (elm.PREC_FP64, 1e-9)):
+        res, beta = train_mixed(elm, ctx, p, prec)
+        assert res["status"] == 0 and res["rank"] == r
+        assert np.linalg.norm(beta - ref) / np.linalg.norm(ref) < tol

@@ -17,6 +17,8 @@ CASES = {
     "scaled": lambda: synth.make_problem(1500, 20, 140, 5, n_dup=10, n_scaled=30,
                                          x_kind="uniform11"),
     "wide": lambda: synth.make_problem(50, 8, 80, 3, x_dtype=np.float64, x_kind="normal"),
+    "gina_shaped_500": lambda: synth.workload_gina_shaped(L=500),
+    "gina_shaped_2000": lambda: synth.workload_gina_shaped(L=2000),
 }
 
 
