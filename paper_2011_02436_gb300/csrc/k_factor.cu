@@ -124,9 +124,8 @@ struct PanelArith<true> {
     static __device__ __forceinline__ double to_double(T v) { return f2d(v.h) + f2d(v.l); }
 };
 
-// S -> A = diag(s) S diag(s), s_j = 1/sqrt(S_jj) (0 if S_jj <= 0); dS = diag(S).
-// s_j = 1/sqrt(S_jj) (0 if S_jj <= 0), dS = diag(S), act = identity, and
-// the factorisation state; one thread per column.
+// Equilibration scales s_j = 1/sqrt(S_jj) (0 if S_jj <= 0), dS = diag(S),
+// act = identity, and the factorisation state; one thread per column.
 __global__ void equil_scale_kernel(const double *__restrict__ S, int64_t lds, int64_t L,
                                    double *__restrict__ sc, double *__restrict__ dS,
                                    int32_t *__restrict__ act, FactorState *st) {
@@ -308,7 +307,6 @@ panel_kernel(const double *__restrict__ A, int64_t lda, const int32_t *__restric
     T *Pg = reinterpret_cast<T *>(P);          // panel rows (global)
     T *Rg = reinterpret_cast<T *>(Rrow);       // pivot rows (global)
     int32_t *piv = (int32_t *)(d + wmax);      // wmax
-    int32_t *acts = piv + wmax;                // wmax: original index of own columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {

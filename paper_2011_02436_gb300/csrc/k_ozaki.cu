@@ -10,13 +10,17 @@
 // tensor memory) sums products |d_p d_q| <= 2^(2B-2); over a K chunk of
 // 2^(24-2B+2) / 4 elements (256 for B = 8, 1024 for B = 7) the partial sums
 // stay below 2^24, so the FP32 accumulation is exact.  Pairs with the same
-// weight 2^(-B(p+q-2)) share one accumulator ("diagonal" t = p + q).  After
-// each chunk four drain warps fold the diagonals, as exact integers, into a
-// per-element int64 fixed-point running sum kept in tensor memory; the
-// epilogue converts it to FP64 once.  So the only roundings are the final
-// FP64 conversion and, for diagonals holding more than four pairs (weight
-// at most 2^(-4B) of the leading one), the FP32 accumulator itself.  Pairs
-// with p + q > TMAX are dropped.
+// weight 2^(-B(p+q-2)) share one accumulator ("diagonal" t = p + q), and
+// the pairs of one A plane with consecutive B planes form one MMA of width
+// up to 256 (B planes stored in descending order, diagonal t at TMEM column
+// (TMAX - t) 64).  After each chunk the drain warps fold the diagonals, as
+// exact integers, into a per-element int64 fixed-point running sum kept in
+// tensor memory; the epilogue converts it to FP64 once (the hidden layer,
+// one chunk deep, forms its pre-activation directly as a double-float
+// pair).  So the only roundings are the final conversion and, for
+// diagonals holding more than four pairs (weight at most 2^(-4B) of the
+// leading one), the FP32 accumulator itself.  Pairs with p + q > TMAX are
+// dropped.
 //
 // Kernel layout (persistent, 128 x 64 output tiles, 320 threads):
 //   warp 0      TMA producer: digit tiles of A (128 rows) and B (64 rows),
