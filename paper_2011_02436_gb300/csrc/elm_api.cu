@@ -160,7 +160,9 @@ struct Solver {
     int64_t r = 0, L = 0, m = 0;
     double *DinvF = nullptr, *DinvB = nullptr;
     // r < L
-    double *K = nullptr, *G2 = nullptr, *R2 = nullptr, *Rt2 = nullptr;
+    double *K = nullptr, *G2 = nullptr, *R2 = nullptr, *Rt2 = nullptr, *syrk_part = nullptr;
+    double *atv_part = nullptr;
+    int atv_split = 1;
     double *DinvF2 = nullptr, *DinvB2 = nullptr;
     int64_t ld2 = 0;
     FactorWs f2{};
@@ -181,6 +183,9 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
     sv.m = m;
     const int64_t q = L - r;
     sv.ld2 = q > 0 ? tri_ld(q) : 0;
+    const int syrk_split = syrk_f64_splits(r, q, ctx->sm_count);
+    const int atv_split = atv_splits(r, q, ctx->sm_count);
+    sv.atv_split = atv_split;
     with_arena(&ctx->aux, &ctx->aux_size, s, [&](Arena &a) {
         sv.yb = a.take<double>(L * m);
         sv.DinvF = a.take<double>(trsm_dinv_doubles(r));
@@ -189,6 +194,8 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
         if (q > 0 && r > 0) {
             sv.K = a.take<double>(r * q);
             sv.G2 = a.take<double>(q * q);
+            sv.syrk_part = a.take<double>(syrk_f64_ws(q, syrk_split));
+            sv.atv_part = a.take<double>((int64_t)atv_split * q * m);
             sv.v = a.take<double>(q * m);
             sv.w = a.take<double>(q * m);
             sv.R2 = a.take<double>(q * sv.ld2);
@@ -204,8 +211,7 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
         copy2d(sv.K, q * sizeof(double), R + r, ld * sizeof(double),
                                    q * sizeof(double), r, cudaMemcpyDeviceToDevice, s);
         trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag);
-        set_identity(s, sv.G2, q);
-        gemm_f64(s, q, q, r, 1.0, sv.K, 1, q, sv.K, q, 1, 1.0, sv.G2, q);
+        syrk_f64(s, sv.K, r, q, q, sv.G2, q, sv.syrk_part, syrk_split);   // I + K^T K
         // I + K^T K is SPD with eigenvalues >= 1: full rank q
         factor_pivoted(s, sv.G2, q, q, 0.0, sv.f2, sv.R2, sv.Rt2, sv.ld2, ctx->sm_count);
         trsm_prepare(s, sv.R2, sv.ld2, q, sv.DinvF2, sv.DinvB2);
@@ -222,14 +228,14 @@ void solver_apply(cudaStream_t s, const Solver &sv, const double *Z, int64_t ldz
     trsm_bwd(s, sv.Rt, sv.ld, sv.DinvB, r, yb, m, m, sv.tflag);
     if (q > 0) {
         if (r > 0) {
-            gemm_f64(s, q, m, r, 1.0, sv.K, 1, q, yb, m, 1, 0.0, sv.v, m);
+            atv_f64(s, sv.K, r, q, q, yb, m, sv.v, sv.atv_part, sv.atv_split);   // K^T y
             ELM_CUDA(cudaMemsetAsync(sv.w, 0, sizeof(double) * q * m, s));
             gather_rows(s, sv.v, m, sv.f2.perm, &sv.f2.st->rank, q, m, sv.w, m);
             trsm_fwd(s, sv.R2, sv.ld2, sv.DinvF2, q, sv.w, m, m, sv.tflag);
             trsm_bwd(s, sv.Rt2, sv.ld2, sv.DinvB2, q, sv.w, m, m, sv.tflag);
             scatter_rows(s, sv.w, m, sv.f2.perm, q, sv.v, m, 1.0, 0);
-            gemm_f64(s, r, m, q, -1.0, sv.K, q, 1, sv.v, m, 1, 1.0, yb, m);
-            gemm_f64(s, q, m, r, 1.0, sv.K, 1, q, yb, m, 1, 0.0, yb + r * m, m);
+            av_sub_f64(s, sv.K, r, q, q, sv.v, m, yb);                           // y -= K v
+            atv_f64(s, sv.K, r, q, q, yb, m, yb + r * m, sv.atv_part, sv.atv_split);
         } else {
             ELM_CUDA(cudaMemsetAsync(yb, 0, sizeof(double) * L * m, s));
         }

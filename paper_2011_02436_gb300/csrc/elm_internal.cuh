@@ -181,6 +181,22 @@ void sumsq(cudaStream_t s, const double *x, int64_t rows, int64_t cols, int64_t 
 void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, double *out);
 // A (n x n) = I.
 void set_identity(cudaStream_t s, double *A, int64_t n);
+// C (q x q, both triangles) = I + A^T A for A (k x q, row-major, lda) in
+// FP64; part: syrk_f64_ws(q, S) doubles, S = syrk_f64_splits(k, q, sms)
+// pieces of the k range summed in a fixed order.
+// Skinny FP64 products with a tall A (k x q, row-major, lda) and m columns
+// (memory-bound on A, read once): out (q x m, contiguous) = A^T Y with Y
+// (k x m, contiguous), split over the rows into S = atv_splits(k, q, sms)
+// pieces summed in order (part: S q m doubles); Y (k x m) -= A V.
+int atv_splits(int64_t k, int64_t q, int sms);
+void atv_f64(cudaStream_t s, const double *A, int64_t k, int64_t q, int64_t lda, const double *Y,
+             int64_t m, double *out, double *part, int S);
+void av_sub_f64(cudaStream_t s, const double *A, int64_t k, int64_t q, int64_t lda,
+                const double *V, int64_t m, double *Y);
+int syrk_f64_splits(int64_t k, int64_t q, int sms);
+size_t syrk_f64_ws(int64_t q, int S);
+void syrk_f64(cudaStream_t s, const double *A, int64_t k, int64_t q, int64_t lda, double *C,
+              int64_t ldc, double *part, int S);
 // Scan for non-finite entries; sets *flag = 1 if any.
 void check_finite(cudaStream_t s, const void *x, int xdt, int64_t rows, int64_t cols,
                   int64_t ld, int32_t *flag);

@@ -657,6 +657,138 @@ void gram_f64(cudaStream_t s, const double *Ht, int64_t ldh, int64_t L,
     ELM_CHECK_LAUNCH();
 }
 
+// Products of a tall r x q matrix A (row-major, lda) with a few columns
+// (m <= 32 per pass, RC a compile-time count >= the pass width): memory-bound
+// on A, so A is read once, coalesced.
+// part[s, i, c] = sum over the rows k of split s of A[k, i] Y[k, c0 + c]:
+// thread per column i, 64 rows of Y staged in shared memory at a time.
+template <int RC>
+__global__ void __launch_bounds__(256)
+atv_kernel(const double *__restrict__ A, int64_t k, int64_t q, int64_t lda,
+           const double *__restrict__ Y, int64_t ldy, int64_t m, int64_t c0, int mc,
+           int64_t kchunk, double *__restrict__ part) {
+    __shared__ double ys[64][RC];
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t kb = (int64_t)blockIdx.y * kchunk, ke = kb + kchunk < k ? kb + kchunk : k;
+    double acc[RC];
+#pragma unroll
+    for (int c = 0; c < RC; c++) acc[c] = 0.0;
+    for (int64_t k0 = kb; k0 < ke; k0 += 64) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 64 * RC; e += 256) {
+            const int kk = e / RC, c = e % RC;
+            ys[kk][c] = (k0 + kk < ke && c < mc) ? Y[(k0 + kk) * ldy + c0 + c] : 0.0;
+        }
+        __syncthreads();
+        if (i < q) {
+            const int n = (int)(ke - k0 < 64 ? ke - k0 : 64);
+            for (int kk = 0; kk < n; kk++) {
+                const double a = A[(k0 + kk) * lda + i];
+#pragma unroll
+                for (int c = 0; c < RC; c++) acc[c] = fma(a, ys[kk][c], acc[c]);
+            }
+        }
+    }
+    if (i < q)
+#pragma unroll
+        for (int c = 0; c < RC; c++)
+            if (c < mc) part[((int64_t)blockIdx.y * q + i) * m + c0 + c] = acc[c];
+}
+
+// Y[k, c0 + c] -= sum_i A[k, i] V[i, c0 + c]: warp per row k, lanes over i,
+// a fixed shuffle tree.
+template <int RC>
+__global__ void __launch_bounds__(256)
+av_sub_kernel(const double *__restrict__ A, int64_t k, int64_t q, int64_t lda,
+              const double *__restrict__ V, int64_t ldv, int64_t c0, int mc,
+              double *__restrict__ Y, int64_t ldy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= k) return;   // warp-uniform
+    double acc[RC];
+#pragma unroll
+    for (int c = 0; c < RC; c++) acc[c] = 0.0;
+    for (int64_t i = lane; i < q; i += 32) {
+        const double a = A[row * lda + i];
+#pragma unroll
+        for (int c = 0; c < RC; c++)
+            if (c < mc) acc[c] = fma(a, V[i * ldv + c0 + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < RC; c++) {
+        double v = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && c < mc) Y[row * ldy + c0 + c] -= v;
+    }
+}
+
+// I + A^T A for A (k x q, row-major, stride lda): lower TB x TB tiles of
+// the q x q result, the k range split into S contiguous pieces (one CTA per
+// tile and piece), each piece's tile written to its own buffer; both operands
+// are rows of A, so every load is coalesced.
+__global__ void __launch_bounds__(NT)
+syrk_f64_kernel(const double *__restrict__ A, int64_t k, int64_t q, int64_t lda,
+                int64_t kchunk, double *__restrict__ part) {
+    __shared__ double As[TK][TB + 1];
+    __shared__ double Bs[TK][TB + 1];
+    const int64_t t = blockIdx.x, sp = blockIdx.y;
+    int64_t J = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (J * (J + 1) / 2 > t) J--;
+    while ((J + 1) * (J + 2) / 2 <= t) J++;
+    const int64_t I = t - J * (J + 1) / 2;
+    const int64_t i0 = J * TB, j0 = I * TB;
+    const int64_t kb = sp * kchunk, ke = kb + kchunk < k ? kb + kchunk : k;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int64_t k0 = kb; k0 < ke; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * TB; e += NT) {
+            const int kk = e / TB, c = e % TB;
+            const int64_t kr = k0 + kk;
+            As[kk][c] = (kr < ke && i0 + c < q) ? A[kr * lda + i0 + c] : 0.0;
+            Bs[kk][c] = (kr < ke && j0 + c < q) ? A[kr * lda + j0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk++) {
+            double u[4], v[4];
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                u[w] = As[kk][ty + 16 * w];
+                v[w] = Bs[kk][tx + 16 * w];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = fma(u[a], v[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+    double *out = part + (sp * (int64_t)gridDim.x + t) * (TB * TB);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) out[(ty + 16 * a) * TB + tx + 16 * b] = acc[a][b];
+}
+
+// C = I + sum of the S pieces, added in piece order, both triangles.
+__global__ void syrk_sum_kernel(const double *__restrict__ part, int S, int64_t ntiles, int64_t q,
+                                double *__restrict__ C, int64_t ldc) {
+    const int64_t t = blockIdx.x;
+    int64_t J = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (J * (J + 1) / 2 > t) J--;
+    while ((J + 1) * (J + 2) / 2 <= t) J++;
+    const int64_t I = t - J * (J + 1) / 2;
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        const int64_t i = J * TB + e / TB, j = I * TB + e % TB;
+        if (i >= q || j >= q || j > i) continue;
+        double v = i == j ? 1.0 : 0.0;
+        for (int sp = 0; sp < S; sp++) v += part[(sp * ntiles + t) * (TB * TB) + e];
+        C[i * ldc + j] = v;
+        C[j * ldc + i] = v;
+    }
+}
+
 void gemm_f64(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha,
               const double *A, int64_t sAm, int64_t sAk, const double *B,
               int64_t sBk, int64_t sBn, double beta, double *C, int64_t ldc) {
@@ -664,6 +796,30 @@ void gemm_f64(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha,
     dim3 grid((unsigned)((N + TB - 1) / TB), (unsigned)((M + TB - 1) / TB));
     gemm_f64_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C,
                                         ldc);
+    ELM_CHECK_LAUNCH();
+}
+
+int syrk_f64_splits(int64_t k, int64_t q, int sms) {
+    const int64_t T = (q + TB - 1) / TB, tiles = T * (T + 1) / 2;
+    int64_t S = (4 * (int64_t)sms + tiles - 1) / tiles;   // about four CTAs per SM
+    const int64_t cap = (k + 255) / 256;                    // at least 256 rows a piece
+    if (S > cap) S = cap;
+    return (int)(S < 1 ? 1 : S);
+}
+
+size_t syrk_f64_ws(int64_t q, int S) {
+    const int64_t T = (q + TB - 1) / TB;
+    return (size_t)S * (T * (T + 1) / 2) * TB * TB;
+}
+
+void syrk_f64(cudaStream_t s, const double *A, int64_t k, int64_t q, int64_t lda, double *C,
+              int64_t ldc, double *part, int S) {
+    if (q <= 0) return;
+    const int64_t T = (q + TB - 1) / TB, tiles = T * (T + 1) / 2;
+    const int64_t kchunk = ((k + S - 1) / S + TK - 1) / TK * TK;
+    syrk_f64_kernel<<<dim3((unsigned)tiles, (unsigned)S), NT, 0, s>>>(A, k, q, lda, kchunk, part);
+    ELM_CHECK_LAUNCH();
+    syrk_sum_kernel<<<(unsigned)tiles, 256, 0, s>>>(part, S, tiles, q, C, ldc);
     ELM_CHECK_LAUNCH();
 }
 
@@ -709,6 +865,45 @@ static void with_rc(int64_t m, F &&f) {
     else if (m <= 20) f(std::integral_constant<int, 20>());
     else if (m <= 26) f(std::integral_constant<int, 26>());
     else f(std::integral_constant<int, 32>());
+}
+
+int atv_splits(int64_t k, int64_t q, int sms) {
+    const int64_t cols = (q + 255) / 256;
+    int64_t S = (4 * (int64_t)sms + cols - 1) / cols;
+    const int64_t cap = (k + 63) / 64;   // at least 64 rows a split
+    if (S > cap) S = cap;
+    return (int)(S < 1 ? 1 : S);
+}
+
+void atv_f64(cudaStream_t s, const double *A, int64_t k, int64_t q, int64_t lda, const double *Y,
+             int64_t m, double *out, double *part, int S) {
+    if (q <= 0 || m <= 0) return;
+    const int64_t kchunk = (k + S - 1) / S;
+    for (int64_t c0 = 0; c0 < m; c0 += 32) {
+        const int64_t mc = m - c0 < 32 ? m - c0 : 32;
+        with_rc(mc, [&](auto rc) {
+            constexpr int RC = decltype(rc)::value;
+            atv_kernel<RC><<<dim3((unsigned)((q + 255) / 256), (unsigned)S), 256, 0, s>>>(
+                A, k, q, lda, Y, m, m, c0, (int)mc, kchunk, part);
+        });
+        ELM_CHECK_LAUNCH();
+    }
+    split_sum_kernel<<<blocks_for(q * m), 256, 0, s>>>(part, S, q * m, out);
+    ELM_CHECK_LAUNCH();
+}
+
+void av_sub_f64(cudaStream_t s, const double *A, int64_t k, int64_t q, int64_t lda,
+                const double *V, int64_t m, double *Y) {
+    if (k <= 0 || m <= 0) return;
+    for (int64_t c0 = 0; c0 < m; c0 += 32) {
+        const int64_t mc = m - c0 < 32 ? m - c0 : 32;
+        with_rc(mc, [&](auto rc) {
+            constexpr int RC = decltype(rc)::value;
+            av_sub_kernel<RC><<<(unsigned)((k + 7) / 8), 256, 0, s>>>(A, k, q, lda, V, m, c0,
+                                                                      (int)mc, Y, m);
+        });
+        ELM_CHECK_LAUNCH();
+    }
 }
 
 void resid_df(cudaStream_t s, const void *H, int64_t L, int64_t N, const double *beta,
