@@ -150,3 +150,15 @@ def test_bad_arguments_are_rejected_before_launch(elm, ctx):
     with pytest.raises(elm.ElmError) as e:                   # unknown activation
         elm.elm_hidden(ctx, t["X"], t["W"], t["b"], None, 7)
     assert e.value.status == 1
+
+
+def test_train_many_targets_rank_deficient(elm, ctx):
+    # m = 40 targets: column passes in the residual kernels and the skinny
+    # K products of the rank-deficient solve
+    p = synth.make_problem(3000, 11, 150, 40, n_dup=20, n_scaled=10, x_kind="normal",
+                           target="regression")
+    prob = problem(p)
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_FP64)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["rank"] == r == 150
+    assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-9

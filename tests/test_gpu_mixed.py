@@ -107,3 +107,32 @@ def test_nonfinite_input_is_reported_mixed(elm, ctx, xdt, bad):
     p["X"][117, 4] = bad
     res = elm.elm_train(ctx, problem(p), precision=elm.PREC_MIXED, check=False)[0]
     assert res["status"] == 4                                # ELM_ERR_NUMERIC
+
+
+def test_train_many_targets_rank_deficient_mixed(elm, ctx):
+    # m = 40 targets run the column passes of 32 + 8 in the residual and the
+    # skinny K products; duplicates and scaled copies make r < L
+    p = synth.make_problem(3000, 11, 150, 40, n_dup=20, n_scaled=10, x_kind="normal",
+                           target="regression")
+    prob = problem(p)
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["rank"] == r == 150
+    assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("n", [1100, 2100])
+def test_deep_inputs_span_several_exact_chunks(elm, ctx, n):
+    # n > 1024 inputs: the hidden layer's K range spans several exact chunks
+    # (the drain's int64 running sums, then the double-float pre-activation)
+    p = synth.make_problem(400, n, 70, 3, x_kind="uniform01", x_sparsity=0.5)
+    t = to_dev(p)
+    Ht = elm.elm_hidden(ctx, t["X"], t["W"], t["b"], t["a"], 0,
+                        precision=elm.PREC_MIXED).cpu().numpy()
+    H = oracle.hidden(p["X"], p["W"], p["b"], p["a"], 0)
+    assert np.max(np.abs(Ht.T - H)) < 1e-9
+    prob = problem(p)
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], 0, p["T"])
+    assert res["rank"] == r
+    assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
