@@ -136,3 +136,22 @@ def test_deep_inputs_span_several_exact_chunks(elm, ctx, n):
     ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], 0, p["T"])
     assert res["rank"] == r
     assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("xdt", [np.float32, np.float64])
+def test_train_pinned_host_inputs_mixed(elm, ctx, xdt):
+    # page-locked host inputs (the e2e path of bench.py), staged by the library
+    import torch
+    p = synth.make_problem(1500, 37, 90, 3, n_dup=6, x_dtype=xdt, x_sparsity=0.3)
+    prob = dict(X=torch.from_numpy(p["X"]).pin_memory(), W=torch.from_numpy(p["W"]).pin_memory(),
+                b=torch.from_numpy(p["b"]).pin_memory(), a=None, act=0,
+                T=torch.from_numpy(p["T"]).pin_memory(),
+                beta=torch.empty((p["L"], 3), dtype=torch.float64).pin_memory())
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], None, 0, p["T"])
+    assert res["rank"] == r == 90
+    assert rel(prob["beta"].numpy(), ref) <= 1e-6
+    bad = torch.from_numpy(p["X"]).pin_memory()
+    bad[100, 5] = float("nan")
+    res = elm.elm_train(ctx, dict(prob, X=bad), precision=elm.PREC_MIXED, check=False)[0]
+    assert res["status"] == 4
