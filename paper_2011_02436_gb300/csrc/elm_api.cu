@@ -396,8 +396,19 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     int *err;
     OzHidWs hw;
     FactorWs f;
+    // host X is uploaded in row chunks on a second stream; the hidden layer
+    // takes each chunk as it lands (below)
+    const bool x_host = !on_device(pb.X);
+    char *xdev = nullptr;
     with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
-        X = stage(ar, s, pb.X, N, n, pb.ldx, xsz);
+        if (x_host) {
+            xdev = ar.take<char>((size_t)(N * n) * xsz);
+            X.p = xdev;
+            X.ld = n;
+            X.host = true;
+        } else {
+            X = stage(ar, s, pb.X, N, n, pb.ldx, xsz);
+        }
         W = stage(ar, s, pb.W, n, L, pb.ldw, 8);
         b = stage(ar, s, pb.b, 1, L, L, 8);
         a = stage(ar, s, pb.a, 1, L, L, 8);
@@ -425,11 +436,39 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
                  *ad = (const double *)a.p, *Td = (const double *)T.p;
+    OzRowChunks xc;
+    if (x_host) {
+        if (!ctx->copy_stream) {
+            ELM_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+            ELM_CUDA(cudaEventCreateWithFlags(&ctx->xstart, cudaEventDisableTiming));
+            for (auto &e : ctx->xready)
+                ELM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        // the buffer is free once the work already queued on s is done
+        ELM_CUDA(cudaEventRecord(ctx->xstart, s));
+        ELM_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->xstart, 0));
+        const int64_t Np = oz_pad(N, 64);
+        const int64_t nch = Np / 64 < 4 ? Np / 64 : 4;
+        xc.count = (int)nch;
+        for (int c = 0; c < xc.count; c++) {
+            xc.row[c] = c * Np / nch / 64 * 64;
+            xc.ready[c] = ctx->xready[c];
+        }
+        for (int c = 0; c < xc.count; c++) {
+            const int64_t r0 = xc.row[c];
+            const int64_t r1 = c + 1 < xc.count ? xc.row[c + 1] : N;
+            if (r1 > r0 && r0 < N)
+                copy2d(xdev + (size_t)r0 * n * xsz, n * xsz,
+                       (const char *)pb.X + (size_t)r0 * pb.ldx * xsz, pb.ldx * xsz, n * xsz,
+                       (r1 < N ? r1 : N) - r0, cudaMemcpyHostToDevice, ctx->copy_stream);
+            ELM_CUDA(cudaEventRecord(xc.ready[c], ctx->copy_stream));
+        }
+    }
     mark(ctx, 0);
     // Algorithm 1 step 2 (Eq. 1, 3): pre-activation on the tensor cores,
     // activation in the epilogue, digit planes of H and H itself
     oz_hidden(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, pb.act, L, m, planes, hs,
-              nullptr, 0, err, Hdf, /*nonfinite=*/flag);
+              nullptr, 0, err, Hdf, /*nonfinite=*/flag, x_host ? &xc : nullptr);
     // digit rows of the targets beside those of H (part of the hidden phase,
     // so the Gram phase times the Gram kernel alone)
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
@@ -555,6 +594,13 @@ int elm_destroy(elm_ctx *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->aux) cudaFree(ctx->aux);
     for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    if (ctx->xstart) cudaEventDestroy(ctx->xstart);
+    for (auto &e : ctx->xready)
         if (e) cudaEventDestroy(e);
     delete ctx;
     return ELM_OK;

@@ -73,6 +73,10 @@ struct elm_ctx {
     bool timing = false;
     cudaEvent_t ev[ELM_NUM_PHASES + 1] = {};
     double phase_ms[ELM_NUM_PHASES] = {};
+    // upload of host X in chunks, overlapped with the hidden layer (mixed form)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t xstart = nullptr;
+    cudaEvent_t xready[8] = {};
 };
 
 // ---------------------------------------------------------------- kernels
@@ -216,6 +220,16 @@ struct OzHidWs {
     float4 *tab;             // sigmoid table
     float4 *rowc;            // per hidden row: epilogue constants (two float4)
 };
+// Sample rows of X arriving in chunks (copies in flight on another stream):
+// chunk c covers rows row[c] .. row[c+1]-1 (the last one up to the padded
+// row count), multiples of 64, ready once `ready[c]` has fired.
+constexpr int OZ_MAX_CHUNKS = 8;
+static_assert(OZ_MAX_CHUNKS == sizeof(elm_ctx::xready) / sizeof(cudaEvent_t), "chunk events");
+struct OzRowChunks {
+    int count = 0;
+    int64_t row[OZ_MAX_CHUNKS] = {};
+    cudaEvent_t ready[OZ_MAX_CHUNKS] = {};
+};
 // Scratch of oz_hidden for an N x n input and L (+ m target) rows.
 OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m);
 // Bytes of the Gram digit planes (5 planes of Lp x Np bf16,
@@ -232,7 +246,7 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
                int64_t ldh, int *err, void *Hdf = nullptr,
-               int32_t *nonfinite = nullptr);
+               int32_t *nonfinite = nullptr, const OzRowChunks *chunks = nullptr);
 // T -> digit plane rows L .. L+m-1.
 void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
                  __nv_bfloat16 *planes, double *hs);

@@ -287,6 +287,7 @@ struct OzParams {
     int64_t ntiles;     // tiles in the tile set
     int64_t whole;      // tiles below this run over the whole K range, one CTA each
     long long *part;    // EPI == 0: int64 partial sums of the tiles from `whole` on
+    int64_t n_base;     // non-Gram tiles: first B row (column) of the tile set
     ActParams ap;       // used when the kernel's EPI != 0
 };
 
@@ -408,7 +409,7 @@ __device__ __forceinline__ void tile_coords(const OzParams &P, int64_t t, int64_
         n0 = (t - J * (J + 1)) * BN;
     } else {
         m0 = (t % P.ntile_m) * BM;
-        n0 = (t / P.ntile_m) * BN;
+        n0 = P.n_base + (t / P.ntile_m) * BN;
     }
 }
 
@@ -847,11 +848,11 @@ template <int PD, int DBITS, typename XT>
 __global__ void digits_rows_kernel(const XT *__restrict__ X, int64_t N, int64_t n, int64_t ldx,
                                    int64_t Np, int64_t nK, __nv_bfloat16 *__restrict__ planes,
                                    double *__restrict__ xs, float *__restrict__ xsf,
-                                   int32_t *__restrict__ nonfinite) {
+                                   int32_t *__restrict__ nonfinite, int64_t i0, int64_t i1) {
     constexpr int SH = (DBITS - 1) + DBITS * (PD - 1);
-    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t i = i0 + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= Np) return;
+    if (i >= i1) return;   // rows i0 .. i1-1 (i1 <= Np)
     double mx = 0.0;
     bool bad = false;
     if (i < N)
@@ -888,10 +889,10 @@ __global__ void digits_rows_f32_kernel(const float *__restrict__ X, int64_t N, i
                                        int64_t ldx, int64_t Np, int64_t nK,
                                        __nv_bfloat16 *__restrict__ planes,
                                        double *__restrict__ xs, float *__restrict__ xsf,
-                                       int32_t *__restrict__ nonfinite) {
-    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+                                       int32_t *__restrict__ nonfinite, int64_t i0, int64_t i1) {
+    const int64_t i = i0 + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= Np) return;
+    if (i >= i1) return;   // rows i0 .. i1-1 (i1 <= Np)
     float mx = 0.f;
     bool bad = false;
     if (i < N)
@@ -1168,15 +1169,8 @@ size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m) {
 void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
-               int64_t ldh, int *err, void *Hdf, int32_t *nonfinite) {
+               int64_t ldh, int *err, void *Hdf, int32_t *nonfinite, const OzRowChunks *chunks) {
     const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
-    if (xdt == ELM_F64)
-        digits_rows_kernel<HID_PX, HID_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf, nonfinite);
-    else
-        digits_rows_f32_kernel<HID_PX, HID_BITS><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
-            (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf, nonfinite);
-    ELM_CHECK_LAUNCH();
     col_scale_kernel<<<(unsigned)((Lp + 31) / 32), 256, 0, s>>>(W, n, L, ldw, Lp, w.ws);
     ELM_CHECK_LAUNCH();
     digits_cols_par_kernel<HID_PW, HID_BITS>
@@ -1219,13 +1213,30 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ap.Hdf = (float2 *)Hdf;
     P.ap.ldhd = L;
     P.ap.ldh = ldh;
-    P.whole = (Lp / BM) * (Np / BN);   // no split tiles
-    if (Ht)
-        launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 2>(s, w.wp, w.xp, P,
-                                                               (Lp / BM) * (Np / BN));
-    else
-        launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P,
-                                                               (Lp / BM) * (Np / BN));
+    // the samples in row windows (one window, or the caller's chunks as their
+    // copies land): digits of the window's X rows, then its tiles
+    const int nc = chunks ? chunks->count : 1;
+    for (int c = 0; c < nc; c++) {
+        const int64_t r0 = chunks ? chunks->row[c] : 0;
+        const int64_t r1 = chunks ? (c + 1 < nc ? chunks->row[c + 1] : Np) : Np;
+        if (r1 <= r0) continue;
+        if (chunks && chunks->ready[c]) ELM_CUDA(cudaStreamWaitEvent(s, chunks->ready[c], 0));
+        const unsigned g = (unsigned)((r1 - r0 + 7) / 8);
+        if (xdt == ELM_F64)
+            digits_rows_kernel<HID_PX, HID_BITS, double><<<g, 256, 0, s>>>(
+                (const double *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf, nonfinite, r0, r1);
+        else
+            digits_rows_f32_kernel<HID_PX, HID_BITS><<<g, 256, 0, s>>>(
+                (const float *)X, N, n, ldx, Np, nK, w.xp, w.xs, w.xsf, nonfinite, r0, r1);
+        ELM_CHECK_LAUNCH();
+        const int64_t tiles = (Lp / BM) * ((r1 - r0) / BN);
+        P.n_base = r0;
+        P.whole = tiles;   // no split tiles
+        if (Ht)
+            launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 2>(s, w.wp, w.xp, P, tiles);
+        else
+            launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P, tiles);
+    }
 }
 
 // Target rows L .. L+m-1 of the Gram digit planes.
