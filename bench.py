@@ -64,9 +64,9 @@ def peaks():
 
 
 # DRAM bytes (read + write) of one Gram tensor-kernel launch per sample row:
-# 745.6 MB at 20000 rows in profiles/tensor_refine_sparse_pixels_20000rows_full.md
+# 745.3 MB at 20000 rows in profiles/tensor_refine_sparse_pixels_20000rows_full.md
 # (the launch streams the digit planes, whose size is proportional to the rows).
-GRAM_DRAM_BYTES_PER_ROW = (720.854272e6 + 24.718592e6) / 20000
+GRAM_DRAM_BYTES_PER_ROW = (720.571904e6 + 24.740352e6) / 20000
 
 
 class Clocks:
