@@ -371,7 +371,8 @@ def run_native(args):
                     e2e=dict(value=ws * count * 1000.0 / e2e_ms, unit="trainings/s",
                              h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches, roofline=roof, clocks=clk.summary(), check=check)
-        if args.workload == "sparse_pixels" and not args.no_cpu_baseline:
+        # the oracle on the host cores: rank 0 of a single-GPU run only
+        if args.workload == "sparse_pixels" and not args.no_cpu_baseline and ws == 1:
             cb = cpu_baseline(WORKLOAD, sample_rows=args.ref_rows)
             cb.pop("projected_s_per_training", None)
             line["cpu_baseline"] = cb
