@@ -3,7 +3,8 @@ X 60000 x 784 with 80% zeros, L = 2000 sigmoid neurons, 10 one-hot classes,
 full column rank), beta checked against the FP64 CPU oracle's accuracy bar.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                  [--impl native|reference] [--no-cpu-baseline]
+                  [--impl native|reference] [--workload W] [--fp64-steps K64]
+                  [--no-oracle-check]
 
 One step = one complete training (hidden layer, Gram, pivoted rank
 decision, solves, refinement) of the workload, inputs resident in HBM.
@@ -16,9 +17,20 @@ With --gpus N > 1 (torchrun, one process per GPU) every rank trains its own
 replica of the workload (independent problems, no collective); the value is
 the trainings of all ranks divided by the slowest rank's time.
 
+Before timing, a verified run checks every problem: status OK (or
+NOT_CONVERGED with beta written), the planted rank, and beta against the
+FP64 CPU oracle's (within 1e-6 relative Frobenius for the mixed form, 1e-9
+for the FP64 form).  The oracle trains the sparse-pixel workload in full on
+the host cores (that run is also the line's cpu_baseline); the other
+workloads are checked against the oracle's stored results in tests/golden
+where they exist.  A line that fails a check carries "valid": false and the
+script exits 1.  The default line also times the plain FP64 GPU form of the
+same workload (fp64_form) and reports the mixed form's speedup over it.
+
 --impl reference times the FP64 CPU oracle (the method's plain definition)
-on the host cores on a bounded sample of the workload (the first rows of X;
-N-proportional phases scaled to the full N).
+on the host cores: each step trains a bounded sample of the workload (the
+first rows of X; N-proportional phases scaled to the full N), and one full
+training of the workload, timed once, gives the line's value.
 """
 from __future__ import annotations
 
@@ -63,10 +75,11 @@ def peaks():
                 fp64=1.25)
 
 
-# DRAM bytes (read + write) of one Gram tensor-kernel launch per sample row:
-# 745.3 MB at 20000 rows in profiles/tensor_refine_sparse_pixels_20000rows_full.md
-# (the launch streams the digit planes, whose size is proportional to the rows).
+# DRAM bytes (read + write) of one Gram tensor-kernel launch per sample row,
+# from an ncu capture of the same kernel at 20000 rows (745.3 MB); the launch
+# streams the digit planes, whose size is proportional to the rows.
 GRAM_DRAM_BYTES_PER_ROW = (720.571904e6 + 24.740352e6) / 20000
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 class Clocks:
@@ -152,6 +165,19 @@ def shard(count, rank, world):
     return list(range(start, start + base + (1 if rank < extra else 0)))
 
 
+def oracle_full(p):
+    """One full training of problem p by the oracle (Alg. 1), timed:
+    (beta, rank, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    beta, r, _ = oracle.train(p["X"], p["W"], p["b"], p.get("a"), int(p["act"]), p["T"])
+    return beta, r, time.perf_counter() - t0
+
+
+def cores_used():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
 def cpu_baseline(full, sample_rows=2000, threads=None):
     """Time the oracle, as it stands, on the first `sample_rows` rows of the
     workload and scale its N-proportional phases to the full N."""
@@ -174,13 +200,13 @@ def cpu_baseline(full, sample_rows=2000, threads=None):
     t4 = time.perf_counter()
     scale = N / float(sample_rows)
     t_full = (t1 - t0 + t2 - t1 + t4 - t3) * scale + (t3 - t2)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = cores_used()
     return dict(value=1.0 / t_full, unit="trainings/s", cores=cores, kind="oracle",
                 sample="first %d of %d rows of the workload; hidden/Gram/refinement times "
                        "scaled by N, factorisation+solve (L=%d) timed in full "
                        "(%.1f s of CPU time: hidden %.1f, Gram %.1f, factor %.1f, refine %.1f)"
                        % (sample_rows, N, L, t4 - t0, t1 - t0, t2 - t1, t3 - t2, t4 - t3),
-                projected_s_per_training=t_full)
+                projected_s_per_training=t_full, step_s=t4 - t0)
 
 
 def run_reference(args):
@@ -188,20 +214,32 @@ def run_reference(args):
     if rank != 0:
         return 0
     full = dict(WORKLOAD)
-    times = []
+    steps, proj = [], []
     cb = None
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(full, sample_rows=args.ref_rows)
         if i >= args.warmup:
-            times.append(cb["projected_s_per_training"])
-    t = statistics.median(times)
-    val = 1.0 / t
+            steps.append(cb["step_s"])
+            proj.append(cb["projected_s_per_training"])
+    # one full training of the workload, timed once: the line's value
+    # (--ref-full-rows < N only to test the arm quickly)
+    nfull = args.ref_full_rows
+    _, _, t_full = oracle_full(synth.workload_sparse_pixels(N=nfull))
+    val = nfull / float(full["N"]) / t_full
     line = dict(metric=METRIC, value=val, unit="trainings/s", n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=t * 1e3, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(WORKLOAD, inputs="oracle sample; CPU caches"), impl="reference",
-                cpu_baseline=dict(value=val, unit="trainings/s", kind="oracle",
-                                  cores=cb["cores"], sample=cb["sample"]),
+                warmup=args.warmup, ms_per_step=statistics.median(steps) * 1e3,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic",
+                config=dict(WORKLOAD, inputs="host memory; oracle on the host cores"),
+                impl="reference",
+                cpu_baseline=dict(value=val, unit="trainings/s", kind="oracle", cores=cores_used(),
+                                  sample="value: one training of the workload on %d of "
+                                         "its %d rows, %.1f s; each timed step: the first %d "
+                                         "rows (%s); median projection of the steps to the "
+                                         "full N: %.4f trainings/s"
+                                         % (nfull, full["N"], t_full, args.ref_rows,
+                                            cb["sample"], 1.0 / statistics.median(proj)),
+                                  full_training_s=t_full),
                 e2e=dict(value=val, unit="trainings/s", h2d_bytes_per_step=0,
                          d2h_bytes_per_step=0))
     print(json.dumps(line))
@@ -229,6 +267,50 @@ WORKLOADS = {
 ARGS_HIDDEN = [2000]
 
 
+def reference_results(workload, plist, time_first=False):
+    """The oracle's (beta, rank) per problem, or None where unavailable:
+    trained live for the workloads the oracle finishes in seconds to
+    minutes on the host cores, else read from the results the oracle stored
+    in tests/golden (written by tests/golden/make_full_goldens.py).
+    Returns (list, seconds of the first live training or None)."""
+    if workload in ("sparse_pixels", "small", "gina_shaped"):
+        out, t_first = [], None
+        for p in plist:
+            beta, r, t = oracle_full(p)
+            out.append((beta, r))
+            if t_first is None:
+                t_first = t
+        return out, t_first
+    path = os.path.join(GOLDEN, "full_%s.npz" % workload)
+    if not os.path.exists(path):
+        return [None] * len(plist), None
+    g = np.load(path)
+    return [(g["beta_%03d" % i], int(g["rank"][i])) for i in range(len(plist))], None
+
+
+def check_results(res, betas, refs, planted, tol):
+    """Per problem: status OK (or NOT_CONVERGED, beta written), the planted
+    rank, the oracle's rank, beta within tol (relative Frobenius) of the
+    oracle's.  Returns (worst error, list of failure descriptions)."""
+    worst, bad = 0.0, []
+    for i, (r, beta, ref, pr) in enumerate(zip(res, betas, refs, planted)):
+        if r["status"] not in (0, 5):
+            bad.append("problem %d: status %d" % (i, r["status"]))
+            continue
+        if pr is not None and r["rank"] != pr:
+            bad.append("problem %d: rank %d, planted %d" % (i, r["rank"], pr))
+        if ref is None:
+            continue
+        bref, rref = ref
+        if r["rank"] != rref:
+            bad.append("problem %d: rank %d, oracle %d" % (i, r["rank"], rref))
+        err = float(np.linalg.norm(beta - bref) / np.linalg.norm(bref))
+        worst = max(worst, err)
+        if not err <= tol:
+            bad.append("problem %d: beta error %.3g > %.0e" % (i, err, tol))
+    return worst, bad
+
+
 def run_native(args):
     import torch
     import __graft_entry__
@@ -242,6 +324,7 @@ def run_native(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = elm.PREC_MIXED if args.precision == "mixed" else elm.PREC_FP64
+    tol = 1e-6 if prec == elm.PREC_MIXED else 1e-9
 
     gen, desc = WORKLOADS[args.workload]
     desc = desc.replace("{L}", str(args.hidden))
@@ -258,44 +341,87 @@ def run_native(args):
     count = len(probs)
     stream = torch.cuda.current_stream(dev)
     ctx = elm.elm_create(local, stream)
+    planted = [int(p["rank"]) if p.get("rank") is not None else None for p in hosts]
+    full_rows = args.rows == WORKLOAD["N"] or args.workload != "sparse_pixels"
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # verified run: rank and accuracy (beta against the FP64 GPU path, whose
-    # own parity with the oracle is tested in tests/)
-    res = elm.elm_train(ctx, probs, precision=prec)
+    invalid = []
+
+    def timed_ok(res, what):
+        for i, r in enumerate(res):
+            if r["status"] not in (0, 5) or (planted[i] is not None and r["rank"] != planted[i]):
+                invalid.append("%s problem %d: status %d rank %d" % (what, i, r["status"], r["rank"]))
+
+    # verified run: statuses, ranks and beta against the oracle (rank 0)
+    res = elm.elm_train(ctx, probs, precision=prec, check=False)
+    betas = [pr["beta"].cpu().numpy() for pr in probs]
     check = dict(rank=[r["rank"] for r in res] if count > 1 else res[0]["rank"],
-                 refine_iters=max(r["refine_iters"] for r in res))
-    if prec != elm.PREC_FP64 and not args.no_fp64_check:
-        errs = []
-        for pr in probs:
-            p64 = dict(pr, beta=torch.empty_like(pr["beta"]))
-            elm.elm_train(ctx, p64, precision=elm.PREC_FP64)
-            b64, bm = p64["beta"].cpu().numpy(), pr["beta"].cpu().numpy()
-            errs.append(float(np.linalg.norm(bm - b64) / np.linalg.norm(b64)))
-        check["rel_err_vs_fp64_path"] = max(errs)
+                 refine_iters=max(r["refine_iters"] for r in res),
+                 statuses=sorted(set(r["status"] for r in res)),
+                 forms={str(f): sum(r["form"] == f for r in res) for f in (0, 1, 2)})
+    t_oracle, refs = None, None
+    if rank == 0 and full_rows and not args.no_oracle_check:
+        refs, t_oracle = reference_results(args.workload, hosts)
+        if any(x is not None for x in refs):
+            worst, bad = check_results(res, betas, refs, planted, tol)
+            check["rel_err_vs_oracle"] = worst
+            check["oracle_checked"] = sum(x is not None for x in refs)
+            invalid += bad
+        else:
+            check["oracle_checked"] = 0
+            timed_ok(res, "verified")
+    else:
+        timed_ok(res, "verified")
 
     for _ in range(args.warmup):
-        elm.elm_train(ctx, probs, precision=prec)
+        timed_ok(elm.elm_train(ctx, probs, precision=prec, check=False), "warm-up")
     elm.elm_phase_times(ctx)                       # reset
     barrier()
     l0 = elm.elm_launch_counter()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    step_res = []
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            elm.elm_train(ctx, probs, precision=prec, flags=elm.FLAG_PHASE_TIMING)
+            step_res.append(elm.elm_train(ctx, probs, precision=prec,
+                                          flags=elm.FLAG_PHASE_TIMING, check=False))
         e1.record(stream)
         barrier()
     launches = elm.elm_launch_counter() - l0
     phases = elm.elm_phase_times(ctx)
+    for r in step_res:
+        timed_ok(r, "timed")
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ms, dev)
     value = ws * count * 1000.0 / ms_max
+
+    # the plain FP64 GPU form of the same workload, for the metric's ratio
+    fp64 = None
+    if prec == elm.PREC_MIXED and args.fp64_steps > 0:
+        p64 = [dict(pr, beta=torch.empty_like(pr["beta"])) for pr in probs]
+        r64 = elm.elm_train(ctx, p64, precision=elm.PREC_FP64, check=False)     # warm-up
+        if refs is not None and any(x is not None for x in refs):
+            w64, bad64 = check_results(r64, [q["beta"].cpu().numpy() for q in p64], refs,
+                                       planted, 1e-9)
+            check["fp64_form_rel_err_vs_oracle"] = w64
+            if bad64:
+                check["fp64_form_failures"] = bad64[:8]
+        barrier()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.fp64_steps):
+            timed_ok(elm.elm_train(ctx, p64, precision=elm.PREC_FP64, check=False), "fp64")
+        g1.record(stream)
+        barrier()
+        ms64 = max_over_ranks(g0.elapsed_time(g1) / args.fp64_steps, dev)
+        fp64 = dict(value=ws * count * 1000.0 / ms64, unit="trainings/s", ms_per_step=ms64,
+                    steps=args.fp64_steps)
 
     # e2e through the C ABI with pinned host buffers
     hprobs = []
@@ -311,14 +437,14 @@ def run_native(args):
                    if hp[k] is not None)
         hprobs.append(hp)
     d2h = sum(hp["beta"].numel() * 8 for hp in hprobs)
-    elm.elm_train(ctx, hprobs, precision=prec)
+    timed_ok(elm.elm_train(ctx, hprobs, precision=prec, check=False), "e2e warm-up")
     barrier()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     e2e_steps = max(1, min(args.steps, 5))
     for _ in range(e2e_steps):
-        elm.elm_train(ctx, hprobs, precision=prec)
+        timed_ok(elm.elm_train(ctx, hprobs, precision=prec, check=False), "e2e")
     f1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, dev)
@@ -336,7 +462,7 @@ def run_native(args):
             issued += 15 * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
         N_all = sum(p["X"].shape[0] for p in hosts)
         if prec == elm.PREC_FP64:
-            # Gram on the FP64 pipe (nominal rate; MEASURED_PEAKS.json has no FP64 entry)
+            # Gram on the FP64 pipe (nominal rate; the measured peaks have no FP64 entry)
             achieved = gram_fl / (ph_ms["gram"] * 1e-3) / 1e12
             roof = dict(bound="alu", achieved=achieved, peak=pk["fp64"], unit="TFLOP/s",
                         frac=achieved / pk["fp64"], traffic=None, kernel="gram_f64_kernel",
@@ -349,6 +475,8 @@ def run_native(args):
             achieved = gram_fl / (ph_ms["gram"] * 1e-3) / 1e12
             roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16"], unit="TFLOP/s",
                         frac=achieved / pk["bf16"], traffic=GRAM_DRAM_BYTES_PER_ROW * N_all,
+                        traffic_source="ncu capture of the same kernel at 20000 rows "
+                                       "(745.3 MB), scaled by the rows",
                         kernel="ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
                         peak_source="%s bf16 dense burst" % pk["source"],
                         issued_tflops=issued / (ph_ms["gram"] * 1e-3) / 1e12,
@@ -371,16 +499,24 @@ def run_native(args):
                     e2e=dict(value=ws * count * 1000.0 / e2e_ms, unit="trainings/s",
                              h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches, roofline=roof, clocks=clk.summary(), check=check)
-        # the oracle on the host cores: rank 0 of a single-GPU run only
-        if args.workload == "sparse_pixels" and not args.no_cpu_baseline and ws == 1:
-            cb = cpu_baseline(WORKLOAD, sample_rows=args.ref_rows)
-            cb.pop("projected_s_per_training", None)
-            line["cpu_baseline"] = cb
+        if fp64 is not None:
+            line["fp64_form"] = fp64
+            line["speedup_vs_fp64_form"] = value / fp64["value"]
+        # the oracle on the host cores (rank 0 of a single-GPU run): the
+        # verified run's full training of the default workload
+        if args.workload == "sparse_pixels" and ws == 1 and t_oracle is not None:
+            line["cpu_baseline"] = dict(value=1.0 / t_oracle, unit="trainings/s",
+                                        cores=cores_used(), kind="oracle",
+                                        sample="one full training of the workload (%d rows), "
+                                               "%.1f s" % (WORKLOAD["N"], t_oracle))
+        line["valid"] = not invalid
+        if invalid:
+            line["invalid_reasons"] = invalid[:16]
         print(json.dumps(line))
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
-    return 0
+    return 1 if invalid else 0
 
 
 def main():
@@ -390,10 +526,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64-check", action="store_true",
-                    help="skip the cross-check of the mixed beta against the FP64 GPU path")
-    ap.add_argument("--ref-rows", type=int, default=6000)
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the check of beta against the oracle (and so the CPU baseline)")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed trainings of the plain FP64 GPU form (0: skip)")
+    ap.add_argument("--ref-rows", type=int, default=6000,
+                    help="rows of the oracle's sample per step of --impl reference")
+    ap.add_argument("--ref-full-rows", type=int, default=WORKLOAD["N"],
+                    help="rows of the one timed full training of --impl reference "
+                         "(the workload's N; smaller only to test the arm)")
     ap.add_argument("--rows", type=int, default=WORKLOAD["N"],
                     help="rows of the sparse-pixel workload (smaller only for profiling captures)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sparse_pixels",

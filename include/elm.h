@@ -42,7 +42,8 @@ typedef enum elm_status {
     ELM_ERR_CUDA = 2,           /* a CUDA runtime call failed               */
     ELM_ERR_NOMEM = 3,          /* device workspace allocation failed       */
     ELM_ERR_NUMERIC = 4,        /* non-finite input or Gram matrix          */
-    ELM_ERR_NOT_CONVERGED = 5,  /* refinement did not reach refine_tol      */
+    ELM_ERR_NOT_CONVERGED = 5,  /* refinement did not reach refine_tol; beta
+                                   is still written (see elm_train)          */
     ELM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up       */
     ELM_ERR_UNSUPPORTED = 7     /* size or mode outside the supported range */
 } elm_status;
@@ -124,7 +125,13 @@ typedef struct elm_train_opts {
     double refine_tol;  /* stop when ||dbeta||_F <= refine_tol ||beta||_F (<=0: 1e-12
                            for FP64, 1e-9 for MIXED)                          */
     int32_t flags;      /* ELM_FLAG_* bits                                   */
-    int32_t reserved;
+    int32_t wait_limit_ns; /* bound, in ns, of each pipeline wait inside the
+                           tensor-core kernels of ELM_PREC_MIXED (<= 0: 2 s).
+                           When a bound expires the kernel stops issuing
+                           work, lets its own copies and MMAs finish, frees
+                           its tensor memory and returns; the problem's
+                           status is ELM_ERR_TIMEOUT and the context stays
+                           usable.  Small values exist to exercise that path */
 } elm_train_opts;
 
 /* elm_train_opts.flags: record CUDA events around each training phase on
@@ -156,6 +163,12 @@ typedef struct elm_result {
  * tensor-core Gram cannot settle it: a rejected pivot above the FP64 rank
  * threshold, or refinement that does not reach refine_tol (results[i].form
  * tells which route produced beta).
+ * A problem whose FP64 refinement ends (after max_refine steps) with an
+ * update above refine_tol gets ELM_ERR_NOT_CONVERGED: beta is written, and
+ * results[i].rel_update tells how far the last step still moved it.  That
+ * happens when H is so ill-conditioned that FP64 arithmetic cannot fix beta
+ * to refine_tol (the residual equations contract by about kappa(H)^2 u per
+ * step).  Every other non-OK status leaves beta unwritten.
  */
 int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
               const elm_train_opts *opts, elm_result *results);
@@ -206,14 +219,15 @@ int64_t elm_launch_counter(void);
  * ELM_NOALLOC_SCRATCH_BYTES per device, held by every device that loads the
  * library until the process exits.  elm_hidden_noalloc_bytes() reports how
  * much of it a problem needs; larger problems get ELM_ERR_UNSUPPORTED.
- * X, W, b, a and Ht must be device pointers (host pointers: ELM_ERR_ARG);
- * the layouts are those of elm_hidden.  Work runs on `stream` (a
- * cudaStream_t, NULL for the legacy default stream), and the call
- * synchronises that stream before returning.
+ * X, W, b, a and Ht must be device memory of the current device, and
+ * `stream` (a cudaStream_t, NULL for the legacy default stream) a stream of
+ * that device; anything else is ELM_ERR_ARG.  The layouts are those of
+ * elm_hidden.  The call synchronises `stream` before returning.
  *
  * The first call on a device looks up the array's device address with that
- * device current (once per device); call it once outside any
- * latency-critical section first.  Every call on a device shares the same
+ * device current (once per device and CUDA context: a call after
+ * cudaDeviceReset looks it up again); make that first call outside any
+ * latency-critical section.  Every call on a device shares the same
  * array and leaves its contents behind, so calls that overlap on the GPU
  * (other threads or other streams) race and must be serialised by the
  * caller.

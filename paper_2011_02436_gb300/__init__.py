@@ -119,10 +119,32 @@ def elm_destroy(ctx: Context):
     ctx.close()
 
 
+def _is_f64(x):
+    return str(x.dtype).endswith("float64")
+
+
+def _check_hidden_args(X, W, b, a, Ht):
+    """Shapes and element types the C ABI takes on trust (it reads L
+    doubles of b and a and writes L x N doubles of Ht)."""
+    N, n = X.shape
+    if W.ndim != 2 or W.shape[0] != n:
+        raise ValueError("W must be n x L with n = X.shape[1]")
+    L = W.shape[1]
+    for name, v in (("W", W), ("b", b), ("a", a), ("Ht", Ht)):
+        if v is not None and not _is_f64(v):
+            raise ValueError("%s must be float64" % name)
+    if tuple(b.shape) != (L,):
+        raise ValueError("b must have shape (L,)")
+    if a is not None and tuple(a.shape) != (L,):
+        raise ValueError("a must have shape (L,)")
+    if Ht is not None and tuple(Ht.shape) != (L, N):
+        raise ValueError("Ht must have shape (L, N)")
+    return N, n, L
+
+
 def elm_hidden(ctx, X, W, b, a=None, act=ACT_SIGMOID, precision=PREC_FP64, Ht=None):
     """Ht (L x N) = a * g(X W + b), transposed (Eq. 1, Eq. 3)."""
-    N, n = X.shape
-    L = W.shape[1]
+    N, n, L = _check_hidden_args(X, W, b, a, Ht)
     if Ht is None:
         Ht = _empty_like_device(X, (L, N))
     st = _lib.load().elm_hidden(ctx.handle, _ptr(X), _xdtype(X), N, n, _ld(X), _ptr(W), _ld(W),
@@ -165,15 +187,16 @@ def elm_problem_struct(X, n, N, W, b, a, L, T, m, beta, act):
 
 
 def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
-              refine_tol=0.0, check=True, flags=0):
+              refine_tol=0.0, check=True, flags=0, wait_limit_ns=0):
     """Train each problem (dict with X, W, b, a, act, T and optional beta
     output).  Returns a list of dicts (rank, refine_iters, status,
-    rel_update, form: FORM_*); beta is written into problem['beta']."""
+    rel_update, form: FORM_*); beta is written into problem['beta'].
+    check: raise ElmError when the call returns a status other than OK."""
     if isinstance(problems, dict):
         problems = [problems]
     arr = (_lib.elm_problem * len(problems))(*[_problem(p) for p in problems])
     opts = _lib.elm_train_opts(precision=precision, max_refine=max_refine, tol_rank=tol_rank,
-                               refine_tol=refine_tol, flags=flags, reserved=0)
+                               refine_tol=refine_tol, flags=flags, wait_limit_ns=wait_limit_ns)
     res = (_lib.elm_result * len(problems))()
     st = _lib.load().elm_train(ctx.handle, arr, len(problems), C.byref(opts), res)
     if check:
@@ -192,15 +215,16 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 def elm_hidden_noalloc(X, W, b, a=None, act=ACT_SIGMOID, Ht=None, stream=None):
     """elm_hidden (mixed precision) without any device allocation by the
     library: scratch comes from a fixed device array inside libelm.so.  All
-    arrays must be CUDA tensors; Ht is allocated here (by torch) when not
-    given."""
-    N, n = X.shape
-    L = W.shape[1]
-    if Ht is None:
-        Ht = _empty_like_device(X, (L, N))
-    st = _lib.load().elm_hidden_noalloc(_ptr(X), _xdtype(X), N, n, _ld(X), _ptr(W), _ld(W),
-                                        _ptr(b), _ptr(a), L, act, _ptr(Ht), _ld(Ht),
-                                        _stream_ptr(stream))
+    arrays must be CUDA tensors of one device, which the call makes current;
+    Ht is allocated here (by torch) when not given."""
+    N, n, L = _check_hidden_args(X, W, b, a, Ht)
+    torch = _torch()
+    with torch.cuda.device(X.device):
+        if Ht is None:
+            Ht = _empty_like_device(X, (L, N))
+        st = _lib.load().elm_hidden_noalloc(_ptr(X), _xdtype(X), N, n, _ld(X), _ptr(W), _ld(W),
+                                            _ptr(b), _ptr(a), L, act, _ptr(Ht), _ld(Ht),
+                                            _stream_ptr(stream))
     if st != OK:
         raise ElmError(st, "elm_hidden_noalloc")
     return Ht

@@ -275,6 +275,7 @@ struct Problem {
     double tau;
     double tau64;      // the FP64 form's rank threshold L 2^-52 (unit-diagonal scale)
     double refine_tol;
+    uint64_t wait_ns;  // bound of the tensor kernels' pipeline waits (0: default)
 };
 
 void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res);
@@ -349,6 +350,7 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     mark(ctx, 4);
     // refinement with the residual T - H beta
     double nrm[2] = {0.0, 0.0};
+    bool converged = P.max_refine == 0;
     for (int it = 0; it < P.max_refine; it++) {
         resid_f64(s, Ht, N, L, N, beta, m, Td, T.ld, Rres);
         htr_f64(s, Ht, N, L, N, Rres, m, G, hpart, hs);
@@ -358,9 +360,15 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
         ELM_CUDA(cudaStreamSynchronize(s));
         res->refine_iters = it + 1;
         res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
-        if (res->rel_update <= P.refine_tol) break;
+        if (res->rel_update <= P.refine_tol) {
+            converged = true;
+            break;
+        }
     }
     mark(ctx, 5);
+    // the last step still moved beta by more than refine_tol: beta is
+    // returned, flagged as not converged
+    if (!converged) res->status = ELM_ERR_NOT_CONVERGED;
     if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
     if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
     const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
@@ -468,7 +476,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     // Algorithm 1 step 2 (Eq. 1, 3): pre-activation on the tensor cores,
     // activation in the epilogue, digit planes of H and H itself
     oz_hidden(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, pb.act, L, m, planes, hs,
-              nullptr, 0, err, Hdf, /*nonfinite=*/flag, x_host ? &xc : nullptr);
+              nullptr, 0, err, Hdf, /*nonfinite=*/flag, x_host ? &xc : nullptr, P.wait_ns);
     // digit rows of the targets beside those of H (part of the hidden phase,
     // so the Gram phase times the Gram kernel alone)
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
@@ -483,7 +491,7 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         res->form = ELM_FORM_MIXED_TO_FP64;
     };
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
-    oz_gram(s, planes, hs, N, L, m, G, Lt, err, gpart);
+    oz_gram(s, planes, hs, N, L, m, G, Lt, err, gpart, P.wait_ns);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4 (double-float)
     factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true);
@@ -765,6 +773,7 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             // update is that small the remaining error is smaller still
             P.refine_tol = o.refine_tol > 0.0 ? o.refine_tol
                                               : (P.prec == ELM_PREC_MIXED ? 1e-9 : 1e-12);
+            P.wait_ns = o.wait_limit_ns > 0 ? (uint64_t)o.wait_limit_ns : 0;
             elm_result r{};
             train_one(ctx, P, &r);
             if (results) results[i] = r;

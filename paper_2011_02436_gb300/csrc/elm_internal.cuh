@@ -241,12 +241,14 @@ size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m);
 // FP64 H^T (row stride ldh) when Ht != NULL, and as double-float H (N x L,
 // sample-major, eight bytes per element, about 2^-43 relative) when
 // Hdf != NULL.  *err set on a device-side timeout; *nonfinite (if given)
-// |= 1 when X holds a NaN or an infinity.
+// |= 1 when X holds a NaN or an infinity.  wait_ns bounds each pipeline
+// wait of the tensor kernel (0: 2 s).
 void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
                int64_t ldh, int *err, void *Hdf = nullptr,
-               int32_t *nonfinite = nullptr, const OzRowChunks *chunks = nullptr);
+               int32_t *nonfinite = nullptr, const OzRowChunks *chunks = nullptr,
+               uint64_t wait_ns = 0);
 // T -> digit plane rows L .. L+m-1.
 void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
                  __nv_bfloat16 *planes, double *hs);
@@ -256,7 +258,8 @@ void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_
 // by K chunks (NULL: no split).
 size_t oz_gram_part_bytes();
 void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
-             int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part);
+             int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part,
+             uint64_t wait_ns = 0);
 // out[i, c] = A[i * lda + c] - B[i * m + c]  (rows x m)
 void sub_rows(cudaStream_t s, const double *A, int64_t lda, const double *B, int64_t rows,
               int64_t m, double *out);

@@ -16,30 +16,64 @@ static __device__ __align__(256) char elm_noalloc_scratch[ELM_NOALLOC_SCRATCH_BY
 constexpr int kMaxDevices = 128;
 std::mutex g_mu;
 char *g_base[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, resolved
-// once per device with that device current.
+// Unique id of the current CUDA context (never reused within a process),
+// through the driver entry point the runtime exposes; 0 if unavailable.
+unsigned long long current_context_id() {
+    typedef CUresult (*PFN_get)(CUcontext *);
+    typedef CUresult (*PFN_id)(CUcontext, unsigned long long *);
+    static PFN_get get = nullptr;
+    static PFN_id id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get = (PFN_get)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            id = (PFN_id)p;
+        cudaGetLastError();
+        tried = true;
+    }
+    CUcontext c = nullptr;
+    unsigned long long v = 0;
+    if (!get || !id || get(&c) != CUDA_SUCCESS || !c || id(c, &v) != CUDA_SUCCESS) return 0;
+    return v;
+}
+
+// Device address of the scratch array in the current context.  It is
+// looked up with cudaGetSymbolAddress the first time a device is used, and
+// again whenever that device's context has changed since (after
+// cudaDeviceReset the module, and so the array, is loaded anew).
 char *scratch_base(int dev) {
     if (dev < 0 || dev >= kMaxDevices) throw ElmError(ELM_ERR_UNSUPPORTED, "device ordinal too large");
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_base[dev]) {
+    const unsigned long long cid = current_context_id();
+    if (!g_base[dev] || cid == 0 || cid != g_ctx_id[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, elm_noalloc_scratch);
         if (e != cudaSuccess || !p)
             throw ElmError(ELM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") +
                                              cudaGetErrorString(e));
         g_base[dev] = (char *)p;
+        g_ctx_id[dev] = cid;
     }
     return g_base[dev];
 }
 
-bool device_ptr(const void *p) {
+// Device memory of device `dev` (or managed memory).
+bool device_ptr(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 void carve(Arena &ar, int64_t N, int64_t n, int64_t L, elm::OzHidWs *hw,
@@ -73,9 +107,15 @@ extern "C" int elm_hidden_noalloc(const void *X, int x_dtype, int64_t N, int64_t
         if (x_dtype != ELM_F32 && x_dtype != ELM_F64) return ELM_ERR_ARG;
         if (act != ELM_ACT_SIGMOID && act != ELM_ACT_TANH) return ELM_ERR_ARG;
         if (!X || !W || !b || !Ht) return ELM_ERR_ARG;
-        if (!device_ptr(X) || !device_ptr(W) || !device_ptr(b) || !device_ptr(Ht) ||
-            (a && !device_ptr(a)))
+        // everything runs on the current device: operands and stream must be its own
+        int dev = 0;
+        ELM_CUDA(cudaGetDevice(&dev));
+        if (!device_ptr(X, dev) || !device_ptr(W, dev) || !device_ptr(b, dev) ||
+            !device_ptr(Ht, dev) || (a && !device_ptr(a, dev)))
             return ELM_ERR_ARG;
+        int sdev = dev;
+        ELM_CUDA(cudaStreamGetDevice((cudaStream_t)stream, &sdev));
+        if (sdev != dev) return ELM_ERR_ARG;
         Arena m;
         elm::OzHidWs hw;
         __nv_bfloat16 *planes;
@@ -83,8 +123,6 @@ extern "C" int elm_hidden_noalloc(const void *X, int x_dtype, int64_t N, int64_t
         int *err;
         carve(m, N, n, L, &hw, &planes, &hs, &err);
         if (m.used > (size_t)ELM_NOALLOC_SCRATCH_BYTES) return ELM_ERR_UNSUPPORTED;
-        int dev = 0;
-        ELM_CUDA(cudaGetDevice(&dev));
         Arena ar;
         ar.base = scratch_base(dev);
         ar.cap = ELM_NOALLOC_SCRATCH_BYTES;

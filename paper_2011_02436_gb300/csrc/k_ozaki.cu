@@ -85,15 +85,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait.  Returns false when the bound expires or another warp has
-// already given up (abort flag in shared memory).
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort) {
+// Bounded wait (bound `lim` ns).  Returns false when the bound expires or
+// another warp has already given up (abort flag in shared memory).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort,
+                                          uint64_t lim) {
     if (mbar_try(b, parity)) return true;
     const uint64_t t0 = gtime();
     for (;;) {
         if (mbar_try(b, parity)) return true;
         if (*abort) return false;
-        if (gtime() - t0 > WAIT_NS) {
+        if (gtime() - t0 > lim) {
             *abort = 1;
             return false;
         }
@@ -287,6 +288,7 @@ struct OzParams {
     int64_t ntiles;     // tiles in the tile set
     int64_t whole;      // tiles below this run over the whole K range, one CTA each
     long long *part;    // EPI == 0: int64 partial sums of the tiles from `whole` on
+    uint64_t wait_ns;   // bound of each pipeline wait (0: WAIT_NS)
     int64_t n_base;     // non-Gram tiles: first B row (column) of the tile set
     ActParams ap;       // used when the kernel's EPI != 0
 };
@@ -478,6 +480,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nslab = (int)(P.K / SK);
+    // pipeline waits use the caller's bound; the waits that only let this
+    // CTA's own copies and MMAs finish before it exits keep WAIT_NS
+    const uint64_t lim = P.wait_ns ? P.wait_ns : WAIT_NS;
     const int nchunk = (nslab + CHUNK_SLABS - 1) / CHUNK_SLABS;
 
     if (threadIdx.x == 0) {
@@ -516,7 +521,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 for (int s = c_lo * CHUNK_SLABS; s < s_hi; s++, g++) {
                     const int st = (int)(g % STAGES);
                     if (g >= STAGES &&
-                        !mbar_wait(&empty_bar[st], (uint32_t)(((g / STAGES) - 1) & 1), abort))
+                        !mbar_wait(&empty_bar[st], (uint32_t)(((g / STAGES) - 1) & 1), abort, lim))
                         break;
                     uint8_t *base = smem + (size_t)st * STAGE_BYTES;
                     mbar_expect_tx(&full_bar[st], STAGE_BYTES);
@@ -553,9 +558,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     const int st = (int)(g % STAGES);
                     const bool first = (s % CHUNK_SLABS) == 0;
                     // accumulators free again once the previous chunk is read
-                    if (first && gc > 0 && !mbar_wait(&acc_empty, (uint32_t)((gc - 1) & 1), abort))
+                    if (first && gc > 0 && !mbar_wait(&acc_empty, (uint32_t)((gc - 1) & 1), abort, lim))
                         break;
-                    if (!mbar_wait(&full_bar[st], (uint32_t)((g / STAGES) & 1), abort)) break;
+                    if (!mbar_wait(&full_bar[st], (uint32_t)((g / STAGES) & 1), abort, lim)) break;
                     tc_fence_after();
                     // one descriptor per stage; planes and K steps are compile-time
                     // offsets in its 16-byte start-address field (smem < 256 KB)
@@ -621,7 +626,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             long long run[32];     // EPI == 0: final sums of this warp's 32 columns
             for (int c = c_lo; c < c_hi; c++, gc++) {
                 // warp-uniform decision: TMEM loads below are warp-collective
-                ok = __all_sync(0xffffffffu, mbar_wait(&acc_full, (uint32_t)(gc & 1), abort));
+                ok = __all_sync(0xffffffffu, mbar_wait(&acc_full, (uint32_t)(gc & 1), abort, lim));
                 if (!ok) break;
                 tc_fence_after();
                 const bool last = c == c_hi - 1;
@@ -1169,7 +1174,8 @@ size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m) {
 void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
-               int64_t ldh, int *err, void *Hdf, int32_t *nonfinite, const OzRowChunks *chunks) {
+               int64_t ldh, int *err, void *Hdf, int32_t *nonfinite, const OzRowChunks *chunks,
+               uint64_t wait_ns) {
     const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
     col_scale_kernel<<<(unsigned)((Lp + 31) / 32), 256, 0, s>>>(W, n, L, ldw, Lp, w.ws);
     ELM_CHECK_LAUNCH();
@@ -1197,6 +1203,7 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.out = nullptr;
     P.ldo = 0;
     P.err = err;
+    P.wait_ns = wait_ns;
     P.ap.b = b;
     P.ap.a = a;
     P.ap.act = act;
@@ -1258,7 +1265,8 @@ void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_
 size_t oz_gram_part_bytes() { return (size_t)sm_count() * BM * BN * sizeof(long long); }
 
 void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
-             int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part) {
+             int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part,
+             uint64_t wait_ns) {
     const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
     const int64_t nJ = Lp / BM, ntiles = nJ * (nJ + 1);
     const int64_t sms = sm_count();
@@ -1283,6 +1291,7 @@ void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int6
     P.out = G;
     P.ldo = ldg;
     P.err = err;
+    P.wait_ns = wait_ns;
     if (P.whole < ntiles)
         ELM_CUDA(cudaMemsetAsync(part, 0, (size_t)(ntiles - P.whole) * BM * BN * sizeof(long long),
                                  s));

@@ -11,7 +11,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_prints_one_contract_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0", "--ref-rows", "300"],
+                          "--steps", "1", "--warmup", "0", "--ref-rows", "300",
+                          "--ref-full-rows", "600"],
                          capture_output=True, text=True, check=True, cwd=ROOT, env=env,
                          timeout=600).stdout.strip().splitlines()
     line = json.loads(out[-1])
