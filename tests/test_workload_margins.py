@@ -2,6 +2,8 @@
 oracle: the smallest accepted pivot (unit-diagonal scale) must clear both
 rank thresholds -- L 2^-52 (FP64 Gram) and 2^-32 (mixed Gram) -- by a wide
 factor, so that the GPU's rank can be compared bit-exactly."""
+import os
+
 import numpy as np
 import pytest
 
@@ -32,3 +34,28 @@ def test_rank_margins_cover_mixed_threshold(name):
     piv = np.diag(R)[:r] ** 2 / np.diag(S)[perm[:r]]
     assert piv.min() > 1000 * 2.0 ** -32
     assert piv.min() > 1e6 * oracle.default_tau(S.shape[0])
+
+
+FULL = ("rank_deficient", "batched", "large")
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.mark.parametrize("name", FULL)
+def test_full_size_margins_from_the_oracle(name):
+    """The same margins at every workload's full size, as the oracle recorded
+    them (tests/golden/make_full_goldens.py): the FP64 rank rule's decision
+    (tau = L 2^-52) is clear by at least three orders of magnitude on both
+    sides, so the rank can be compared bit-exactly.  Problems whose smallest
+    pivot lies within 1000x of the mixed threshold 2^-32 stay a minority;
+    for them the rank decision rests on the FP64 hand-over of the mixed
+    form, and the GPU tests compare their rank with the oracle's."""
+    path = os.path.join(GOLD, "full_%s.npz" % name)
+    if not os.path.exists(path):
+        pytest.skip("golden file not written yet")
+    g = np.load(path)
+    tau = g["tau"]
+    assert np.all(g["piv_min"] > 1e3 * tau)
+    assert np.all(g["rejected_max"] < 1e-2 * tau)
+    tight = [i for i in range(int(g["count"])) if g["piv_min"][i] < 1000 * 2.0 ** -32]
+    # the well-separated majority
+    assert len(tight) <= int(g["count"]) // 4
