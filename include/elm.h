@@ -142,6 +142,8 @@ typedef struct elm_train_opts {
 #define ELM_FORM_FP64 0          /* FP64 form (ELM_PREC_FP64)                   */
 #define ELM_FORM_MIXED 1         /* mixed form                                  */
 #define ELM_FORM_MIXED_TO_FP64 2 /* mixed form handed over to the FP64 form     */
+#define ELM_FORM_WIDE 3          /* N < L: H^+ = H^T (H H^T)^+ in FP64 (the
+                                    branch stated with Eq. 8), either precision */
 
 typedef struct elm_result {
     int64_t rank;         /* r                                              */
@@ -163,6 +165,11 @@ typedef struct elm_result {
  * tensor-core Gram cannot settle it: a rejected pivot above the FP64 rank
  * threshold, or refinement that does not reach refine_tol (results[i].form
  * tells which route produced beta).
+ * A problem with fewer samples than hidden neurons (N < L) takes the wide
+ * branch in either precision: the N x N Gram H H^T of the rows of H is
+ * factorised by the same pivoted Cholesky (rank r over the rows, tol_rank
+ * default N 2^-52), and beta = H^T (H H^T)^+ T is formed through the
+ * full-rank factorisation of the rows, with refinement steps as above.
  * A problem whose FP64 refinement ends (after max_refine steps) with an
  * update above refine_tol gets ELM_ERR_NOT_CONVERGED: beta is written, and
  * results[i].rel_update tells how far the last step still moved it.  That

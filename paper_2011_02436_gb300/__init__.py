@@ -205,7 +205,7 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
                  rel_update=r.rel_update, form=r.form) for r in res]
 
 
-FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64 = 0, 1, 2
+FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64, FORM_WIDE = 0, 1, 2, 3
 
 
 FLAG_PHASE_TIMING = 1

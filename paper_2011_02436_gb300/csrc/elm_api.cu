@@ -276,11 +276,14 @@ struct Problem {
     double tau64;      // the FP64 form's rank threshold L 2^-52 (unit-diagonal scale)
     double refine_tol;
     uint64_t wait_ns;  // bound of the tensor kernels' pipeline waits (0: default)
+    bool wide;         // N < L: the branch H^+ = H^T (H H^T)^+
 };
 
 void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res);
+void train_wide(elm_ctx *ctx, const Problem &P, elm_result *res);
 
 void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
+    if (P.wide) return train_wide(ctx, P, res);
     if (P.prec == ELM_PREC_MIXED) return train_mixed(ctx, P, res);
     res->form = ELM_FORM_FP64;
     res->reserved = 0;
@@ -375,6 +378,148 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
                                                    : cudaMemcpyDeviceToHost;
     copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double),
                                m * sizeof(double), L, kind, s);
+    ELM_CUDA(cudaStreamSynchronize(s));
+    collect_phases(ctx);
+}
+
+// ----------------------------------------------------------- wide branch
+// N < L (the branch stated with Eq. 8): H^+ = H^T (H H^T)^+.  The N x N Gram
+// of the rows of H is factorised by the pivoted Cholesky of the tall case,
+// which now pivots over samples: P H = [I; K^T] H1 with H1 the r
+// independent rows and K = R11^{-1} R12 (H2 = K^T H1 follows from
+// H2 H1^T = R12^T R11).  Both factors have full rank, so
+//   H^+ = H1^+ [I; K^T]^+ P = H1^T (R11^T R11)^{-1} (I + K K^T)^{-1} [I K] P,
+// the Moore-Penrose inverse for every rank (Eq. 5).  (I + K K^T)^{-1} is
+// applied through I + K^T K (Woodbury), whose factor the solver prepares.
+struct WideScratch {
+    double *PT, *ym, *zf, *hpart;
+    int hs;
+};
+
+void wide_apply(cudaStream_t s, const Solver &sv, const double *Ht, int64_t L, int64_t N,
+                const double *Tin, int64_t ldt, double *out, const WideScratch &ws) {
+    const int64_t r = sv.r, q = N - r, m = sv.m;
+    if (r == 0) {
+        ELM_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * L * m, s));
+        return;
+    }
+    double *w = sv.yb;                                              // r x m
+    gather_rows(s, Tin, ldt, sv.perm, nullptr, N, m, ws.PT, m);     // P T
+    ELM_CUDA(cudaMemcpyAsync(w, ws.PT, sizeof(double) * r * m, cudaMemcpyDeviceToDevice, s));
+    if (q > 0) {
+        // w = [I K] P T
+        ELM_CUDA(cudaMemsetAsync(ws.ym, 0, sizeof(double) * r * m, s));
+        av_sub_f64(s, sv.K, r, q, q, ws.PT + r * m, m, ws.ym);      // ym = -K (P T)[r:]
+        sub_rows(s, w, m, ws.ym, r, m, w);
+        // w = (I + K K^T)^{-1} w = w - K (I + K^T K)^{-1} K^T w
+        atv_f64(s, sv.K, r, q, q, w, m, sv.v, sv.atv_part, sv.atv_split);
+        ELM_CUDA(cudaMemsetAsync(sv.w, 0, sizeof(double) * q * m, s));
+        gather_rows(s, sv.v, m, sv.f2.perm, &sv.f2.st->rank, q, m, sv.w, m);
+        trsm_fwd(s, sv.R2, sv.ld2, sv.DinvF2, q, sv.w, m, m, sv.tflag);
+        trsm_bwd(s, sv.Rt2, sv.ld2, sv.DinvB2, q, sv.w, m, m, sv.tflag);
+        scatter_rows(s, sv.w, m, sv.f2.perm, q, sv.v, m, 1.0, 0);
+        av_sub_f64(s, sv.K, r, q, q, sv.v, m, w);
+    }
+    // (R11^T R11)^{-1} w, then beta = H1^T z (z scattered to the rows of H)
+    trsm_fwd(s, sv.R, sv.ld, sv.DinvF, r, w, m, m, sv.tflag);
+    trsm_bwd(s, sv.Rt, sv.ld, sv.DinvB, r, w, m, m, sv.tflag);
+    ELM_CUDA(cudaMemsetAsync(ws.zf, 0, sizeof(double) * N * m, s));
+    scatter_rows(s, w, m, sv.perm, r, ws.zf, m, 1.0, 0);
+    htr_f64(s, Ht, N, L, N, ws.zf, m, out, ws.hpart, ws.hs);
+}
+
+void train_wide(elm_ctx *ctx, const Problem &P, elm_result *res) {
+    res->form = ELM_FORM_WIDE;
+    res->reserved = 0;
+    const elm_problem &pb = *P.p;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
+    const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
+    const int ns = gram_f64_nsplit(N, 0, L, ctx->sm_count);
+    const int hs = htr_f64_nsplit(L, N, ctx->sm_count);
+    In X, W, b, a, T;
+    double *Ht, *H, *K, *gpart, *R, *Rt, *beta, *dB, *Rres, *norms;
+    int32_t *flag;
+    FactorWs f;
+    WideScratch ws{};
+    ws.hs = hs;
+    with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+        X = stage(ar, s, pb.X, N, n, pb.ldx, xsz);
+        W = stage(ar, s, pb.W, n, L, pb.ldw, 8);
+        b = stage(ar, s, pb.b, 1, L, L, 8);
+        a = stage(ar, s, pb.a, 1, L, L, 8);
+        T = stage(ar, s, pb.T, N, m, pb.ldt, 8);
+        Ht = ar.take<double>(L * N);
+        H = ar.take<double>(N * L);
+        K = ar.take<double>(N * N);
+        gpart = ar.take<double>(gram_f64_ws(N, 0, ns));
+        R = ar.take<double>(N * tri_ld(N));
+        Rt = ar.take<double>(N * tri_ld(N));
+        beta = ar.take<double>(L * m);
+        dB = ar.take<double>(L * m);
+        Rres = ar.take<double>(N * m);
+        ws.PT = ar.take<double>(N * m);
+        ws.ym = ar.take<double>(N * m);
+        ws.zf = ar.take<double>(N * m);
+        ws.hpart = ar.take<double>(htr_f64_ws(L, m, hs));
+        norms = ar.take<double>(2);
+        flag = ar.take<int32_t>(1);
+        f = factor_ws_carve(ar, N);
+    });
+    ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    check_finite(s, X.p, pb.x_dtype, N, n, X.ld, flag);
+    const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
+                 *ad = (const double *)a.p, *Td = (const double *)T.p;
+    mark(ctx, 0);
+    hidden_f64(s, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, L, pb.act, Ht, N);
+    transpose_f64(s, Ht, L, N, N, H, L);
+    mark(ctx, 1);
+    // H H^T: the Gram of the rows of H
+    gram_f64(s, H, L, N, L, nullptr, 0, 0, K, N, nullptr, 0, gpart, ns);
+    mark(ctx, 2);
+    factor_pivoted(s, K, N, N, P.tau, f, R, Rt, tri_ld(N), ctx->sm_count);
+    mark(ctx, 3);
+    int32_t fl = 0, xfl = 0;
+    const int64_t r = read_rank(s, f, &fl);
+    ELM_CUDA(cudaMemcpy(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost));
+    res->rank = r;
+    res->refine_iters = 0;
+    res->rel_update = 0.0;
+    res->status = ELM_OK;
+    if (fl & 2) {
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if ((fl & 1) || xfl) {
+        res->status = ELM_ERR_NUMERIC;
+        return;
+    }
+    const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(N), f.perm, r, N, m);
+    wide_apply(s, sv, Ht, L, N, Td, T.ld, beta, ws);
+    mark(ctx, 4);
+    double nrm[2] = {0.0, 0.0};
+    bool converged = P.max_refine == 0;
+    for (int it = 0; it < P.max_refine; it++) {
+        resid_f64(s, Ht, N, L, N, beta, m, Td, T.ld, Rres);          // T - H beta
+        wide_apply(s, sv, Ht, L, N, Rres, m, dB, ws);                 // H^+ (T - H beta)
+        axpy_norms(s, beta, dB, L * m, norms);
+        ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
+        ELM_CUDA(cudaStreamSynchronize(s));
+        res->refine_iters = it + 1;
+        res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        if (res->rel_update <= P.refine_tol) {
+            converged = true;
+            break;
+        }
+    }
+    mark(ctx, 5);
+    if (!converged) res->status = ELM_ERR_NOT_CONVERGED;
+    if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
+    if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
+    const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyDeviceToHost;
+    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double), m * sizeof(double), L,
+           kind, s);
     ELM_CUDA(cudaStreamSynchronize(s));
     collect_phases(ctx);
 }
@@ -774,6 +919,15 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             P.refine_tol = o.refine_tol > 0.0 ? o.refine_tol
                                               : (P.prec == ELM_PREC_MIXED ? 1e-9 : 1e-12);
             P.wait_ns = o.wait_limit_ns > 0 ? (uint64_t)o.wait_limit_ns : 0;
+            // fewer samples than neurons: the wide branch, FP64 rules on the
+            // N x N Gram
+            P.wide = probs[i].N < probs[i].L;
+            if (P.wide) {
+                P.tau = o.tol_rank > 0.0 ? o.tol_rank : (double)probs[i].N * ldexp(1.0, -52);
+                P.tau64 = P.tau;
+                if (o.max_refine < 0) P.max_refine = 2;
+                if (!(o.refine_tol > 0.0)) P.refine_tol = 1e-12;
+            }
             elm_result r{};
             train_one(ctx, P, &r);
             if (results) results[i] = r;

@@ -185,6 +185,9 @@ void sumsq(cudaStream_t s, const double *x, int64_t rows, int64_t cols, int64_t 
 void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, double *out);
 // A (n x n) = I.
 void set_identity(cudaStream_t s, double *A, int64_t n);
+// B (cols x rows, ldb) = A^T for A (rows x cols, lda).
+void transpose_f64(cudaStream_t s, const double *A, int64_t rows, int64_t cols, int64_t lda,
+                   double *B, int64_t ldb);
 // C (q x q, both triangles) = I + A^T A for A (k x q, row-major, lda) in
 // FP64; part: syrk_f64_ws(q, S) doubles, S = syrk_f64_splits(k, q, sms)
 // pieces of the k range summed in a fixed order.

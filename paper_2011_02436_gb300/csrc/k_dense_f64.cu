@@ -608,6 +608,24 @@ __global__ void sub_rows_kernel(const double *__restrict__ A, int64_t lda,
     }
 }
 
+// B (cols x rows, ldb) = A^T for A (rows x cols, lda): 32 x 32 tiles through
+// shared memory, both sides coalesced.
+__global__ void transpose_f64_kernel(const double *__restrict__ A, int64_t rows, int64_t cols,
+                                     int64_t lda, double *__restrict__ B, int64_t ldb) {
+    __shared__ double t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t r = r0 + yy, c = c0 + tx;
+        if (r < rows && c < cols) t[yy][tx] = A[r * lda + c];
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t c = c0 + yy, r = r0 + tx;
+        if (r < rows && c < cols) B[c * ldb + r] = t[tx][yy];
+    }
+}
+
 inline unsigned blocks_for(int64_t work, int per = 256, int64_t cap = 65535 * 8) {
     int64_t g = (work + per - 1) / per;
     if (g < 1) g = 1;
@@ -1006,6 +1024,14 @@ void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, d
 void sub_rows(cudaStream_t s, const double *A, int64_t lda, const double *B, int64_t rows,
               int64_t m, double *out) {
     sub_rows_kernel<<<blocks_for(rows * m), 256, 0, s>>>(A, lda, B, rows, m, out);
+    ELM_CHECK_LAUNCH();
+}
+
+void transpose_f64(cudaStream_t s, const double *A, int64_t rows, int64_t cols, int64_t lda,
+                   double *B, int64_t ldb) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 g((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    transpose_f64_kernel<<<g, 256, 0, s>>>(A, rows, cols, lda, B, ldb);
     ELM_CHECK_LAUNCH();
 }
 
