@@ -357,7 +357,8 @@ def run_native(args):
                 invalid.append("%s problem %d: status %d rank %d" % (what, i, r["status"], r["rank"]))
 
     # verified run: statuses, ranks and beta against the oracle (rank 0)
-    res = elm.elm_train(ctx, probs, precision=prec, check=False)
+    bs = dict(block_split=args.block_split) if args.block_split > 0 else {}
+    res = elm.elm_train(ctx, probs, precision=prec, check=False, **bs)
     betas = [pr["beta"].cpu().numpy() for pr in probs]
     check = dict(rank=[r["rank"] for r in res] if count > 1 else res[0]["rank"],
                  refine_iters=max(r["refine_iters"] for r in res),
@@ -378,7 +379,7 @@ def run_native(args):
         timed_ok(res, "verified")
 
     for _ in range(args.warmup):
-        timed_ok(elm.elm_train(ctx, probs, precision=prec, check=False), "warm-up")
+        timed_ok(elm.elm_train(ctx, probs, precision=prec, check=False, **bs), "warm-up")
     elm.elm_phase_times(ctx)                       # reset
     barrier()
     l0 = elm.elm_launch_counter()
@@ -389,7 +390,7 @@ def run_native(args):
         e0.record(stream)
         for _ in range(args.steps):
             step_res.append(elm.elm_train(ctx, probs, precision=prec,
-                                          flags=elm.FLAG_PHASE_TIMING, check=False))
+                                          flags=elm.FLAG_PHASE_TIMING, check=False, **bs))
         e1.record(stream)
         barrier()
     launches = elm.elm_launch_counter() - l0
@@ -402,7 +403,7 @@ def run_native(args):
 
     # the plain FP64 GPU form of the same workload, for the metric's ratio
     fp64 = None
-    if prec == elm.PREC_MIXED and args.fp64_steps > 0:
+    if prec == elm.PREC_MIXED and args.fp64_steps > 0 and not bs:
         p64 = [dict(pr, beta=torch.empty_like(pr["beta"])) for pr in probs]
         r64 = elm.elm_train(ctx, p64, precision=elm.PREC_FP64, check=False)     # warm-up
         if refs is not None and any(x is not None for x in refs):
@@ -437,14 +438,14 @@ def run_native(args):
                    if hp[k] is not None)
         hprobs.append(hp)
     d2h = sum(hp["beta"].numel() * 8 for hp in hprobs)
-    timed_ok(elm.elm_train(ctx, hprobs, precision=prec, check=False), "e2e warm-up")
+    timed_ok(elm.elm_train(ctx, hprobs, precision=prec, check=False, **bs), "e2e warm-up")
     barrier()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     e2e_steps = max(1, min(args.steps, 5))
     for _ in range(e2e_steps):
-        timed_ok(elm.elm_train(ctx, hprobs, precision=prec, check=False), "e2e")
+        timed_ok(elm.elm_train(ctx, hprobs, precision=prec, check=False, **bs), "e2e")
     f1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, dev)
@@ -483,9 +484,12 @@ def run_native(args):
                         issued_frac=issued / (ph_ms["gram"] * 1e-3) / 1e12 / pk["bf16"])
         roof["phase_ms"] = ph_ms
         first = hosts[0]
-        cfg = dict(workload=desc, precision=args.precision,
+        cfg = dict(workload=desc, precision=args.precision if not bs else "fp64 (block route)",
                    parallelism="replicas" if ws > 1 else "single",
                    l2="inputs larger than L2 (X and the digit planes stream from HBM): no flush")
+        if bs:
+            cfg.update(route="the paper's block formulae (Eqs. 19-23), H1 = first %d columns"
+                       % args.block_split)
         if count == 1:
             cfg.update(N=first["X"].shape[0], n=first["X"].shape[1], L=first["W"].shape[1],
                        m=first["T"].shape[1])
@@ -494,7 +498,7 @@ def run_native(args):
         line = dict(metric=METRIC, value=value, unit="trainings/s", n_gpus=ws, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms_max, higher_is_better=True,
                     scaling="weak", vs_baseline=None,
-                    dtype="f64" if prec == elm.PREC_FP64 else "bf16-slices+f64",
+                    dtype="f64" if (prec == elm.PREC_FP64 or bs) else "bf16-slices+f64",
                     data="synthetic", config=cfg,
                     e2e=dict(value=ws * count * 1000.0 / e2e_ms, unit="trainings/s",
                              h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
@@ -539,6 +543,9 @@ def main():
                     help="rows of the sparse-pixel workload (smaller only for profiling captures)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sparse_pixels",
                     help="the timed workload (the default is the headline configuration)")
+    ap.add_argument("--block-split", type=int, default=0,
+                    help="> 0: train by the paper's block formulae (Eqs. 19-23) with H1 the "
+                         "first BLOCK_SPLIT columns instead of the rank-based route")
     ap.add_argument("--hidden", type=int, default=2000,
                     help="hidden width L of the gina_shaped workload (the paper's Table 1 "
                          "uses 500, 1000, 1500, 2000)")

@@ -132,6 +132,17 @@ typedef struct elm_train_opts {
                            its tensor memory and returns; the problem's
                            status is ELM_ERR_TIMEOUT and the context stays
                            usable.  Small values exist to exercise that path */
+    int32_t block_split; /* > 0: instead of the rank-based route, the paper's
+                           block formulae for the split H = [H1 H2] with H1
+                           the first block_split columns (Eqs. 19-23: A =
+                           H2^T H2, B = A^{-1} H2^T T, D = H1^T C H1 as the
+                           Schur complement S11 - S12 A^{-1} S21, beta1 =
+                           D^{-1} H1^T (T - H2 B), beta2 = B - A^{-1} H2^T H1
+                           beta1), in FP64, followed by the refinement steps.
+                           Needs 0 < block_split < L and H of full column
+                           rank (A or D singular: ELM_ERR_NUMERIC); wide
+                           problems (N < L) are rejected (ELM_ERR_ARG)     */
+    int32_t reserved;   /* 0                                                */
 } elm_train_opts;
 
 /* elm_train_opts.flags: record CUDA events around each training phase on
@@ -144,6 +155,8 @@ typedef struct elm_train_opts {
 #define ELM_FORM_MIXED_TO_FP64 2 /* mixed form handed over to the FP64 form     */
 #define ELM_FORM_WIDE 3          /* N < L: H^+ = H^T (H H^T)^+ in FP64 (the
                                     branch stated with Eq. 8), either precision */
+#define ELM_FORM_BLOCK 4         /* the paper's block formulae (Eqs. 19-23),
+                                    elm_train_opts.block_split, FP64          */
 
 typedef struct elm_result {
     int64_t rank;         /* r                                              */

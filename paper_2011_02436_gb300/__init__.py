@@ -187,7 +187,7 @@ def elm_problem_struct(X, n, N, W, b, a, L, T, m, beta, act):
 
 
 def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
-              refine_tol=0.0, check=True, flags=0, wait_limit_ns=0):
+              refine_tol=0.0, check=True, flags=0, wait_limit_ns=0, block_split=0):
     """Train each problem (dict with X, W, b, a, act, T and optional beta
     output).  Returns a list of dicts (rank, refine_iters, status,
     rel_update, form: FORM_*); beta is written into problem['beta'].
@@ -196,7 +196,8 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
         problems = [problems]
     arr = (_lib.elm_problem * len(problems))(*[_problem(p) for p in problems])
     opts = _lib.elm_train_opts(precision=precision, max_refine=max_refine, tol_rank=tol_rank,
-                               refine_tol=refine_tol, flags=flags, wait_limit_ns=wait_limit_ns)
+                               refine_tol=refine_tol, flags=flags, wait_limit_ns=wait_limit_ns,
+                               block_split=block_split, reserved=0)
     res = (_lib.elm_result * len(problems))()
     st = _lib.load().elm_train(ctx.handle, arr, len(problems), C.byref(opts), res)
     if check:
@@ -205,7 +206,7 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
                  rel_update=r.rel_update, form=r.form) for r in res]
 
 
-FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64, FORM_WIDE = 0, 1, 2, 3
+FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64, FORM_WIDE, FORM_BLOCK = 0, 1, 2, 3, 4
 
 
 FLAG_PHASE_TIMING = 1

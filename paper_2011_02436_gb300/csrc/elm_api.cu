@@ -277,12 +277,15 @@ struct Problem {
     double refine_tol;
     uint64_t wait_ns;  // bound of the tensor kernels' pipeline waits (0: default)
     bool wide;         // N < L: the branch H^+ = H^T (H H^T)^+
+    int64_t block;     // > 0: the paper's block formulae, H1 = first `block` columns
 };
 
 void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res);
 void train_wide(elm_ctx *ctx, const Problem &P, elm_result *res);
+void train_block(elm_ctx *ctx, const Problem &P, elm_result *res);
 
 void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
+    if (P.block > 0) return train_block(ctx, P, res);
     if (P.wide) return train_wide(ctx, P, res);
     if (P.prec == ELM_PREC_MIXED) return train_mixed(ctx, P, res);
     res->form = ELM_FORM_FP64;
@@ -516,6 +519,192 @@ void train_wide(elm_ctx *ctx, const Problem &P, elm_result *res) {
     if (!converged) res->status = ELM_ERR_NOT_CONVERGED;
     if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
     if (solver_timed_out(s, sv)) res->status = ELM_ERR_TIMEOUT;
+    const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyDeviceToHost;
+    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double), m * sizeof(double), L,
+           kind, s);
+    ELM_CUDA(cudaStreamSynchronize(s));
+    collect_phases(ctx);
+}
+
+// ------------------------------------------------ the paper's block route
+// Eqs. 19-23 (transposition of Eq. 19 fixed) for a full-rank split
+// H = [H1 H2], H1 the first r1 columns:
+//   A = H2^T H2 = S22,  B = A^{-1} H2^T Y = A^{-1} Z2,
+//   D = H1^T C H1 = S11 - S12 A^{-1} S21  (C = I - H2 A^{-1} H2^T, Eq. 22),
+//   beta1 = D^{-1} H1^T (Y - H2 B) = D^{-1} (Z1 - S12 B),
+//   beta2 = B - A^{-1} H2^T H1 beta1 = B - (A^{-1} S21) beta1,
+// everything from the Gram blocks S = H^T H and Z = H^T Y, so the N x N
+// matrix C is never formed.  A and D are SPD when H has full column rank;
+// they are factorised by the pivoted Cholesky and a rank below their size
+// means the split is singular.
+struct SpdFactor {
+    const double *R, *Rt;
+    int64_t ld, n;
+    const int32_t *perm;
+    double *DinvF, *DinvB;
+    int *tflag;
+};
+
+// out (n x mc, ldo) = M^{-1} Z for the factorised SPD matrix M (n x n)
+void spd_apply(cudaStream_t s, const SpdFactor &F, const double *Z, int64_t ldz, double *out,
+               int64_t ldo, int64_t mc, double *yb) {
+    gather_rows(s, Z, ldz, F.perm, nullptr, F.n, mc, yb, mc);
+    trsm_fwd(s, F.R, F.ld, F.DinvF, F.n, yb, mc, mc, F.tflag);
+    trsm_bwd(s, F.Rt, F.ld, F.DinvB, F.n, yb, mc, mc, F.tflag);
+    scatter_rows(s, yb, mc, F.perm, F.n, out, ldo, 1.0, 0);
+}
+
+struct BlockRoute {
+    SpdFactor A, D;
+    const double *S;    // L x L Gram (ld L)
+    int64_t L, r1, q, m;
+    double *M;          // A^{-1} S21 (q x r1)
+    double *Bv, *rhs, *yb;
+};
+
+// out (L x m) = the block formulae applied to Zin (L x m, ldz)
+void block_apply(cudaStream_t s, const BlockRoute &b, const double *Zin, int64_t ldz,
+                 double *out) {
+    const int64_t L = b.L, r1 = b.r1, q = b.q, m = b.m;
+    spd_apply(s, b.A, Zin + r1 * ldz, ldz, b.Bv, m, m, b.yb);                 // B
+    copy2d(b.rhs, m * 8, Zin, ldz * 8, m * 8, r1, cudaMemcpyDeviceToDevice, s);
+    gemm_f64(s, r1, m, q, -1.0, b.S + r1, L, 1, b.Bv, m, 1, 1.0, b.rhs, m);  // Z1 - S12 B
+    spd_apply(s, b.D, b.rhs, m, out, m, m, b.yb);                              // beta1
+    ELM_CUDA(cudaMemcpyAsync(out + r1 * m, b.Bv, sizeof(double) * q * m,
+                             cudaMemcpyDeviceToDevice, s));
+    gemm_f64(s, q, m, r1, -1.0, b.M, r1, 1, out, m, 1, 1.0, out + r1 * m, m);  // beta2
+}
+
+void train_block(elm_ctx *ctx, const Problem &P, elm_result *res) {
+    res->form = ELM_FORM_BLOCK;
+    res->reserved = 0;
+    const elm_problem &pb = *P.p;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m, r1 = P.block, q = L - r1;
+    const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
+    const int ns = gram_f64_nsplit(L, m, N, ctx->sm_count);
+    const int hs = htr_f64_nsplit(L, N, ctx->sm_count);
+    const int64_t nm = r1 > q ? r1 : q, mm = m > r1 ? m : r1;
+    In X, W, b, a, T;
+    double *Ht, *S, *Z, *gpart, *RA, *RtA, *RD, *RtD, *Dm, *beta, *dB, *Rres, *G, *hpart, *norms;
+    int32_t *flag;
+    int *tflag;
+    FactorWs fA, fD;
+    BlockRoute br{};
+    with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+        X = stage(ar, s, pb.X, N, n, pb.ldx, xsz);
+        W = stage(ar, s, pb.W, n, L, pb.ldw, 8);
+        b = stage(ar, s, pb.b, 1, L, L, 8);
+        a = stage(ar, s, pb.a, 1, L, L, 8);
+        T = stage(ar, s, pb.T, N, m, pb.ldt, 8);
+        Ht = ar.take<double>(L * N);
+        S = ar.take<double>(L * L);
+        Z = ar.take<double>(L * m);
+        gpart = ar.take<double>(gram_f64_ws(L, m, ns));
+        RA = ar.take<double>(q * tri_ld(q));
+        RtA = ar.take<double>(q * tri_ld(q));
+        RD = ar.take<double>(r1 * tri_ld(r1));
+        RtD = ar.take<double>(r1 * tri_ld(r1));
+        Dm = ar.take<double>(r1 * r1);
+        br.A.DinvF = ar.take<double>(trsm_dinv_doubles(q));
+        br.A.DinvB = ar.take<double>(trsm_dinv_doubles(q));
+        br.D.DinvF = ar.take<double>(trsm_dinv_doubles(r1));
+        br.D.DinvB = ar.take<double>(trsm_dinv_doubles(r1));
+        br.M = ar.take<double>(q * r1);
+        br.Bv = ar.take<double>(q * m);
+        br.rhs = ar.take<double>(r1 * m);
+        br.yb = ar.take<double>(nm * mm);
+        beta = ar.take<double>(L * m);
+        dB = ar.take<double>(L * m);
+        Rres = ar.take<double>(N * m);
+        G = ar.take<double>(L * m);
+        hpart = ar.take<double>(htr_f64_ws(L, m, hs));
+        norms = ar.take<double>(2);
+        flag = ar.take<int32_t>(1);
+        tflag = ar.take<int>(1);
+        fA = factor_ws_carve(ar, q);
+        fD = factor_ws_carve(ar, r1);
+    });
+    ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    ELM_CUDA(cudaMemsetAsync(tflag, 0, sizeof(int), s));
+    check_finite(s, X.p, pb.x_dtype, N, n, X.ld, flag);
+    const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
+                 *ad = (const double *)a.p, *Td = (const double *)T.p;
+    mark(ctx, 0);
+    hidden_f64(s, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, L, pb.act, Ht, N);
+    mark(ctx, 1);
+    gram_f64(s, Ht, N, L, N, Td, T.ld, m, S, L, Z, m, gpart, ns);       // Eqs. 9-13
+    mark(ctx, 2);
+    res->rank = 0;
+    res->refine_iters = 0;
+    res->rel_update = 0.0;
+    res->status = ELM_OK;
+    // A = S22 (Eq. 20), then M = A^{-1} S21 and D = S11 - S12 M (Eq. 23)
+    factor_pivoted(s, S + r1 * L + r1, L, q, (double)q * ldexp(1.0, -52), fA, RA, RtA,
+                   tri_ld(q), ctx->sm_count);
+    int32_t fl = 0, xfl = 0;
+    const int64_t rA = read_rank(s, fA, &fl);
+    ELM_CUDA(cudaMemcpy(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost));
+    if (fl & 2) {
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if ((fl & 1) || xfl || rA < q) {     // non-finite, or A singular
+        res->status = ELM_ERR_NUMERIC;
+        res->rank = rA;
+        return;
+    }
+    br.A = SpdFactor{RA, RtA, tri_ld(q), q, fA.perm, br.A.DinvF, br.A.DinvB, tflag};
+    trsm_prepare(s, RA, tri_ld(q), q, br.A.DinvF, br.A.DinvB);
+    spd_apply(s, br.A, S + r1 * L, L, br.M, r1, r1, br.yb);
+    copy2d(Dm, r1 * 8, S, L * 8, r1 * 8, r1, cudaMemcpyDeviceToDevice, s);
+    gemm_f64(s, r1, r1, q, -1.0, S + r1, L, 1, br.M, r1, 1, 1.0, Dm, r1);
+    factor_pivoted(s, Dm, r1, r1, (double)r1 * ldexp(1.0, -52), fD, RD, RtD, tri_ld(r1),
+                   ctx->sm_count);
+    const int64_t rD = read_rank(s, fD, &fl);
+    if (fl & 2) {
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if ((fl & 1) || rD < r1) {           // D singular: H is rank deficient
+        res->status = ELM_ERR_NUMERIC;
+        res->rank = rA + rD;
+        return;
+    }
+    res->rank = L;
+    br.D = SpdFactor{RD, RtD, tri_ld(r1), r1, fD.perm, br.D.DinvF, br.D.DinvB, tflag};
+    trsm_prepare(s, RD, tri_ld(r1), r1, br.D.DinvF, br.D.DinvB);
+    br.S = S;
+    br.L = L;
+    br.r1 = r1;
+    br.q = q;
+    br.m = m;
+    block_apply(s, br, Z, m, beta);                                      // Eqs. 19, 21
+    mark(ctx, 4);
+    double nrm[2] = {0.0, 0.0};
+    bool converged = P.max_refine == 0;
+    for (int it = 0; it < P.max_refine; it++) {
+        resid_f64(s, Ht, N, L, N, beta, m, Td, T.ld, Rres);
+        htr_f64(s, Ht, N, L, N, Rres, m, G, hpart, hs);
+        block_apply(s, br, G, m, dB);
+        axpy_norms(s, beta, dB, L * m, norms);
+        ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
+        ELM_CUDA(cudaStreamSynchronize(s));
+        res->refine_iters = it + 1;
+        res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        if (res->rel_update <= P.refine_tol) {
+            converged = true;
+            break;
+        }
+    }
+    mark(ctx, 5);
+    if (!converged) res->status = ELM_ERR_NOT_CONVERGED;
+    if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
+    int tf = 0;
+    ELM_CUDA(cudaMemcpyAsync(&tf, tflag, sizeof tf, cudaMemcpyDeviceToHost, s));
+    ELM_CUDA(cudaStreamSynchronize(s));
+    if (tf) res->status = ELM_ERR_TIMEOUT;
     const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyDeviceToHost;
     copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double), m * sizeof(double), L,
@@ -889,6 +1078,7 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
         require(count >= 0, "count < 0");
         require(count == 0 || probs, "probs is NULL");
         require(o.precision == ELM_PREC_FP64 || o.precision == ELM_PREC_MIXED, "precision");
+        require(o.block_split >= 0, "block_split < 0");
         for (int64_t i = 0; i < count; i++) {
             const elm_problem &p = probs[i];
             check_dims(p.N, p.n, p.ldx, p.L, p.ldw);
@@ -896,6 +1086,8 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             require(p.X && p.W && p.b && p.T && p.beta, "NULL problem pointer");
             require(p.x_dtype == ELM_F32 || p.x_dtype == ELM_F64, "x_dtype");
             require(p.act == ELM_ACT_SIGMOID || p.act == ELM_ACT_TANH, "act");
+            require(o.block_split == 0 || (o.block_split < p.L && p.N >= p.L),
+                    "block_split needs 0 < block_split < L <= N");
         }
         ELM_CUDA(cudaSetDevice(ctx->device));
         ctx->timing = (o.flags & ELM_FLAG_PHASE_TIMING) != 0;
@@ -922,6 +1114,12 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             // fewer samples than neurons: the wide branch, FP64 rules on the
             // N x N Gram
             P.wide = probs[i].N < probs[i].L;
+            P.block = o.block_split;
+            if (P.block > 0) {                 // the paper's block route: FP64 rules
+                P.tau = P.tau64 = o.tol_rank > 0.0 ? o.tol_rank : tau64;
+                if (o.max_refine < 0) P.max_refine = 2;
+                if (!(o.refine_tol > 0.0)) P.refine_tol = 1e-12;
+            }
             if (P.wide) {
                 P.tau = o.tol_rank > 0.0 ? o.tol_rank : (double)probs[i].N * ldexp(1.0, -52);
                 P.tau64 = P.tau;
