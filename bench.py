@@ -363,7 +363,7 @@ def run_native(args):
     check = dict(rank=[r["rank"] for r in res] if count > 1 else res[0]["rank"],
                  refine_iters=max(r["refine_iters"] for r in res),
                  statuses=sorted(set(r["status"] for r in res)),
-                 forms={str(f): sum(r["form"] == f for r in res) for f in (0, 1, 2)})
+                 forms={str(f): sum(r["form"] == f for r in res) for f in (0, 1, 2, 3, 4)})
     t_oracle, refs = None, None
     if rank == 0 and full_rows and not args.no_oracle_check:
         refs, t_oracle = reference_results(args.workload, hosts)
@@ -523,6 +523,117 @@ def run_native(args):
     return 1 if invalid else 0
 
 
+def run_sharded(args):
+    """--shard rows: one training of the workload with its rows split over
+    the ranks (paper_2011_02436_gb300.sharded): every rank forms its block's
+    Gram blocks, one exchange sums them in rank order, every rank factorises
+    the same sum, refinement residuals are summed the same way.  Strong
+    scaling: the work per step is one whole training however many ranks."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2011_02436_gb300 as elm
+    from paper_2011_02436_gb300.sharded import LibraryOps, train_row_blocks
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = elm.PREC_MIXED if args.precision == "mixed" else elm.PREC_FP64
+    gen, desc = WORKLOADS[args.workload]
+    plist = gen(args.rows)
+    if len(plist) != 1:
+        raise SystemExit("--shard rows takes a single-problem workload")
+    p = plist[0]
+    rows = shard(p["X"].shape[0], rank, ws)
+    r0, r1 = rows[0], rows[-1] + 1
+
+    def dev_block(src):
+        return (torch.from_numpy(src["X"][r0:r1]).to(dev), torch.from_numpy(src["W"]).to(dev),
+                torch.from_numpy(src["b"]).to(dev),
+                None if src.get("a") is None else torch.from_numpy(src["a"]).to(dev),
+                int(src.get("act", 0)), torch.from_numpy(src["T"][r0:r1]).to(dev))
+
+    blk = dev_block(p)
+    ctx = elm.elm_create(local, torch.cuda.current_stream(dev))
+    ops = LibraryOps(ctx, prec)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    invalid = []
+    beta, r, info = train_row_blocks(ops, [blk], precision=prec)
+    check = dict(rank=r, refine_iters=info["refine_iters"], converged=info["converged"])
+    if r != p["rank"]:
+        invalid.append("rank %d, planted %d" % (r, p["rank"]))
+    if rank == 0 and not args.no_oracle_check and args.workload in ("sparse_pixels", "small",
+                                                                    "gina_shaped"):
+        refs, _ = reference_results(args.workload, [p])
+        bref, rref = refs[0]
+        err = float(np.linalg.norm(beta.cpu().numpy() - bref) / np.linalg.norm(bref))
+        check["rel_err_vs_oracle"] = err
+        if rref != r or not err <= (1e-6 if prec == elm.PREC_MIXED else 1e-9):
+            invalid.append("beta error %.3g or rank %d against the oracle's %d" % (err, r, rref))
+    for _ in range(args.warmup):
+        train_row_blocks(ops, [blk], precision=prec)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, rr, inf = train_row_blocks(ops, [blk], precision=prec)
+            if rr != p["rank"] or not inf["converged"]:
+                invalid.append("timed step: rank %d converged %s" % (rr, inf["converged"]))
+        e1.record(stream)
+        barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    # e2e: this rank's rows from pinned host memory each step, beta to the host
+    hp = {k: (None if p.get(k) is None else torch.from_numpy(
+        np.ascontiguousarray(p[k][r0:r1] if k in ("X", "T") else p[k])).pin_memory())
+        for k in ("X", "W", "b", "a", "T")}
+    h2d = sum(v.numel() * v.element_size() for v in hp.values() if v is not None)
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        hb = tuple(None if hp[k] is None else hp[k].to(dev, non_blocking=True)
+                   for k in ("X", "W", "b", "a"))
+        b2 = (hb[0], hb[1], hb[2], hb[3], int(p.get("act", 0)), hp["T"].to(dev, non_blocking=True))
+        bh, _, _ = train_row_blocks(ops, [b2], precision=prec)
+        bh = bh.cpu()
+    f1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, dev)
+    if rank == 0:
+        cfg = dict(workload=desc.replace("{L}", str(args.hidden)), precision=args.precision,
+                   parallelism="rows sharded over %d rank(s), one exchange per sum" % ws,
+                   l2="inputs larger than L2: no flush", N=p["X"].shape[0], L=p["W"].shape[1],
+                   m=p["T"].shape[1], rows_per_rank=r1 - r0)
+        line = dict(metric=METRIC, value=1000.0 / ms, unit="trainings/s", n_gpus=ws,
+                    steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+                    higher_is_better=True, scaling="strong", vs_baseline=None,
+                    dtype="f64" if prec == elm.PREC_FP64 else "bf16-slices+f64",
+                    data="synthetic", config=cfg,
+                    e2e=dict(value=1000.0 / e2e_ms, unit="trainings/s", h2d_bytes_per_step=h2d,
+                             d2h_bytes_per_step=int(beta.numel() * 8)),
+                    clocks=clk.summary(), check=check, valid=not invalid)
+        if invalid:
+            line["invalid_reasons"] = invalid[:16]
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 1 if invalid else 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,6 +654,8 @@ def main():
                     help="rows of the sparse-pixel workload (smaller only for profiling captures)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sparse_pixels",
                     help="the timed workload (the default is the headline configuration)")
+    ap.add_argument("--shard", choices=["none", "rows"], default="none",
+                    help="rows: one training with the rows of H split over the ranks")
     ap.add_argument("--block-split", type=int, default=0,
                     help="> 0: train by the paper's block formulae (Eqs. 19-23) with H1 the "
                          "first BLOCK_SPLIT columns instead of the rank-based route")
@@ -553,6 +666,8 @@ def main():
     ARGS_HIDDEN[0] = args.hidden
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard == "rows":
+        return run_sharded(args)
     return run_native(args)
 
 

@@ -204,6 +204,54 @@ int elm_predict(elm_ctx *ctx, const void *X, int x_dtype, int64_t N,
                 int64_t ldy);
 
 /*
+ * Row-sharded training: the rows of H split into blocks (one per process or
+ * GPU), each block contributing H_p^T H_p and H_p^T T_p, which a caller sums
+ * over the blocks (one all-reduce) before a single factorisation; the
+ * refinement residual H^T (T - H beta) is summed the same way.  This is the
+ * distributed setting the paper names as future work (Section 5); the
+ * arithmetic is that of elm_train (Eqs. 5-13, Algorithm 1) with the sums
+ * over samples split.  The caller owns the exchange (for example
+ * torch.distributed); the library never communicates.
+ *
+ * elm_rows_create: hidden layer of one row block (X: N x n, T: N x m) in the
+ * given precision, kept on the device by the handle (FP64 H^T, or the
+ * double-float H of the mixed form), and the block's Gram blocks.  Inputs
+ * are staged as for elm_train; nothing is retained from them afterwards.
+ * elm_rows_gram: S (L x L, lds >= L) = H_p^T H_p and Z (L x m, ldz >= m) =
+ * H_p^T T_p of the block (host or device outputs; the call synchronises).
+ * elm_rows_residual: Gres (L x m, ldr >= m) = H_p^T (T_p - H_p beta) for
+ * beta (L x m, ldb >= m).  elm_rows_destroy frees the handle (NULL is
+ * accepted).  A handle uses its context's stream and workspace: use it from
+ * the context's thread, and destroy it before the context.
+ *
+ * elm_factor_gram: the pivoted rank decision and factorisation of a summed
+ * Gram matrix S (L x L, lds) (Eq. 6; Algorithm 1 steps 3-4) with the rules
+ * of elm_train for `precision` (tol_rank <= 0: the default threshold), kept
+ * by the handle with everything the solves need for up to m right-hand
+ * sides; *rank_out (host) receives r.  A mixed-precision decision that the
+ * mixed Gram cannot settle (a rejected pivot above L 2^-52) returns
+ * ELM_ERR_NUMERIC; factor the FP64 Gram instead.
+ * elm_factor_solve: out (L x mc, ldo) = P [I; K^T] (I + K K^T)^{-1}
+ * R11^{-1} R11^{-T} Z[perm[0..r-1]] for Z (L x mc, ldz), mc <= m: beta for
+ * Z = H^T T, the correction for Z = Gres (Eq. 5, Eq. 7).
+ */
+typedef struct elm_rows elm_rows;
+typedef struct elm_factor elm_factor;
+int elm_rows_create(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n,
+                    int64_t ldx, const double *W, int64_t ldw, const double *b,
+                    const double *a, int64_t L, int act, const double *T, int64_t m,
+                    int64_t ldt, int precision, elm_rows **out);
+int elm_rows_gram(elm_rows *rows, double *S, int64_t lds, double *Z, int64_t ldz);
+int elm_rows_residual(elm_rows *rows, const double *beta, int64_t ldb, double *Gres,
+                      int64_t ldr);
+int elm_rows_destroy(elm_rows *rows);
+int elm_factor_gram(elm_ctx *ctx, const double *S, int64_t lds, int64_t L, int64_t m,
+                    int precision, double tol_rank, elm_factor **out, int64_t *rank_out);
+int elm_factor_solve(elm_factor *f, const double *Z, int64_t ldz, int64_t mc, double *out,
+                     int64_t ldo);
+int elm_factor_destroy(elm_factor *f);
+
+/*
  * Instrumentation (the paper has no counterpart; it reports wall-clock
  * training time only, Section 4).
  *

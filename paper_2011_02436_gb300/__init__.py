@@ -269,3 +269,75 @@ def elm_predict(ctx, X, W, b, a, act, beta, Y=None):
                                  _ld(Y))
     _check(ctx, st)
     return Y
+
+
+class RowBlock:
+    """One row block of a problem (elm_rows_*): its hidden layer stays on the
+    device; gram() gives the block's H^T H and H^T T, residual(beta) its
+    H^T (T - H beta)."""
+
+    def __init__(self, ctx, X, W, b, a, act, T, precision=PREC_MIXED):
+        N, n = X.shape
+        L = W.shape[1]
+        m = T.shape[1]
+        self.ctx, self.L, self.m, self.ref = ctx, L, m, X
+        self.handle = C.c_void_p()
+        st = _lib.load().elm_rows_create(ctx.handle, _ptr(X), _xdtype(X), N, n, _ld(X), _ptr(W),
+                                         _ld(W), _ptr(b), _ptr(a), L, act, _ptr(T), m, _ld(T),
+                                         precision, C.byref(self.handle))
+        _check(ctx, st)
+
+    def gram(self):
+        S = _empty_like_device(self.ref, (self.L, self.L))
+        Z = _empty_like_device(self.ref, (self.L, self.m))
+        _check(self.ctx, _lib.load().elm_rows_gram(self.handle, _ptr(S), _ld(S), _ptr(Z), _ld(Z)))
+        return S, Z
+
+    def residual(self, beta):
+        G = _empty_like_device(self.ref, (self.L, self.m))
+        _check(self.ctx, _lib.load().elm_rows_residual(self.handle, _ptr(beta), _ld(beta),
+                                                       _ptr(G), _ld(G)))
+        return G
+
+    def close(self):
+        if self.handle:
+            _lib.load().elm_rows_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GramFactor:
+    """The pivoted factorisation of a (summed) Gram matrix (elm_factor_*);
+    solve(Z) applies the full-rank route to Z (L x mc)."""
+
+    def __init__(self, ctx, S, m, precision=PREC_MIXED, tol_rank=0.0):
+        L = S.shape[0]
+        self.ctx, self.L, self.ref = ctx, L, S
+        self.handle = C.c_void_p()
+        r = C.c_int64(0)
+        st = _lib.load().elm_factor_gram(ctx.handle, _ptr(S), _ld(S), L, m, precision, tol_rank,
+                                         C.byref(self.handle), C.byref(r))
+        _check(ctx, st)
+        self.rank = int(r.value)
+
+    def solve(self, Z):
+        out = _empty_like_device(self.ref, (self.L, Z.shape[1]))
+        _check(self.ctx, _lib.load().elm_factor_solve(self.handle, _ptr(Z), _ld(Z), Z.shape[1],
+                                                      _ptr(out), _ld(out)))
+        return out
+
+    def close(self):
+        if self.handle:
+            _lib.load().elm_factor_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

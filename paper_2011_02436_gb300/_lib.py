@@ -48,6 +48,15 @@ SIGNATURES = [
     ("elm_hidden_noalloc", C.c_int, [vp, C.c_int, i64, i64, i64, vp, i64, vp, vp, i64, C.c_int,
                                      vp, i64, vp]),
     ("elm_hidden_noalloc_bytes", C.c_int, [i64, i64, i64, C.POINTER(i64)]),
+    ("elm_rows_create", C.c_int, [vp, vp, C.c_int, i64, i64, i64, vp, i64, vp, vp, i64, C.c_int,
+                                  vp, i64, i64, C.c_int, C.POINTER(vp)]),
+    ("elm_rows_gram", C.c_int, [vp, vp, i64, vp, i64]),
+    ("elm_rows_residual", C.c_int, [vp, vp, i64, vp, i64]),
+    ("elm_rows_destroy", C.c_int, [vp]),
+    ("elm_factor_gram", C.c_int, [vp, vp, i64, i64, i64, C.c_int, dbl, C.POINTER(vp),
+                                  C.POINTER(i64)]),
+    ("elm_factor_solve", C.c_int, [vp, vp, i64, i64, vp, i64]),
+    ("elm_factor_destroy", C.c_int, [vp]),
 ]
 
 _lib = None

@@ -172,7 +172,8 @@ struct Solver {
 };
 
 Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const double *Rt,
-                      int64_t ld, const int32_t *perm, int64_t r, int64_t L, int64_t m) {
+                      int64_t ld, const int32_t *perm, int64_t r, int64_t L, int64_t m,
+                      char **buf = nullptr, size_t *bufsize = nullptr) {
     Solver sv;
     sv.R = R;
     sv.Rt = Rt;
@@ -186,7 +187,7 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
     const int syrk_split = syrk_f64_splits(r, q, ctx->sm_count);
     const int atv_split = atv_splits(r, q, ctx->sm_count);
     sv.atv_split = atv_split;
-    with_arena(&ctx->aux, &ctx->aux_size, s, [&](Arena &a) {
+    with_arena(buf ? buf : &ctx->aux, buf ? bufsize : &ctx->aux_size, s, [&](Arena &a) {
         sv.yb = a.take<double>(L * m);
         sv.DinvF = a.take<double>(trsm_dinv_doubles(r));
         sv.DinvB = a.take<double>(trsm_dinv_doubles(r));
@@ -220,8 +221,8 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
 }
 
 void solver_apply(cudaStream_t s, const Solver &sv, const double *Z, int64_t ldz, double *out,
-                  int64_t ldo) {
-    const int64_t r = sv.r, L = sv.L, m = sv.m, q = L - r;
+                  int64_t ldo, int64_t mcols = -1) {
+    const int64_t r = sv.r, L = sv.L, m = mcols > 0 ? mcols : sv.m, q = L - r;
     double *yb = sv.yb;
     gather_rows(s, Z, ldz, sv.perm, nullptr, r, m, yb, m);
     trsm_fwd(s, sv.R, sv.ld, sv.DinvF, r, yb, m, m, sv.tflag);
@@ -673,6 +674,7 @@ void train_block(elm_ctx *ctx, const Problem &P, elm_result *res) {
         return;
     }
     res->rank = L;
+    mark(ctx, 3);
     br.D = SpdFactor{RD, RtD, tri_ld(r1), r1, fD.perm, br.D.DinvF, br.D.DinvB, tflag};
     trsm_prepare(s, RD, tri_ld(r1), r1, br.D.DinvF, br.D.DinvB);
     br.S = S;
@@ -891,6 +893,129 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
            kind, s);
     ELM_CUDA(cudaStreamSynchronize(s));
     collect_phases(ctx);
+}
+
+// ------------------------------------------------------ row-sharded route
+// Owned device memory of a handle (freed with it).
+struct OwnedMem {
+    char *p = nullptr;
+    size_t size = 0;
+    ~OwnedMem() {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+// One row block of a problem: its hidden layer kept on the device.
+struct elm_rows {
+    elm_ctx *ctx = nullptr;
+    int precision = ELM_PREC_FP64;
+    int64_t N = 0, L = 0, m = 0;
+    OwnedMem mem;                 // H, T, S, Z and the residual scratch
+    double *Ht = nullptr;         // FP64 form: L x N
+    void *Hdf = nullptr;          // mixed form: N x L double-float pairs
+    double *T = nullptr, *S = nullptr, *Z = nullptr, *Rres = nullptr, *part = nullptr,
+           *betaT = nullptr, *beta = nullptr;
+    int nsplit = 1;
+};
+
+// A factorised Gram matrix and everything its solves need.
+struct elm_factor {
+    elm_ctx *ctx = nullptr;
+    int64_t L = 0, m = 0, r = 0;
+    OwnedMem mem;                 // R, R^T, permutation
+    OwnedMem aux;                 // the solver's buffers
+    Solver sv;
+    double *stage = nullptr, *out = nullptr;   // staging of host right-hand sides
+};
+
+namespace {
+
+void rows_build(elm_rows *h, const void *X, int xdt, int64_t n, int64_t ldx, const double *Wp,
+                int64_t ldw, const double *bp, const double *ap, int act, const double *Tp,
+                int64_t ldt) {
+    elm_ctx *ctx = h->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = h->N, L = h->L, m = h->m;
+    const bool mixed = h->precision == ELM_PREC_MIXED;
+    const size_t xsz = xdt == ELM_F64 ? 8 : 4;
+    h->nsplit = mixed ? htr_df_nsplit(L, N, ctx->sm_count) : htr_f64_nsplit(L, N, ctx->sm_count);
+    // owned: H, T, S, Z, residual scratch
+    Arena plan;
+    auto carve = [&](Arena &ar) {
+        if (mixed) h->Hdf = ar.take<double>(N * L);
+        else h->Ht = ar.take<double>(L * N);
+        h->T = ar.take<double>(N * m);
+        h->S = ar.take<double>(L * L);
+        h->Z = ar.take<double>(L * m);
+        h->Rres = ar.take<double>(N * m);
+        h->part = ar.take<double>((size_t)h->nsplit * L * m);
+        h->betaT = ar.take<double>(L * (m < 32 ? m : 32));
+        h->beta = ar.take<double>(L * m);
+    };
+    carve(plan);
+    if (cudaMalloc(&h->mem.p, plan.used) != cudaSuccess) {
+        cudaGetLastError();
+        h->mem.p = nullptr;
+        throw ElmError(ELM_ERR_NOMEM, "cudaMalloc of the row block failed");
+    }
+    h->mem.size = plan.used;
+    Arena own;
+    own.base = h->mem.p;
+    own.cap = h->mem.size;
+    carve(own);
+    // transient scratch in the context's workspace
+    In Xs, Ws, bs, as, Ts;
+    double *G = nullptr, *hs = nullptr, *gpart = nullptr;
+    __nv_bfloat16 *planes = nullptr;
+    long long *ipart = nullptr;
+    int *err = nullptr;
+    int32_t *flag = nullptr;
+    OzHidWs hw{};
+    const int64_t Lt = L + m, Lp = oz_pad(Lt, 128);
+    const int ns = gram_f64_nsplit(L, m, N, ctx->sm_count);
+    with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+        Xs = stage(ar, s, X, N, n, ldx, xsz);
+        Ws = stage(ar, s, Wp, n, L, ldw, 8);
+        bs = stage(ar, s, bp, 1, L, L, 8);
+        as = stage(ar, s, ap, 1, L, L, 8);
+        Ts = stage(ar, s, Tp, N, m, ldt, 8);
+        flag = ar.take<int32_t>(1);
+        err = ar.take<int>(1);
+        if (mixed) {
+            planes = (__nv_bfloat16 *)ar.take<char>(oz_gram_planes_bytes(N, L, m));
+            hs = ar.take<double>(Lp);
+            G = ar.take<double>(Lt * Lt);
+            hw = oz_hid_carve(ar, N, n, L, m);
+            ipart = (long long *)ar.take<char>(oz_gram_part_bytes());
+        } else {
+            gpart = ar.take<double>(gram_f64_ws(L, m, ns));
+        }
+    });
+    copy2d(h->T, m * 8, Ts.p, Ts.ld * 8, m * 8, N, cudaMemcpyDeviceToDevice, s);
+    ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    const double *Wd = (const double *)Ws.p, *bd = (const double *)bs.p, *ad = (const double *)as.p;
+    if (mixed) {
+        oz_hidden(s, hw, Xs.p, xdt, N, n, Xs.ld, Wd, Ws.ld, bd, ad, act, L, m, planes, hs, nullptr,
+                  0, err, h->Hdf, flag);
+        oz_t_digits(s, h->T, m, N, L, m, planes, hs);
+        oz_gram(s, planes, hs, N, L, m, G, Lt, err, ipart);
+        copy2d(h->S, L * 8, G, Lt * 8, L * 8, L, cudaMemcpyDeviceToDevice, s);
+        copy2d(h->Z, m * 8, G + L, Lt * 8, m * 8, L, cudaMemcpyDeviceToDevice, s);
+    } else {
+        check_finite(s, Xs.p, xdt, N, n, Xs.ld, flag);
+        hidden_f64(s, Xs.p, xdt, N, n, Xs.ld, Wd, Ws.ld, bd, ad, L, act, h->Ht, N);
+        gram_f64(s, h->Ht, N, L, N, h->T, m, m, h->S, L, h->Z, m, gpart, ns);
+    }
+    int32_t xfl = 0;
+    int terr = 0;
+    ELM_CUDA(cudaMemcpyAsync(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost, s));
+    ELM_CUDA(cudaMemcpyAsync(&terr, err, sizeof terr, cudaMemcpyDeviceToHost, s));
+    ELM_CUDA(cudaStreamSynchronize(s));
+    if (terr) throw ElmError(ELM_ERR_TIMEOUT, "tensor-core kernel wait expired");
+    if (xfl) throw ElmError(ELM_ERR_NUMERIC, "non-finite input");
 }
 
 }  // namespace
@@ -1127,7 +1252,14 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
                 if (!(o.refine_tol > 0.0)) P.refine_tol = 1e-12;
             }
             elm_result r{};
-            train_one(ctx, P, &r);
+            try {
+                train_one(ctx, P, &r);
+            } catch (const ElmError &e) {
+                // the problem's own entry reports the failure too
+                r.status = e.status;
+                if (results) results[i] = r;
+                throw;
+            }
             if (results) results[i] = r;
             if (first == ELM_OK && r.status != ELM_OK) first = r.status;
         }
@@ -1186,6 +1318,187 @@ int elm_predict(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, 
             ELM_CUDA(cudaStreamSynchronize(s));
         }
     });
+}
+
+int elm_rows_create(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n,
+                    int64_t ldx, const double *W, int64_t ldw, const double *b,
+                    const double *a, int64_t L, int act, const double *T, int64_t m,
+                    int64_t ldt, int precision, elm_rows **out) {
+    if (!ctx || !out) return ELM_ERR_ARG;
+    *out = nullptr;
+    elm_rows *h = nullptr;
+    int st = guarded(ctx, [&] {
+        check_dims(N, n, ldx, L, ldw);
+        require(X && W && b && T, "X, W, b and T must be non-NULL");
+        require(m >= 1 && ldt >= m, "m or ldt");
+        require(x_dtype == ELM_F32 || x_dtype == ELM_F64, "x_dtype");
+        require(act == ELM_ACT_SIGMOID || act == ELM_ACT_TANH, "act");
+        require(precision == ELM_PREC_FP64 || precision == ELM_PREC_MIXED, "precision");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        h = new elm_rows;
+        h->ctx = ctx;
+        h->precision = precision;
+        h->N = N;
+        h->L = L;
+        h->m = m;
+        rows_build(h, X, x_dtype, n, ldx, W, ldw, b, a, act, T, ldt);
+    });
+    if (st != ELM_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return ELM_OK;
+}
+
+int elm_rows_gram(elm_rows *h, double *S, int64_t lds, double *Z, int64_t ldz) {
+    if (!h) return ELM_ERR_ARG;
+    elm_ctx *ctx = h->ctx;
+    return guarded(ctx, [&] {
+        require(S && Z && lds >= h->L && ldz >= h->m, "S, Z, lds or ldz");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const int64_t L = h->L, m = h->m;
+        copy2d(S, lds * 8, h->S, L * 8, L * 8, L,
+               on_device(S) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        copy2d(Z, ldz * 8, h->Z, m * 8, m * 8, L,
+               on_device(Z) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        ELM_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int elm_rows_residual(elm_rows *h, const double *beta, int64_t ldb, double *Gres, int64_t ldr) {
+    if (!h) return ELM_ERR_ARG;
+    elm_ctx *ctx = h->ctx;
+    return guarded(ctx, [&] {
+        require(beta && Gres && ldb >= h->m && ldr >= h->m, "beta, Gres, ldb or ldr");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const int64_t N = h->N, L = h->L, m = h->m;
+        copy2d(h->beta, m * 8, beta, ldb * 8, m * 8, L,
+               on_device(beta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        double *G = nullptr;
+        const bool dev_out = on_device(Gres) && ldr == m;
+        with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+            G = dev_out ? Gres : ar.take<double>(L * m);
+        });
+        if (h->precision == ELM_PREC_MIXED) {
+            resid_df(s, h->Hdf, L, N, h->beta, m, h->T, m, h->Rres, h->betaT);
+            htr_df(s, h->Hdf, L, N, h->Rres, m, G, h->part, h->nsplit);
+        } else {
+            resid_f64(s, h->Ht, N, L, N, h->beta, m, h->T, m, h->Rres);
+            htr_f64(s, h->Ht, N, L, N, h->Rres, m, G, h->part, h->nsplit);
+        }
+        if (!dev_out)
+            copy2d(Gres, ldr * 8, G, m * 8, m * 8, L,
+                   on_device(Gres) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        ELM_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int elm_rows_destroy(elm_rows *h) {
+    if (!h) return ELM_OK;
+    cudaSetDevice(h->ctx->device);
+    if (h->ctx->stream) cudaStreamSynchronize(h->ctx->stream);
+    delete h;
+    return ELM_OK;
+}
+
+int elm_factor_gram(elm_ctx *ctx, const double *S, int64_t lds, int64_t L, int64_t m,
+                    int precision, double tol_rank, elm_factor **out, int64_t *rank_out) {
+    if (!ctx || !out) return ELM_ERR_ARG;
+    *out = nullptr;
+    elm_factor *f = nullptr;
+    int st = guarded(ctx, [&] {
+        require(S && rank_out, "S and rank_out must be non-NULL");
+        require(L >= 1 && L <= ELM_MAX_L && lds >= L && m >= 1, "L, lds or m");
+        require(precision == ELM_PREC_FP64 || precision == ELM_PREC_MIXED, "precision");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const bool mixed = precision == ELM_PREC_MIXED;
+        const double tau64 = (double)L * ldexp(1.0, -52);
+        const double tau = tol_rank > 0.0 ? tol_rank : (mixed ? fmax(tau64, ldexp(1.0, -32)) : tau64);
+        f = new elm_factor;
+        f->ctx = ctx;
+        f->L = L;
+        f->m = m;
+        double *R = nullptr, *Rt = nullptr;
+        int32_t *perm = nullptr;
+        auto carve = [&](Arena &ar) {
+            R = ar.take<double>(L * tri_ld(L));
+            Rt = ar.take<double>(L * tri_ld(L));
+            perm = ar.take<int32_t>(L);
+            f->stage = ar.take<double>(L * m);
+            f->out = ar.take<double>(L * m);
+        };
+        Arena plan;
+        carve(plan);
+        if (cudaMalloc(&f->mem.p, plan.used) != cudaSuccess) {
+            cudaGetLastError();
+            f->mem.p = nullptr;
+            throw ElmError(ELM_ERR_NOMEM, "cudaMalloc of the factor failed");
+        }
+        f->mem.size = plan.used;
+        Arena own;
+        own.base = f->mem.p;
+        own.cap = f->mem.size;
+        carve(own);
+        In Sd;
+        FactorWs fw;
+        with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+            Sd = stage(ar, s, S, L, L, lds, 8);
+            fw = factor_ws_carve(ar, L);
+        });
+        factor_pivoted(s, (const double *)Sd.p, Sd.ld, L, tau, fw, R, Rt, tri_ld(L),
+                       ctx->sm_count, mixed);
+        int32_t fl = 0;
+        double stop_val = 0.0;
+        const int64_t r = read_rank(s, fw, &fl, &stop_val);
+        if (fl & 2) throw ElmError(ELM_ERR_TIMEOUT, "factorisation wait expired");
+        if (fl & 1) throw ElmError(ELM_ERR_NUMERIC, "non-finite Gram matrix");
+        if (mixed && tol_rank <= 0.0 && r < L && stop_val > tau64)
+            throw ElmError(ELM_ERR_NUMERIC,
+                           "mixed rank decision unsettled: a rejected pivot lies above L 2^-52; "
+                           "factor the FP64 Gram");
+        ELM_CUDA(cudaMemcpyAsync(perm, fw.perm, sizeof(int32_t) * L, cudaMemcpyDeviceToDevice, s));
+        f->r = r;
+        f->sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), perm, r, L, m, &f->aux.p, &f->aux.size);
+        ELM_CUDA(cudaStreamSynchronize(s));
+        *rank_out = r;
+    });
+    if (st != ELM_OK) {
+        delete f;
+        return st;
+    }
+    *out = f;
+    return ELM_OK;
+}
+
+int elm_factor_solve(elm_factor *f, const double *Z, int64_t ldz, int64_t mc, double *out,
+                     int64_t ldo) {
+    if (!f) return ELM_ERR_ARG;
+    elm_ctx *ctx = f->ctx;
+    return guarded(ctx, [&] {
+        require(Z && out && mc >= 1 && mc <= f->m && ldz >= mc && ldo >= mc, "Z, out or mc");
+        ELM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const int64_t L = f->L;
+        copy2d(f->stage, mc * 8, Z, ldz * 8, mc * 8, L,
+               on_device(Z) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        solver_apply(s, f->sv, f->stage, mc, f->out, mc, mc);
+        if (solver_timed_out(s, f->sv)) throw ElmError(ELM_ERR_TIMEOUT, "solve wait expired");
+        copy2d(out, ldo * 8, f->out, mc * 8, mc * 8, L,
+               on_device(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        ELM_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int elm_factor_destroy(elm_factor *f) {
+    if (!f) return ELM_OK;
+    cudaSetDevice(f->ctx->device);
+    if (f->ctx->stream) cudaStreamSynchronize(f->ctx->stream);
+    delete f;
+    return ELM_OK;
 }
 
 }  // extern "C"
