@@ -50,7 +50,15 @@ typedef enum elm_status {
 
 enum { ELM_ACT_SIGMOID = 0, ELM_ACT_TANH = 1 };   /* g: logistic (Section 4) or tanh */
 enum { ELM_F32 = 0, ELM_F64 = 1 };               /* element type of X              */
-enum { ELM_PREC_FP64 = 0, ELM_PREC_MIXED = 1 };  /* arithmetic of the dense products */
+/* Arithmetic of the dense products.  ELM_PREC_FP64: FP64 FMAs throughout.
+ * ELM_PREC_MIXED: hidden layer and Gram from exact integer-digit slices on
+ * the tensor cores (H to about 2^-44, the Gram to about 2^-34), rank
+ * decision and factorisation in double-float, FP64 solves, refinement
+ * against the double-float H.  ELM_PREC_FP64_TC: the FP64 form with its
+ * Gram on the tensor cores, split into eight 7-bit digits per element and
+ * summed exactly (as accurate as the FP64 Gram); the mixed form hands the
+ * problems its Gram cannot settle to this form. */
+enum { ELM_PREC_FP64 = 0, ELM_PREC_MIXED = 1, ELM_PREC_FP64_TC = 2 };
 
 /* Largest hidden-layer width L the factorisation kernels accept. */
 #define ELM_MAX_L 16384
@@ -116,7 +124,7 @@ typedef struct elm_problem {
 } elm_problem;
 
 typedef struct elm_train_opts {
-    int32_t precision;  /* ELM_PREC_FP64 or ELM_PREC_MIXED                   */
+    int32_t precision;  /* ELM_PREC_FP64, ELM_PREC_MIXED or ELM_PREC_FP64_TC */
     int32_t max_refine; /* refinement steps (< 0: default 2 FP64, 12 mixed;
                            mixed steps stop early once they stop contracting) */
     double tol_rank;    /* rank threshold on the unit-diagonal scale (<=0: L*2^-52
@@ -157,6 +165,7 @@ typedef struct elm_train_opts {
                                     branch stated with Eq. 8), either precision */
 #define ELM_FORM_BLOCK 4         /* the paper's block formulae (Eqs. 19-23),
                                     elm_train_opts.block_split, FP64          */
+#define ELM_FORM_FP64_TC 5       /* FP64 form, Gram on the tensor cores       */
 
 typedef struct elm_result {
     int64_t rank;         /* r                                              */
@@ -174,10 +183,12 @@ typedef struct elm_result {
  * (H1^T H1)^{-1} H1^T T), then refinement steps with the residual
  * H^T (T - H beta).  opts may be NULL (FP64 defaults).  results: host array
  * of `count` entries, or NULL.  Returns ELM_OK or the first failing status.
- * ELM_PREC_MIXED trains a problem in the FP64 form instead when its
- * tensor-core Gram cannot settle it: a rejected pivot above the FP64 rank
- * threshold, or refinement that does not reach refine_tol (results[i].form
- * tells which route produced beta).
+ * ELM_PREC_MIXED trains a problem in the FP64 form (ELM_PREC_FP64_TC)
+ * instead when its tensor-core Gram cannot settle it: a rejected pivot above
+ * the FP64 rank threshold, or refinement that does not reach refine_tol
+ * (results[i].form tells which route produced beta).  With more than one
+ * problem, the mixed form runs the hidden layers and Grams of the whole
+ * call as one tensor-core launch each before the problems' solves.
  * A problem with fewer samples than hidden neurons (N < L) takes the wide
  * branch in either precision: the N x N Gram H H^T of the rows of H is
  * factorised by the same pivoted Cholesky (rank r over the rows, tol_rank

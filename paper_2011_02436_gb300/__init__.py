@@ -17,7 +17,7 @@ from . import _lib
 
 ACT_SIGMOID, ACT_TANH = 0, 1
 F32, F64 = 0, 1
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 OK = 0
 
 
@@ -206,7 +206,7 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
                  rel_update=r.rel_update, form=r.form) for r in res]
 
 
-FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64, FORM_WIDE, FORM_BLOCK = 0, 1, 2, 3, 4
+FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64, FORM_WIDE, FORM_BLOCK, FORM_FP64_TC = 0, 1, 2, 3, 4, 5
 
 
 FLAG_PHASE_TIMING = 1

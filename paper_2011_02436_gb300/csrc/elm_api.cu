@@ -26,10 +26,11 @@ void mark(elm_ctx *ctx, int i) {
     if (ctx->timing) ELM_CUDA(cudaEventRecord(ctx->ev[i], ctx->stream));
 }
 
-void collect_phases(elm_ctx *ctx) {
+// Adds the phases first .. last-1 (events first .. last) to the sums.
+void collect_phases(elm_ctx *ctx, int first = 0, int last = ELM_NUM_PHASES) {
     if (!ctx->timing) return;
-    ELM_CUDA(cudaEventSynchronize(ctx->ev[ELM_NUM_PHASES]));
-    for (int i = 0; i < ELM_NUM_PHASES; i++) {
+    ELM_CUDA(cudaEventSynchronize(ctx->ev[last]));
+    for (int i = first; i < last; i++) {
         float ms = 0.f;
         ELM_CUDA(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
         ctx->phase_ms[i] += ms;
@@ -289,16 +290,23 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     if (P.block > 0) return train_block(ctx, P, res);
     if (P.wide) return train_wide(ctx, P, res);
     if (P.prec == ELM_PREC_MIXED) return train_mixed(ctx, P, res);
-    res->form = ELM_FORM_FP64;
+    // FP64 form; ELM_PREC_FP64_TC forms its Gram on the tensor cores
+    const bool tc = P.prec == ELM_PREC_FP64_TC;
+    res->form = tc ? ELM_FORM_FP64_TC : ELM_FORM_FP64;
     res->reserved = 0;
     const elm_problem &pb = *P.p;
     cudaStream_t s = ctx->stream;
-    const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
+    const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m, Lt = L + m;
     const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
     const int ns = gram_f64_nsplit(L, m, N, ctx->sm_count);
     const int hs = htr_f64_nsplit(L, N, ctx->sm_count);
     In X, W, b, a, T;
-    double *Ht, *S, *Z, *gpart, *R, *Rt, *beta, *dB, *Rres, *G, *hpart, *norms;
+    double *Ht, *S, *Z, *gpart = nullptr, *R, *Rt, *beta, *dB, *Rres, *G, *hpart, *norms;
+    double *rs = nullptr;
+    float *rsf = nullptr;
+    __nv_bfloat16 *planes = nullptr;
+    int *err = nullptr;
+    int64_t lds = L, ldz = m;
     int32_t *flag;
     FactorWs f;
     with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
@@ -307,10 +315,22 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
         b = stage(ar, s, pb.b, 1, L, L, 8);
         a = stage(ar, s, pb.a, 1, L, L, 8);
         T = stage(ar, s, pb.T, N, m, pb.ldt, 8);
-        Ht = ar.take<double>(L * N);
-        S = ar.take<double>(L * L);
-        Z = ar.take<double>(L * m);
-        gpart = ar.take<double>(gram_f64_ws(L, m, ns));
+        if (tc) {
+            // [H^T; T^T] in one buffer, the Gram [H^T H, H^T T] beside it
+            Ht = ar.take<double>(Lt * N);
+            S = ar.take<double>(Lt * Lt);
+            Z = S + L;
+            lds = ldz = Lt;
+            planes = (__nv_bfloat16 *)ar.take<char>(oz_exact_planes_bytes(N, L, m));
+            rs = ar.take<double>(oz_pad(Lt, 128));
+            rsf = ar.take<float>(oz_pad(Lt, 128));
+            err = ar.take<int>(1);
+        } else {
+            Ht = ar.take<double>(L * N);
+            S = ar.take<double>(L * L);
+            Z = ar.take<double>(L * m);
+            gpart = ar.take<double>(gram_f64_ws(L, m, ns));
+        }
         R = ar.take<double>(L * tri_ld(L));
         Rt = ar.take<double>(L * tri_ld(L));
         beta = ar.take<double>(L * m);
@@ -323,27 +343,32 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
         f = factor_ws_carve(ar, L);
     });
     ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    if (tc) ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     check_finite(s, X.p, pb.x_dtype, N, n, X.ld, flag);
     const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
                  *ad = (const double *)a.p, *Td = (const double *)T.p;
     mark(ctx, 0);
     // Algorithm 1 step 2: H (stored transposed)
     hidden_f64(s, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, L, pb.act, Ht, N);
+    if (tc) transpose_f64(s, Td, N, m, T.ld, Ht + L * N, N);      // T^T below H^T
     mark(ctx, 1);
     // Eqs. 9-13: Gram blocks H^T H and H^T T
-    gram_f64(s, Ht, N, L, N, Td, T.ld, m, S, L, Z, m, gpart, ns);
+    if (tc) oz_gram_exact(s, Ht, N, N, L, m, planes, rs, rsf, S, Lt, err, nullptr, P.wait_ns);
+    else gram_f64(s, Ht, N, L, N, Td, T.ld, m, S, L, Z, m, gpart, ns);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4: permutation, rank, split
-    factor_pivoted(s, S, L, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count);
+    factor_pivoted(s, S, lds, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
+    int terr = 0;
     const int64_t r = read_rank(s, f, &fl);
     ELM_CUDA(cudaMemcpy(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost));
+    if (tc) ELM_CUDA(cudaMemcpy(&terr, err, sizeof terr, cudaMemcpyDeviceToHost));
     res->rank = r;
     res->refine_iters = 0;
     res->rel_update = 0.0;
     res->status = ELM_OK;
-    if (fl & 2) {                       // a bounded wait in the factorisation expired
+    if ((fl & 2) || terr) {             // a bounded device-side wait expired
         res->status = ELM_ERR_TIMEOUT;
         return;
     }
@@ -353,7 +378,7 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     }
     // Eq. 5, Eq. 7: beta = H^+ T
     const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m);
-    solver_apply(s, sv, Z, m, beta, m);
+    solver_apply(s, sv, Z, ldz, beta, m);
     mark(ctx, 4);
     // refinement with the residual T - H beta
     double nrm[2] = {0.0, 0.0};
@@ -725,26 +750,134 @@ void train_block(elm_ctx *ctx, const Problem &P, elm_result *res) {
 // above the FP64 threshold L 2^-52 (the FP64 rank rule might keep it), and
 // refinement that does not reach refine_tol (H too ill-conditioned for a
 // Gram accurate to 2^-34 to precondition the steps).
+// The front half (hidden layer and Gram) keeps its results in the
+// context's batch buffer; the back half below takes its scratch from the main
+// workspace, which the FP64 hand-over reuses.
+struct MixedData {
+    const double *T;     // staged targets (N x m, ldt)
+    int64_t ldt;
+    double *G;           // [H^T H, H^T T] (Lt x Lt)
+    void *Hdf;           // H as double-float pairs, sample-major
+    int32_t *flag;       // non-finite X
+    int *err;            // a tensor-kernel wait expired
+};
+
+// Factorisation, solves, refinement and the FP64 hand-over of one mixed
+// training whose Gram is ready.
+void mixed_back(elm_ctx *ctx, const Problem &P, elm_result *res, const MixedData &D,
+                int first_phase) {
+    const elm_problem &pb = *P.p;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = pb.N, L = pb.L, m = pb.m;
+    const int64_t Lt = L + m;
+    const int hs_split = htr_df_nsplit(L, N, ctx->sm_count);
+    double *R, *Rt, *beta, *dB, *Rres, *Gres, *hpart, *norms, *betaT;
+    FactorWs f;
+    with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+        R = ar.take<double>(L * tri_ld(L));
+        Rt = ar.take<double>(L * tri_ld(L));
+        beta = ar.take<double>(L * m);
+        dB = ar.take<double>(L * m);
+        Rres = ar.take<double>(N * m);
+        Gres = ar.take<double>(L * m);
+        hpart = ar.take<double>((int64_t)hs_split * L * m);
+        betaT = ar.take<double>(L * (m < 32 ? m : 32));
+        norms = ar.take<double>(2);
+        f = factor_ws_carve(ar, L);
+    });
+    auto fallback = [&]() {
+        Problem P64 = P;
+        P64.prec = ELM_PREC_FP64_TC;
+        P64.max_refine = 2;
+        P64.tau = P.tau64;
+        P64.refine_tol = 1e-12;
+        train_one(ctx, P64, res);
+        res->form = ELM_FORM_MIXED_TO_FP64;
+    };
+    // Eq. 6, Algorithm 1 steps 3-4 (double-float)
+    factor_pivoted(s, D.G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true);
+    mark(ctx, 3);
+    int32_t fl = 0, xfl = 0;
+    int terr = 0;
+    double stop_val = 0.0;
+    const int64_t r = read_rank(s, f, &fl, &stop_val);
+    ELM_CUDA(cudaMemcpy(&xfl, D.flag, sizeof xfl, cudaMemcpyDeviceToHost));
+    ELM_CUDA(cudaMemcpy(&terr, D.err, sizeof terr, cudaMemcpyDeviceToHost));
+    res->rank = r;
+    res->refine_iters = 0;
+    res->rel_update = 0.0;
+    res->status = ELM_OK;
+    res->form = ELM_FORM_MIXED;
+    res->reserved = 0;
+    if (terr || (fl & 2)) {
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if ((fl & 1) || xfl) {
+        res->status = ELM_ERR_NUMERIC;
+        return;
+    }
+    // a rank decision the mixed Gram cannot settle goes to the FP64 form
+    if (r < L && stop_val > P.tau64) return fallback();
+    const double *Z = D.G + L;   // Z[l, c] = G[l, L + c]
+    // Eq. 5, Eq. 7 (FP64)
+    const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m);
+    solver_apply(s, sv, Z, Lt, beta, m);
+    mark(ctx, 4);
+    double nrm[2] = {0.0, 0.0};
+    bool converged = P.max_refine == 0;
+    double prev = INFINITY;
+    for (int it = 0; it < P.max_refine; it++) {
+        resid_df(s, D.Hdf, L, N, beta, m, D.T, D.ldt, Rres, betaT);     // T - H beta (pairs)
+        htr_df(s, D.Hdf, L, N, Rres, m, Gres, hpart, hs_split);        // H^T (T - H beta)
+        solver_apply(s, sv, Gres, m, dB, m);
+        axpy_norms(s, beta, dB, L * m, norms);
+        ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
+        ELM_CUDA(cudaStreamSynchronize(s));
+        res->refine_iters = it + 1;
+        res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
+        if (res->rel_update <= P.refine_tol) {
+            converged = true;
+            break;
+        }
+        // the steps must contract; once they stop doing so the grid Gram
+        // is too coarse a preconditioner for this H
+        if (it >= 1 && !(res->rel_update < 0.5 * prev)) break;
+        prev = res->rel_update;
+    }
+    mark(ctx, 5);
+    if (solver_timed_out(s, sv)) {
+        res->status = ELM_ERR_TIMEOUT;
+        return;
+    }
+    if (!converged) return fallback();
+    if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
+    const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyDeviceToHost;
+    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double), m * sizeof(double), L,
+           kind, s);
+    ELM_CUDA(cudaStreamSynchronize(s));
+    collect_phases(ctx, first_phase, ELM_NUM_PHASES);
+}
+
 void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     const elm_problem &pb = *P.p;
     cudaStream_t s = ctx->stream;
     const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m;
     const int64_t Lt = L + m, Lp = oz_pad(Lt, 128);
     const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
-    const int hs_split = htr_df_nsplit(L, N, ctx->sm_count);
     In X, W, b, a, T;
-    double *hs, *G, *R, *Rt, *beta, *dB, *Rres, *Gres, *hpart, *norms, *Hdf, *betaT;
+    double *hs, *G, *Hdf;
     long long *gpart;
     __nv_bfloat16 *planes;
     int32_t *flag;
     int *err;
     OzHidWs hw;
-    FactorWs f;
     // host X is uploaded in row chunks on a second stream; the hidden layer
     // takes each chunk as it lands (below)
     const bool x_host = !on_device(pb.X);
     char *xdev = nullptr;
-    with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
+    with_arena(&ctx->batch, &ctx->batch_size, s, [&](Arena &ar) {
         if (x_host) {
             xdev = ar.take<char>((size_t)(N * n) * xsz);
             X.p = xdev;
@@ -762,19 +895,9 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
         G = ar.take<double>(Lt * Lt);
         hw = oz_hid_carve(ar, N, n, L, m);
         Hdf = ar.take<double>(N * L);    // H as double-float pairs, eight bytes each
-        R = ar.take<double>(L * tri_ld(L));
-        Rt = ar.take<double>(L * tri_ld(L));
-        beta = ar.take<double>(L * m);
-        dB = ar.take<double>(L * m);
-        Rres = ar.take<double>(N * m);
-        Gres = ar.take<double>(L * m);
-        hpart = ar.take<double>((int64_t)hs_split * L * m);
         gpart = (long long *)ar.take<char>(oz_gram_part_bytes());
-        betaT = ar.take<double>(L * (m < 32 ? m : 32));
-        norms = ar.take<double>(2);
         flag = ar.take<int32_t>(1);
         err = ar.take<int>(1);
-        f = factor_ws_carve(ar, L);
     });
     ELM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
     ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
@@ -817,82 +940,114 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     // so the Gram phase times the Gram kernel alone)
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
     mark(ctx, 1);
-    auto fallback = [&]() {
-        Problem P64 = P;
-        P64.prec = ELM_PREC_FP64;
-        P64.max_refine = 2;
-        P64.tau = P.tau64;
-        P64.refine_tol = 1e-12;
-        train_one(ctx, P64, res);
-        res->form = ELM_FORM_MIXED_TO_FP64;
-    };
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
     oz_gram(s, planes, hs, N, L, m, G, Lt, err, gpart, P.wait_ns);
     mark(ctx, 2);
-    // Eq. 6, Algorithm 1 steps 3-4 (double-float)
-    factor_pivoted(s, G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true);
-    mark(ctx, 3);
-    int32_t fl = 0, xfl = 0;
-    int terr = 0;
-    double stop_val = 0.0;
-    const int64_t r = read_rank(s, f, &fl, &stop_val);
-    ELM_CUDA(cudaMemcpy(&xfl, flag, sizeof xfl, cudaMemcpyDeviceToHost));
-    ELM_CUDA(cudaMemcpy(&terr, err, sizeof terr, cudaMemcpyDeviceToHost));
-    res->rank = r;
-    res->refine_iters = 0;
-    res->rel_update = 0.0;
-    res->status = ELM_OK;
-    res->form = ELM_FORM_MIXED;
-    res->reserved = 0;
-    if (terr || (fl & 2)) {
-        res->status = ELM_ERR_TIMEOUT;
-        return;
-    }
-    if ((fl & 1) || xfl) {
-        res->status = ELM_ERR_NUMERIC;
-        return;
-    }
-    // a rank decision the mixed Gram cannot settle goes to the FP64 form
-    if (r < L && stop_val > P.tau64) return fallback();
-    const double *Z = G + L;   // Z[l, c] = G[l, L + c]
-    // Eq. 5, Eq. 7 (FP64)
-    const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m);
-    solver_apply(s, sv, Z, Lt, beta, m);
-    mark(ctx, 4);
-    double nrm[2] = {0.0, 0.0};
-    bool converged = P.max_refine == 0;
-    double prev = INFINITY;
-    for (int it = 0; it < P.max_refine; it++) {
-        resid_df(s, Hdf, L, N, beta, m, Td, T.ld, Rres, betaT);        // T - H beta (pairs)
-        htr_df(s, Hdf, L, N, Rres, m, Gres, hpart, hs_split);           // H^T (T - H beta)
-        solver_apply(s, sv, Gres, m, dB, m);
-        axpy_norms(s, beta, dB, L * m, norms);
-        ELM_CUDA(cudaMemcpyAsync(nrm, norms, sizeof nrm, cudaMemcpyDeviceToHost, s));
-        ELM_CUDA(cudaStreamSynchronize(s));
-        res->refine_iters = it + 1;
-        res->rel_update = nrm[1] > 0.0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
-        if (res->rel_update <= P.refine_tol) {
-            converged = true;
-            break;
+    mixed_back(ctx, P, res, MixedData{Td, T.ld, G, Hdf, flag, err}, 0);
+}
+
+// Several mixed-form problems: their hidden layers and Grams as one
+// tensor-core launch each (the problems' data side by side in the batch
+// buffer, in groups that fit half of the free device memory), then each
+// problem's factorisation, solves and refinement.
+void train_batch_mixed(elm_ctx *ctx, const std::vector<Problem> &Ps, elm_result *res) {
+    cudaStream_t s = ctx->stream;
+    const int64_t count = (int64_t)Ps.size();
+    auto need = [&](const elm_problem &pb) {
+        Arena m;
+        const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
+        const int64_t Lt = pb.L + pb.m;
+        if (!on_device(pb.X)) m.take<char>((size_t)(pb.N * pb.n) * xsz);
+        if (!on_device(pb.W)) m.take<double>(pb.n * pb.L);
+        if (!on_device(pb.b)) m.take<double>(pb.L);
+        if (pb.a && !on_device(pb.a)) m.take<double>(pb.L);
+        if (!on_device(pb.T)) m.take<double>(pb.N * pb.m);
+        m.take<char>(oz_gram_planes_bytes(pb.N, pb.L, pb.m));
+        m.take<double>(oz_pad(Lt, 128));
+        m.take<double>(Lt * Lt);
+        oz_hid_carve(m, pb.N, pb.n, pb.L, pb.m);
+        m.take<double>(pb.N * pb.L);
+        m.take<int32_t>(1);
+        return m.used + 256;
+    };
+    size_t free_b = 0, total_b = 0;
+    ELM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = (free_b + ctx->batch_size) / 2;
+    int64_t i0 = 0;
+    while (i0 < count) {
+        // the next group: as many problems as the budget holds (at least one)
+        size_t used = oz_batch_bytes(1);
+        int64_t i1 = i0;
+        while (i1 < count) {
+            const size_t add = need(*Ps[i1].p) + oz_batch_bytes(i1 - i0 + 1) - oz_batch_bytes(i1 - i0);
+            if (i1 > i0 && used + add > budget) break;
+            used += add;
+            i1++;
         }
-        // the steps must contract; once they stop doing so the grid Gram
-        // is too coarse a preconditioner for this H
-        if (it >= 1 && !(res->rel_update < 0.5 * prev)) break;
-        prev = res->rel_update;
+        const int64_t gn = i1 - i0;
+        std::vector<OzBatchItem> items(gn);
+        std::vector<MixedData> data(gn);
+        char *dev = nullptr;
+        int *err = nullptr;
+        with_arena(&ctx->batch, &ctx->batch_size, s, [&](Arena &ar) {
+            dev = ar.take<char>(oz_batch_bytes(gn));
+            err = ar.take<int>(1);
+            for (int64_t j = 0; j < gn; j++) {
+                const elm_problem &pb = *Ps[i0 + j].p;
+                const size_t xsz = pb.x_dtype == ELM_F64 ? 8 : 4;
+                const int64_t N = pb.N, n = pb.n, L = pb.L, m = pb.m, Lt = L + m;
+                const In X = stage(ar, s, pb.X, N, n, pb.ldx, xsz);
+                const In W = stage(ar, s, pb.W, n, L, pb.ldw, 8);
+                const In b = stage(ar, s, pb.b, 1, L, L, 8);
+                const In a = stage(ar, s, pb.a, 1, L, L, 8);
+                const In T = stage(ar, s, pb.T, N, m, pb.ldt, 8);
+                OzBatchItem &q = items[j];
+                q.X = X.p;
+                q.xdt = pb.x_dtype;
+                q.N = N;
+                q.n = n;
+                q.ldx = X.ld;
+                q.W = (const double *)W.p;
+                q.ldw = W.ld;
+                q.b = (const double *)b.p;
+                q.a = (const double *)a.p;
+                q.act = pb.act;
+                q.L = L;
+                q.m = m;
+                q.T = (const double *)T.p;
+                q.ldt = T.ld;
+                q.planes = (__nv_bfloat16 *)ar.take<char>(oz_gram_planes_bytes(N, L, m));
+                q.hs = ar.take<double>(oz_pad(Lt, 128));
+                q.G = ar.take<double>(Lt * Lt);
+                q.ldg = Lt;
+                q.hw = oz_hid_carve(ar, N, n, L, m);
+                q.Hdf = ar.take<double>(N * L);
+                q.nonfinite = ar.take<int32_t>(1);
+                data[j] = MixedData{q.T, q.ldt, q.G, q.Hdf, q.nonfinite, err};
+            }
+        });
+        ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        for (int64_t j = 0; j < gn; j++)
+            ELM_CUDA(cudaMemsetAsync(items[j].nonfinite, 0, sizeof(int32_t), s));
+        mark(ctx, 0);
+        oz_hidden_gram_batch(s, items.data(), gn, dev, err, Ps[i0].wait_ns,
+                             ctx->timing ? ctx->ev[1] : nullptr);
+        mark(ctx, 2);
+        collect_phases(ctx, 0, 2);
+        for (int64_t j = 0; j < gn; j++) {
+            elm_result r{};
+            mark(ctx, 2);
+            try {
+                mixed_back(ctx, Ps[i0 + j], &r, data[j], 2);
+            } catch (const ElmError &e) {
+                r.status = e.status;
+                if (res) res[i0 + j] = r;
+                throw;
+            }
+            if (res) res[i0 + j] = r;
+        }
+        i0 = i1;
     }
-    mark(ctx, 5);
-    if (solver_timed_out(s, sv)) {
-        res->status = ELM_ERR_TIMEOUT;
-        return;
-    }
-    if (!converged) return fallback();
-    if (!isfinite(res->rel_update)) res->status = ELM_ERR_NUMERIC;
-    const cudaMemcpyKind kind = on_device(pb.beta) ? cudaMemcpyDeviceToDevice
-                                                   : cudaMemcpyDeviceToHost;
-    copy2d(pb.beta, pb.ldb * sizeof(double), beta, m * sizeof(double), m * sizeof(double), L,
-           kind, s);
-    ELM_CUDA(cudaStreamSynchronize(s));
-    collect_phases(ctx);
 }
 
 // ------------------------------------------------------ row-sharded route
@@ -1060,6 +1215,7 @@ int elm_destroy(elm_ctx *ctx) {
     else cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->aux) cudaFree(ctx->aux);
+    if (ctx->batch) cudaFree(ctx->batch);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->copy_stream) {
@@ -1202,7 +1358,8 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
     int st = guarded(ctx, [&] {
         require(count >= 0, "count < 0");
         require(count == 0 || probs, "probs is NULL");
-        require(o.precision == ELM_PREC_FP64 || o.precision == ELM_PREC_MIXED, "precision");
+        require(o.precision == ELM_PREC_FP64 || o.precision == ELM_PREC_MIXED ||
+                    o.precision == ELM_PREC_FP64_TC, "precision");
         require(o.block_split >= 0, "block_split < 0");
         for (int64_t i = 0; i < count; i++) {
             const elm_problem &p = probs[i];
@@ -1216,12 +1373,13 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
         }
         ELM_CUDA(cudaSetDevice(ctx->device));
         ctx->timing = (o.flags & ELM_FLAG_PHASE_TIMING) != 0;
+        std::vector<Problem> plan(count);
         for (int64_t i = 0; i < count; i++) {
-            Problem P;
+            Problem &P = plan[i];
             P.p = &probs[i];
             P.prec = o.precision;
             P.max_refine = o.max_refine >= 0 ? o.max_refine
-                                             : (o.precision == ELM_PREC_FP64 ? 2 : 12);
+                                             : (o.precision == ELM_PREC_MIXED ? 12 : 2);
             // default rank threshold on the unit-diagonal scale: L 2^-52 for
             // the FP64 Gram; the mixed Gram drops digit pairs below 2^-34 of
             // the leading term, so its threshold sits above that level
@@ -1251,14 +1409,42 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
                 if (o.max_refine < 0) P.max_refine = 2;
                 if (!(o.refine_tol > 0.0)) P.refine_tol = 1e-12;
             }
-            elm_result r{};
+        }
+        // mixed-form problems of a multi-problem call: hidden layers and
+        // Grams batched; the others one by one
+        std::vector<Problem> batch;
+        std::vector<int64_t> where;
+        for (int64_t i = 0; i < count; i++) {
+            const Problem &P = plan[i];
+            if (count > 1 && P.prec == ELM_PREC_MIXED && !P.wide && P.block == 0) {
+                batch.push_back(P);
+                where.push_back(i);
+            }
+        }
+        std::vector<elm_result> bres(batch.size());
+        if (!batch.empty()) {
             try {
-                train_one(ctx, P, &r);
-            } catch (const ElmError &e) {
-                // the problem's own entry reports the failure too
-                r.status = e.status;
-                if (results) results[i] = r;
+                train_batch_mixed(ctx, batch, bres.data());
+            } catch (...) {
+                for (size_t j = 0; j < batch.size(); j++)
+                    if (results) results[where[j]] = bres[j];
                 throw;
+            }
+        }
+        size_t nb = 0;
+        for (int64_t i = 0; i < count; i++) {
+            elm_result r{};
+            if (nb < where.size() && where[nb] == i) {
+                r = bres[nb++];
+            } else {
+                try {
+                    train_one(ctx, plan[i], &r);
+                } catch (const ElmError &e) {
+                    // the problem's own entry reports the failure too
+                    r.status = e.status;
+                    if (results) results[i] = r;
+                    throw;
+                }
             }
             if (results) results[i] = r;
             if (first == ELM_OK && r.status != ELM_OK) first = r.status;

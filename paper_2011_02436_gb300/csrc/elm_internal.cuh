@@ -68,6 +68,8 @@ struct elm_ctx {
     size_t ws_size = 0;
     char *aux = nullptr;     // solve workspace (sized once the rank is known)
     size_t aux_size = 0;
+    char *batch = nullptr;   // mixed form: hidden layers and Grams awaiting their solves
+    size_t batch_size = 0;
     std::string last_error;
     // phase timing (ELM_FLAG_PHASE_TIMING)
     bool timing = false;
@@ -263,6 +265,43 @@ size_t oz_gram_part_bytes();
 void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
              int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part,
              uint64_t wait_ns = 0);
+// [H^T H, H^T T] (Lt x Lt, ldg, both triangles, Lt = L + m) of the FP64
+// matrix A = [H^T; T^T] (Lt x N, lda) on the tensor cores, accurate to FP64
+// level (eight 7-bit digits per element, every digit pair of weight above
+// 2^-68 summed exactly).  planes: oz_exact_planes_bytes(N, L, m) bytes; hs,
+// hsf: pad(Lt, 128) row scales; *err set on a device-side timeout,
+// *nonfinite (if given) |= 1 when A holds a NaN or an infinity.
+size_t oz_exact_planes_bytes(int64_t N, int64_t L, int64_t m);
+void oz_gram_exact(cudaStream_t s, const double *A, int64_t lda, int64_t N, int64_t L, int64_t m,
+                   __nv_bfloat16 *planes, double *hs, float *hsf, double *G, int64_t ldg, int *err,
+                   int32_t *nonfinite, uint64_t wait_ns = 0);
+// Several problems' hidden layers (mixed form, H as double-float pairs and
+// the Gram digit planes) and Grams [H^T H, H^T T] as one tensor-core launch
+// each.  Every item carries its own inputs (device pointers), scratch (hw,
+// planes, hs) and outputs (Hdf, G); dev: oz_batch_bytes(count) bytes of
+// device memory for the launch descriptors; after_hidden (may be NULL) is
+// recorded between the two launches.
+struct OzBatchItem {
+    const void *X;
+    int xdt;
+    int64_t N, n, ldx;
+    const double *W;
+    int64_t ldw;
+    const double *b, *a;
+    int act;
+    int64_t L, m;
+    const double *T;
+    int64_t ldt;
+    __nv_bfloat16 *planes;
+    double *hs, *G;
+    int64_t ldg;
+    OzHidWs hw;
+    void *Hdf;
+    int32_t *nonfinite;
+};
+size_t oz_batch_bytes(int64_t count);
+void oz_hidden_gram_batch(cudaStream_t s, const OzBatchItem *items, int64_t count, void *dev,
+                          int *err, uint64_t wait_ns, cudaEvent_t after_hidden);
 // out[i, c] = A[i * lda + c] - B[i * m + c]  (rows x m)
 void sub_rows(cudaStream_t s, const double *A, int64_t lda, const double *B, int64_t rows,
               int64_t m, double *out);

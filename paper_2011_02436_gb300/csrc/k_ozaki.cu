@@ -35,6 +35,8 @@
 #include <cudaTypedefs.h>
 #include <math.h>
 
+#include <vector>
+
 #include "elm_internal.cuh"
 
 namespace elm {
@@ -289,6 +291,7 @@ struct OzParams {
     int64_t whole;      // tiles below this run over the whole K range, one CTA each
     long long *part;    // EPI == 0: int64 partial sums of the tiles from `whole` on
     uint64_t wait_ns;   // bound of each pipeline wait (0: WAIT_NS)
+    int accumulate;     // EPI == 0, whole tiles: add to the output instead of storing
     int64_t n_base;     // non-Gram tiles: first B row (column) of the tile set
     ActParams ap;       // used when the kernel's EPI != 0
 };
@@ -449,18 +452,47 @@ __device__ __forceinline__ bool work_next(const OzParams &P, int nchunk, WorkIte
     return true;
 }
 
+// A batched launch: several problems (the same digit scheme, any sizes) in
+// one persistent grid.  Unit u in [first[j], first[j+1]) is tile
+// u - first[j] of problem j, over its whole K range (no split tiles).  The
+// problems' parameters and tensor maps (A then B) sit in global memory; a
+// tensor map there must be 64-byte aligned and written before the launch.
+struct OzBatch {
+    const OzParams *params;   // [nprob]
+    const CUtensorMap *maps;  // [2 nprob]
+    const int64_t *first;     // [nprob + 1]
+    int nprob;                // 0: single-problem launch (the kernel's P, tmA, tmB)
+    int *err;
+    uint64_t wait_ns;
+};
+
+// What one role of the kernel works on next: the unit's parameters, tensor
+// maps, tile, chunk range and K extent.
+struct Unit {
+    const OzParams *P;
+    const CUtensorMap *ma, *mb;
+    int64_t t;
+    int c_lo, c_hi, nslab, nchunk;
+};
+struct Walk {
+    WorkIter wi;   // single problem
+    int64_t u;     // batched: next unit of this CTA
+};
+
 // Persistent kernel: CTA b processes tiles b, b + G, b + 2G, ... (G = grid
-// size).  The TMA ring and all barrier phases run on across tiles, so the
+// size) of one problem, or units b, b + G, ... of a batch of problems.  The TMA ring and all barrier phases run on across tiles, so the
 // producer prefetches the next tile while the epilogue of the last one runs;
 // the epilogue copies its final values out of tensor memory into registers
 // and releases it before doing the output arithmetic, so the next tile's
 // MMAs overlap that arithmetic.
-template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI>
+template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI, int TMIN = 2,
+          int CHUNK = 0>
 __global__ void __launch_bounds__(NTHREADS, 1)
 ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             const OzParams P) {
-    constexpr int CHUNK_SLABS = chunk_slabs<DBITS>();
-    constexpr int ND = TMAX - 1;                 // diagonals t = 2..TMAX
+             const __grid_constant__ OzParams P, const __grid_constant__ OzBatch B) {
+    // K stages per exact chunk (CHUNK = 0: four pairs per diagonal)
+    constexpr int CHUNK_SLABS = CHUNK ? CHUNK : chunk_slabs<DBITS>();
+    constexpr int ND = TMAX - TMIN + 1;          // diagonals t = TMIN..TMAX
     constexpr uint32_t A_BYTES = BM * SK * 2;    // 8 KB per plane
     constexpr uint32_t B_BYTES = BN * SK * 2;    // 4 KB per plane
     constexpr uint32_t STAGE_BYTES = PA * A_BYTES + PB * B_BYTES;
@@ -479,11 +511,48 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     __shared__ int abort_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nslab = (int)(P.K / SK);
+    const bool batched = B.nprob > 0;
     // pipeline waits use the caller's bound; the waits that only let this
     // CTA's own copies and MMAs finish before it exits keep WAIT_NS
-    const uint64_t lim = P.wait_ns ? P.wait_ns : WAIT_NS;
-    const int nchunk = (nslab + CHUNK_SLABS - 1) / CHUNK_SLABS;
+    const uint64_t wns = batched ? B.wait_ns : P.wait_ns;
+    const uint64_t lim = wns ? wns : WAIT_NS;
+    // every role walks the same sequence of units
+    auto walk_begin = [&]() {
+        Walk w;
+        w.u = blockIdx.x;
+        if (!batched) {
+            const int nslab = (int)(P.K / SK);
+            w.wi = work_begin(P, (nslab + CHUNK_SLABS - 1) / CHUNK_SLABS);
+        }
+        return w;
+    };
+    auto walk_next = [&](Walk &w, Unit &U) {
+        if (!batched) {
+            U.P = &P;
+            U.ma = &tmA;
+            U.mb = &tmB;
+            U.nslab = (int)(P.K / SK);
+            U.nchunk = (U.nslab + CHUNK_SLABS - 1) / CHUNK_SLABS;
+            return work_next(P, U.nchunk, w.wi, U.t, U.c_lo, U.c_hi);
+        }
+        if (w.u >= B.first[B.nprob]) return false;
+        int lo = 0, hi = B.nprob - 1;      // the problem holding unit w.u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.first[mid] <= w.u) lo = mid;
+            else hi = mid - 1;
+        }
+        U.P = B.params + lo;
+        U.ma = B.maps + 2 * lo;
+        U.mb = B.maps + 2 * lo + 1;
+        U.t = w.u - B.first[lo];
+        U.nslab = (int)(U.P->K / SK);
+        U.nchunk = (U.nslab + CHUNK_SLABS - 1) / CHUNK_SLABS;
+        U.c_lo = 0;
+        U.c_hi = U.nchunk;
+        w.u += gridDim.x;
+        return true;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -511,14 +580,15 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (warp == 0) {
         if (lane == 0) {
             // ---------------------------------------------------- producer
-            int64_t g = 0, issued = 0, t;
-            int c_lo, c_hi;
-            WorkIter wi = work_begin(P, nchunk);
-            while (!*abort && work_next(P, nchunk, wi, t, c_lo, c_hi)) {
+            int64_t g = 0, issued = 0;
+            Unit U;
+            Walk wk = walk_begin();
+            while (!*abort && walk_next(wk, U)) {
                 int64_t m0, n0;
-                tile_coords(P, t, m0, n0);
-                const int s_hi = c_hi * CHUNK_SLABS < nslab ? c_hi * CHUNK_SLABS : nslab;
-                for (int s = c_lo * CHUNK_SLABS; s < s_hi; s++, g++) {
+                tile_coords(*U.P, U.t, m0, n0);
+                const int s_hi = U.c_hi * CHUNK_SLABS < U.nslab ? U.c_hi * CHUNK_SLABS : U.nslab;
+                const int64_t a_rows = U.P->a_rows, b_rows = U.P->b_rows;
+                for (int s = U.c_lo * CHUNK_SLABS; s < s_hi; s++, g++) {
                     const int st = (int)(g % STAGES);
                     if (g >= STAGES &&
                         !mbar_wait(&empty_bar[st], (uint32_t)(((g / STAGES) - 1) & 1), abort, lim))
@@ -527,12 +597,12 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     mbar_expect_tx(&full_bar[st], STAGE_BYTES);
 #pragma unroll
                     for (int p = 0; p < PA; p++)
-                        tma_2d(&tmA, &full_bar[st], base + p * A_BYTES, s * SK,
-                               (int)(p * P.a_rows + m0));
+                        tma_2d(U.ma, &full_bar[st], base + p * A_BYTES, s * SK,
+                               (int)(p * a_rows + m0));
 #pragma unroll
                     for (int q = 0; q < PB; q++)   // digit q + 1, stored in descending order
-                        tma_2d(&tmB, &full_bar[st], base + PA * A_BYTES + (PB - 1 - q) * B_BYTES,
-                               s * SK, (int)(q * P.b_rows + n0));
+                        tma_2d(U.mb, &full_bar[st], base + PA * A_BYTES + (PB - 1 - q) * B_BYTES,
+                               s * SK, (int)(q * b_rows + n0));
                     issued = g + 1;
                 }
             }
@@ -549,12 +619,12 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issue
-            int64_t g = 0, gc = 0, t;
-            int c_lo, c_hi;
-            WorkIter wi = work_begin(P, nchunk);
-            while (!*abort && work_next(P, nchunk, wi, t, c_lo, c_hi)) {
-                const int s_hi = c_hi * CHUNK_SLABS < nslab ? c_hi * CHUNK_SLABS : nslab;
-                for (int s = c_lo * CHUNK_SLABS; s < s_hi && !*abort; s++, g++) {
+            int64_t g = 0, gc = 0;
+            Unit U;
+            Walk wk = walk_begin();
+            while (!*abort && walk_next(wk, U)) {
+                const int s_hi = U.c_hi * CHUNK_SLABS < U.nslab ? U.c_hi * CHUNK_SLABS : U.nslab;
+                for (int s = U.c_lo * CHUNK_SLABS; s < s_hi && !*abort; s++, g++) {
                     const int st = (int)(g % STAGES);
                     const bool first = (s % CHUNK_SLABS) == 0;
                     // accumulators free again once the previous chunk is read
@@ -566,32 +636,34 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     // offsets in its 16-byte start-address field (smem < 256 KB)
                     const uint64_t da0 = desc_sw64(su32(smem + (size_t)st * STAGE_BYTES));
                     const uint64_t db0 = da0 + (uint64_t)((PA * A_BYTES) >> 4);
-                    // A plane p against the B planes q = TMAX-p .. 1 (diagonals
-                    // t = TMAX .. p+1) in MMAs of width up to 256: B planes are
-                    // stored in descending order and diagonal t's accumulator sits
-                    // at column (TMAX - t) BN, so the group starts at column 0 (and,
-                    // past four planes, continues at column 256 with width 64 or
-                    // 128): A is read once per group instead of once per pair, and
-                    // every accumulator address is a multiple of its MMA width.
-                    // p = 1 reaches every diagonal and comes first, so it alone
-                    // starts the chunk's accumulators.
-                    static_assert(PB >= TMAX - 1, "plane 1 must reach every diagonal");
-                    static_assert(TMAX - 1 <= 8, "at most two MMA groups per plane");
+                    // A plane p against the B planes q = min(PB, TMAX-p) ..
+                    // max(1, TMIN-p) (diagonals t = p + q in TMIN..TMAX) in MMAs of
+                    // width up to 256: B planes are stored in descending order and
+                    // diagonal t's accumulator sits at column (TMAX - t) BN, so a
+                    // group starts at column 0 (and, past four planes, continues at
+                    // column 256 with width 64 or 128): A is read once per group
+                    // instead of once per pair, and every accumulator address is a
+                    // multiple of its MMA width.  p = 1 reaches every diagonal and
+                    // comes first, so it alone starts the chunk's accumulators.
+                    static_assert(PB >= TMAX - 1 && TMIN >= 2,
+                                  "plane 1 must reach every diagonal");
+                    static_assert(TMAX - TMIN + 1 <= 8, "at most two MMA groups per plane");
 #pragma unroll
                     for (int p = 1; p <= PA && p < TMAX; p++) {
-                        const int nall = TMAX - p;        // planes q = nall .. 1
+                        const int q_top = PB < TMAX - p ? PB : TMAX - p;
+                        const int q_lo = TMIN - p > 1 ? TMIN - p : 1;
 #pragma unroll
-                        for (int g = 0; g * 4 < nall; g++) {
-                            const int q_hi = nall - 4 * g;
-                            const int nq = q_hi < 4 ? q_hi : 4;
+                        for (int g = 0; q_top - 4 * g >= q_lo; g++) {
+                            const int q_hi = q_top - 4 * g;
+                            const int nq = q_hi - q_lo + 1 < 4 ? q_hi - q_lo + 1 : 4;
+                            const uint32_t col = (uint32_t)((TMAX - p - q_hi) * BN);
                             const uint32_t idesc = IDESC_M | ((uint32_t)((BN * nq) >> 3) << 17);
                             const uint64_t da = da0 + (uint64_t)(((p - 1) * A_BYTES) >> 4);
                             const uint64_t db = db0 + (uint64_t)(((PB - q_hi) * B_BYTES) >> 4);
 #pragma unroll
                             for (int kk = 0; kk < SK / 16; kk++) {
                                 const uint32_t acc = (first && p == 1 && kk == 0) ? 0u : 1u;
-                                mma_bf16(tmem + (uint32_t)(4 * g * BN), da + 2 * kk, db + 2 * kk,
-                                         idesc, acc);
+                                mma_bf16(tmem + col, da + 2 * kk, db + 2 * kk, idesc, acc);
                             }
                         }
                     }
@@ -614,14 +686,17 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int quarter = warp & 3;
         const int c0 = ((warp - 2) >> 2) * 32;       // this warp's 32 columns of the tile
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-        const bool direct = (EPI != 0) && nchunk == 1;
-        int64_t gc = 0, t;
-        int c_lo, c_hi;
+        int64_t gc = 0;
         bool ok = true;
-        WorkIter wi = work_begin(P, nchunk);
-        while (ok && work_next(P, nchunk, wi, t, c_lo, c_hi)) {
+        Unit U;
+        Walk wk = walk_begin();
+        while (ok && walk_next(wk, U)) {
+            const OzParams &Pu = *U.P;
+            const int64_t t = U.t;
+            const int c_lo = U.c_lo, c_hi = U.c_hi;
+            const bool direct = (EPI != 0) && U.nchunk == 1;
             int64_t m0, n0;
-            tile_coords(P, t, m0, n0);
+            tile_coords(Pu, t, m0, n0);
             const int64_t m = m0 + quarter * 32 + lane;
             long long run[32];     // EPI == 0: final sums of this warp's 32 columns
             for (int c = c_lo; c < c_hi; c++, gc++) {
@@ -633,7 +708,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 // Each TMEM load is issued before the arithmetic on the previous
                 // one (two register buffers), so its latency overlaps that work.
                 const auto diag_addr = [&](int k) {   // k = h ND + (t - 2)
-                    return lane_base + (uint32_t)((TMAX - 2 - k % ND) * BN + (k / ND) * 16);
+                    return lane_base + (uint32_t)((TMAX - TMIN - k % ND) * BN + (k / ND) * 16);
                 };
                 uint32_t wb[2][16];
                 if (direct) {
@@ -695,8 +770,8 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         tmem_wait_ld();
                         reg_fence16(wb[0]);
 #pragma unroll
-                        for (int td = 2; td <= TMAX; td++) {
-                            const int k = td - 2;
+                        for (int td = TMIN; td <= TMAX; td++) {
+                            const int k = td - TMIN;
                             if (td < TMAX) tmem_ld16(diag_addr(h * ND + k + 1), wb[(k + 1) & 1]);
                             const uint32_t *w = wb[k & 1];
                             // accumulators are exact integers below 2^25
@@ -739,11 +814,11 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             }
             if (!ok || *abort) break;
             // ---------------------------------------------------- output
-            if (EPI == 0 && t >= P.whole) {
+            if (EPI == 0 && t >= Pu.whole) {
                 // a piece of a split tile (all of it, possibly): exact int64 adds,
                 // column-major in the tile so a warp's 32 lanes (rows) hit
                 // consecutive addresses; gram_tail_kernel writes the tile
-                long long *pt = P.part + (t - P.whole) * (BM * BN) + (int64_t)c0 * BM +
+                long long *pt = Pu.part + (t - Pu.whole) * (BM * BN) + (int64_t)c0 * BM +
                                 quarter * 32 + lane;
 #pragma unroll
                 for (int i = 0; i < 32; i++)
@@ -751,20 +826,25 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                               (unsigned long long)run[i]);
             } else if (EPI == 0) {
                 const double unit = ldexp(1.0, -DBITS * (TMAX - 2));
-                if (m < P.m_valid) {
-                    const double rs = P.out_scale * unit * P.rscale[m];
+                if (m < Pu.m_valid) {
+                    const double rs = Pu.out_scale * unit * Pu.rscale[m];
+                    double *out = Pu.out;
+                    const int64_t ldo = Pu.ldo, n_valid = Pu.n_valid;
+                    const bool gram = Pu.gram != 0, accum = Pu.accumulate != 0;
+                    const double *cscale = Pu.cscale;
 #pragma unroll
                     for (int i = 0; i < 32; i++) {
                         const int64_t n = n0 + c0 + i;
-                        if (n >= P.n_valid || (P.gram && n > m)) continue;
-                        const double v = (double)run[i] * rs * P.cscale[n];
-                        P.out[m * P.ldo + n] = v;
-                        if (P.gram && n < m) P.out[n * P.ldo + m] = v;   // lanes: consecutive m
+                        if (n >= n_valid || (gram && n > m)) continue;
+                        double v = (double)run[i] * rs * cscale[n];
+                        if (accum) v += out[m * ldo + n];
+                        out[m * ldo + n] = v;
+                        if (gram && n < m) out[n * ldo + m] = v;   // lanes: consecutive m
                     }
                 }
             } else {
                 // the running-sum columns are this warp's until its next drain
-                const RowAct ra = row_setup(P, m);
+                const RowAct ra = row_setup(Pu, m);
 #pragma unroll 1
                 for (int h = 0; h < 2; h++) {
                     uint32_t w0[16], w1[16];
@@ -774,8 +854,8 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     dfl V[16];
 #pragma unroll
                     for (int i = 0; i < 16; i++) V[i] = {__uint_as_float(w0[i]), __uint_as_float(w1[i])};
-                    hidden_emit8<EPI == 2>(P, ra, m, n0 + c0 + h * 16, V);
-                    hidden_emit8<EPI == 2>(P, ra, m, n0 + c0 + h * 16 + 8, V + 8);
+                    hidden_emit8<EPI == 2>(Pu, ra, m, n0 + c0 + h * 16, V);
+                    hidden_emit8<EPI == 2>(Pu, ra, m, n0 + c0 + h * 16 + 8, V + 8);
                 }
             }
         }
@@ -787,7 +867,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
     }
-    if (threadIdx.x == 0 && *abort) atomicExch(P.err, 1);
+    if (threadIdx.x == 0 && *abort) atomicExch(batched ? B.err : P.err, 1);
 }
 
 // Split tiles of the Gram: FP64 values from the int64 sums of their pieces,
@@ -1099,17 +1179,25 @@ int sm_count() {
     return sms;
 }
 
-template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI>
-void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B, OzParams P,
-                  int64_t ntiles) {
+// Dynamic shared memory of an ozaki_kernel instance, set up once per process.
+template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI, int TMIN = 2, int CHUNK = 0>
+size_t ozaki_smem() {
     constexpr size_t stage = (size_t)PA * BM * SK * 2 + (size_t)PB * BN * SK * 2;
     const size_t smem = STAGES * stage + 1024;
-    auto k = ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI>;
     static bool attr = false;
     if (!attr) {
-        ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ELM_CUDA(cudaFuncSetAttribute(ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI, TMIN, CHUNK>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
+    return smem;
+}
+
+template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI, int TMIN = 2, int CHUNK = 0>
+void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B, OzParams P,
+                  int64_t ntiles) {
+    const size_t smem = ozaki_smem<PA, PB, TMAX, STAGES, DBITS, EPI, TMIN, CHUNK>();
+    auto k = ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI, TMIN, CHUNK>;
     const int sms = sm_count();
     CUtensorMap ma = make_map(A, PA * P.a_rows, P.K, BM);
     CUtensorMap mb = make_map(B, PB * P.b_rows, P.K, BN);
@@ -1118,7 +1206,7 @@ void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B
     if (EPI != 0 || !P.part || P.whole > ntiles || P.whole < 0) P.whole = ntiles;
     // split tiles spread over every SM; otherwise one CTA per tile at most
     const int64_t grid = (ntiles < sms && P.whole == ntiles) ? ntiles : sms;
-    k<<<(unsigned)grid, NTHREADS, smem, s>>>(ma, mb, P);
+    k<<<(unsigned)grid, NTHREADS, smem, s>>>(ma, mb, P, OzBatch{});
     ELM_CHECK_LAUNCH();
 }
 
@@ -1302,6 +1390,210 @@ void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int6
             <<<dim3(BM * BN / 256, (unsigned)(ntiles - P.whole)), 256, 0, s>>>(P);
         ELM_CHECK_LAUNCH();
     }
+}
+
+// ------------------------------------------------------ FP64-accurate Gram
+// [H^T H, H^T T] of an FP64 matrix A = [H^T; T^T] ((L + m) x N, row-major)
+// on the tensor cores, as accurate as an FP64 Gram.  Each row is split into
+// EX_PH = 8 balanced digits of 7 bits on a 2^-55 grid of its power-of-two
+// scale (the FP64 value, rounded once at 2^-56 of the row's maximum), and
+// every digit-pair product of weight above 2^-68 (p + q <= 9) is summed
+// exactly: diagonals 2..5 (10 pairs, at most four per diagonal, K chunks of
+// 1024) in one launch, diagonals 6..9 (26 pairs, at most eight per diagonal,
+// K chunks of 512, so every FP32 partial sum stays within 8 * 2^12 * 512 =
+// 2^24) in a second launch that adds its FP64 result to the first.  The
+// dropped pairs weigh at most 2^-56 relative, the FP64 conversions 2^-53.
+constexpr int EX_PH = 8, EX_BITS = 7;
+
+size_t oz_exact_planes_bytes(int64_t N, int64_t L, int64_t m) {
+    return (size_t)EX_PH * oz_pad(L + m, BM) * oz_pad(N, BN) * 2;
+}
+
+void oz_gram_exact(cudaStream_t s, const double *A, int64_t lda, int64_t N, int64_t L, int64_t m,
+                   __nv_bfloat16 *planes, double *hs, float *hsf, double *G, int64_t ldg, int *err,
+                   int32_t *nonfinite, uint64_t wait_ns) {
+    const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
+    const int64_t nJ = Lp / BM, ntiles = nJ * (nJ + 1);
+    digits_rows_kernel<EX_PH, EX_BITS, double><<<(unsigned)((Lp + 7) / 8), 256, 0, s>>>(
+        A, L + m, N, lda, Lp, Np, planes, hs, hsf, nonfinite, 0, Lp);
+    ELM_CHECK_LAUNCH();
+    OzParams P{};
+    P.whole = ntiles;
+    P.part = nullptr;
+    P.a_rows = Lp;
+    P.b_rows = Lp;
+    P.K = Np;
+    P.m_valid = L + m;
+    P.n_valid = L + m;
+    P.ntile_m = nJ;
+    P.gram = 1;
+    P.out_scale = ldexp(1.0, -2 * (EX_BITS - 1));
+    P.rscale = hs;
+    P.cscale = hs;
+    P.out = G;
+    P.ldo = ldg;
+    P.err = err;
+    P.wait_ns = wait_ns;
+    P.accumulate = 0;
+    launch_ozaki<4, 4, 5, 3, EX_BITS, 0, 2, 0>(s, planes, planes, P, ntiles);
+    P.accumulate = 1;
+    launch_ozaki<8, 8, 9, 2, EX_BITS, 0, 6, 16>(s, planes, planes, P, ntiles);
+}
+
+// ------------------------------------------------------------ batched launch
+// The hidden layer and the Gram of several problems as one launch each: the
+// slicing kernels run per problem, then one persistent grid walks the tiles
+// of every problem (ozaki_kernel with an OzBatch).  Whole tiles only.
+namespace {
+
+template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI>
+void launch_ozaki_batch(cudaStream_t s, const std::vector<OzParams> &ps,
+                        const std::vector<CUtensorMap> &maps, const std::vector<int64_t> &first,
+                        char *dev, int *err, uint64_t wait_ns) {
+    const int64_t count = (int64_t)ps.size();
+    const int64_t units = first[count];
+    if (units <= 0) return;
+    const size_t smem = ozaki_smem<PA, PB, TMAX, STAGES, DBITS, EPI>();
+    // device copies: maps (64-byte aligned), parameters, unit offsets
+    CUtensorMap *dmaps = reinterpret_cast<CUtensorMap *>(dev);
+    const size_t mbytes = (sizeof(CUtensorMap) * maps.size() + 255) / 256 * 256;
+    OzParams *dps = reinterpret_cast<OzParams *>(dev + mbytes);
+    const size_t pbytes = (sizeof(OzParams) * ps.size() + 255) / 256 * 256;
+    int64_t *dfirst = reinterpret_cast<int64_t *>(dev + mbytes + pbytes);
+    ELM_CUDA(cudaMemcpyAsync(dmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                             cudaMemcpyHostToDevice, s));
+    ELM_CUDA(cudaMemcpyAsync(dps, ps.data(), sizeof(OzParams) * ps.size(), cudaMemcpyHostToDevice,
+                             s));
+    ELM_CUDA(cudaMemcpyAsync(dfirst, first.data(), sizeof(int64_t) * first.size(),
+                             cudaMemcpyHostToDevice, s));
+    OzBatch B{};
+    B.params = dps;
+    B.maps = dmaps;
+    B.first = dfirst;
+    B.nprob = (int)count;
+    B.err = err;
+    B.wait_ns = wait_ns;
+    const int64_t sms = sm_count();
+    const int64_t grid = units < sms ? units : sms;
+    CUtensorMap none{};
+    ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI><<<(unsigned)grid, NTHREADS, smem, s>>>(
+        none, none, OzParams{}, B);
+    ELM_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+size_t oz_batch_bytes(int64_t count) {
+    const size_t mbytes = (sizeof(CUtensorMap) * 2 * count + 255) / 256 * 256;
+    const size_t pbytes = (sizeof(OzParams) * count + 255) / 256 * 256;
+    const size_t fbytes = (sizeof(int64_t) * (count + 1) + 255) / 256 * 256;
+    return 2 * (mbytes + pbytes + fbytes);    // the hidden layer's, then the Gram's
+}
+
+void oz_hidden_gram_batch(cudaStream_t s, const OzBatchItem *it, int64_t count, void *dev,
+                          int *err, uint64_t wait_ns, cudaEvent_t after_hidden) {
+    if (count <= 0) return;
+    std::vector<OzParams> ph, pg;
+    std::vector<CUtensorMap> mh, mg;
+    std::vector<int64_t> fh(1, 0), fg(1, 0);
+    for (int64_t i = 0; i < count; i++) {
+        const OzBatchItem &q = it[i];
+        const int64_t Np = oz_pad(q.N, BN), nK = oz_pad(q.n, SK), Lp = oz_pad(q.L + q.m, BM);
+        const OzHidWs &w = q.hw;
+        // the slicing and per-row kernels of oz_hidden, whole X at once
+        col_scale_kernel<<<(unsigned)((Lp + 31) / 32), 256, 0, s>>>(q.W, q.n, q.L, q.ldw, Lp, w.ws);
+        ELM_CHECK_LAUNCH();
+        digits_cols_par_kernel<HID_PW, HID_BITS>
+            <<<(unsigned)((Lp * (nK / 8) + 255) / 256), 256, 0, s>>>(q.W, q.n, q.L, q.ldw, Lp, nK,
+                                                                      w.wp, w.ws);
+        ELM_CHECK_LAUNCH();
+        hs_kernel<<<(unsigned)((Lp + 255) / 256), 256, 0, s>>>(q.a, q.L, q.m, Lp, q.hs);
+        ELM_CHECK_LAUNCH();
+        sigmoid_table_kernel<<<(SIG_N + 255) / 256, 256, 0, s>>>(w.tab);
+        ELM_CHECK_LAUNCH();
+        rowconst_kernel<HID_BITS, HID_TMAX><<<(unsigned)((Lp + 255) / 256), 256, 0, s>>>(
+            ldexp(1.0, -2 * (HID_BITS - 1)), w.ws, q.b, q.a, q.hs, q.L, Lp, w.rowc);
+        ELM_CHECK_LAUNCH();
+        const unsigned g = (unsigned)((Np + 7) / 8);
+        if (q.xdt == ELM_F64)
+            digits_rows_kernel<HID_PX, HID_BITS, double><<<g, 256, 0, s>>>(
+                (const double *)q.X, q.N, q.n, q.ldx, Np, nK, w.xp, w.xs, w.xsf, q.nonfinite, 0,
+                Np);
+        else
+            digits_rows_f32_kernel<HID_PX, HID_BITS><<<g, 256, 0, s>>>(
+                (const float *)q.X, q.N, q.n, q.ldx, Np, nK, w.xp, w.xs, w.xsf, q.nonfinite, 0,
+                Np);
+        ELM_CHECK_LAUNCH();
+        OzParams P{};
+        P.a_rows = Lp;
+        P.b_rows = Np;
+        P.K = nK;
+        P.m_valid = q.L;
+        P.n_valid = q.N;
+        P.ntile_m = Lp / BM;
+        P.gram = 0;
+        P.out_scale = ldexp(1.0, -2 * (HID_BITS - 1));
+        P.rscale = w.ws;
+        P.cscale = w.xs;
+        P.err = err;
+        P.wait_ns = wait_ns;
+        P.ap.b = q.b;
+        P.ap.a = q.a;
+        P.ap.act = q.act;
+        P.ap.L = q.L;
+        P.ap.m = q.m;
+        P.ap.planes = q.planes;
+        P.ap.plane_stride = Lp * Np;
+        P.ap.Np = Np;
+        P.ap.hs = q.hs;
+        P.ap.tab = w.tab;
+        P.ap.csf = w.xsf;
+        P.ap.rowc = w.rowc;
+        P.ap.Ht = nullptr;
+        P.ap.Hdf = (float2 *)q.Hdf;
+        P.ap.ldhd = q.L;
+        P.ap.ldh = 0;
+        const int64_t tiles = (Lp / BM) * (Np / BN);
+        P.ntiles = tiles;
+        P.whole = tiles;
+        P.n_base = 0;
+        ph.push_back(P);
+        mh.push_back(make_map(w.wp, HID_PW * Lp, nK, BM));
+        mh.push_back(make_map(w.xp, HID_PX * Np, nK, BN));
+        fh.push_back(fh.back() + tiles);
+        // the target rows of the Gram digit planes
+        oz_t_digits(s, q.T, q.ldt, q.N, q.L, q.m, q.planes, q.hs);
+        // the Gram's parameters
+        const int64_t nJ = Lp / BM, gt = nJ * (nJ + 1);
+        OzParams G{};
+        G.whole = gt;
+        G.ntiles = gt;
+        G.part = nullptr;
+        G.a_rows = Lp;
+        G.b_rows = Lp;
+        G.K = Np;
+        G.m_valid = q.L + q.m;
+        G.n_valid = q.L + q.m;
+        G.ntile_m = nJ;
+        G.gram = 1;
+        G.out_scale = ldexp(1.0, -2 * (GRAM_BITS - 1));
+        G.rscale = q.hs;
+        G.cscale = q.hs;
+        G.out = q.G;
+        G.ldo = q.ldg;
+        G.err = err;
+        G.wait_ns = wait_ns;
+        pg.push_back(G);
+        mg.push_back(make_map(q.planes, GRAM_PH * Lp, Np, BM));
+        mg.push_back(make_map(q.planes, GRAM_PH * Lp, Np, BN));
+        fg.push_back(fg.back() + gt);
+    }
+    char *d = (char *)dev;
+    const size_t half = oz_batch_bytes(count) / 2;
+    launch_ozaki_batch<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, ph, mh, fh, d, err, wait_ns);
+    if (after_hidden) ELM_CUDA(cudaEventRecord(after_hidden, s));
+    launch_ozaki_batch<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS, 0>(s, pg, mg, fg, d + half, err,
+                                                                   wait_ns);
 }
 
 }  // namespace elm

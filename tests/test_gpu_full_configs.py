@@ -15,14 +15,18 @@ element by element against the FP64 CPU oracle's beta (Eq. 5, beta = H^+ T):
     that closely, the bar widens to the problem's least-squares forward
     error scale (below), which the golden file records per problem.
 
-Forward error scale of a least-squares solution computed in FP64 (Wedin's
-perturbation bound, as used for semi-normal equations with refinement):
-    u (kappa + kappa^2 eta),   eta = ||T - H beta|| / (||H||_2 ||beta||),
+Forward error scale of a least-squares solution computed in FP64 through
+the normal equations with k refinement steps (both sides take k = 2):
+    u (kappa + kappa^2 eta) + (kappa^2 u)^(k+1),
+    eta = ||T - H beta|| / (||H||_2 ||beta||),
 with kappa the condition number of H after column equilibration (both the
-oracle and the library equilibrate) and u = 2^-53.  Two FP64 solvers may
-each be that far from the exact beta, so they agree to about twice it; the
-widened bar is 8 times the scale.  It is used only for problems whose
-recorded scale exceeds 1/100 of the bar.
+oracle and the library equilibrate) and u = 2^-53.  The first term is
+Wedin's perturbation bound, the level a converged refinement reaches; the
+second is what k steps leave of the first solve's error kappa(S) u, each
+step contracting it by kappa(S) u = kappa^2 u (Higham, Accuracy and
+Stability of Numerical Algorithms, ch. 20).  Two FP64 solvers may each be
+that far from the exact beta, so the widened bar is 8 times the scale.  It
+is used only for problems whose recorded scale exceeds 1/100 of the bar.
 """
 import hashlib
 import os
@@ -89,13 +93,14 @@ def golden(name, probs):
     return g
 
 
-def error_scale(g, i):
-    """u (kappa + kappa^2 eta) of problem i (equilibrated H)."""
+def error_scale(g, i, steps=2):
+    """u (kappa + kappa^2 eta) + (kappa^2 u)^(steps+1) of problem i
+    (equilibrated H)."""
     kappa = float(g["kappa"][i])
     L = g["beta_%03d" % i].shape[0]
     h2 = np.sqrt(float(g["ev_max"][i])) * float(g["h_fro"][i]) / np.sqrt(L)   # ~ ||H||_2
     eta = float(g["res_norm"][i]) / (h2 * float(g["beta_norm"][i]))
-    return U * (kappa + kappa * kappa * eta)
+    return U * (kappa + kappa * kappa * eta) + (kappa * kappa * U) ** (steps + 1)
 
 
 def bar_for(g, i, bar):
