@@ -95,3 +95,80 @@ def test_four_pair_diagonals_are_exact_in_fp32_over_a_chunk():
         for p in range(4):
             acc = np.float32(acc + np.float32(a[p, k] * b[p, k]))
     assert int(acc) == int(np.sum(a.astype(np.int64) * b.astype(np.int64)))
+
+
+# ---------------------------------------------------------------------------
+# The FP64-accurate Gram (ELM_PREC_FP64_TC): eight digits, every pair of
+# weight above 2^-68 (p + q <= 9), split into the bands of diagonals 2..5
+# and 6..9 that the two tensor-core launches sum.
+EX_P, EX_TMAX = 8, 9
+BANDS = ((2, 5, 4, 1024), (6, 9, 8, 512))      # (first, last diagonal, planes, K chunk)
+
+
+def test_exact_gram_bands_cover_every_kept_pair_once():
+    kept = {(p, q) for p in range(1, EX_P + 1) for q in range(1, EX_P + 1) if p + q <= EX_TMAX}
+    seen = []
+    for t0, t1, planes, _ in BANDS:
+        for p in range(1, planes + 1):
+            for q in range(1, planes + 1):
+                if t0 <= p + q <= t1:
+                    seen.append((p, q))
+    assert sorted(seen) == sorted(kept) and len(seen) == 36
+
+
+def test_exact_gram_band_partial_sums_fit_fp32():
+    """The largest partial sum of one diagonal over one K chunk: at most
+    (pairs on the diagonal) x 2^12 x chunk, which must stay within 2^24."""
+    for t0, t1, planes, chunk in BANDS:
+        for t in range(t0, t1 + 1):
+            pairs = sum(1 for p in range(1, planes + 1) if 1 <= t - p <= planes)
+            assert pairs * 2 ** 12 * chunk <= 2 ** 24, (t, pairs, chunk)
+
+
+def test_exact_gram_is_fp64_accurate():
+    """Band sums in exact integers, one FP64 conversion per band, against the
+    exact Gram in rational arithmetic.  The digits hold each element to
+    2^-56 of its row's scale sc (the FP64 value rounded once on that grid),
+    the dropped pairs (p + q >= 10) weigh at most 7.1 2^-56 sc_j sc_k per
+    product, and each band is rounded once to FP64 (two roundings of u):
+        |G' - G|_jk <= 2u sum|h_ij h_ik| + 2^-56 (sc_j sum|h_ik| + sc_k sum|h_ij|)
+                       + (7.1 + 2^-56) n 2^-56 sc_j sc_k.
+    For rows of similar magnitude this is the FP64 dot-product level, without
+    its factor n on the first term; rows spanning many binades are held
+    relative to their largest element.  Rows of sigmoid and tanh values, of
+    values spread over twenty binades and of values near 1e-7."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    n = 300
+    cols = [1.0 / (1.0 + np.exp(-rng.normal(0, 3, n))),
+            np.tanh(rng.normal(0, 4, n)),
+            rng.normal(0, 1, n) * np.exp(rng.uniform(-20, 0, n)),
+            rng.uniform(-1, 1, n) * 1e-7]
+    Hc = np.stack(cols)                    # rows of the matrix the kernel slices
+    D, S = [], []
+    for row in Hc:
+        d, sc = digits(row, EX_P)
+        D.append(d.astype(np.int64))
+        S.append(sc)
+    u = 2.0 ** -53
+    for j in range(len(cols)):
+        for k in range(len(cols)):
+            total = 0.0
+            for t0, t1, planes, _ in BANDS:
+                acc = 0                    # int64 running sum of the band, as the drains keep it
+                for t in range(t0, t1 + 1):
+                    s_t = sum(int(np.dot(D[j][p - 1], D[k][t - p - 1]))
+                              for p in range(1, planes + 1) if 1 <= t - p <= planes)
+                    acc += s_t * 2 ** (B * (t1 - t))
+                unit = 2.0 ** (-2 * (B - 1)) * 2.0 ** (-B * (t1 - 2))
+                total += float(acc) * unit * S[j] * S[k]
+            exact = sum(Fraction(a) * Fraction(b) for a, b in zip(Hc[j], Hc[k]))
+            g = 2.0 ** -56
+            bound = (2 * u * float(np.sum(np.abs(Hc[j] * Hc[k])))
+                     + g * (S[j] * float(np.sum(np.abs(Hc[k]))) + S[k] * float(np.sum(np.abs(Hc[j]))))
+                     + (7.1 + g) * n * g * S[j] * S[k])
+            err = abs(Fraction(total) - exact)
+            assert err <= Fraction(bound), (j, k)
+            # and in practice far inside it: below the FP64 dot-product level
+            # of the row scales
+            assert float(err) <= 4 * u * np.sqrt(n) * S[j] * S[k], (j, k)
