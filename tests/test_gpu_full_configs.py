@@ -82,6 +82,8 @@ def digest(a):
 def golden(name, probs):
     """The stored oracle results, after checking the inputs' fingerprints."""
     path = os.path.join(GOLD, "full_%s.npz" % name)
+    if not os.path.exists(path):
+        pytest.skip("oracle results not written: tests/golden/make_full_goldens.py %s" % name)
     g = np.load(path)
     assert int(g["count"]) == len(probs)
     for i, p in enumerate(probs):
