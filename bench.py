@@ -381,6 +381,8 @@ def run_native(args):
 
     # verified run: statuses, ranks and beta against the oracle (rank 0)
     bs = dict(block_split=args.block_split) if args.block_split > 0 else {}
+    if args.lanes > 0:
+        bs["lanes"] = args.lanes
     res = elm.elm_train(ctx, probs, precision=prec, check=False, **bs)
     betas = [pr["beta"].cpu().numpy() for pr in probs]
     check = dict(rank=[r["rank"] for r in res] if count > 1 else res[0]["rank"],
@@ -509,17 +511,19 @@ def run_native(args):
                         issued_frac=issued / (ph_ms["gram"] * 1e-3) / 1e12 / pk["bf16"])
         roof["phase_ms"] = ph_ms
         first = hosts[0]
-        cfg = dict(workload=desc, precision=args.precision if not bs else "fp64 (block route)",
+        cfg = dict(workload=desc,
+                   precision=args.precision if args.block_split <= 0 else "fp64 (block route)",
                    parallelism="replicas" if ws > 1 else "single",
                    l2="inputs larger than L2 (X and the digit planes stream from HBM): no flush")
-        if bs:
+        if args.block_split > 0:
             cfg.update(route="the paper's block formulae (Eqs. 19-23), H1 = first %d columns"
                        % args.block_split)
         if count == 1:
             cfg.update(N=first["X"].shape[0], n=first["X"].shape[1], L=first["W"].shape[1],
                        m=first["T"].shape[1])
         else:
-            cfg.update(problems=count)
+            cfg.update(problems=count, lanes=args.lanes or 4,
+                       phases="factor, solve and refine summed over the lanes")
         line = dict(metric=METRIC, value=value, unit="trainings/s", n_gpus=ws, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms_max, higher_is_better=True,
                     scaling="weak", vs_baseline=None,
@@ -682,6 +686,9 @@ def main():
                     help="the timed workload (the default is the headline configuration)")
     ap.add_argument("--shard", choices=["none", "rows"], default="none",
                     help="rows: one training with the rows of H split over the ranks")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="batched mixed trainings: problems whose factorisation, solves and "
+                         "refinement run at once (0: the library's default, 4)")
     ap.add_argument("--block-split", type=int, default=0,
                     help="> 0: train by the paper's block formulae (Eqs. 19-23) with H1 the "
                          "first BLOCK_SPLIT columns instead of the rank-based route")

@@ -150,8 +150,18 @@ typedef struct elm_train_opts {
                            Needs 0 < block_split < L and H of full column
                            rank (A or D singular: ELM_ERR_NUMERIC); wide
                            problems (N < L) are rejected (ELM_ERR_ARG)     */
-    int32_t reserved;   /* 0                                                */
+    int32_t lanes;      /* several ELM_PREC_MIXED problems in one call: how
+                           many problems' factorisations, solves and
+                           refinements run at the same time, each on its own
+                           stream, workspaces and host thread, once the
+                           call's batched hidden layers and Grams are done
+                           (0: 4; at most ELM_MAX_LANES; 1: one after
+                           another on the context's stream).  Every
+                           problem's arithmetic is the same whatever lane
+                           runs it, so beta does not depend on this value */
 } elm_train_opts;
+
+#define ELM_MAX_LANES 32
 
 /* elm_train_opts.flags: record CUDA events around each training phase on
  * the context's stream (read them with elm_phase_times). */

@@ -187,17 +187,19 @@ def elm_problem_struct(X, n, N, W, b, a, L, T, m, beta, act):
 
 
 def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
-              refine_tol=0.0, check=True, flags=0, wait_limit_ns=0, block_split=0):
+              refine_tol=0.0, check=True, flags=0, wait_limit_ns=0, block_split=0, lanes=0):
     """Train each problem (dict with X, W, b, a, act, T and optional beta
     output).  Returns a list of dicts (rank, refine_iters, status,
     rel_update, form: FORM_*); beta is written into problem['beta'].
-    check: raise ElmError when the call returns a status other than OK."""
+    check: raise ElmError when the call returns a status other than OK.
+    lanes: batched mixed trainings, problems whose back halves run at once
+    (0: the library's default)."""
     if isinstance(problems, dict):
         problems = [problems]
     arr = (_lib.elm_problem * len(problems))(*[_problem(p) for p in problems])
     opts = _lib.elm_train_opts(precision=precision, max_refine=max_refine, tol_rank=tol_rank,
                                refine_tol=refine_tol, flags=flags, wait_limit_ns=wait_limit_ns,
-                               block_split=block_split, reserved=0)
+                               block_split=block_split, lanes=lanes)
     res = (_lib.elm_result * len(problems))()
     st = _lib.load().elm_train(ctx.handle, arr, len(problems), C.byref(opts), res)
     if check:

@@ -20,7 +20,7 @@ class elm_problem(C.Structure):
 class elm_train_opts(C.Structure):
     _fields_ = [("precision", i32), ("max_refine", i32), ("tol_rank", dbl),
                 ("refine_tol", dbl), ("flags", i32), ("wait_limit_ns", i32),
-                ("block_split", i32), ("reserved", i32)]
+                ("block_split", i32), ("lanes", i32)]
 
 
 class elm_result(C.Structure):

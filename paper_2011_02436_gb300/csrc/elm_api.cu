@@ -6,7 +6,9 @@
 
 #include <atomic>
 #include <functional>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "elm_internal.cuh"
@@ -280,7 +282,58 @@ struct Problem {
     uint64_t wait_ns;  // bound of the tensor kernels' pipeline waits (0: default)
     bool wide;         // N < L: the branch H^+ = H^T (H H^T)^+
     int64_t block;     // > 0: the paper's block formulae, H1 = first `block` columns
+    int lanes;         // batched mixed trainings: back halves run side by side
 };
+
+// Frees a context's device buffers, events, owned stream and lanes (not the
+// object itself).
+void release_ctx(elm_ctx *ctx) {
+    cudaSetDevice(ctx->device);
+    for (elm_ctx *l : ctx->lanes) {
+        release_ctx(l);
+        delete l;
+    }
+    ctx->lanes.clear();
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->aux) cudaFree(ctx->aux);
+    if (ctx->batch) cudaFree(ctx->batch);
+    ctx->ws = ctx->aux = ctx->batch = nullptr;
+    ctx->ws_size = ctx->aux_size = ctx->batch_size = 0;
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+        ctx->copy_stream = nullptr;
+    }
+    if (ctx->xstart) cudaEventDestroy(ctx->xstart), ctx->xstart = nullptr;
+    for (auto &e : ctx->xready)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    ctx->stream = nullptr;
+}
+
+// Lane i of a context: its own non-blocking stream, workspaces and events.
+elm_ctx *lane_of(elm_ctx *ctx, size_t i) {
+    while (ctx->lanes.size() <= i) {
+        elm_ctx *l = new elm_ctx;
+        l->device = ctx->device;
+        l->sm_count = ctx->sm_count;
+        try {
+            ELM_CUDA(cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking));
+            l->own_stream = true;
+            for (auto &e : l->ev) ELM_CUDA(cudaEventCreate(&e));
+        } catch (...) {
+            release_ctx(l);
+            delete l;
+            throw;
+        }
+        ctx->lanes.push_back(l);
+    }
+    return ctx->lanes[i];
+}
 
 void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res);
 void train_wide(elm_ctx *ctx, const Problem &P, elm_result *res);
@@ -946,6 +999,82 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     mixed_back(ctx, P, res, MixedData{Td, T.ld, G, Hdf, flag, err}, 0);
 }
 
+// The back halves (factorisation, solves, refinement, and the FP64 form for
+// a problem handed over) of problems i0 .. i0+gn-1 of a batched call, on nl
+// lanes at once: one host thread per lane (this thread drives lane 0) takes
+// the next problem and runs it on the lane's own stream and workspaces, so
+// one problem's host waits and small launches overlap another's kernels.
+// Each problem's arithmetic is the serial route's, whatever lane runs it.
+// The first error stops the hand-out; the call reports it after the lanes
+// are done.  Phase times are summed over the lanes.
+void back_halves_on_lanes(elm_ctx *ctx, const std::vector<Problem> &Ps, int64_t i0, int64_t gn,
+                          const std::vector<MixedData> &data, elm_result *res, int nl) {
+    std::vector<elm_ctx *> ls((size_t)nl);
+    for (int l = 0; l < nl; l++) ls[(size_t)l] = lane_of(ctx, (size_t)l);
+    // the lanes start once the batch's hidden layers and Grams are done
+    cudaEvent_t ready = nullptr;
+    ELM_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    struct EvGuard {
+        cudaEvent_t e;
+        ~EvGuard() { cudaEventDestroy(e); }
+    } guard{ready};
+    ELM_CUDA(cudaEventRecord(ready, ctx->stream));
+    for (elm_ctx *l : ls) {
+        l->timing = ctx->timing;
+        ELM_CUDA(cudaStreamWaitEvent(l->stream, ready, 0));
+    }
+    std::atomic<int64_t> next{0};
+    std::atomic<bool> stop{false};
+    std::mutex mu;
+    int err_status = ELM_OK;
+    std::string err_msg;
+    auto work = [&](elm_ctx *lc) {
+        if (cudaSetDevice(lc->device) != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (err_status == ELM_OK) err_status = ELM_ERR_CUDA, err_msg = "cudaSetDevice failed";
+            stop = true;
+            return;
+        }
+        for (;;) {
+            if (stop.load()) return;
+            const int64_t j = next.fetch_add(1);
+            if (j >= gn) return;
+            elm_result r{};
+            try {
+                mark(lc, 2);
+                mixed_back(lc, Ps[i0 + j], &r, data[(size_t)j], 2);
+            } catch (const ElmError &e) {
+                r.status = e.status;
+                std::lock_guard<std::mutex> lk(mu);
+                if (err_status == ELM_OK) err_status = e.status, err_msg = e.msg;
+                stop = true;
+            } catch (...) {
+                r.status = ELM_ERR_CUDA;
+                std::lock_guard<std::mutex> lk(mu);
+                if (err_status == ELM_OK) err_status = ELM_ERR_CUDA, err_msg = "lane failed";
+                stop = true;
+            }
+            if (res) res[i0 + j] = r;
+        }
+    };
+    std::vector<std::thread> th;
+    try {
+        for (int l = 1; l < nl; l++) th.emplace_back(work, ls[(size_t)l]);
+    } catch (...) {
+        stop = true;   // no thread for this lane: the running ones finish
+    }
+    work(ls[0]);
+    for (auto &t : th) t.join();
+    for (elm_ctx *l : ls) {
+        ELM_CUDA(cudaStreamSynchronize(l->stream));
+        for (int i = 0; i < ELM_NUM_PHASES; i++) {
+            ctx->phase_ms[i] += l->phase_ms[i];
+            l->phase_ms[i] = 0.0;
+        }
+    }
+    if (err_status != ELM_OK) throw ElmError(err_status, err_msg);
+}
+
 // Several mixed-form problems: their hidden layers and Grams as one
 // tensor-core launch each (the problems' data side by side in the batch
 // buffer, in groups that fit half of the free device memory), then each
@@ -1034,17 +1163,22 @@ void train_batch_mixed(elm_ctx *ctx, const std::vector<Problem> &Ps, elm_result 
                              ctx->timing ? ctx->ev[1] : nullptr);
         mark(ctx, 2);
         collect_phases(ctx, 0, 2);
-        for (int64_t j = 0; j < gn; j++) {
-            elm_result r{};
-            mark(ctx, 2);
-            try {
-                mixed_back(ctx, Ps[i0 + j], &r, data[j], 2);
-            } catch (const ElmError &e) {
-                r.status = e.status;
+        const int nl = (int)(Ps[i0].lanes < gn ? Ps[i0].lanes : gn);
+        if (nl > 1) {
+            back_halves_on_lanes(ctx, Ps, i0, gn, data, res, nl);
+        } else {
+            for (int64_t j = 0; j < gn; j++) {
+                elm_result r{};
+                mark(ctx, 2);
+                try {
+                    mixed_back(ctx, Ps[i0 + j], &r, data[j], 2);
+                } catch (const ElmError &e) {
+                    r.status = e.status;
+                    if (res) res[i0 + j] = r;
+                    throw;
+                }
                 if (res) res[i0 + j] = r;
-                throw;
             }
-            if (res) res[i0 + j] = r;
         }
         i0 = i1;
     }
@@ -1210,21 +1344,7 @@ int elm_create(elm_ctx **out, int device, void *stream) {
 
 int elm_destroy(elm_ctx *ctx) {
     if (!ctx) return ELM_OK;
-    cudaSetDevice(ctx->device);
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    else cudaDeviceSynchronize();
-    if (ctx->ws) cudaFree(ctx->ws);
-    if (ctx->aux) cudaFree(ctx->aux);
-    if (ctx->batch) cudaFree(ctx->batch);
-    for (auto &e : ctx->ev)
-        if (e) cudaEventDestroy(e);
-    if (ctx->copy_stream) {
-        cudaStreamSynchronize(ctx->copy_stream);
-        cudaStreamDestroy(ctx->copy_stream);
-    }
-    if (ctx->xstart) cudaEventDestroy(ctx->xstart);
-    for (auto &e : ctx->xready)
-        if (e) cudaEventDestroy(e);
+    release_ctx(ctx);
     delete ctx;
     return ELM_OK;
 }
@@ -1361,6 +1481,7 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
         require(o.precision == ELM_PREC_FP64 || o.precision == ELM_PREC_MIXED ||
                     o.precision == ELM_PREC_FP64_TC, "precision");
         require(o.block_split >= 0, "block_split < 0");
+        require(o.lanes >= 0 && o.lanes <= ELM_MAX_LANES, "lanes");
         for (int64_t i = 0; i < count; i++) {
             const elm_problem &p = probs[i];
             check_dims(p.N, p.n, p.ldx, p.L, p.ldw);
@@ -1398,6 +1519,7 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
             // N x N Gram
             P.wide = probs[i].N < probs[i].L;
             P.block = o.block_split;
+            P.lanes = o.lanes > 0 ? o.lanes : 4;
             if (P.block > 0) {                 // the paper's block route: FP64 rules
                 P.tau = P.tau64 = o.tol_rank > 0.0 ? o.tol_rank : tau64;
                 if (o.max_refine < 0) P.max_refine = 2;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "elm.h"
 
@@ -79,6 +80,10 @@ struct elm_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t xstart = nullptr;
     cudaEvent_t xready[8] = {};
+    // batched mixed trainings: sub-contexts (own stream and workspaces) that
+    // run problems' factorisations, solves and refinements side by side
+    std::vector<elm_ctx *> lanes;
+    bool own_stream = false;   // a lane's stream, created and destroyed with it
 };
 
 // ---------------------------------------------------------------- kernels

@@ -19,6 +19,9 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "df_arith.cuh"
 #include "elm_internal.cuh"
 
@@ -1175,10 +1178,19 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
     }
 }
 
-int g_cluster = 0;  // chosen cluster size (per process; devices are alike)
+// chosen cluster size (per process; devices are alike); the first caller
+// probes under the lock, host threads of batched trainings share the result
+std::atomic<int> g_cluster{0};
+std::mutex g_cluster_mu;
+// largest dynamic shared memory of a panel launch (panel_geometry's budget);
+// the kernels' attribute is set to it once, so concurrent launches of
+// different sizes never lower it under one another
+constexpr size_t PANEL_SMEM_MAX = 200 * 1024 + 64;
 
 int pick_cluster(size_t smem_for16, size_t smem_for8) {
-    if (g_cluster) return g_cluster;
+    if (int c = g_cluster.load()) return c;
+    std::lock_guard<std::mutex> lk(g_cluster_mu);
+    if (int c = g_cluster.load()) return c;
     cudaFuncSetAttribute(panel_kernel<1, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     int best = 8;
     for (int cs : {16, 8}) {
@@ -1202,7 +1214,7 @@ int pick_cluster(size_t smem_for16, size_t smem_for8) {
         }
         cudaGetLastError();
     }
-    g_cluster = best;
+    g_cluster.store(best);
     return best;
 }
 
@@ -1263,9 +1275,10 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                      : (wmax <= FT ? panel_kernel<1, false>
                         : wmax <= 2 * FT ? panel_kernel<2, false>
                         : wmax <= 4 * FT ? panel_kernel<4, false> : panel_kernel<8, false>);
+    if (smem > PANEL_SMEM_MAX) throw ElmError(ELM_ERR_UNSUPPORTED, "panel shared memory");
     cudaFuncSetAttribute(kpanel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     ELM_CUDA(cudaFuncSetAttribute(kpanel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+                                  (int)PANEL_SMEM_MAX));
 
     ELM_CUDA(cudaMemsetAsync(w.st, 0, sizeof(FactorState), s));
     ELM_CUDA(cudaMemsetAsync(w.Rrow, 0, sizeof(double) * L * L, s));
@@ -1322,15 +1335,17 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     ELM_CHECK_LAUNCH();
 }
 
-static int g_tcluster = 0;
+static std::atomic<int> g_tcluster{0};
+static std::mutex g_tcluster_mu;
+constexpr size_t TRSM_SMEM_MAX = 200 * 1024;   // trsm_launch's budget
 
 template <bool REV, int CB>
 static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const double *Dinv,
                         int64_t r, double *B, int64_t ldb, int64_t q, int *tflag) {
     auto k = trsm_kernel<REV, CB>;
     const int64_t nblk = (r + TB_ - 1) / TB_;
-    const size_t budget = 200 * 1024;
-    int cs = g_tcluster ? g_tcluster : 16;
+    const size_t budget = TRSM_SMEM_MAX;
+    int cs = g_tcluster.load() ? g_tcluster.load() : 16;
     for (;;) {
         const int nown = (int)((nblk + cs - 1) / cs);
         // slab window: as many own blocks as fit (all of them up to r of
@@ -1347,7 +1362,8 @@ static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const doub
         if (nsl > nown) nsl = nown;
         const size_t smem = trsm_smem_bytes(nown, nsl, CB);
         cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ELM_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TRSM_SMEM_MAX));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(cs * ((q + CB - 1) / CB)));
         cfg.blockDim = dim3(FT);
@@ -1360,17 +1376,23 @@ static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const doub
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        if (!g_tcluster) {
-            int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n == 0) {
-                cudaGetLastError();
-                if (cs == 16) {
-                    cs = 8;
-                    continue;
+        if (!g_tcluster.load()) {
+            std::lock_guard<std::mutex> lk(g_tcluster_mu);
+            if (!g_tcluster.load()) {
+                int n = 0;
+                if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n == 0) {
+                    cudaGetLastError();
+                    if (cs == 16) {
+                        cs = 8;
+                        continue;
+                    }
+                    throw ElmError(ELM_ERR_CUDA, "no cluster configuration for the solve");
                 }
-                throw ElmError(ELM_ERR_CUDA, "no cluster configuration for the solve");
+                g_tcluster.store(cs);
+            } else if (g_tcluster.load() != cs) {
+                cs = g_tcluster.load();
+                continue;
             }
-            g_tcluster = cs;
         }
         const CUtensorMap tmC = make_map_f64(C, r, ldc, ldc, TB_, TB_);
         ELM_CUDA(cudaLaunchKernelEx(&cfg, k, tmC, C, ldc, Dinv, r, B, ldb, q, nown, nsl, tflag));

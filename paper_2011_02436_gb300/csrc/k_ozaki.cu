@@ -486,7 +486,7 @@ struct Walk {
 // and releases it before doing the output arithmetic, so the next tile's
 // MMAs overlap that arithmetic.
 template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI, int TMIN = 2,
-          int CHUNK = 0>
+          int CHUNK = 0, bool BAT = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
 ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const __grid_constant__ OzParams P, const __grid_constant__ OzBatch B) {
@@ -511,7 +511,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     __shared__ int abort_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool batched = B.nprob > 0;
+    // a batched launch (BAT) reads each unit's parameters from global
+    // memory; a single launch reads P from the parameter space directly
+    constexpr bool batched = BAT;
     // pipeline waits use the caller's bound; the waits that only let this
     // CTA's own copies and MMAs finish before it exits keep WAIT_NS
     const uint64_t wns = batched ? B.wait_ns : P.wait_ns;
@@ -585,9 +587,10 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             Walk wk = walk_begin();
             while (!*abort && walk_next(wk, U)) {
                 int64_t m0, n0;
-                tile_coords(*U.P, U.t, m0, n0);
+                const OzParams &Pp = BAT ? *U.P : P;
+                tile_coords(Pp, U.t, m0, n0);
                 const int s_hi = U.c_hi * CHUNK_SLABS < U.nslab ? U.c_hi * CHUNK_SLABS : U.nslab;
-                const int64_t a_rows = U.P->a_rows, b_rows = U.P->b_rows;
+                const int64_t a_rows = Pp.a_rows, b_rows = Pp.b_rows;
                 for (int s = U.c_lo * CHUNK_SLABS; s < s_hi; s++, g++) {
                     const int st = (int)(g % STAGES);
                     if (g >= STAGES &&
@@ -691,7 +694,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         Unit U;
         Walk wk = walk_begin();
         while (ok && walk_next(wk, U)) {
-            const OzParams &Pu = *U.P;
+            const OzParams &Pu = BAT ? *U.P : P;
             const int64_t t = U.t;
             const int c_lo = U.c_lo, c_hi = U.c_hi;
             const bool direct = (EPI != 0) && U.nchunk == 1;
@@ -1139,16 +1142,16 @@ __global__ void t_digits_kernel(const double *__restrict__ T, int64_t ldt, int64
 
 // ------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // initialised once, thread-safely (a throwing initialiser is retried)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         ELM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
                                                   cudaEnableDefault, &q));
         if (!p || q != cudaDriverEntryPointSuccess)
             throw ElmError(ELM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
     return fn;
 }
 
@@ -1170,26 +1173,27 @@ CUtensorMap make_map(const __nv_bfloat16 *base, int64_t rows, int64_t K, int box
 }
 
 int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {
+        int dev = 0, n = 0;
         ELM_CUDA(cudaGetDevice(&dev));
-        ELM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    }
+        ELM_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        return n;
+    }();
     return sms;
 }
 
 // Dynamic shared memory of an ozaki_kernel instance, set up once per process.
-template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI, int TMIN = 2, int CHUNK = 0>
+template <int PA, int PB, int TMAX, int STAGES, int DBITS, int EPI, int TMIN = 2, int CHUNK = 0,
+          bool BAT = false>
 size_t ozaki_smem() {
     constexpr size_t stage = (size_t)PA * BM * SK * 2 + (size_t)PB * BN * SK * 2;
     const size_t smem = STAGES * stage + 1024;
-    static bool attr = false;
-    if (!attr) {
-        ELM_CUDA(cudaFuncSetAttribute(ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI, TMIN, CHUNK>,
+    static const bool attr = [&] {   // once per variant, thread-safely
+        ELM_CUDA(cudaFuncSetAttribute(ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI, TMIN, CHUNK, BAT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     return smem;
 }
 
@@ -1453,7 +1457,7 @@ void launch_ozaki_batch(cudaStream_t s, const std::vector<OzParams> &ps,
     const int64_t count = (int64_t)ps.size();
     const int64_t units = first[count];
     if (units <= 0) return;
-    const size_t smem = ozaki_smem<PA, PB, TMAX, STAGES, DBITS, EPI>();
+    const size_t smem = ozaki_smem<PA, PB, TMAX, STAGES, DBITS, EPI, 2, 0, true>();
     // device copies: maps (64-byte aligned), parameters, unit offsets
     CUtensorMap *dmaps = reinterpret_cast<CUtensorMap *>(dev);
     const size_t mbytes = (sizeof(CUtensorMap) * maps.size() + 255) / 256 * 256;
@@ -1476,8 +1480,8 @@ void launch_ozaki_batch(cudaStream_t s, const std::vector<OzParams> &ps,
     const int64_t sms = sm_count();
     const int64_t grid = units < sms ? units : sms;
     CUtensorMap none{};
-    ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI><<<(unsigned)grid, NTHREADS, smem, s>>>(
-        none, none, OzParams{}, B);
+    ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI, 2, 0, true><<<(unsigned)grid, NTHREADS, smem,
+                                                                 s>>>(none, none, OzParams{}, B);
     ELM_CHECK_LAUNCH();
 }
 

@@ -185,10 +185,11 @@ def workload_rank_deficient(**kw):
 
 def workload_batched(count: int = 128, N_range=(5000, 50000),
                      L_range=(100, 3000), d_choices=(16, 54, 128),
-                     m_range=(2, 26), seed: int = SEED_BASE + 1000 * 4):
+                     m_range=(2, 26), seed: int = SEED_BASE + 1000 * 4, only=None):
     """`count` independent uneven problems: N uniform in N_range, d in
     d_choices, L uniform in L_range, sigmoid/tanh 50/50, m one-hot classes
-    uniform in m_range, X U[0,1] FP32."""
+    uniform in m_range, X U[0,1] FP32.  only: indices of the problems to
+    generate (the same bytes as in the full list)."""
     Ns = integers(seed + 1, count, *N_range)
     ds = np.array(d_choices)[integers(seed + 2, count, 0, len(d_choices) - 1)]
     Ls = integers(seed + 3, count, *L_range)
@@ -197,7 +198,7 @@ def workload_batched(count: int = 128, N_range=(5000, 50000),
     return [make_problem(int(Ns[i]), int(ds[i]), int(Ls[i]), int(ms[i]),
                          act=int(acts[i]), x_dtype=np.float32,
                          seed=seed + 100 * (i + 1))
-            for i in range(count)]
+            for i in (range(count) if only is None else only)]
 
 
 def workload_gina_shaped(L: int = 2000, **kw):

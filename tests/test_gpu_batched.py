@@ -71,3 +71,38 @@ def test_batched_wait_bound_expires_then_trains(elm, ctx):
         ref, rr, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
         assert r["status"] == 0 and r["rank"] == rr
         assert rel(pr["beta"].cpu().numpy(), ref) <= 1e-6
+
+
+LANE_CASES = [12, 108, 74, 5, 36, 91]   # kappa(H) 4.7e7 .. 1e4, L 194 .. 2687
+
+
+def test_lanes_do_not_change_results(elm, ctx):
+    """The back halves (factorisation, solves, refinement, hand-over to the
+    FP64 form) of a batched call run on several lanes at once, each with its
+    own stream, workspaces and host thread: every result is bit for bit the
+    one of a single lane, and each beta meets its bar against the oracle's
+    stored result for that problem of the batched workload."""
+    import os
+    from test_gpu_full_configs import GOLD, bar_for, digest
+    path = os.path.join(GOLD, "full_batched.npz")
+    if not os.path.exists(path):
+        pytest.skip("oracle results not written")
+    g = np.load(path)
+    ps = synth.workload_batched(only=LANE_CASES)
+    for i, p in zip(LANE_CASES, ps):
+        assert digest(p["X"]) == str(g["fp_X"][i])
+    out = {}
+    for lanes in (1, 3, 8):
+        probs = [problem(p) for p in ps]
+        res = elm.elm_train(ctx, probs, precision=elm.PREC_MIXED, lanes=lanes, check=False)
+        out[lanes] = (res, [pr["beta"].cpu().numpy() for pr in probs])
+    keys = ("status", "rank", "form", "refine_iters", "rel_update")
+    for lanes in (3, 8):
+        for r1, b1, r, b in zip(*out[1], *out[lanes]):
+            assert [r[k] for k in keys] == [r1[k] for k in keys]
+            assert np.array_equal(b, b1)
+    res, betas = out[1]
+    assert any(r["form"] == elm.FORM_MIXED_TO_FP64 for r in res)
+    for i, r, b in zip(LANE_CASES, res, betas):
+        assert r["status"] in (0, 5) and r["rank"] == int(g["rank"][i])
+        assert rel(b, g["beta_%03d" % i]) <= bar_for(g, i, 1e-6)
