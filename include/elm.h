@@ -55,9 +55,11 @@ enum { ELM_F32 = 0, ELM_F64 = 1 };               /* element type of X           
  * the tensor cores (H to about 2^-44, the Gram to about 2^-34), rank
  * decision and factorisation in double-float, FP64 solves, refinement
  * against the double-float H.  ELM_PREC_FP64_TC: the FP64 form with its
- * Gram on the tensor cores, split into eight 7-bit digits per element and
- * summed exactly (as accurate as the FP64 Gram); the mixed form hands the
- * problems its Gram cannot settle to this form. */
+ * hidden-layer products and Gram on the tensor cores, every operand element
+ * rounded once at 2^-56 of its row's power-of-two scale, split into eight
+ * 7-bit digits, and every digit pair above 2^-68 summed exactly (FP64-level
+ * products; activation, factorisation, solves and refinement in FP64); the
+ * mixed form hands the problems its Gram cannot settle to this form. */
 enum { ELM_PREC_FP64 = 0, ELM_PREC_MIXED = 1, ELM_PREC_FP64_TC = 2 };
 
 /* Largest hidden-layer width L the factorisation kernels accept. */
@@ -82,7 +84,10 @@ const char *elm_last_error(elm_ctx *ctx);
  * b: L FP64.  a: L FP64 output scales, or NULL for all ones.  act: ELM_ACT_*.
  * Ht: L x N FP64 output (ldh >= N).  precision: ELM_PREC_FP64 computes the
  * products with FP64 FMAs; ELM_PREC_MIXED with exact integer-digit slices on
- * the tensor cores (the result is FP64 to about 2^-40 absolute).
+ * the tensor cores (the result is FP64 to about 2^-40 absolute);
+ * ELM_PREC_FP64_TC with eight-digit slices on the tensor cores (X rows and W
+ * columns rounded at 2^-56 of their largest magnitude, the rest exact) and
+ * the activation in FP64.
  */
 int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n,
                int64_t ldx, const double *W, int64_t ldw, const double *b,

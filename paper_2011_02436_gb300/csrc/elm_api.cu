@@ -374,7 +374,9 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
             S = ar.take<double>(Lt * Lt);
             Z = S + L;
             lds = ldz = Lt;
-            planes = (__nv_bfloat16 *)ar.take<char>(oz_exact_planes_bytes(N, L, m));
+            // the hidden product's digit planes, then the Gram's, in one buffer
+            const size_t hb = oz_hidden_exact_bytes(N, n, L), gb = oz_exact_planes_bytes(N, L, m);
+            planes = (__nv_bfloat16 *)ar.take<char>(hb > gb ? hb : gb);
             rs = ar.take<double>(oz_pad(Lt, 128));
             rsf = ar.take<float>(oz_pad(Lt, 128));
             err = ar.take<int>(1);
@@ -401,9 +403,16 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     const double *Wd = (const double *)W.p, *bd = (const double *)b.p,
                  *ad = (const double *)a.p, *Td = (const double *)T.p;
     mark(ctx, 0);
-    // Algorithm 1 step 2: H (stored transposed)
-    hidden_f64(s, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, L, pb.act, Ht, N);
-    if (tc) transpose_f64(s, Td, N, m, T.ld, Ht + L * N, N);      // T^T below H^T
+    // Algorithm 1 step 2: H (stored transposed); ELM_PREC_FP64_TC forms the
+    // pre-activations on the tensor cores to FP64 accuracy
+    if (tc) {
+        oz_hidden_exact(s, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, L, (char *)planes, Ht, N, err,
+                        nullptr, P.wait_ns);
+        act_rows_f64(s, Ht, N, L, N, bd, ad, pb.act);
+        transpose_f64(s, Td, N, m, T.ld, Ht + L * N, N);           // T^T below H^T
+    } else {
+        hidden_f64(s, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, L, pb.act, Ht, N);
+    }
     mark(ctx, 1);
     // Eqs. 9-13: Gram blocks H^T H and H^T T
     if (tc) oz_gram_exact(s, Ht, N, N, L, m, planes, rs, rsf, S, Lt, err, nullptr, P.wait_ns);
@@ -1364,7 +1373,8 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
         require(X && W && b && Ht, "X, W, b and Ht must be non-NULL");
         require(x_dtype == ELM_F32 || x_dtype == ELM_F64, "x_dtype");
         require(act == ELM_ACT_SIGMOID || act == ELM_ACT_TANH, "act");
-        require(precision == ELM_PREC_FP64 || precision == ELM_PREC_MIXED, "precision");
+        require(precision == ELM_PREC_FP64 || precision == ELM_PREC_MIXED ||
+                    precision == ELM_PREC_FP64_TC, "precision");
         require(ldh >= N, "ldh < N");
         ELM_CUDA(cudaSetDevice(ctx->device));
         cudaStream_t s = ctx->stream;
@@ -1374,7 +1384,8 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
         __nv_bfloat16 *planes = nullptr;
         int *err = nullptr;
         OzHidWs hw{};
-        const bool mixed = precision == ELM_PREC_MIXED;
+        char *xws = nullptr;
+        const bool mixed = precision == ELM_PREC_MIXED, tc = precision == ELM_PREC_FP64_TC;
         const bool dev_out = on_device(Ht);
         with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
             Xs = stage(ar, s, X, N, n, ldx, xsz);
@@ -1388,6 +1399,10 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
                 err = ar.take<int>(1);
                 hw = oz_hid_carve(ar, N, n, L, 0);
             }
+            if (tc) {
+                xws = ar.take<char>(oz_hidden_exact_bytes(N, n, L));
+                err = ar.take<int>(1);
+            }
         });
         const int64_t ldo = dev_out ? ldh : N;
         if (mixed) {
@@ -1395,6 +1410,15 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
             oz_hidden(s, hw, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld,
                       (const double *)bs.p, (const double *)as.p, act, L, 0, planes, hs, out, ldo,
                       err);
+            int terr = 0;
+            ELM_CUDA(cudaMemcpyAsync(&terr, err, sizeof terr, cudaMemcpyDeviceToHost, s));
+            ELM_CUDA(cudaStreamSynchronize(s));
+            if (terr) throw ElmError(ELM_ERR_TIMEOUT, "tensor-core kernel wait expired");
+        } else if (tc) {
+            ELM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+            oz_hidden_exact(s, Xs.p, x_dtype, N, n, Xs.ld, (const double *)Ws.p, Ws.ld, L, xws,
+                            out, ldo, err, nullptr);
+            act_rows_f64(s, out, ldo, L, N, (const double *)bs.p, (const double *)as.p, act);
             int terr = 0;
             ELM_CUDA(cudaMemcpyAsync(&terr, err, sizeof terr, cudaMemcpyDeviceToHost, s));
             ELM_CUDA(cudaStreamSynchronize(s));

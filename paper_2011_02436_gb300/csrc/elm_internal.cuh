@@ -94,6 +94,11 @@ void hidden_f64(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n,
                 int64_t ldx, const double *W, int64_t ldw, const double *b,
                 const double *a, int64_t L, int act, double *Ht, int64_t ldh);
 
+// Ht[j, i] = a_j g(Ht[j, i] + b_j) in place for j < L, i < N (FP64): the
+// activation of pre-activations formed elsewhere.
+void act_rows_f64(cudaStream_t s, double *Ht, int64_t ldh, int64_t L, int64_t N, const double *b,
+                  const double *a, int act);
+
 // FP64 Gram of the augmented rows [Ht; T^T]: S = H^T H (full, both
 // triangles), Z = H^T T.  part: workspace of gram_f64_parts(...) doubles.
 int gram_f64_nsplit(int64_t L, int64_t m, int64_t N, int sms);
@@ -280,6 +285,17 @@ size_t oz_exact_planes_bytes(int64_t N, int64_t L, int64_t m);
 void oz_gram_exact(cudaStream_t s, const double *A, int64_t lda, int64_t N, int64_t L, int64_t m,
                    __nv_bfloat16 *planes, double *hs, float *hsf, double *G, int64_t ldg, int *err,
                    int32_t *nonfinite, uint64_t wait_ns = 0);
+// Pre-activations Ht[j, i] = sum_k X[i, k] W[k, j] (L x N, ldh) on the
+// tensor cores, accurate to FP64 level: both operands split into eight 7-bit
+// digits on a 2^-55 grid of their row's (X) or column's (W) power-of-two
+// scale, every digit pair of weight above 2^-68 summed exactly, in two
+// launches.  ws: oz_hidden_exact_bytes(N, n, L) bytes of device scratch;
+// *err set on a device-side timeout, *nonfinite (if given) |= 1 when X or W
+// holds a NaN or an infinity.
+size_t oz_hidden_exact_bytes(int64_t N, int64_t n, int64_t L);
+void oz_hidden_exact(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n, int64_t ldx,
+                     const double *W, int64_t ldw, int64_t L, char *ws, double *Ht, int64_t ldh,
+                     int *err, int32_t *nonfinite, uint64_t wait_ns = 0);
 // Several problems' hidden layers (mixed form, H as double-float pairs and
 // the Gram digit planes) and Grams [H^T H, H^T T] as one tensor-core launch
 // each.  Every item carries its own inputs (device pointers), scratch (hw,

@@ -610,6 +610,17 @@ __global__ void sub_rows_kernel(const double *__restrict__ A, int64_t lda,
 
 // B (cols x rows, ldb) = A^T for A (rows x cols, lda): 32 x 32 tiles through
 // shared memory, both sides coalesced.
+// Ht[j, i] = a_j g(Ht[j, i] + b_j): row j = blockIdx.y (the same
+// expression as the FP64 hidden layer's epilogue)
+__global__ void act_rows_f64_kernel(double *__restrict__ Ht, int64_t ldh, int64_t N,
+                                    const double *__restrict__ b, const double *__restrict__ a,
+                                    int act) {
+    const int64_t j = blockIdx.y, i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double aj = a ? a[j] : 1.0;
+    Ht[j * ldh + i] = aj * act_f64(Ht[j * ldh + i] + b[j], act);
+}
+
 __global__ void transpose_f64_kernel(const double *__restrict__ A, int64_t rows, int64_t cols,
                                      int64_t lda, double *__restrict__ B, int64_t ldb) {
     __shared__ double t[32][33];
@@ -1024,6 +1035,14 @@ void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, d
 void sub_rows(cudaStream_t s, const double *A, int64_t lda, const double *B, int64_t rows,
               int64_t m, double *out) {
     sub_rows_kernel<<<blocks_for(rows * m), 256, 0, s>>>(A, lda, B, rows, m, out);
+    ELM_CHECK_LAUNCH();
+}
+
+void act_rows_f64(cudaStream_t s, double *Ht, int64_t ldh, int64_t L, int64_t N, const double *b,
+                  const double *a, int act) {
+    if (L <= 0 || N <= 0) return;
+    const dim3 g((unsigned)((N + 255) / 256), (unsigned)L);
+    act_rows_f64_kernel<<<g, 256, 0, s>>>(Ht, ldh, N, b, a, act);
     ELM_CHECK_LAUNCH();
 }
 

@@ -1444,6 +1444,31 @@ void oz_gram_exact(cudaStream_t s, const double *A, int64_t lda, int64_t N, int6
     launch_ozaki<8, 8, 9, 2, EX_BITS, 0, 6, 16>(s, planes, planes, P, ntiles);
 }
 
+// ------------------------------------------- FP64-accurate hidden product
+// Pre-activations of the FP64 form on the tensor cores: W^T (one row per
+// neuron) and X (one row per sample) split like the rows of the exact Gram
+// (EX_PH digits of EX_BITS bits on a 2^-55 grid of the row's power-of-two
+// scale); the rectangular tile walk of the hidden layer, and the exact
+// Gram's two bands of diagonals (2-5, then 6-9 added onto the FP64 sums).
+struct OzExactHidWs {
+    double *wt;                    // W^T, L x n
+    __nv_bfloat16 *wp, *xp;        // digit planes of W^T and X
+    double *wsc, *xsc;             // row scales
+    float *wscf, *xscf;
+};
+OzExactHidWs oz_hidden_exact_carve(Arena &ar, int64_t N, int64_t n, int64_t L) {
+    const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L, BM);
+    OzExactHidWs w;
+    w.wt = ar.take<double>(L * n);
+    w.wp = ar.take<__nv_bfloat16>(EX_PH * Lp * nK);
+    w.xp = ar.take<__nv_bfloat16>(EX_PH * Np * nK);
+    w.wsc = ar.take<double>(Lp);
+    w.xsc = ar.take<double>(Np);
+    w.wscf = ar.take<float>(Lp);
+    w.xscf = ar.take<float>(Np);
+    return w;
+}
+
 // ------------------------------------------------------------ batched launch
 // The hidden layer and the Gram of several problems as one launch each: the
 // slicing kernels run per problem, then one persistent grid walks the tiles
@@ -1486,6 +1511,57 @@ void launch_ozaki_batch(cudaStream_t s, const std::vector<OzParams> &ps,
 }
 
 }  // namespace
+
+size_t oz_hidden_exact_bytes(int64_t N, int64_t n, int64_t L) {
+    Arena m;
+    oz_hidden_exact_carve(m, N, n, L);
+    return m.used;
+}
+
+void oz_hidden_exact(cudaStream_t s, const void *X, int xdt, int64_t N, int64_t n, int64_t ldx,
+                     const double *W, int64_t ldw, int64_t L, char *ws, double *Ht, int64_t ldh,
+                     int *err, int32_t *nonfinite, uint64_t wait_ns) {
+    if (N <= 0 || L <= 0) return;
+    const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L, BM);
+    Arena ar;
+    ar.base = ws;
+    ar.cap = oz_hidden_exact_bytes(N, n, L);
+    const OzExactHidWs w = oz_hidden_exact_carve(ar, N, n, L);
+    transpose_f64(s, W, n, L, ldw, w.wt, n);
+    digits_rows_kernel<EX_PH, EX_BITS, double><<<(unsigned)((Lp + 7) / 8), 256, 0, s>>>(
+        w.wt, L, n, n, Lp, nK, w.wp, w.wsc, w.wscf, nonfinite, 0, Lp);
+    ELM_CHECK_LAUNCH();
+    if (xdt == ELM_F64)
+        digits_rows_kernel<EX_PH, EX_BITS, double><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
+            (const double *)X, N, n, ldx, Np, nK, w.xp, w.xsc, w.xscf, nonfinite, 0, Np);
+    else
+        digits_rows_kernel<EX_PH, EX_BITS, float><<<(unsigned)((Np + 7) / 8), 256, 0, s>>>(
+            (const float *)X, N, n, ldx, Np, nK, w.xp, w.xsc, w.xscf, nonfinite, 0, Np);
+    ELM_CHECK_LAUNCH();
+    const int64_t ntiles = (Lp / BM) * (Np / BN);
+    OzParams P{};
+    P.whole = ntiles;
+    P.part = nullptr;
+    P.a_rows = Lp;
+    P.b_rows = Np;
+    P.K = nK;
+    P.m_valid = L;
+    P.n_valid = N;
+    P.ntile_m = Lp / BM;
+    P.n_base = 0;
+    P.gram = 0;
+    P.out_scale = ldexp(1.0, -2 * (EX_BITS - 1));
+    P.rscale = w.wsc;
+    P.cscale = w.xsc;
+    P.out = Ht;
+    P.ldo = ldh;
+    P.err = err;
+    P.wait_ns = wait_ns;
+    P.accumulate = 0;
+    launch_ozaki<4, 4, 5, 3, EX_BITS, 0, 2, 0>(s, w.wp, w.xp, P, ntiles);
+    P.accumulate = 1;
+    launch_ozaki<8, 8, 9, 2, EX_BITS, 0, 6, 16>(s, w.wp, w.xp, P, ntiles);
+}
 
 size_t oz_batch_bytes(int64_t count) {
     const size_t mbytes = (sizeof(CUtensorMap) * 2 * count + 255) / 256 * 256;
