@@ -33,8 +33,15 @@ namespace {
 using namespace df;
 
 constexpr int FT = 256;       // threads per CTA in the panel / solves
-constexpr int MAXNB = 32;     // largest panel width of the data structures
-constexpr int PNB = 24;       // largest panel width the pivot kernel runs
+constexpr int MAXNB = 64;     // largest panel width of the data structures
+constexpr int PNB = 24;       // largest panel width of the FP64 pivot kernel
+// largest panel width of the double-float pivot kernel: a wider panel costs
+// each pivot a longer dot product with the pivot column but saves trailing
+// passes over the active matrix (factor phase of the sparse-pixel Gram,
+// L = 2000: 5.62 / 5.21 / 5.16 / 5.42 ms at widths 16 / 24 / 32 / 48; of the
+// rank-deficient one, L = 6000: 41.4 / 36.7 / 35.3 / 35.1 ms)
+constexpr int PNB_DF = 32;
+constexpr int TSTAGE = 32;    // panel rows staged at a time by the trailing updates
 constexpr int MAXCPT = 8;     // panel columns per thread: wmax <= MAXCPT * FT
 
 // Order key of a double as an unsigned integer (larger key = larger value,
@@ -640,19 +647,13 @@ trailing_kernel(const double *__restrict__ A, double *__restrict__ An, int64_t l
     const int64_t I = t - J * (J + 1) / 2;
     const int64_t r0 = J * TT, c0 = I * TT;
     if (r0 >= Lr) return;
-    __shared__ double Pr[MAXNB][TT + 1];
-    __shared__ double Pc[MAXNB][TT + 1];
+    __shared__ double Pr[TSTAGE][TT + 1];
+    __shared__ double Pc[TSTAGE][TT + 1];
     __shared__ int32_t rr_[TT], rc_[TT];
     if (threadIdx.x < TT) {
         int64_t x = r0 + threadIdx.x, y = c0 + threadIdx.x;
         rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
         rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < MAXNB * TT; e += 256) {
-        int tt = e / TT, k = e % TT;
-        Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : 0.0;
-        Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : 0.0;
     }
     __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -664,13 +665,23 @@ trailing_kernel(const double *__restrict__ A, double *__restrict__ An, int64_t l
             int a = rr_[ty + 16 * p], b = rc_[tx + 16 * q];
             acc[p][q] = (a >= 0 && b >= 0) ? A[(int64_t)a * lda + b] : 0.0;
         }
-    for (int tt = 0; tt < steps; tt++) {
-        const double u0 = Pr[tt][ty], u1 = Pr[tt][ty + 16];
-        const double v0 = Pc[tt][tx], v1 = Pc[tt][tx + 16];
-        acc[0][0] = fma(-u0, v0, acc[0][0]);
-        acc[0][1] = fma(-u0, v1, acc[0][1]);
-        acc[1][0] = fma(-u1, v0, acc[1][0]);
-        acc[1][1] = fma(-u1, v1, acc[1][1]);
+    for (int t0 = 0; t0 < steps; t0 += TSTAGE) {   // panel rows TSTAGE at a time
+        const int nt = steps - t0 < TSTAGE ? steps - t0 : TSTAGE;
+        if (t0 > 0) __syncthreads();
+        for (int e = threadIdx.x; e < TSTAGE * TT; e += 256) {
+            int tt = e / TT, k = e % TT;
+            Pr[tt][k] = (tt < nt && rr_[k] >= 0) ? P[(int64_t)(t0 + tt) * ldp + rr_[k]] : 0.0;
+            Pc[tt][k] = (tt < nt && rc_[k] >= 0) ? P[(int64_t)(t0 + tt) * ldp + rc_[k]] : 0.0;
+        }
+        __syncthreads();
+        for (int tt = 0; tt < nt; tt++) {
+            const double u0 = Pr[tt][ty], u1 = Pr[tt][ty + 16];
+            const double v0 = Pc[tt][tx], v1 = Pc[tt][tx + 16];
+            acc[0][0] = fma(-u0, v0, acc[0][0]);
+            acc[0][1] = fma(-u0, v1, acc[0][1]);
+            acc[1][0] = fma(-u1, v0, acc[1][0]);
+            acc[1][1] = fma(-u1, v1, acc[1][1]);
+        }
     }
 #pragma unroll
     for (int p = 0; p < 2; p++) {
@@ -718,19 +729,13 @@ trailing_df_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     const int64_t I = t - J * (J + 1) / 2;
     const int64_t r0 = J * TT, c0 = I * TT;
     if (r0 >= Lr) return;
-    __shared__ F2 Pr[MAXNB][TT + 1];
-    __shared__ F2 Pc[MAXNB][TT + 1];
+    __shared__ F2 Pr[TSTAGE][TT + 1];
+    __shared__ F2 Pc[TSTAGE][TT + 1];
     __shared__ int32_t rr_[TT], rc_[TT];
     if (threadIdx.x < TT) {
         int64_t x = r0 + threadIdx.x, y = c0 + threadIdx.x;
         rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
         rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < MAXNB * TT; e += 256) {
-        int tt = e / TT, k = e % TT;
-        Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : F2{0.f, 0.f};
-        Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : F2{0.f, 0.f};
     }
     __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -744,13 +749,25 @@ trailing_df_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
             ah[p][q] = v.h;
             al[p][q] = v.l;
         }
-    for (int tt = 0; tt < steps; tt++) {
-        const F2 u0 = Pr[tt][ty], u1 = Pr[tt][ty + 16];
-        const F2 v0 = Pc[tt][tx], v1 = Pc[tt][tx + 16];
-        df_sub_prod(ah[0][0], al[0][0], u0, v0);
-        df_sub_prod(ah[0][1], al[0][1], u0, v1);
-        df_sub_prod(ah[1][0], al[1][0], u1, v0);
-        df_sub_prod(ah[1][1], al[1][1], u1, v1);
+    for (int t0 = 0; t0 < steps; t0 += TSTAGE) {   // panel rows TSTAGE at a time
+        const int nt = steps - t0 < TSTAGE ? steps - t0 : TSTAGE;
+        if (t0 > 0) __syncthreads();
+        for (int e = threadIdx.x; e < TSTAGE * TT; e += 256) {
+            int tt = e / TT, k = e % TT;
+            Pr[tt][k] = (tt < nt && rr_[k] >= 0) ? P[(int64_t)(t0 + tt) * ldp + rr_[k]]
+                                                 : F2{0.f, 0.f};
+            Pc[tt][k] = (tt < nt && rc_[k] >= 0) ? P[(int64_t)(t0 + tt) * ldp + rc_[k]]
+                                                 : F2{0.f, 0.f};
+        }
+        __syncthreads();
+        for (int tt = 0; tt < nt; tt++) {
+            const F2 u0 = Pr[tt][ty], u1 = Pr[tt][ty + 16];
+            const F2 v0 = Pc[tt][tx], v1 = Pc[tt][tx + 16];
+            df_sub_prod(ah[0][0], al[0][0], u0, v0);
+            df_sub_prod(ah[0][1], al[0][1], u0, v1);
+            df_sub_prod(ah[1][0], al[1][0], u1, v0);
+            df_sub_prod(ah[1][1], al[1][1], u1, v1);
+        }
     }
 #pragma unroll
     for (int p = 0; p < 2; p++) {
@@ -789,8 +806,8 @@ trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     const int64_t I = t - J * (J + 1) / 2;
     const int64_t r0 = J * TT2 + (int64_t)blockIdx.y * TR2, c0 = I * TT2;
     if (r0 >= Lr) return;
-    __shared__ F2 Pr[PNB][TR2];
-    __shared__ F2 Pc[PNB][TT2];
+    __shared__ F2 Pr[TSTAGE][TR2];
+    __shared__ F2 Pc[TSTAGE][TT2];
     __shared__ int32_t rr_[TR2], rc_[TT2];
     if (threadIdx.x < TR2) {
         const int64_t x = r0 + threadIdx.x;
@@ -799,13 +816,6 @@ trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     if (threadIdx.x < TT2) {
         const int64_t y = c0 + threadIdx.x;
         rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < PNB * TT2; e += 128) {
-        const int tt = e / TT2, k = e % TT2;
-        Pc[tt][k] = (tt < steps && rc_[k] >= 0) ? P[(int64_t)tt * ldp + rc_[k]] : F2{0.f, 0.f};
-        if (k < TR2)
-            Pr[tt][k] = (tt < steps && rr_[k] >= 0) ? P[(int64_t)tt * ldp + rr_[k]] : F2{0.f, 0.f};
     }
     __syncthreads();
     // thread (ty, tx) owns rows ty + 8 p and columns tx + 16 q, p, q < 4
@@ -820,17 +830,28 @@ trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
             ah[p][q] = v.h;
             al[p][q] = v.l;
         }
-    for (int tt = 0; tt < steps; tt++) {
-        F2 u[4], w[4];
-#pragma unroll
-        for (int p = 0; p < 4; p++) {
-            u[p] = Pr[tt][ty + 8 * p];
-            w[p] = Pc[tt][tx + 16 * p];
+    for (int t0 = 0; t0 < steps; t0 += TSTAGE) {   // panel rows TSTAGE at a time
+        const int nt = steps - t0 < TSTAGE ? steps - t0 : TSTAGE;
+        if (t0 > 0) __syncthreads();
+        for (int e = threadIdx.x; e < TSTAGE * TT2; e += 128) {
+            const int tt = e / TT2, k = e % TT2;
+            const int64_t row = (int64_t)(t0 + tt) * ldp;
+            Pc[tt][k] = (tt < nt && rc_[k] >= 0) ? P[row + rc_[k]] : F2{0.f, 0.f};
+            if (k < TR2) Pr[tt][k] = (tt < nt && rr_[k] >= 0) ? P[row + rr_[k]] : F2{0.f, 0.f};
         }
+        __syncthreads();
+        for (int tt = 0; tt < nt; tt++) {
+            F2 u[4], w[4];
 #pragma unroll
-        for (int p = 0; p < 4; p++)
+            for (int p = 0; p < 4; p++) {
+                u[p] = Pr[tt][ty + 8 * p];
+                w[p] = Pc[tt][tx + 16 * p];
+            }
 #pragma unroll
-            for (int q = 0; q < 4; q++) df_sub_prod(ah[p][q], al[p][q], u[p], w[q]);
+            for (int p = 0; p < 4; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) df_sub_prod(ah[p][q], al[p][q], u[p], w[q]);
+        }
     }
 #pragma unroll
     for (int p = 0; p < 4; p++) {
@@ -1218,11 +1239,12 @@ int pick_cluster(size_t smem_for16, size_t smem_for8) {
     return best;
 }
 
-void panel_geometry(int64_t L, int cs, int *nb, int64_t *wmax, size_t *smem) {
+void panel_geometry(int64_t L, int cs, int *nb, int64_t *wmax, size_t *smem, bool df) {
     *wmax = (L + cs - 1) / cs;
     const size_t budget = 200 * 1024;
     int64_t fit = (int64_t)((budget - (size_t)(*wmax) * 16) / ((size_t)(*wmax) * 8));
-    int b = (int)(fit < PNB ? fit : PNB);
+    const int nbmax = df ? PNB_DF : PNB;
+    int b = (int)(fit < nbmax ? fit : nbmax);
     if (b < 1) b = 1;
     *nb = b;
     *smem = (size_t)b * (*wmax) * 8 + (size_t)(*wmax) * 16 + 64;
@@ -1260,13 +1282,13 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     int nb16, nb8;
     int64_t w16, w8;
     size_t sm16, sm8;
-    panel_geometry(L, 16, &nb16, &w16, &sm16);
-    panel_geometry(L, 8, &nb8, &w8, &sm8);
+    panel_geometry(L, 16, &nb16, &w16, &sm16, df);
+    panel_geometry(L, 8, &nb8, &w8, &sm8, df);
     const int cs = pick_cluster(sm16, sm8);
     int nb;
     int64_t wmax;
     size_t smem;
-    panel_geometry(L, cs, &nb, &wmax, &smem);
+    panel_geometry(L, cs, &nb, &wmax, &smem, df);
     if (wmax > (int64_t)MAXCPT * FT) throw ElmError(ELM_ERR_UNSUPPORTED, "L too large for the panel");
     // columns per thread, as a compile-time count
     auto kpanel = df ? (wmax <= FT ? panel_kernel<1, true>
