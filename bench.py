@@ -76,9 +76,9 @@ def peaks():
 
 
 # DRAM bytes (read + write) of one Gram tensor-kernel launch per sample row,
-# from an ncu capture of the same kernel at 20000 rows (745.3 MB); the launch
+# from an ncu capture of the same kernel at 20000 rows (745.5 MB); the launch
 # streams the digit planes, whose size is proportional to the rows.
-GRAM_DRAM_BYTES_PER_ROW = (720.571904e6 + 24.740352e6) / 20000
+GRAM_DRAM_BYTES_PER_ROW = (720.844544e6 + 24.663040e6) / 20000
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
@@ -504,7 +504,7 @@ def run_native(args):
             roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16"], unit="TFLOP/s",
                         frac=achieved / pk["bf16"], traffic=GRAM_DRAM_BYTES_PER_ROW * N_all,
                         traffic_source="ncu capture of the same kernel at 20000 rows "
-                                       "(745.3 MB), scaled by the rows",
+                                       "(745.5 MB), scaled by the rows",
                         kernel="ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
                         peak_source="%s bf16 dense burst" % pk["source"],
                         issued_tflops=issued / (ph_ms["gram"] * 1e-3) / 1e12,
