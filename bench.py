@@ -247,7 +247,8 @@ def run_reference(args):
 
 
 WORKLOADS = {
-    "sparse_pixels": (lambda rows: [synth.workload_sparse_pixels(N=rows)], WORKLOAD["workload"]),
+    "sparse_pixels": (lambda rows: [synth.workload_sparse_pixels(N=rows or WORKLOAD["N"])],
+                      WORKLOAD["workload"]),
     "small": (lambda rows: [synth.workload_small_fp64()],
               "small ELM: X 2000x16 U[0,1] FP64, L=200 sigmoid (180 unique + 20 duplicates, "
               "rank 180), 4 one-hot classes"),
@@ -257,7 +258,7 @@ WORKLOADS = {
     "batched": (lambda rows: synth.workload_batched(),
                 "batched uneven ELMs: 128 problems, N in [5000,50000], d in {16,54,128}, "
                 "L in [100,3000], sigmoid/tanh, 2-26 one-hot classes"),
-    "large": (lambda rows: [synth.workload_large()],
+    "large": (lambda rows: [synth.workload_large(**({"N": rows} if rows else {}))],
               "large ELM: X 500000x128 U[-1,1] FP32, L=8000 sigmoid, 20 one-hot classes"),
     # the shape of the paper's Table 1 experiment; L from --hidden
     "gina_shaped": (lambda rows: [synth.workload_gina_shaped(L=ARGS_HIDDEN[0])],
@@ -365,7 +366,7 @@ def run_native(args):
     stream = torch.cuda.current_stream(dev)
     ctx = elm.elm_create(local, stream)
     planted = [int(p["rank"]) if p.get("rank") is not None else None for p in hosts]
-    full_rows = args.rows == WORKLOAD["N"] or args.workload != "sparse_pixels"
+    full_rows = args.rows is None or args.workload not in ("sparse_pixels", "large")
 
     def barrier():
         if ws > 1:
@@ -487,7 +488,8 @@ def run_native(args):
             gram_fl += flops_model(N, n, L, m)["gram"]
             Lp, Np = -(-(L + m) // 128) * 128, -(-N // 64) * 64
             nJ = Lp // 128
-            issued += 15 * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
+            pairs = 36 if prec == elm.PREC_FP64_TC else 15
+            issued += pairs * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
         N_all = sum(p["X"].shape[0] for p in hosts)
         if prec == elm.PREC_FP64:
             # Gram on the FP64 pipe (nominal rate; the measured peaks have no FP64 entry)
@@ -501,11 +503,19 @@ def run_native(args):
             # against the measured bf16 burst peak; the digit emulation issues 15
             # digit-pair products of the lower-triangle tiles, reported beside it
             achieved = gram_fl / (ph_ms["gram"] * 1e-3) / 1e12
+            tc = prec == elm.PREC_FP64_TC
+            # the captured DRAM traffic per row holds for the sparse-pixel
+            # workload's mixed Gram (L = 2000) only
+            captured = args.workload == "sparse_pixels" and not tc
             roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16"], unit="TFLOP/s",
-                        frac=achieved / pk["bf16"], traffic=GRAM_DRAM_BYTES_PER_ROW * N_all,
-                        traffic_source="ncu capture of the same kernel at 20000 rows "
-                                       "(745.5 MB), scaled by the rows",
-                        kernel="ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
+                        frac=achieved / pk["bf16"],
+                        traffic=GRAM_DRAM_BYTES_PER_ROW * N_all if captured else None,
+                        traffic_source=("ncu capture of the same kernel at 20000 rows "
+                                        "(745.5 MB), scaled by the rows") if captured
+                        else "no capture of this kernel at this shape",
+                        kernel=("ozaki_kernel (FP64-accurate Gram, 8 digits x 7 bits, 36 pairs "
+                                "in two launches)") if tc
+                        else "ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
                         peak_source="%s bf16 dense burst" % pk["source"],
                         issued_tflops=issued / (ph_ms["gram"] * 1e-3) / 1e12,
                         issued_frac=issued / (ph_ms["gram"] * 1e-3) / 1e12 / pk["bf16"])
@@ -680,8 +690,9 @@ def main():
     ap.add_argument("--ref-full-rows", type=int, default=WORKLOAD["N"],
                     help="rows of the one timed full training of --impl reference "
                          "(the workload's N; smaller only to test the arm)")
-    ap.add_argument("--rows", type=int, default=WORKLOAD["N"],
-                    help="rows of the sparse-pixel workload (smaller only for profiling captures)")
+    ap.add_argument("--rows", type=int, default=None,
+                    help="rows of the sparse-pixel or large workload (fewer only for profiling "
+                         "captures; the oracle check needs the full size)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sparse_pixels",
                     help="the timed workload (the default is the headline configuration)")
     ap.add_argument("--shard", choices=["none", "rows"], default="none",

@@ -1284,7 +1284,11 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     size_t sm16, sm8;
     panel_geometry(L, 16, &nb16, &w16, &sm16, df);
     panel_geometry(L, 8, &nb8, &w8, &sm8, df);
-    const int cs = pick_cluster(sm16, sm8);
+    // Up to 2048 columns (one column per thread on 8 CTAs) the double-float
+    // panel exchanges with 7 peers instead of 15: factor phase of the
+    // sparse-pixel Gram (L = 2000) 5.03 ms on 8 CTAs against 5.17 on 16; for
+    // L = 6000 the 16-CTA cluster is faster (35.2 against 38.3 ms).
+    const int cs = (df && L <= 8 * FT) ? 8 : pick_cluster(sm16, sm8);
     int nb;
     int64_t wmax;
     size_t smem;

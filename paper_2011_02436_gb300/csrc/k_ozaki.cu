@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "elm_internal.cuh"
+#include "oz_tiles.cuh"
 
 namespace elm {
 
@@ -102,12 +103,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
         }
     }
 }
-__device__ __forceinline__ void tma_2d(const CUtensorMap *tm, uint64_t *bar, void *dst, int x,
-                                       int y) {
+// one tile of a 3-D tensor map (K within a block, row, K block)
+__device__ __forceinline__ void tma_3d(const CUtensorMap *tm, uint64_t *bar, void *dst, int x,
+                                       int y, int z) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
-        "l"((uint64_t)tm), "r"(su32(bar)), "r"(x), "r"(y)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(su32(dst)),
+        "l"((uint64_t)tm), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
         : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -260,9 +262,10 @@ struct ActParams {
     const double *b, *a;    // bias and output scale (a may be NULL)
     int act;                // ELM_ACT_*
     int64_t L, m;           // hidden width; rows L .. L+m-1 belong to targets
-    __nv_bfloat16 *planes;  // Gram digit planes (GRAM_PH x Lp x Np)
-    int64_t plane_stride;   // Lp * Np
-    int64_t Np;
+    __nv_bfloat16 *planes;  // Gram digit planes: blocks of kb samples, [block][plane][row][kb]
+    int64_t plane_stride;   // Lp * kb
+    int64_t kb;             // samples per block (gram_kblk)
+    int64_t blk_stride;     // GRAM_PH * Lp * kb
     const double *hs;       // Gram row scales (pow2_ceil(a_j))
     const float4 *tab;      // sigmoid table (s0 hi/lo, s1 hi/lo) on a 2^-6 grid
     const float *csf;       // per-sample scales as floats
@@ -293,6 +296,8 @@ struct OzParams {
     uint64_t wait_ns;   // bound of each pipeline wait (0: WAIT_NS)
     int accumulate;     // EPI == 0, whole tiles: add to the output instead of storing
     int64_t n_base;     // non-Gram tiles: first B row (column) of the tile set
+    int64_t kblk;       // > 0: operand planes stored in blocks of kblk K elements
+                        // ([block][row][kblk], 3-D tensor maps); 0: one block of K
     ActParams ap;       // used when the kernel's EPI != 0
 };
 
@@ -391,7 +396,8 @@ __device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R,
             rl = r.l * (float)(1 << GRAM_BITS_);
         }
     }
-    __nv_bfloat16 *row = A.planes + m * A.Np + n0;
+    const int64_t blk = n0 / A.kb;      // n0 .. n0+7 lie in one block
+    __nv_bfloat16 *row = A.planes + blk * A.blk_stride + m * A.kb + (n0 - blk * A.kb);
 #pragma unroll
     for (int p = 0; p < GRAM_PH_; p++) {
         uint4 v;
@@ -406,12 +412,11 @@ __device__ __forceinline__ void hidden_emit8(const OzParams &P, const RowAct &R,
 __device__ __forceinline__ void tile_coords(const OzParams &P, int64_t t, int64_t &m0,
                                             int64_t &n0) {
     if (P.gram) {
-        // lower tiles: row block J has 2(J+1) column blocks of 64
-        int64_t J = (int64_t)((sqrt(4.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while (J * (J + 1) > t) J--;
-        while ((J + 1) * (J + 2) <= t) J++;
+        // lower tiles in super-blocks (oz_tiles.cuh); ntile_m is the row blocks
+        int64_t J, cb;
+        gram_tile(t, P.ntile_m, J, cb);
         m0 = J * BM;
-        n0 = (t - J * (J + 1)) * BN;
+        n0 = cb * BN;
     } else {
         m0 = (t % P.ntile_m) * BM;
         n0 = P.n_base + (t / P.ntile_m) * BN;
@@ -591,6 +596,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 tile_coords(Pp, U.t, m0, n0);
                 const int s_hi = U.c_hi * CHUNK_SLABS < U.nslab ? U.c_hi * CHUNK_SLABS : U.nslab;
                 const int64_t a_rows = Pp.a_rows, b_rows = Pp.b_rows;
+                const int kb = (int)(Pp.kblk ? Pp.kblk : Pp.K);
                 for (int s = U.c_lo * CHUNK_SLABS; s < s_hi; s++, g++) {
                     const int st = (int)(g % STAGES);
                     if (g >= STAGES &&
@@ -598,14 +604,15 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         break;
                     uint8_t *base = smem + (size_t)st * STAGE_BYTES;
                     mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+                    const int kz = (s * SK) / kb, kx = s * SK - kz * kb;   // block, offset
 #pragma unroll
                     for (int p = 0; p < PA; p++)
-                        tma_2d(U.ma, &full_bar[st], base + p * A_BYTES, s * SK,
-                               (int)(p * a_rows + m0));
+                        tma_3d(U.ma, &full_bar[st], base + p * A_BYTES, kx,
+                               (int)(p * a_rows + m0), kz);
 #pragma unroll
                     for (int q = 0; q < PB; q++)   // digit q + 1, stored in descending order
-                        tma_2d(U.mb, &full_bar[st], base + PA * A_BYTES + (PB - 1 - q) * B_BYTES,
-                               s * SK, (int)(q * b_rows + n0));
+                        tma_3d(U.mb, &full_bar[st], base + PA * A_BYTES + (PB - 1 - q) * B_BYTES,
+                               kx, (int)(q * b_rows + n0), kz);
                     issued = g + 1;
                 }
             }
@@ -1125,7 +1132,7 @@ __global__ void t_colmax_kernel(const double *__restrict__ T, int64_t ldt, int64
 // it afterwards gets the same scale (pow2_ceil is idempotent).
 template <int PD, int DBITS>
 __global__ void t_digits_kernel(const double *__restrict__ T, int64_t ldt, int64_t N, int64_t L,
-                                int64_t Lp, int64_t Np, __nv_bfloat16 *__restrict__ planes,
+                                int64_t Lp, int64_t Np, int64_t kb, __nv_bfloat16 *__restrict__ planes,
                                 double *__restrict__ hs) {
     const int64_t c = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1137,7 +1144,8 @@ __global__ void t_digits_kernel(const double *__restrict__ T, int64_t ldt, int64
     split_digits<PD, DBITS>(i < N ? T[i * ldt + c] * (1.0 / sc) : 0.0, d);
 #pragma unroll
     for (int p = 0; p < PD; p++)
-        planes[(int64_t)p * Lp * Np + (L + c) * Np + i] = __float2bfloat16_rn(d[p]);
+        planes[(i / kb) * PD * Lp * kb + ((int64_t)p * Lp + L + c) * kb + i % kb] =
+            __float2bfloat16_rn(d[p]);
 }
 
 // ------------------------------------------------------------ host side
@@ -1156,15 +1164,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2-D bf16 map over `rows` x `K` (row-major), box 32 x box_rows, 64-B swizzle.
-CUtensorMap make_map(const __nv_bfloat16 *base, int64_t rows, int64_t K, int box_rows) {
-    if (((uintptr_t)base & 15) || (K * 2) % 16)
+// 3-D bf16 map over K blocks of kb elements (kb = 0: one block of K):
+// [block][rows][kb] row-major, box 32 x box_rows x 1, 64-B swizzle.
+CUtensorMap make_map(const __nv_bfloat16 *base, int64_t rows, int64_t K, int box_rows,
+                     int64_t kb = 0) {
+    if (kb <= 0) kb = K;
+    if (((uintptr_t)base & 15) || (kb * 2) % 16 || kb % SK)
         throw ElmError(ELM_ERR_ARG, "digit planes misaligned for TMA");
     CUtensorMap m;
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(K * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)SK, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides,
+    const int64_t nblk = (K + kb - 1) / kb;
+    cuuint64_t dims[3] = {(cuuint64_t)kb, (cuuint64_t)rows, (cuuint64_t)nblk};
+    cuuint64_t strides[2] = {(cuuint64_t)(kb * 2), (cuuint64_t)(rows * kb * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)SK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)base, dims, strides,
                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1203,8 +1216,8 @@ void launch_ozaki(cudaStream_t s, const __nv_bfloat16 *A, const __nv_bfloat16 *B
     const size_t smem = ozaki_smem<PA, PB, TMAX, STAGES, DBITS, EPI, TMIN, CHUNK>();
     auto k = ozaki_kernel<PA, PB, TMAX, STAGES, DBITS, EPI, TMIN, CHUNK>;
     const int sms = sm_count();
-    CUtensorMap ma = make_map(A, PA * P.a_rows, P.K, BM);
-    CUtensorMap mb = make_map(B, PB * P.b_rows, P.K, BN);
+    CUtensorMap ma = make_map(A, PA * P.a_rows, P.K, BM, P.kblk);
+    CUtensorMap mb = make_map(B, PB * P.b_rows, P.K, BN, P.kblk);
     P.ntiles = ntiles;
     // only the Gram epilogue handles split tiles
     if (EPI != 0 || !P.part || P.whole > ntiles || P.whole < 0) P.whole = ntiles;
@@ -1255,8 +1268,18 @@ OzHidWs oz_hid_carve(Arena &ar, int64_t N, int64_t n, int64_t L, int64_t m) {
     return w;
 }
 
+// Samples per block of the Gram digit planes.  The planes are stored as
+// [block][plane][row][kb]: with one block of all N samples, a row of a plane
+// lies N * 2 bytes from the next, and for N of a few hundred thousand the
+// Gram kernel's loads of a tile's rows spread over so many pages that it
+// slows down by up to 2x (measured: 40000 samples with the rows 320K or 512K
+// samples apart, 1.23x and 1.83x the time of the rows 40K apart).
+constexpr int64_t GRAM_KBLK = 65536;
+int64_t gram_kblk(int64_t Np) { return Np > GRAM_KBLK ? GRAM_KBLK : Np; }
+
 size_t oz_gram_planes_bytes(int64_t N, int64_t L, int64_t m) {
-    return (size_t)GRAM_PH * oz_pad(L + m, BM) * oz_pad(N, BN) * 2;
+    const int64_t Np = oz_pad(N, BN), kb = gram_kblk(Np), nblk = (Np + kb - 1) / kb;
+    return (size_t)nblk * GRAM_PH * oz_pad(L + m, BM) * kb * 2;
 }
 
 // H = a g(X W + b) on the tensor cores, emitted directly as the Gram digit
@@ -1302,8 +1325,9 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
     P.ap.L = L;
     P.ap.m = m;
     P.ap.planes = planes;
-    P.ap.plane_stride = Lp * Np;
-    P.ap.Np = Np;
+    P.ap.kb = gram_kblk(Np);
+    P.ap.plane_stride = Lp * P.ap.kb;
+    P.ap.blk_stride = GRAM_PH * Lp * P.ap.kb;
     P.ap.hs = hs;
     P.ap.tab = w.tab;
     P.ap.csf = w.xsf;
@@ -1348,7 +1372,7 @@ void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_
                       s>>>(T, ldt, N, m, L, hs);
     ELM_CHECK_LAUNCH();
     t_digits_kernel<GRAM_PH, GRAM_BITS><<<dim3((unsigned)((Np + 255) / 256), (unsigned)m), 256, 0,
-                                          s>>>(T, ldt, N, L, Lp, Np, planes, hs);
+                                          s>>>(T, ldt, N, L, Lp, Np, gram_kblk(Np), planes, hs);
     ELM_CHECK_LAUNCH();
 }
 
@@ -1373,6 +1397,7 @@ void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int6
     P.a_rows = Lp;
     P.b_rows = Lp;
     P.K = Np;
+    P.kblk = gram_kblk(Np);
     P.m_valid = L + m;
     P.n_valid = L + m;
     P.ntile_m = nJ;
@@ -1623,8 +1648,9 @@ void oz_hidden_gram_batch(cudaStream_t s, const OzBatchItem *it, int64_t count, 
         P.ap.L = q.L;
         P.ap.m = q.m;
         P.ap.planes = q.planes;
-        P.ap.plane_stride = Lp * Np;
-        P.ap.Np = Np;
+        P.ap.kb = gram_kblk(Np);
+        P.ap.plane_stride = Lp * P.ap.kb;
+        P.ap.blk_stride = GRAM_PH * Lp * P.ap.kb;
         P.ap.hs = q.hs;
         P.ap.tab = w.tab;
         P.ap.csf = w.xsf;
@@ -1652,6 +1678,7 @@ void oz_hidden_gram_batch(cudaStream_t s, const OzBatchItem *it, int64_t count, 
         G.a_rows = Lp;
         G.b_rows = Lp;
         G.K = Np;
+        G.kblk = gram_kblk(Np);
         G.m_valid = q.L + q.m;
         G.n_valid = q.L + q.m;
         G.ntile_m = nJ;
@@ -1664,8 +1691,8 @@ void oz_hidden_gram_batch(cudaStream_t s, const OzBatchItem *it, int64_t count, 
         G.err = err;
         G.wait_ns = wait_ns;
         pg.push_back(G);
-        mg.push_back(make_map(q.planes, GRAM_PH * Lp, Np, BM));
-        mg.push_back(make_map(q.planes, GRAM_PH * Lp, Np, BN));
+        mg.push_back(make_map(q.planes, GRAM_PH * Lp, Np, BM, G.kblk));
+        mg.push_back(make_map(q.planes, GRAM_PH * Lp, Np, BN, G.kblk));
         fg.push_back(fg.back() + gt);
     }
     char *d = (char *)dev;
