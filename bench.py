@@ -365,6 +365,13 @@ def run_native(args):
     count = len(probs)
     stream = torch.cuda.current_stream(dev)
     ctx = elm.elm_create(local, stream)
+    # launch choices picked by the library's autotuner on this workload,
+    # before anything is timed (the tuning runs train the problems too)
+    tune = None
+    if not args.no_autotune:
+        t_tune = time.time()
+        tune = elm.elm_autotune(ctx, probs if len(probs) > 1 else probs[0], precision=prec)
+        tune["seconds"] = round(time.time() - t_tune, 2)
     planted = [int(p["rank"]) if p.get("rank") is not None else None for p in hosts]
     full_rows = args.rows is None or args.workload not in ("sparse_pixels", "large")
 
@@ -521,7 +528,7 @@ def run_native(args):
                         issued_frac=issued / (ph_ms["gram"] * 1e-3) / 1e12 / pk["bf16"])
         roof["phase_ms"] = ph_ms
         first = hosts[0]
-        cfg = dict(workload=desc,
+        cfg = dict(workload=desc, autotune=tune,
                    precision=args.precision if args.block_split <= 0 else "fp64 (block route)",
                    parallelism="replicas" if ws > 1 else "single",
                    l2="inputs larger than L2 (X and the digit planes stream from HBM): no flush")
@@ -697,6 +704,8 @@ def main():
                     help="the timed workload (the default is the headline configuration)")
     ap.add_argument("--shard", choices=["none", "rows"], default="none",
                     help="rows: one training with the rows of H split over the ranks")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch choices instead of tuning them first")
     ap.add_argument("--lanes", type=int, default=0,
                     help="batched mixed trainings: problems whose factorisation, solves and "
                          "refinement run at once (0: the library's default, 4)")

@@ -299,6 +299,44 @@ const char *elm_phase_name(int phase);
 int64_t elm_launch_counter(void);
 
 /*
+ * Autotuner (no counterpart in the paper: it picks launch shapes, not
+ * arithmetic).  elm_autotune trains the given problems several times with
+ * different launch choices and keeps the fastest for their shape bucket
+ * (floor(log2) of L, N and n for one problem; of the problem count for a
+ * batched call; per precision) in the context, where elm_train then uses
+ * it for every problem of that bucket:
+ *   one problem: the cluster size (8 or 16 CTAs) and width (16, 24 or 32
+ *     pivots; FP64 forms up to 24) of the factorisation's pivot panels, by
+ *     the factor phase's time, and for ELM_PREC_MIXED the pipeline depth
+ *     (2 or 3 stages) of the hidden-layer and Gram tensor kernels, by their
+ *     phases' times (CUDA events on the context's stream);
+ *   several problems: elm_train_opts.lanes (1, 2, 4 or 8), by the call's time.
+ * The runs write beta into the problems' outputs like elm_train (launch
+ * choices can move beta only within the form's rounding).  opts: as for
+ * elm_train (flags and lanes are set by the tuner).  cache_path (may be
+ * NULL): a text file, one line per bucket ("<bucket> cs=.. nb=.. hs=.. gs=..
+ * lanes=.."), rewritten with this bucket's choice.  out (may be NULL)
+ * receives the choice.  elm_autotune_load reads such a file into the
+ * context (lines that do not parse, or hold values outside the ranges
+ * above, are skipped; ELM_ERR_ARG if the file cannot be opened).  Choices
+ * hold until the context is destroyed; 0 in a field means the built-in
+ * default.
+ */
+typedef struct elm_tune_choice {
+    int32_t panel_cluster;  /* CTAs of a pivot-panel cluster                      */
+    int32_t panel_width;    /* pivots per factorisation panel                     */
+    int32_t hidden_stages;  /* pipeline stages of the mixed hidden-layer kernel   */
+    int32_t gram_stages;    /* pipeline stages of the mixed Gram kernel           */
+    int32_t lanes;          /* lanes of a batched mixed call                      */
+    int32_t reserved;
+    double best_ms;         /* one problem: chosen factor + hidden + Gram phase
+                               times; several: the call's time (ms)            */
+} elm_tune_choice;
+int elm_autotune(elm_ctx *ctx, const elm_problem *probs, int64_t count,
+                 const elm_train_opts *opts, const char *cache_path, elm_tune_choice *out);
+int elm_autotune_load(elm_ctx *ctx, const char *cache_path);
+
+/*
  * elm_hidden_noalloc -- the mixed-precision hidden layer of elm_hidden
  * (ELM_PREC_MIXED) for callers that may not allocate device memory, neither
  * themselves nor through the library: for example a plugin inside a host

@@ -10,6 +10,7 @@ arrays for host inputs).
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -206,6 +207,28 @@ def elm_train(ctx, problems, precision=PREC_FP64, max_refine=-1, tol_rank=0.0,
         _check(ctx, st)
     return [dict(rank=r.rank, refine_iters=r.refine_iters, status=r.status,
                  rel_update=r.rel_update, form=r.form) for r in res]
+
+
+def elm_autotune(ctx, problems, precision=PREC_FP64, path=None, max_refine=-1):
+    """Time launch choices on these problems (trains them; beta is written)
+    and keep the fastest for their shape bucket in the context, and in the
+    cache file `path` if given.  Returns the choice as a dict."""
+    if isinstance(problems, dict):
+        problems = [problems]
+    arr = (_lib.elm_problem * len(problems))(*[_problem(p) for p in problems])
+    opts = _lib.elm_train_opts(precision=precision, max_refine=max_refine)
+    out = _lib.elm_tune_choice()
+    st = _lib.load().elm_autotune(ctx.handle, arr, len(problems), C.byref(opts),
+                                  None if path is None else os.fsencode(path), C.byref(out))
+    _check(ctx, st)
+    return dict(panel_cluster=out.panel_cluster, panel_width=out.panel_width,
+                hidden_stages=out.hidden_stages, gram_stages=out.gram_stages, lanes=out.lanes,
+                best_ms=out.best_ms)
+
+
+def elm_autotune_load(ctx, path):
+    """Read an autotune cache file into the context."""
+    _check(ctx, _lib.load().elm_autotune_load(ctx.handle, os.fsencode(path)))
 
 
 FORM_FP64, FORM_MIXED, FORM_MIXED_TO_FP64, FORM_WIDE, FORM_BLOCK, FORM_FP64_TC = 0, 1, 2, 3, 4, 5

@@ -23,6 +23,11 @@ class elm_train_opts(C.Structure):
                 ("block_split", i32), ("lanes", i32)]
 
 
+class elm_tune_choice(C.Structure):
+    _fields_ = [("panel_cluster", i32), ("panel_width", i32), ("hidden_stages", i32),
+                ("gram_stages", i32), ("lanes", i32), ("reserved", i32), ("best_ms", dbl)]
+
+
 class elm_result(C.Structure):
     _fields_ = [("rank", i64), ("refine_iters", i32), ("status", i32), ("rel_update", dbl),
                 ("form", i32), ("reserved", i32)]
@@ -57,6 +62,9 @@ SIGNATURES = [
                                   C.POINTER(i64)]),
     ("elm_factor_solve", C.c_int, [vp, vp, i64, i64, vp, i64]),
     ("elm_factor_destroy", C.c_int, [vp]),
+    ("elm_autotune", C.c_int, [vp, C.POINTER(elm_problem), i64, C.POINTER(elm_train_opts),
+                               C.c_char_p, C.POINTER(elm_tune_choice)]),
+    ("elm_autotune_load", C.c_int, [vp, C.c_char_p]),
 ]
 
 _lib = None

@@ -2,6 +2,7 @@
 // host/device staging, workspace planning and the order of the training
 // steps of Algorithm 1.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <atomic>
@@ -283,6 +284,7 @@ struct Problem {
     bool wide;         // N < L: the branch H^+ = H^T (H H^T)^+
     int64_t block;     // > 0: the paper's block formulae, H1 = first `block` columns
     int lanes;         // batched mixed trainings: back halves run side by side
+    Tune tune;         // autotuned launch choices of the problem's shape bucket
 };
 
 // Frees a context's device buffers, events, owned stream and lanes (not the
@@ -333,6 +335,24 @@ elm_ctx *lane_of(elm_ctx *ctx, size_t i) {
         ctx->lanes.push_back(l);
     }
     return ctx->lanes[i];
+}
+
+// Shape buckets of the autotune cache: floor(log2) of L, N and n per
+// precision for one problem; of the problem count for a batched call.
+int ilog2(int64_t v) {
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        r++;
+    }
+    return r;
+}
+std::string tune_key(int prec, const elm_problem &p) {
+    return "p" + std::to_string(prec) + "_L" + std::to_string(ilog2(p.L)) + "_N" +
+           std::to_string(ilog2(p.N)) + "_n" + std::to_string(ilog2(p.n));
+}
+std::string tune_batch_key(int prec, int64_t count) {
+    return "p" + std::to_string(prec) + "_batch" + std::to_string(ilog2(count));
 }
 
 void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res);
@@ -419,7 +439,8 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     else gram_f64(s, Ht, N, L, N, Td, T.ld, m, S, L, Z, m, gpart, ns);
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4: permutation, rank, split
-    factor_pivoted(s, S, lds, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count);
+    factor_pivoted(s, S, lds, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/false,
+                   P.tune.panel_cs, P.tune.panel_nb);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
     int terr = 0;
@@ -857,7 +878,8 @@ void mixed_back(elm_ctx *ctx, const Problem &P, elm_result *res, const MixedData
         res->form = ELM_FORM_MIXED_TO_FP64;
     };
     // Eq. 6, Algorithm 1 steps 3-4 (double-float)
-    factor_pivoted(s, D.G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true);
+    factor_pivoted(s, D.G, Lt, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/true,
+                   P.tune.panel_cs, P.tune.panel_nb);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
     int terr = 0;
@@ -997,13 +1019,15 @@ void train_mixed(elm_ctx *ctx, const Problem &P, elm_result *res) {
     // Algorithm 1 step 2 (Eq. 1, 3): pre-activation on the tensor cores,
     // activation in the epilogue, digit planes of H and H itself
     oz_hidden(s, hw, X.p, pb.x_dtype, N, n, X.ld, Wd, W.ld, bd, ad, pb.act, L, m, planes, hs,
-              nullptr, 0, err, Hdf, /*nonfinite=*/flag, x_host ? &xc : nullptr, P.wait_ns);
+              nullptr, 0, err, Hdf, /*nonfinite=*/flag, x_host ? &xc : nullptr, P.wait_ns,
+              P.tune.hid_stages ? P.tune.hid_stages : 3);
     // digit rows of the targets beside those of H (part of the hidden phase,
     // so the Gram phase times the Gram kernel alone)
     oz_t_digits(s, Td, T.ld, N, L, m, planes, hs);
     mark(ctx, 1);
     // Eqs. 9-13: [H^T H, H^T T] on the tensor cores
-    oz_gram(s, planes, hs, N, L, m, G, Lt, err, gpart, P.wait_ns);
+    oz_gram(s, planes, hs, N, L, m, G, Lt, err, gpart, P.wait_ns,
+            P.tune.gram_stages ? P.tune.gram_stages : 3);
     mark(ctx, 2);
     mixed_back(ctx, P, res, MixedData{Td, T.ld, G, Hdf, flag, err}, 0);
 }
@@ -1556,6 +1580,16 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
                 if (!(o.refine_tol > 0.0)) P.refine_tol = 1e-12;
             }
         }
+        // autotuned launch choices of each problem's shape bucket, and the
+        // lanes of a batched call
+        for (int64_t i = 0; i < count; i++) {
+            const auto it = ctx->tune.find(tune_key(plan[i].prec, probs[i]));
+            if (it != ctx->tune.end()) plan[i].tune = it->second;
+            if (o.lanes == 0 && count > 1) {
+                const auto bt = ctx->tune.find(tune_batch_key(o.precision, count));
+                if (bt != ctx->tune.end() && bt->second.lanes > 0) plan[i].lanes = bt->second.lanes;
+            }
+        }
         // mixed-form problems of a multi-problem call: hidden layers and
         // Grams batched; the others one by one
         std::vector<Problem> batch;
@@ -1597,6 +1631,170 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
         }
     });
     return st != ELM_OK ? st : first;
+}
+
+namespace {
+
+// One line of the autotune cache file: "<bucket> cs=.. nb=.. hs=.. gs=.. lanes=..".
+bool tune_parse(const char *line, std::string &key, Tune &t) {
+    char k[128];
+    int cs, nb, hs, gs, ln;
+    if (sscanf(line, "%127s cs=%d nb=%d hs=%d gs=%d lanes=%d", k, &cs, &nb, &hs, &gs, &ln) != 6)
+        return false;
+    const bool ok = (cs == 0 || cs == 8 || cs == 16) && nb >= 0 && nb <= 64 &&
+                    (hs == 0 || hs == 2 || hs == 3) && (gs == 0 || gs == 2 || gs == 3) &&
+                    ln >= 0 && ln <= ELM_MAX_LANES;
+    if (!ok) return false;
+    key = k;
+    t.panel_cs = cs;
+    t.panel_nb = nb;
+    t.hid_stages = hs;
+    t.gram_stages = gs;
+    t.lanes = ln;
+    return true;
+}
+std::string tune_line(const std::string &key, const Tune &t) {
+    char b[256];
+    snprintf(b, sizeof b, "%s cs=%d nb=%d hs=%d gs=%d lanes=%d", key.c_str(), t.panel_cs,
+             t.panel_nb, t.hid_stages, t.gram_stages, t.lanes);
+    return b;
+}
+// Rewrites the cache file with `key` set to t (other buckets kept).
+void tune_store(const char *path, const std::string &key, const Tune &t) {
+    std::vector<std::string> lines;
+    if (FILE *f = fopen(path, "r")) {
+        char buf[512];
+        while (fgets(buf, sizeof buf, f)) {
+            std::string k;
+            Tune u;
+            if (tune_parse(buf, k, u) && k != key) lines.push_back(tune_line(k, u));
+        }
+        fclose(f);
+    }
+    lines.push_back(tune_line(key, t));
+    FILE *g = fopen(path, "w");
+    if (!g) throw ElmError(ELM_ERR_ARG, "cannot write the autotune cache file");
+    for (const auto &l : lines) fprintf(g, "%s\n", l.c_str());
+    fclose(g);
+}
+
+}  // namespace
+
+int elm_autotune(elm_ctx *ctx, const elm_problem *probs, int64_t count, const elm_train_opts *opts,
+                 const char *cache_path, elm_tune_choice *out) {
+    if (!ctx) return ELM_ERR_ARG;
+    elm_train_opts o{};
+    o.precision = ELM_PREC_FP64;
+    o.max_refine = -1;
+    if (opts) o = *opts;
+    return guarded(ctx, [&] {
+        require(count >= 1 && probs, "no problems to tune on");
+        std::vector<elm_result> res((size_t)count);
+        auto run = [&](const elm_train_opts &oo) {
+            const int st = elm_train(ctx, probs, count, &oo, res.data());
+            if (st != ELM_OK && st != ELM_ERR_NOT_CONVERGED)
+                throw ElmError(st, "training failed while tuning: " + ctx->last_error);
+        };
+        Tune best;
+        double best_ms = 0.0;
+        std::string key;
+        if (count > 1) {
+            // a batched call: the lanes of its back halves, by the call's time
+            key = tune_batch_key(o.precision, count);
+            ctx->tune.erase(key);
+            elm_train_opts oo = o;
+            oo.flags &= ~ELM_FLAG_PHASE_TIMING;
+            run(oo);   // workspaces
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            ELM_CUDA(cudaEventCreate(&e0));
+            ELM_CUDA(cudaEventCreate(&e1));
+            best_ms = INFINITY;
+            best.lanes = 4;
+            for (int ln : {1, 2, 4, 8}) {
+                oo.lanes = ln;
+                ELM_CUDA(cudaEventRecord(e0, ctx->stream));
+                run(oo);   // returns once every lane is done
+                ELM_CUDA(cudaEventRecord(e1, ctx->stream));
+                ELM_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                ELM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.lanes = ln;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        } else {
+            // one problem: the panels' cluster size and width by the factor
+            // phase, the tensor kernels' pipeline depth by their own phases
+            key = tune_key(o.precision, probs[0]);
+            ctx->tune.erase(key);
+            const bool mixed = o.precision == ELM_PREC_MIXED;
+            elm_train_opts oo = o;
+            oo.flags |= ELM_FLAG_PHASE_TIMING;
+            run(oo);   // workspaces
+            std::vector<std::pair<int, int>> combos;
+            for (int cs : {8, 16})
+                for (int nb : {16, 24, 32})
+                    if (mixed || nb <= 24) combos.push_back({cs, nb});
+            double fbest = INFINITY, hsum[4] = {0, 0, 0, 0}, gsum[4] = {0, 0, 0, 0};
+            int cnt[4] = {0, 0, 0, 0};
+            for (size_t i = 0; i < combos.size(); i++) {
+                Tune t;
+                t.panel_cs = combos[i].first;
+                t.panel_nb = combos[i].second;
+                const int stg = i % 2 == 0 ? 3 : 2;
+                if (mixed) t.hid_stages = t.gram_stages = stg;
+                ctx->tune[key] = t;
+                for (double &x : ctx->phase_ms) x = 0.0;
+                run(oo);
+                if (ctx->phase_ms[2] < fbest) {
+                    fbest = ctx->phase_ms[2];
+                    best.panel_cs = t.panel_cs;
+                    best.panel_nb = t.panel_nb;
+                }
+                hsum[stg] += ctx->phase_ms[0];
+                gsum[stg] += ctx->phase_ms[1];
+                cnt[stg]++;
+            }
+            best_ms = fbest;
+            if (mixed && cnt[2] > 0 && cnt[3] > 0) {
+                const double h2 = hsum[2] / cnt[2], h3 = hsum[3] / cnt[3];
+                const double g2 = gsum[2] / cnt[2], g3 = gsum[3] / cnt[3];
+                best.hid_stages = h2 < h3 ? 2 : 3;
+                best.gram_stages = g2 < g3 ? 2 : 3;
+                best_ms += (h2 < h3 ? h2 : h3) + (g2 < g3 ? g2 : g3);
+            }
+            for (double &x : ctx->phase_ms) x = 0.0;
+        }
+        ctx->tune[key] = best;
+        if (cache_path) tune_store(cache_path, key, best);
+        if (out) {
+            out->panel_cluster = best.panel_cs;
+            out->panel_width = best.panel_nb;
+            out->hidden_stages = best.hid_stages;
+            out->gram_stages = best.gram_stages;
+            out->lanes = best.lanes;
+            out->reserved = 0;
+            out->best_ms = best_ms;
+        }
+    });
+}
+
+int elm_autotune_load(elm_ctx *ctx, const char *cache_path) {
+    if (!ctx || !cache_path) return ELM_ERR_ARG;
+    return guarded(ctx, [&] {
+        FILE *f = fopen(cache_path, "r");
+        require(f != nullptr, "cannot open the autotune cache file");
+        char buf[512];
+        while (fgets(buf, sizeof buf, f)) {
+            std::string k;
+            Tune t;
+            if (tune_parse(buf, k, t)) ctx->tune[k] = t;
+        }
+        fclose(f);
+    });
 }
 
 int elm_phase_times(elm_ctx *ctx, double *ms_out, int max_phases) {

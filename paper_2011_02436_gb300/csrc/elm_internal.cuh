@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -61,6 +62,15 @@ struct Arena {
     }
 };
 
+// Launch choices the autotuner times (0: the built-in default).
+struct Tune {
+    int panel_cs = 0;      // CTAs of a pivot-panel cluster: 8 or 16
+    int panel_nb = 0;      // pivots per panel (double-float form up to 64, FP64 up to 24)
+    int hid_stages = 0;    // pipeline stages of the mixed hidden-layer tensor kernel: 2 or 3
+    int gram_stages = 0;   // pipeline stages of the mixed Gram tensor kernel: 2 or 3
+    int lanes = 0;         // batched mixed calls: lanes of the back halves
+};
+
 struct elm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -84,6 +94,8 @@ struct elm_ctx {
     // run problems' factorisations, solves and refinements side by side
     std::vector<elm_ctx *> lanes;
     bool own_stream = false;   // a lane's stream, created and destroyed with it
+    // autotuned launch choices by shape bucket (elm_autotune, elm_autotune_load)
+    std::map<std::string, Tune> tune;
 };
 
 // ---------------------------------------------------------------- kernels
@@ -166,9 +178,11 @@ int64_t tri_ld(int64_t L);
 // double-float pairs and run the trailing updates on the FP32 pipes (about
 // 2^-44 relative per update; for the mixed form, whose Gram matrix is
 // itself accurate to about 2^-34), else FP64 throughout.
+// cs, nb: cluster size (8 or 16) and panel width of the pivot panels
+// (0: the built-in choice; nb is capped at the form's largest width).
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr,
-                    int sms, bool df = false);
+                    int sms, bool df = false, int cs = 0, int nb = 0);
 
 // Solves with the leading r x r block R11 of such a factor.  trsm_prepare
 // inverts its 32 x 32 diagonal blocks (DinvF, DinvB: trsm_dinv_doubles(r)
@@ -263,7 +277,7 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
                int64_t ldh, int *err, void *Hdf = nullptr,
                int32_t *nonfinite = nullptr, const OzRowChunks *chunks = nullptr,
-               uint64_t wait_ns = 0);
+               uint64_t wait_ns = 0, int stages = 3);
 // T -> digit plane rows L .. L+m-1.
 void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_t L, int64_t m,
                  __nv_bfloat16 *planes, double *hs);
@@ -274,7 +288,7 @@ void oz_t_digits(cudaStream_t s, const double *T, int64_t ldt, int64_t N, int64_
 size_t oz_gram_part_bytes();
 void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
              int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part,
-             uint64_t wait_ns = 0);
+             uint64_t wait_ns = 0, int stages = 3);
 // [H^T H, H^T T] (Lt x Lt, ldg, both triangles, Lt = L + m) of the FP64
 // matrix A = [H^T; T^T] (Lt x N, lda) on the tensor cores, accurate to FP64
 // level (eight 7-bit digits per element, every digit pair of weight above

@@ -1239,11 +1239,10 @@ int pick_cluster(size_t smem_for16, size_t smem_for8) {
     return best;
 }
 
-void panel_geometry(int64_t L, int cs, int *nb, int64_t *wmax, size_t *smem, bool df) {
+void panel_geometry(int64_t L, int cs, int *nb, int64_t *wmax, size_t *smem, int nbmax) {
     *wmax = (L + cs - 1) / cs;
     const size_t budget = 200 * 1024;
     int64_t fit = (int64_t)((budget - (size_t)(*wmax) * 16) / ((size_t)(*wmax) * 8));
-    const int nbmax = df ? PNB_DF : PNB;
     int b = (int)(fit < nbmax ? fit : nbmax);
     if (b < 1) b = 1;
     *nb = b;
@@ -1276,23 +1275,27 @@ FactorWs factor_ws_carve(Arena &ar, int64_t L) {
 
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr, int sms,
-                    bool df) {
+                    bool df, int cs_req, int nb_req) {
     if (ldr < tri_ld(L)) throw ElmError(ELM_ERR_ARG, "factor stride below tri_ld(L)");
     if (L > ELM_MAX_L) throw ElmError(ELM_ERR_UNSUPPORTED, "L above ELM_MAX_L");
     int nb16, nb8;
     int64_t w16, w8;
     size_t sm16, sm8;
-    panel_geometry(L, 16, &nb16, &w16, &sm16, df);
-    panel_geometry(L, 8, &nb8, &w8, &sm8, df);
+    const int nbmax = nb_req > 0 ? (nb_req < (df ? MAXNB : PNB) ? nb_req : (df ? MAXNB : PNB))
+                                 : (df ? PNB_DF : PNB);
+    panel_geometry(L, 16, &nb16, &w16, &sm16, nbmax);
+    panel_geometry(L, 8, &nb8, &w8, &sm8, nbmax);
     // Up to 2048 columns (one column per thread on 8 CTAs) the double-float
     // panel exchanges with 7 peers instead of 15: factor phase of the
     // sparse-pixel Gram (L = 2000) 5.03 ms on 8 CTAs against 5.17 on 16; for
     // L = 6000 the 16-CTA cluster is faster (35.2 against 38.3 ms).
-    const int cs = (df && L <= 8 * FT) ? 8 : pick_cluster(sm16, sm8);
+    const int cs_max = pick_cluster(sm16, sm8);
+    const int cs = cs_req == 8 || (cs_req == 16 && cs_max == 16) ? cs_req
+                   : (df && L <= 8 * FT) ? 8 : cs_max;
     int nb;
     int64_t wmax;
     size_t smem;
-    panel_geometry(L, cs, &nb, &wmax, &smem, df);
+    panel_geometry(L, cs, &nb, &wmax, &smem, nbmax);
     if (wmax > (int64_t)MAXCPT * FT) throw ElmError(ELM_ERR_UNSUPPORTED, "L too large for the panel");
     // columns per thread, as a compile-time count
     auto kpanel = df ? (wmax <= FT ? panel_kernel<1, true>

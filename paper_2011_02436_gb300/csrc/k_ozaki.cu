@@ -1290,7 +1290,7 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
                int64_t ldx, const double *W, int64_t ldw, const double *b, const double *a,
                int act, int64_t L, int64_t m, __nv_bfloat16 *planes, double *hs, double *Ht,
                int64_t ldh, int *err, void *Hdf, int32_t *nonfinite, const OzRowChunks *chunks,
-               uint64_t wait_ns) {
+               uint64_t wait_ns, int stages) {
     const int64_t Np = oz_pad(N, BN), nK = oz_pad(n, SK), Lp = oz_pad(L + m, BM);
     col_scale_kernel<<<(unsigned)((Lp + 31) / 32), 256, 0, s>>>(W, n, L, ldw, Lp, w.ws);
     ELM_CHECK_LAUNCH();
@@ -1355,8 +1355,11 @@ void oz_hidden(cudaStream_t s, const OzHidWs &w, const void *X, int xdt, int64_t
         const int64_t tiles = (Lp / BM) * ((r1 - r0) / BN);
         P.n_base = r0;
         P.whole = tiles;   // no split tiles
+        // (two pipeline stages: an autotuner choice; three by default)
         if (Ht)
             launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 2>(s, w.wp, w.xp, P, tiles);
+        else if (stages == 2)
+            launch_ozaki<HID_PW, HID_PX, HID_TMAX, 2, HID_BITS, 1>(s, w.wp, w.xp, P, tiles);
         else
             launch_ozaki<HID_PW, HID_PX, HID_TMAX, 3, HID_BITS, 1>(s, w.wp, w.xp, P, tiles);
     }
@@ -1382,7 +1385,7 @@ size_t oz_gram_part_bytes() { return (size_t)sm_count() * BM * BN * sizeof(long 
 
 void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int64_t N,
              int64_t L, int64_t m, double *G, int64_t ldg, int *err, long long *part,
-             uint64_t wait_ns) {
+             uint64_t wait_ns, int stages) {
     const int64_t Np = oz_pad(N, BN), Lp = oz_pad(L + m, BM);
     const int64_t nJ = Lp / BM, ntiles = nJ * (nJ + 1);
     const int64_t sms = sm_count();
@@ -1412,7 +1415,10 @@ void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int6
     if (P.whole < ntiles)
         ELM_CUDA(cudaMemsetAsync(part, 0, (size_t)(ntiles - P.whole) * BM * BN * sizeof(long long),
                                  s));
-    launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS, 0>(s, planes, planes, P, ntiles);
+    if (stages == 2)
+        launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 2, GRAM_BITS, 0>(s, planes, planes, P, ntiles);
+    else
+        launch_ozaki<GRAM_PH, GRAM_PH, GRAM_TMAX, 3, GRAM_BITS, 0>(s, planes, planes, P, ntiles);
     if (P.whole < ntiles) {
         P.ntiles = ntiles;
         gram_tail_kernel<GRAM_BITS, GRAM_TMAX>

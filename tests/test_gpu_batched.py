@@ -39,7 +39,9 @@ def cases():
             synth.make_problem(700, 128, 90, 26, x_dtype=np.float64),
             synth.make_problem(40, 8, 120, 3),                     # wide: trained on its own
             synth.workload_sparse_pixels(N=2500, L_unique=300),
-            synth.make_problem(65, 5, 7, 1, act=synth.ACT_TANH)]
+            synth.make_problem(65, 5, 7, 1, act=synth.ACT_TANH),
+            # more than 65536 samples: the Gram digit planes in two blocks
+            synth.make_problem(70001, 16, 150, 3, act=synth.ACT_SIGMOID)]
 
 
 def test_batched_call_equals_one_call_per_problem(elm, ctx):
