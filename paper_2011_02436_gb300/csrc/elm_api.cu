@@ -19,6 +19,7 @@ using namespace elm;
 namespace elm {
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace elm
 
 namespace {

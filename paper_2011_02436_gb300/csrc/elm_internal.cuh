@@ -24,6 +24,7 @@
 // Every kernel launch site ends with ELM_CHECK_LAUNCH(), which also counts it.
 namespace elm {
 void count_launch();
+void count_launches(int64_t n);   // kernels of a replayed graph
 }
 #define ELM_CHECK_LAUNCH()              \
     do {                                \

@@ -19,8 +19,13 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <stdio.h>
+
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "df_arith.cuh"
 #include "elm_internal.cuh"
@@ -1273,6 +1278,21 @@ FactorWs factor_ws_carve(Arena &ar, int64_t L) {
     return w;
 }
 
+namespace {
+using PanelFn = void (*)(const double *, int64_t, const int32_t *, double *, int64_t, double *,
+                         int64_t, int32_t *, int32_t *, int32_t *, FactorState *, int64_t, int,
+                         int64_t, double);
+struct FactorGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+};
+std::mutex g_fgraph_mu;
+std::map<std::string, FactorGraph> g_fgraph;
+void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, double tau,
+                    const FactorWs &w, double *R, double *Rt, int64_t ldr, bool df, int cs, int nb,
+                    int64_t wmax, size_t smem, PanelFn kpanel);
+}  // namespace
+
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr, int sms,
                     bool df, int cs_req, int nb_req) {
@@ -1309,6 +1329,88 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     ELM_CUDA(cudaFuncSetAttribute(kpanel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)PANEL_SMEM_MAX));
 
+    // The launch sequence depends only on the arguments, so it is captured
+    // once into a CUDA graph per argument set and replayed: one graph launch
+    // instead of two launches per panel.  (Workspaces are reused between
+    // trainings of one shape, so the pointers repeat.)
+    char key[320];
+    snprintf(key, sizeof key, "%p %ld %ld %a %p %p %p %p %p %p %p %p %p %p %p %p %p %ld %d %d %d",
+             (const void *)S, (long)lds, (long)L, tau, (void *)w.A0, (void *)w.A1,
+             (void *)w.Rrow, (void *)w.P, (void *)w.dS, (void *)w.sc, (void *)w.act0,
+             (void *)w.act1, (void *)w.rem, (void *)w.perm, (void *)w.st, (void *)R, (void *)Rt,
+             (long)ldr, (int)df, cs, nb);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ELM_CUDA(cudaStreamIsCapturing(s, &cap));
+    bool full = false;
+    FactorGraph fg{};
+    {
+        std::lock_guard<std::mutex> lk(g_fgraph_mu);
+        auto it = g_fgraph.find(key);
+        if (it != g_fgraph.end()) fg = it->second;
+        full = g_fgraph.size() >= 256;   // bounded cache: further shapes run uncaptured
+    }
+    if (cap == cudaStreamCaptureStatusNone && (fg.exec || !full)) {
+        if (fg.exec) {
+            ELM_CUDA(cudaGraphLaunch(fg.exec, s));
+            count_launches(fg.kernels);
+            return;
+        }
+        // captured on a stream of this thread's own (the caller's may be the
+        // legacy default stream, which cannot capture); nothing runs until
+        // the graph is launched on the caller's stream
+        thread_local struct CaptureStream {
+            cudaStream_t s = nullptr;
+            ~CaptureStream() {
+                if (s) cudaStreamDestroy(s);
+            }
+        } tls;
+        if (!tls.s) ELM_CUDA(cudaStreamCreateWithFlags(&tls.s, cudaStreamNonBlocking));
+        const cudaStream_t cs_stream = tls.s;
+        ELM_CUDA(cudaStreamBeginCapture(cs_stream, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t graph = nullptr;
+        try {
+            factor_enqueue(cs_stream, S, lds, L, tau, w, R, Rt, ldr, df, cs, nb, wmax, smem,
+                           kpanel);
+        } catch (...) {
+            cudaStreamEndCapture(cs_stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        ELM_CUDA(cudaStreamEndCapture(cs_stream, &graph));
+        size_t nodes = 0;
+        cudaGraphGetNodes(graph, nullptr, &nodes);
+        std::vector<cudaGraphNode_t> nv(nodes);
+        if (nodes) cudaGraphGetNodes(graph, nv.data(), &nodes);
+        for (auto nd : nv) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                fg.kernels++;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&fg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        ELM_CUDA(ie);
+        {
+            std::lock_guard<std::mutex> lk(g_fgraph_mu);
+            auto it = g_fgraph.find(key);
+            if (it != g_fgraph.end()) {   // another thread captured the same meanwhile
+                cudaGraphExecDestroy(fg.exec);
+                fg.exec = it->second.exec;
+            } else {
+                g_fgraph[key] = fg;
+            }
+        }
+        ELM_CUDA(cudaGraphLaunch(fg.exec, s));   // the capture counted its kernels once
+        return;
+    }
+    // inside a caller's capture, or the cache is full: enqueue directly
+    factor_enqueue(s, S, lds, L, tau, w, R, Rt, ldr, df, cs, nb, wmax, smem, kpanel);
+}
+
+namespace {
+
+void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, double tau,
+                    const FactorWs &w, double *R, double *Rt, int64_t ldr, bool df, int cs, int nb,
+                    int64_t wmax, size_t smem, PanelFn kpanel) {
     ELM_CUDA(cudaMemsetAsync(w.st, 0, sizeof(FactorState), s));
     ELM_CUDA(cudaMemsetAsync(w.Rrow, 0, sizeof(double) * L * L, s));
     {
@@ -1363,6 +1465,8 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     else finalize_kernel<false><<<g, 256, 0, s>>>(w.Rrow, L, w.perm, w.dS, w.st, L, R, Rt, ldr);
     ELM_CHECK_LAUNCH();
 }
+
+}  // namespace
 
 static std::atomic<int> g_tcluster{0};
 static std::mutex g_tcluster_mu;

@@ -155,3 +155,24 @@ def test_train_pinned_host_inputs_mixed(elm, ctx, xdt):
     bad[100, 5] = float("nan")
     res = elm.elm_train(ctx, dict(prob, X=bad), precision=elm.PREC_MIXED, check=False)[0]
     assert res["status"] == 4
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_repeated_trainings_replay_the_factorisation_graph(elm, ctx, prec):
+    """The factorisation's launches are captured into a CUDA graph on the
+    first training of a shape and replayed on the next ones (same
+    workspaces): beta is bitwise the same every time, and the launch counter
+    counts the replayed kernels like launched ones."""
+    p = synth.make_problem(2500, 20, 260, 4, n_dup=12, n_scaled=5)
+    prob = problem(p)
+    betas, counts = [], []
+    for _ in range(3):
+        c0 = elm.elm_launch_counter()
+        res = elm.elm_train(ctx, prob, precision=prec)[0]
+        counts.append(elm.elm_launch_counter() - c0)
+        betas.append(prob["beta"].cpu().numpy().copy())
+    assert np.array_equal(betas[0], betas[1]) and np.array_equal(betas[1], betas[2])
+    assert counts[1] == counts[2] and counts[0] >= counts[1] > 0
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["rank"] == r
+    assert rel(betas[2], ref) <= (1e-9 if prec == 0 else 1e-6)
