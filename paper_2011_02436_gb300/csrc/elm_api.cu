@@ -176,9 +176,11 @@ struct Solver {
     int *tflag = nullptr;
 };
 
+// df_k: form K = R11^{-1} R12 in double-float (the mixed form, whose factor
+// is double-float accurate); the solves themselves stay FP64.
 Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const double *Rt,
                       int64_t ld, const int32_t *perm, int64_t r, int64_t L, int64_t m,
-                      char **buf = nullptr, size_t *bufsize = nullptr) {
+                      char **buf = nullptr, size_t *bufsize = nullptr, bool df_k = false) {
     Solver sv;
     sv.R = R;
     sv.Rt = Rt;
@@ -216,7 +218,7 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
     if (q > 0 && r > 0) {
         copy2d(sv.K, q * sizeof(double), R + r, ld * sizeof(double),
                                    q * sizeof(double), r, cudaMemcpyDeviceToDevice, s);
-        trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag);
+        trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag, df_k);
         syrk_f64(s, sv.K, r, q, q, sv.G2, q, sv.syrk_part, syrk_split);   // I + K^T K
         // I + K^T K is SPD with eigenvalues >= 1: full rank q
         factor_pivoted(s, sv.G2, q, q, 0.0, sv.f2, sv.R2, sv.Rt2, sv.ld2, ctx->sm_count);
@@ -906,7 +908,8 @@ void mixed_back(elm_ctx *ctx, const Problem &P, elm_result *res, const MixedData
     if (r < L && stop_val > P.tau64) return fallback();
     const double *Z = D.G + L;   // Z[l, c] = G[l, L + c]
     // Eq. 5, Eq. 7 (FP64)
-    const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m);
+    const Solver sv = solver_prepare(ctx, s, R, Rt, tri_ld(L), f.perm, r, L, m, nullptr, nullptr,
+                                     /*df_k=*/true);
     solver_apply(s, sv, Z, Lt, beta, m);
     mark(ctx, 4);
     double nrm[2] = {0.0, 0.0};

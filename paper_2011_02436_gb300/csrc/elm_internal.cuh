@@ -195,8 +195,10 @@ void trsm_prepare(cudaStream_t s, const double *R, int64_t ldr, int64_t r, doubl
                   double *DinvB);
 void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const double *DinvF, int64_t r,
               double *B, int64_t ldb, int64_t q, int *tflag);
+// df: double-float arithmetic on the FP32 pipes (about 2^-44 per operation;
+// for the mixed form, whose factor is itself double-float accurate).
 void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const double *DinvB, int64_t r,
-              double *B, int64_t ldb, int64_t q, int *tflag);
+              double *B, int64_t ldb, int64_t q, int *tflag, bool df = false);
 
 // Gather rows: dst[i, :] = src[perm[i], :] for i < r_dev.
 void gather_rows(cudaStream_t s, const double *src, int64_t lds, const int32_t *perm,

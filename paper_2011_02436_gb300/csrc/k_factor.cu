@@ -18,6 +18,7 @@
 // pivot order, unscaled, at the end.
 #include <cooperative_groups.h>
 #include <math.h>
+#include <type_traits>
 
 #include <stdio.h>
 
@@ -976,7 +977,7 @@ __host__ __device__ constexpr size_t trsm_smem_bytes(int nown, int nsl, int CB) 
 // data cannot arrive before every receiver has consumed the old.
 // The inverse blocks and the slabs of C arrive by bulk copies issued ahead.
 // Waits are bounded; on expiry *tflag is set.
-template <bool REV, int CB>
+template <bool REV, int CB, bool DF = false>
 __global__ void __launch_bounds__(FT)
 trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ C, int64_t ldc,
             const double *__restrict__ Dinv, int64_t r, double *__restrict__ B, int64_t ldb,
@@ -989,15 +990,18 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
     const int nc = (int)(q - c0 < CB ? q - c0 : CB);
     const int64_t nblk = (r + TB_ - 1) / TB_;
     constexpr uint32_t XBYTES = TB_ * CB * 8;
+    // values of B and of the solution: FP64, or double-float pairs (DF, the
+    // mixed form), eight bytes either way; R and the inverse blocks stay FP64
+    using V = typename std::conditional<DF, F2, double>::type;
     extern __shared__ __align__(128) unsigned char tsm[];
     uint64_t *bar_sl = (uint64_t *)tsm;                 // 2: slab buffers
     uint64_t *bar_dg = bar_sl + 2;                      // NDG: inverse-block buffers
     uint64_t *bar_x = bar_dg + NDG;                     // MAXSLOT: solution slots
-    double *bs = (double *)(tsm + 512);                 // nown x TB_ x CB
-    double *xb = bs + (size_t)nown * TB_ * CB;          // MAXSLOT x TB_ x CB
-    double *part = xb + (size_t)MAXSLOT * TB_ * CB;     // 8 x TB_ x CB
+    V *bs = (V *)(tsm + 512);                           // nown x TB_ x CB
+    V *xb = bs + (size_t)nown * TB_ * CB;               // MAXSLOT x TB_ x CB
+    V *part = xb + (size_t)MAXSLOT * TB_ * CB;          // 8 x TB_ x CB
     const int NS = 2 * CS;                              // slots in use
-    double *dg = part + 8 * TB_ * CB;                   // NDG x TB_ x TB_
+    double *dg = (double *)(part + 8 * TB_ * CB);       // NDG x TB_ x TB_
     double *sl = dg + (size_t)NDG * TB_ * TB_;          // 2 x nsl x TB_ x TB_
     __shared__ int s_abort;
 
@@ -1059,24 +1063,36 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
     auto solve_send = [&](int64_t s) {
         const int64_t k = blk(s);
         const int slot = (int)(s % NS);
-        double *xs = xb + (size_t)slot * TB_ * CB;
-        double *xk = bs + (size_t)(k / CS) * TB_ * CB;
+        V *xs = xb + (size_t)slot * TB_ * CB;
+        V *xk = bs + (size_t)(k / CS) * TB_ * CB;
         wait(&bar_dg[s % NDG], (uint32_t)((s / NDG) & 1));
         {
             constexpr int NQ = 8 / CB, AQ = TB_ / NQ;
             const int c = warp % CB, qi = warp / CB;
             const double *D = dg + (size_t)(s % NDG) * TB_ * TB_;
-            double p = 0.0;
+            if constexpr (DF) {
+                float ph = 0.f, pl = 0.f;
 #pragma unroll
-            for (int a = qi * AQ; a < qi * AQ + AQ; a++) p = fma(D[a * TB_ + lane], xk[a * CB + c], p);
-            part[(qi * TB_ + lane) * CB + c] = p;
+                for (int a = qi * AQ; a < qi * AQ + AQ; a++)
+                    df_acc_prod(ph, pl, d2df(D[a * TB_ + lane]), xk[a * CB + c]);
+                part[(qi * TB_ + lane) * CB + c] = df_renorm(ph, pl);
+            } else {
+                double p = 0.0;
+#pragma unroll
+                for (int a = qi * AQ; a < qi * AQ + AQ; a++)
+                    p = fma(D[a * TB_ + lane], xk[a * CB + c], p);
+                part[(qi * TB_ + lane) * CB + c] = p;
+            }
         }
         __syncthreads();
         if (threadIdx.x < TB_ * CB) {
             constexpr int NQ = 8 / CB;
-            double v = 0.0;
+            V v = part[threadIdx.x];
 #pragma unroll
-            for (int qi = 0; qi < NQ; qi++) v += part[qi * TB_ * CB + threadIdx.x];
+            for (int qi = 1; qi < NQ; qi++) {
+                if constexpr (DF) v = df_add(v, part[qi * TB_ * CB + threadIdx.x]);
+                else v += part[qi * TB_ * CB + threadIdx.x];
+            }
             xs[threadIdx.x] = v;
             xk[threadIdx.x] = v;
         }
@@ -1086,27 +1102,47 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
             bulk_s2c(mapa(su32(xs), lane), xs, XBYTES, mapa(su32(&bar_x[slot]), lane));
     };
     // own block kl with the solution of step s, terms split over all warps
-    auto update_block = [&](int64_t s, const double *xs, int kl) {
+    auto update_block = [&](int64_t s, const V *xs, int kl) {
         const int nb = rows(blk(s));
         const int64_t j = ((int64_t)kl * CS + cr) * TB_ + lane;
-        double acc[CB];
+        if constexpr (DF) {
+            float ah[CB], al[CB];
 #pragma unroll
-        for (int c = 0; c < CB; c++) acc[c] = 0.0;
+            for (int c = 0; c < CB; c++) ah[c] = al[c] = 0.f;
 #pragma unroll
-        for (int a = warp * 4; a < warp * 4 + 4; a++) {
-            if (a >= nb) break;
-            const double rv = coef(s, kl, a, lane);
+            for (int a = warp * 4; a < warp * 4 + 4; a++) {
+                if (a >= nb) break;
+                const F2 rv = d2df(coef(s, kl, a, lane));
 #pragma unroll
-            for (int c = 0; c < CB; c++) acc[c] = fma(rv, xs[a * CB + c], acc[c]);
+                for (int c = 0; c < CB; c++) df_acc_prod(ah[c], al[c], rv, xs[a * CB + c]);
+            }
+#pragma unroll
+            for (int c = 0; c < CB; c++) part[(warp * TB_ + lane) * CB + c] = df_renorm(ah[c], al[c]);
+        } else {
+            double acc[CB];
+#pragma unroll
+            for (int c = 0; c < CB; c++) acc[c] = 0.0;
+#pragma unroll
+            for (int a = warp * 4; a < warp * 4 + 4; a++) {
+                if (a >= nb) break;
+                const double rv = coef(s, kl, a, lane);
+#pragma unroll
+                for (int c = 0; c < CB; c++) acc[c] = fma(rv, xs[a * CB + c], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < CB; c++) part[(warp * TB_ + lane) * CB + c] = acc[c];
         }
-#pragma unroll
-        for (int c = 0; c < CB; c++) part[(warp * TB_ + lane) * CB + c] = acc[c];
         __syncthreads();
         if (threadIdx.x < TB_ * CB && ((int64_t)kl * CS + cr) * TB_ + threadIdx.x / CB < r) {
-            double v = 0.0;
+            V v = part[threadIdx.x];
 #pragma unroll
-            for (int w = 0; w < 8; w++) v += part[w * TB_ * CB + threadIdx.x];
-            bs[(size_t)kl * TB_ * CB + threadIdx.x] -= v;
+            for (int w = 1; w < 8; w++) {
+                if constexpr (DF) v = df_add(v, part[w * TB_ * CB + threadIdx.x]);
+                else v += part[w * TB_ * CB + threadIdx.x];
+            }
+            V &dst = bs[(size_t)kl * TB_ * CB + threadIdx.x];
+            if constexpr (DF) dst = df_add(dst, df_neg(v));
+            else dst -= v;
         }
         (void)j;
         __syncthreads();
@@ -1120,7 +1156,9 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
     for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_ * CB; e += FT) {
         const int kl = (int)(e / (TB_ * CB)), a = (int)((e / CB) % TB_), c = (int)(e % CB);
         const int64_t k = (int64_t)kl * CS + cr, i = k * TB_ + a;
-        bs[e] = (k < nblk && i < r && c < nc) ? B[i * ldb + c0 + c] : 0.0;
+        const double bv = (k < nblk && i < r && c < nc) ? B[i * ldb + c0 + c] : 0.0;
+        if constexpr (DF) bs[e] = d2df(bv);
+        else bs[e] = bv;
     }
     __syncthreads();
     // arm the receive slots for steps 0 .. 2CS-1, then let peers send
@@ -1136,7 +1174,7 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
         const int64_t k = blk(s);
         const int slot = (int)(s % NS);
         const bool mine = owner_of(s) == cr;
-        const double *xs = xb + (size_t)slot * TB_ * CB;
+        const V *xs = xb + (size_t)slot * TB_ * CB;
         if (!mine) wait(&bar_x[slot], (uint32_t)((s / NS) & 1));
         wait(&bar_sl[s & 1], (uint32_t)((s >> 1) & 1));
         __syncthreads();
@@ -1152,29 +1190,58 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
                 const int kl = e / TB_, a2 = e % TB_;
                 const int64_t k2 = (int64_t)kl * CS + cr;
                 if (kl == skip || k2 * TB_ + a2 >= r || !later(k2, k)) continue;
-                double acc[CB];
-                double *bb = bs + (size_t)kl * TB_ * CB + (size_t)a2 * CB;
+                V *bb = bs + (size_t)kl * TB_ * CB + (size_t)a2 * CB;
+                if constexpr (DF) {
+                    // b -= R coefficient * x in double-float (TwoProduct, TwoSum)
+                    float ah[CB], al[CB];
 #pragma unroll
-                for (int c = 0; c < CB; c++) acc[c] = bb[c];
-                if (kl < nsl) {
-                    const double *sp = sl + (((size_t)(s & 1) * nsl + kl) * TB_) * TB_ + a2;
-#pragma unroll 8
-                    for (int a = 0; a < nb; a++) {
-                        const double rv = sp[a * TB_];
-#pragma unroll
-                        for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xs[a * CB + c], acc[c]);
+                    for (int c = 0; c < CB; c++) {
+                        ah[c] = bb[c].h;
+                        al[c] = bb[c].l;
                     }
-                } else {
-                    const double *cp = C + k * TB_ * ldc + k2 * TB_ + a2;
+                    if (kl < nsl) {
+                        const double *sp = sl + (((size_t)(s & 1) * nsl + kl) * TB_) * TB_ + a2;
 #pragma unroll 4
-                    for (int a = 0; a < nb; a++) {
-                        const double rv = cp[a * ldc];
+                        for (int a = 0; a < nb; a++) {
+                            const F2 rv = d2df(sp[a * TB_]);
 #pragma unroll
-                        for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xs[a * CB + c], acc[c]);
+                            for (int c = 0; c < CB; c++) df_sub_prod(ah[c], al[c], rv, xs[a * CB + c]);
+                        }
+                    } else {
+                        const double *cp = C + k * TB_ * ldc + k2 * TB_ + a2;
+#pragma unroll 4
+                        for (int a = 0; a < nb; a++) {
+                            const F2 rv = d2df(cp[a * ldc]);
+#pragma unroll
+                            for (int c = 0; c < CB; c++) df_sub_prod(ah[c], al[c], rv, xs[a * CB + c]);
+                        }
                     }
-                }
 #pragma unroll
-                for (int c = 0; c < CB; c++) bb[c] = acc[c];
+                    for (int c = 0; c < CB; c++) bb[c] = df_renorm(ah[c], al[c]);
+                } else {
+                    double acc[CB];
+#pragma unroll
+                    for (int c = 0; c < CB; c++) acc[c] = bb[c];
+                    if (kl < nsl) {
+                        const double *sp = sl + (((size_t)(s & 1) * nsl + kl) * TB_) * TB_ + a2;
+#pragma unroll 8
+                        for (int a = 0; a < nb; a++) {
+                            const double rv = sp[a * TB_];
+#pragma unroll
+                            for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xs[a * CB + c], acc[c]);
+                        }
+                    } else {
+                        const double *cp = C + k * TB_ * ldc + k2 * TB_ + a2;
+#pragma unroll 4
+                        for (int a = 0; a < nb; a++) {
+                            const double rv = cp[a * ldc];
+#pragma unroll
+                            for (int c = 0; c < CB; c++) acc[c] = fma(-rv, xs[a * CB + c], acc[c]);
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < CB; c++) bb[c] = acc[c];
+                }
             }
         }
         __syncthreads();   // slot s, slab s read; bs updated
@@ -1200,7 +1267,10 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
     for (int64_t e = threadIdx.x; e < (int64_t)nown * TB_ * CB; e += FT) {
         const int kl = (int)(e / (TB_ * CB)), a = (int)((e / CB) % TB_), c = (int)(e % CB);
         const int64_t k = (int64_t)kl * CS + cr, i = k * TB_ + a;
-        if (k < nblk && i < r && c < nc) B[i * ldb + c0 + c] = bs[e];
+        if (k < nblk && i < r && c < nc) {
+            if constexpr (DF) B[i * ldb + c0 + c] = f2d(bs[e].h) + f2d(bs[e].l);
+            else B[i * ldb + c0 + c] = bs[e];
+        }
     }
 }
 
@@ -1472,10 +1542,10 @@ static std::atomic<int> g_tcluster{0};
 static std::mutex g_tcluster_mu;
 constexpr size_t TRSM_SMEM_MAX = 200 * 1024;   // trsm_launch's budget
 
-template <bool REV, int CB>
+template <bool REV, int CB, bool DF = false>
 static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const double *Dinv,
                         int64_t r, double *B, int64_t ldb, int64_t q, int *tflag) {
-    auto k = trsm_kernel<REV, CB>;
+    auto k = trsm_kernel<REV, CB, DF>;
     const int64_t nblk = (r + TB_ - 1) / TB_;
     const size_t budget = TRSM_SMEM_MAX;
     int cs = g_tcluster.load() ? g_tcluster.load() : 16;
@@ -1536,12 +1606,16 @@ static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const doub
 
 // Right-hand sides per cluster: spread small counts over several clusters
 // (each cluster's 16 SMs issue few FP64 operations per clock).
-template <bool REV>
+template <bool REV, bool DF = false>
 static void trsm_any(cudaStream_t s, const double *C, int64_t ldc, const double *Dinv, int64_t r,
                      double *B, int64_t ldb, int64_t q, int *tflag) {
     if (r <= 0 || q <= 0) return;
     if (ldc % TB_ != 0 || ldc < ((r + TB_ - 1) / TB_) * TB_)
         throw ElmError(ELM_ERR_ARG, "triangular factor stride must be a multiple of 32");
+    if (DF) {   // many right-hand sides only (forming K in the mixed form)
+        trsm_launch<REV, 8, DF>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
+        return;
+    }
     if (q <= 8) trsm_launch<REV, 1>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
     else if (q <= 16) trsm_launch<REV, 2>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
     else if (q <= 64) trsm_launch<REV, 4>(s, C, ldc, Dinv, r, B, ldb, q, tflag);
@@ -1565,8 +1639,9 @@ void trsm_fwd(cudaStream_t s, const double *R, int64_t ldr, const double *DinvF,
 }
 
 void trsm_bwd(cudaStream_t s, const double *Rt, int64_t ldr, const double *DinvB, int64_t r,
-              double *B, int64_t ldb, int64_t q, int *tflag) {
-    trsm_any<true>(s, Rt, ldr, DinvB, r, B, ldb, q, tflag);
+              double *B, int64_t ldb, int64_t q, int *tflag, bool df) {
+    if (df) trsm_any<true, true>(s, Rt, ldr, DinvB, r, B, ldb, q, tflag);
+    else trsm_any<true>(s, Rt, ldr, DinvB, r, B, ldb, q, tflag);
 }
 
 }  // namespace elm
