@@ -165,6 +165,8 @@ struct FactorWs {
     int32_t *rem;          // compaction map of the last panel
     int32_t *perm;         // pivot order
     FactorState *st;
+    __nv_bfloat16 *G;      // digit planes of the panel rows (tensor-core trailing update)
+    float *gs;             // their per-column power-of-two scales
 };
 size_t factor_ws_bytes(int64_t L);
 FactorWs factor_ws_carve(Arena &ar, int64_t L);
@@ -176,14 +178,25 @@ int64_t tri_ld(int64_t L);
 // ldr >= tri_ld(L), pivot order, unscaled, zero below the diagonal, in rows
 // >= rank and in the padding columns) and Rt = R^T (same shape), perm.
 // The rank lives in w.st->rank (device).  df: keep the active matrix as
-// double-float pairs and run the trailing updates on the FP32 pipes (about
-// 2^-44 relative per update; for the mixed form, whose Gram matrix is
-// itself accurate to about 2^-34), else FP64 throughout.
+// double-float pairs, run the panels on the FP32 pipes and the trailing
+// updates on the tensor cores from exact digit slices (about 2^-44 relative
+// per update; for the mixed form, whose Gram matrix is itself accurate to
+// about 2^-34), else FP64 throughout.
 // cs, nb: cluster size (8 or 16) and panel width of the pivot panels
 // (0: the built-in choice; nb is capped at the form's largest width).
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr,
                     int sms, bool df = false, int cs = 0, int nb = 0);
+
+// Mixed form's trailing update on the tensor cores: after a panel (st->steps
+// pivots, st->Lr columns left, compaction map rem) An[x, y] = A[rem x,
+// rem y] - sum_t P[t, rem x] P[t, rem y] on double-float pairs, from exact
+// 8-bit digit slices of the panel rows (G: 7 planes of trail_tc_rows(L) rows
+// x 32, gs: trail_tc_rows(L) scales).  Lup: an upper bound of st->Lr.
+int64_t trail_tc_rows(int64_t L);
+void trailing_tc(cudaStream_t s, const double *A, double *An, int64_t lda, const double *P,
+                 int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G, float *gs,
+                 int64_t Lcap, int64_t Lup);
 
 // Solves with the leading r x r block R11 of such a factor.  trsm_prepare
 // inverts its 32 x 32 diagonal blocks (DinvF, DinvB: trsm_dinv_doubles(r)
@@ -242,6 +255,10 @@ void check_finite(cudaStream_t s, const void *x, int xdt, int64_t rows, int64_t 
 // swizzle; out-of-range rows and columns read as zero.
 CUtensorMap make_map_f64(const double *base, int64_t rows, int64_t cols, int64_t ld, int bx,
                          int by);
+// 3-D bf16 map over digit planes [planes][rows][32] (64-byte swizzle), box
+// 32 x box_rows x box_planes.
+CUtensorMap make_map_planes(const __nv_bfloat16 *base, int64_t rows, int planes, int box_rows,
+                            int box_planes);
 
 // ------------------------------------------- tensor-core digit products
 int64_t oz_pad(int64_t v, int64_t q);

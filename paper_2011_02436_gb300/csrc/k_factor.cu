@@ -791,89 +791,9 @@ trailing_df_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
     }
 }
 
-// 64 x 64 lower tiles for large active matrices, each split into two CTAs
-// of 32 rows x 64 columns (128 threads, 4 x 4 independent double-float
-// chains per thread): the finer units balance the single wave over the SMs
-// (up to 8 resident per SM instead of 4).  The tile's panel rows are
-// staged once per CTA in shared memory.
-constexpr int TT2 = 64, TR2 = 32;
-__global__ void __launch_bounds__(128, 8)
-trailing_df64_kernel(const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
-                     const F2 *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
-                     const FactorState *__restrict__ st) {
-    const FactorState s = *st;
-    if (s.done) return;
-    const int64_t Lr = s.Lr;
-    const int steps = (int)s.steps;
-    const int64_t t = blockIdx.x;
-    int64_t J = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while (J * (J + 1) / 2 > t) J--;
-    while ((J + 1) * (J + 2) / 2 <= t) J++;
-    const int64_t I = t - J * (J + 1) / 2;
-    const int64_t r0 = J * TT2 + (int64_t)blockIdx.y * TR2, c0 = I * TT2;
-    if (r0 >= Lr) return;
-    __shared__ F2 Pr[TSTAGE][TR2];
-    __shared__ F2 Pc[TSTAGE][TT2];
-    __shared__ int32_t rr_[TR2], rc_[TT2];
-    if (threadIdx.x < TR2) {
-        const int64_t x = r0 + threadIdx.x;
-        rr_[threadIdx.x] = x < Lr ? rem[x] : -1;
-    }
-    if (threadIdx.x < TT2) {
-        const int64_t y = c0 + threadIdx.x;
-        rc_[threadIdx.x] = y < Lr ? rem[y] : -1;
-    }
-    __syncthreads();
-    // thread (ty, tx) owns rows ty + 8 p and columns tx + 16 q, p, q < 4
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float ah[4][4], al[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; p++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int a = rr_[ty + 8 * p], b = rc_[tx + 16 * q];
-            const F2 v = (a >= 0 && b >= 0) ? A[(int64_t)a * lda + b] : F2{0.f, 0.f};
-            ah[p][q] = v.h;
-            al[p][q] = v.l;
-        }
-    for (int t0 = 0; t0 < steps; t0 += TSTAGE) {   // panel rows TSTAGE at a time
-        const int nt = steps - t0 < TSTAGE ? steps - t0 : TSTAGE;
-        if (t0 > 0) __syncthreads();
-        for (int e = threadIdx.x; e < TSTAGE * TT2; e += 128) {
-            const int tt = e / TT2, k = e % TT2;
-            const int64_t row = (int64_t)(t0 + tt) * ldp;
-            Pc[tt][k] = (tt < nt && rc_[k] >= 0) ? P[row + rc_[k]] : F2{0.f, 0.f};
-            if (k < TR2) Pr[tt][k] = (tt < nt && rr_[k] >= 0) ? P[row + rr_[k]] : F2{0.f, 0.f};
-        }
-        __syncthreads();
-        for (int tt = 0; tt < nt; tt++) {
-            F2 u[4], w[4];
-#pragma unroll
-            for (int p = 0; p < 4; p++) {
-                u[p] = Pr[tt][ty + 8 * p];
-                w[p] = Pc[tt][tx + 16 * p];
-            }
-#pragma unroll
-            for (int p = 0; p < 4; p++)
-#pragma unroll
-                for (int q = 0; q < 4; q++) df_sub_prod(ah[p][q], al[p][q], u[p], w[q]);
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < 4; p++) {
-        const int64_t x = r0 + ty + 8 * p;
-        if (x >= Lr) continue;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int64_t y = c0 + tx + 16 * q;
-            if (y >= Lr) continue;
-            const float sh = ah[p][q] + al[p][q];
-            const F2 v{sh, al[p][q] - (sh - ah[p][q])};
-            An[x * lda + y] = v;
-            if (J != I) An[y * lda + x] = v;
-        }
-    }
-}
+// Active columns above which the mixed form's trailing update runs on the
+// tensor cores (exact digit slices, one launch pair per panel).
+constexpr int64_t TRAIL_TC_MIN = 256;
 
 // R[i, pos] = Rrow[i, perm pos] sqrt(dS[perm pos]) for i < rank, pos >= i;
 // Rt = R^T.  32 x 32 tiles transposed through shared memory.
@@ -1345,6 +1265,8 @@ FactorWs factor_ws_carve(Arena &ar, int64_t L) {
     w.rem = ar.take<int32_t>(L);
     w.perm = ar.take<int32_t>(L);
     w.st = ar.take<FactorState>(1);
+    w.G = ar.take<__nv_bfloat16>(7 * trail_tc_rows(L) * 32);
+    w.gs = ar.take<float>(trail_tc_rows(L));
     return w;
 }
 
@@ -1517,11 +1439,9 @@ void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, dou
         const int64_t Lup = L - (p + 1) * nb;
         if (Lup > 0) {
             int64_t T = (Lup + TT - 1) / TT;
-            if (df && Lup > 768) {
-                const int64_t T2 = (Lup + TT2 - 1) / TT2;
-                trailing_df64_kernel<<<dim3((unsigned)(T2 * (T2 + 1) / 2), TT2 / TR2), 128, 0, s>>>(
-                    (const F2 *)Ac, (F2 *)An, L, (const F2 *)w.P, L, w.rem, w.st);
-            } else if (df)
+            if (df && Lup > TRAIL_TC_MIN)
+                trailing_tc(s, Ac, An, L, w.P, L, w.rem, w.st, w.G, w.gs, trail_tc_rows(L), Lup);
+            else if (df)
                 trailing_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
                     (const F2 *)Ac, (F2 *)An, L, (const F2 *)w.P, L, w.rem, w.st);
             else
