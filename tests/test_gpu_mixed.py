@@ -176,3 +176,33 @@ def test_repeated_trainings_replay_the_factorisation_graph(elm, ctx, prec):
     ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
     assert res["rank"] == r
     assert rel(betas[2], ref) <= (1e-9 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("near_dup", [0.0, 1e-3])
+def test_mixed_factorisation_alone_is_double_float_accurate(elm, ctx, near_dup):
+    """The mixed factorisation by itself (double-float pivot panels, trailing
+    updates on the tensor cores from 8-bit digit slices while more than 256
+    columns remain), with no refinement to hide its error: the full-rank
+    solve of a Gram of L = 1100 columns agrees with the oracle's FP64 solve to
+    L kappa 2^-44 (kappa of the Gram), where a single-float trailing update
+    would be off by about kappa 2^-24.  near_dup > 0 pairs half the columns
+    with near copies of the other half (kappa about 10^7), so the later panels
+    work on small remaining diagonals and small per-column digit scales."""
+    import torch
+    rng = np.random.default_rng(5)
+    N, L, m = 4000, 1100, 3
+    H = rng.uniform(-1, 1, (N, L))
+    if near_dup:
+        H[:, L // 2:] = H[:, :L // 2] + near_dup * rng.uniform(-1, 1, (N, L // 2))
+    T = rng.standard_normal((N, m))
+    S0, Z0 = oracle.gram(H, T)
+    r0, perm0, R0 = oracle.pivchol(S0)
+    assert r0 == L
+    ref = oracle.frsolve(R0, r0, perm0, Z0)
+    kappa = np.linalg.cond(S0)
+    S = torch.from_numpy(S0).cuda()
+    f = elm.GramFactor(ctx, S, m, elm.PREC_MIXED)
+    assert f.rank == L
+    beta = f.solve(torch.from_numpy(Z0).cuda()).cpu().numpy()
+    f.close()
+    assert rel(beta, ref) <= L * kappa * 2.0 ** -44
