@@ -193,6 +193,8 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
 // rem y] - sum_t P[t, rem x] P[t, rem y] on double-float pairs, from exact
 // 8-bit digit slices of the panel rows (G: 7 planes of trail_tc_rows(L) rows
 // x 32, gs: trail_tc_rows(L) scales).  Lup: an upper bound of st->Lr.
+// Panels of up to TRAIL_TC_K pivots (one K block of the digit planes).
+constexpr int TRAIL_TC_K = 32;
 int64_t trail_tc_rows(int64_t L);
 void trailing_tc(cudaStream_t s, const double *A, double *An, int64_t lda, const double *P,
                  int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G, float *gs,

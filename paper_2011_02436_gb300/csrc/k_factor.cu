@@ -1439,7 +1439,7 @@ void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, dou
         const int64_t Lup = L - (p + 1) * nb;
         if (Lup > 0) {
             int64_t T = (Lup + TT - 1) / TT;
-            if (df && Lup > TRAIL_TC_MIN)
+            if (df && Lup > TRAIL_TC_MIN && nb <= TRAIL_TC_K)
                 trailing_tc(s, Ac, An, L, w.P, L, w.rem, w.st, w.G, w.gs, trail_tc_rows(L), Lup);
             else if (df)
                 trailing_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(

@@ -47,6 +47,7 @@ namespace {
 using df::F2;
 using namespace tcx;
 
+static_assert(TRAIL_TC_K == 32, "one 64-byte K row of bf16 digits per plane");
 constexpr int TR = 128;                    // tile rows (TMEM lanes)
 constexpr int TC = 32;                     // tile columns
 constexpr int NDIG = 6;                    // digits per panel entry
@@ -172,19 +173,26 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         tma_3d(&tmB, &full_bar, sB, 0, (int)c0, 0);   // planes 0..6: B digits "6", 5..0
     }
 
-    // this thread's row and columns; their entries of A (read transposed,
-    // A being symmetric, so that a warp's loads are contiguous)
+    // this thread's row x and its 16 columns y = yb + k; the valid ones
+    // (y < Ln, y <= x) are the prefix k < kv.  Their entries of A are read
+    // transposed (A is symmetric), so that a warp's loads are contiguous.
     const int quarter = warp & 3, half = warp >> 2;
     const int64_t x = r0 + quarter * 32 + lane;
-    const bool xin = x < Ln;
-    const int64_t rx = xin ? rem[x] : 0;
-    const float sx = xin ? gs[x] : 0.f;
-    const int cc0 = half * 16;
+    const int64_t yb = c0 + half * 16;
+    int64_t kv = Ln - yb < x - yb + 1 ? Ln - yb : x - yb + 1;
+    kv = x < Ln ? (kv < 16 ? kv : 16) : 0;
+    const int64_t rx = x < Ln ? rem[x] : 0;
+    const float sx = x < Ln ? gs[x] : 0.f;
     F2 av[16];
+    float cy[16];   // s_x s_y, a product of two powers of two
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-        const int64_t y = c0 + cc0 + k;
-        av[k] = (xin && y < Ln && y <= x) ? A[(int64_t)rem[y] * lda + rx] : F2{0.f, 0.f};
+        av[k] = F2{0.f, 0.f};
+        cy[k] = 0.f;
+        if (k < kv) {
+            av[k] = A[(int64_t)rem[yb + k] * lda + rx];
+            cy[k] = sx * gs[yb + k];
+        }
     }
 
     if (threadIdx.x == 0) {
@@ -211,42 +219,40 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     if (ok) {
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+        F2 *up = An + yb * lda + x;                                   // upper entries
+        F2 *sp = stage + (quarter * 32 + lane) * (TC + 1) + half * 16;   // lower, staged
 #pragma unroll
         for (int ps = 0; ps < 2; ps++) {
-            const int cc = cc0 + ps * 8;
             uint32_t dg[NDIAG][8];
 #pragma unroll
             for (int d = 0; d < NDIAG; d++)
-                tmem_ld8(tl + (uint32_t)((NDIAG - 1 - d) * TC + cc), dg[d]);
+                tmem_ld8(tl + (uint32_t)((NDIAG - 1 - d) * TC + half * 16 + ps * 8), dg[d]);
             tmem_wait_ld();
 #pragma unroll
             for (int d = 0; d < NDIAG; d++) reg_fence8(dg[d]);
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int64_t y = c0 + cc + k;
-                if (!(xin && y < Ln && y <= x)) continue;
+            for (int k8 = 0; k8 < 8; k8++) {
+                const int k = ps * 8 + k8;
+                if (k >= kv) break;
                 // sum_d D_d 2^(-14-8d): the two leading pairs exactly by TwoSum,
                 // the three smallest terms (below 2^-24) in FP32
                 float h1, l1, h2, l2, h, e;
-                two_sum(__uint_as_float(dg[0][k]) * 0x1p-14f, __uint_as_float(dg[1][k]) * 0x1p-22f, h1, l1);
-                two_sum(__uint_as_float(dg[2][k]) * 0x1p-30f, __uint_as_float(dg[3][k]) * 0x1p-38f, h2, l2);
-                const float tail = __uint_as_float(dg[4][k]) * 0x1p-46f +
-                                   (__uint_as_float(dg[5][k]) * 0x1p-54f +
-                                    __uint_as_float(dg[6][k]) * 0x1p-62f);
+                two_sum(__uint_as_float(dg[0][k8]) * 0x1p-14f, __uint_as_float(dg[1][k8]) * 0x1p-22f, h1, l1);
+                two_sum(__uint_as_float(dg[2][k8]) * 0x1p-30f, __uint_as_float(dg[3][k8]) * 0x1p-38f, h2, l2);
+                const float tail = __uint_as_float(dg[4][k8]) * 0x1p-46f +
+                                   (__uint_as_float(dg[5][k8]) * 0x1p-54f +
+                                    __uint_as_float(dg[6][k8]) * 0x1p-62f);
                 two_sum(h1, h2, h, e);
-                float l = ((l1 + l2) + e) + tail;
-                const float c = sx * gs[y];   // product of two powers of two
-                h *= c;
-                l *= c;
+                const float l = (((l1 + l2) + e) + tail) * cy[k];
+                h *= cy[k];
                 // A - (h + l), renormalised
-                const F2 a0 = av[cc - cc0 + k];
                 float sh, se;
-                two_sum(a0.h, -h, sh, se);
-                se += a0.l - l;
+                two_sum(av[k].h, -h, sh, se);
+                se += av[k].l - l;
                 const float rh = sh + se;
                 const F2 r{rh, se - (rh - sh)};
-                An[y * lda + x] = r;                                   // upper entry
-                stage[(quarter * 32 + lane) * (TC + 1) + cc + k] = r;  // lower, below
+                up[k * lda] = r;
+                sp[k] = r;
             }
         }
     }
