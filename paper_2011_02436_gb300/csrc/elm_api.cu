@@ -174,10 +174,17 @@ struct Solver {
     // per-solve scratch
     double *yb = nullptr, *v = nullptr, *w = nullptr;
     int *tflag = nullptr;
+    char *kws = nullptr;   // the tensor-core K solve's digit planes
 };
 
+// The mixed form forms K = R11^{-1} R12 on the tensor cores (32-row blocks,
+// exact digit updates) from this size on; smaller ones take the cluster solve.
+static bool ksolve_on_tensor_cores(int64_t r, int64_t q) { return r >= 256 && q >= 64; }
+
 // df_k: form K = R11^{-1} R12 in double-float (the mixed form, whose factor
-// is double-float accurate); the solves themselves stay FP64.
+// is double-float accurate): on the tensor cores by 32-row blocks from
+// ksolve_on_tensor_cores' size on, else by the double-float cluster solve;
+// the per-step solves stay FP64.
 Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const double *Rt,
                       int64_t ld, const int32_t *perm, int64_t r, int64_t L, int64_t m,
                       char **buf = nullptr, size_t *bufsize = nullptr, bool df_k = false) {
@@ -211,6 +218,7 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
             sv.DinvF2 = a.take<double>(trsm_dinv_doubles(q));
             sv.DinvB2 = a.take<double>(trsm_dinv_doubles(q));
             sv.f2 = factor_ws_carve(a, q);
+            if (df_k && ksolve_on_tensor_cores(r, q)) sv.kws = a.take<char>(ksolve_tc_bytes(r, q));
         }
     });
     ELM_CUDA(cudaMemsetAsync(sv.tflag, 0, sizeof(int), s));
@@ -218,7 +226,8 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
     if (q > 0 && r > 0) {
         copy2d(sv.K, q * sizeof(double), R + r, ld * sizeof(double),
                                    q * sizeof(double), r, cudaMemcpyDeviceToDevice, s);
-        trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag, df_k);
+        if (sv.kws) ksolve_tc(s, R, ld, sv.DinvF, r, sv.K, q, q, sv.kws, sv.tflag);
+        else trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag, df_k);
         syrk_f64(s, sv.K, r, q, q, sv.G2, q, sv.syrk_part, syrk_split);   // I + K^T K
         // I + K^T K is SPD with eigenvalues >= 1: full rank q
         factor_pivoted(s, sv.G2, q, q, 0.0, sv.f2, sv.R2, sv.Rt2, sv.ld2, ctx->sm_count);

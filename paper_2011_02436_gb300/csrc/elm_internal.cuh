@@ -200,6 +200,16 @@ void trailing_tc(cudaStream_t s, const double *A, double *An, int64_t lda, const
                  int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G, float *gs,
                  int64_t Lcap, int64_t Lup);
 
+// K = R11^{-1} B in place for the mixed form (B: r x q FP64, row stride ldb;
+// R: upper-triangular factor, row stride ldr; DinvF: the inverses of its
+// 32 x 32 diagonal blocks from trsm_prepare), by 32-row blocks whose updates
+// of the rows above run on the tensor cores from exact 8-bit digit slices
+// (double-float accurate).  ws: ksolve_tc_bytes(r, q) bytes; *flag |= 1 when
+// a bounded device-side wait gives up.
+size_t ksolve_tc_bytes(int64_t r, int64_t q);
+void ksolve_tc(cudaStream_t s, const double *R, int64_t ldr, const double *DinvF, int64_t r,
+               double *B, int64_t ldb, int64_t q, void *ws, int *flag);
+
 // Solves with the leading r x r block R11 of such a factor.  trsm_prepare
 // inverts its 32 x 32 diagonal blocks (DinvF, DinvB: trsm_dinv_doubles(r)
 // each); trsm_fwd then overwrites B (r x q, ldb) with R11^{-T} B reading R,

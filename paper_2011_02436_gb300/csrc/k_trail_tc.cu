@@ -45,6 +45,10 @@ namespace elm {
 namespace {
 
 using df::F2;
+using df::d2df;
+using df::df_acc_prod;
+using df::df_renorm;
+using df::f2d;
 using namespace tcx;
 
 static_assert(TRAIL_TC_K == 32, "one 64-byte K row of bf16 digits per plane");
@@ -70,6 +74,11 @@ static_assert(NDIAG * TC <= (int)TMEM_COLS, "diagonals exceed the allocation");
 static_assert((NPLANE - 0) * TC <= 256, "widest MMA above N = 256");
 static_assert(A_BYTES + B_BYTES + 1024 <= TRAIL_SMEM, "operands exceed shared memory");
 static_assert((size_t)TR * (TC + 1) * 8 + 1024 <= TRAIL_SMEM, "output tile exceeds shared memory");
+// the K solve's staged tile of B sits after the operands
+constexpr size_t KS_STAGE_OFF = 64 * 1024;
+static_assert(A_BYTES + B_BYTES <= KS_STAGE_OFF, "operands overlap the staged tile");
+static_assert(KS_STAGE_OFF + (size_t)TR * (TC + 1) * 8 + 1024 <= TRAIL_SMEM,
+              "staged tile exceeds shared memory");
 
 __device__ __forceinline__ float rint_small(float x) {   // |x| < 2^22: nearest integer
     return __fadd_rn(__fadd_rn(x, 12582912.f), -12582912.f);
@@ -78,6 +87,32 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
+}
+
+// Digits of one K row of 32 values, one per lane of a warp (zero where the
+// row is shorter): the smallest power of two s >= the largest |h| (1 for a
+// zero row; a denormal maximum rounds up to 2^-126), then six signed 8-bit
+// digits of v / s, digit j of weight 2^(-7-8j), into planes 6 - j of g
+// (plane stride pstride elements; plane 0 zero).  *sc = s (lane 0).
+__device__ __forceinline__ void warp_digits(F2 v, __nv_bfloat16 *g, int64_t pstride, float *sc) {
+    const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(v.h)));
+    uint32_t sb = (m + 0x7fffffu) & 0xff800000u;
+    if (sb == 0u) sb = 0x3f800000u;
+    const float inv = __uint_as_float((254u << 23) - sb);   // 1 / s, exact
+    // x = v / s, |x| <= 1 + 2^-24
+    float rh = v.h * inv * 128.f, rl = v.l * inv * 128.f;
+    g[0] = __float2bfloat16_rn(0.f);   // the zero plane
+#pragma unroll
+    for (int j = 0; j < NDIG; j++) {
+        const float a = rint_small(rh);   // |rh| <= 128 + 2^-9, so |a| <= 128
+        float e;
+        two_sum(rh - a, rl, rh, e);        // rh - a is exact, |.| <= 1/2
+        rl = e;
+        rh *= 256.f;
+        rl *= 256.f;
+        g[(int64_t)(NDIG - j) * pstride] = __float2bfloat16_rn(a);   // exact: |a| <= 128
+    }
+    if ((threadIdx.x & 31) == 0) *sc = __uint_as_float(sb);
 }
 
 // One warp per compacted column p < rows: scale and digits of its panel
@@ -95,28 +130,113 @@ trail_digits_kernel(const F2 *__restrict__ P, int64_t ldp, const int32_t *__rest
     if (p >= rows) return;
     F2 v{0.f, 0.f};
     if (p < Ln && lane < steps) v = P[(int64_t)lane * ldp + rem[p]];
-    // smallest power of two >= the largest |h| of the column (1 for a zero
-    // column; a denormal maximum rounds up to 2^-126)
-    const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(v.h)));
-    uint32_t sb = (m + 0x7fffffu) & 0xff800000u;
-    if (sb == 0u) sb = 0x3f800000u;
-    const float inv = __uint_as_float((254u << 23) - sb);   // 1 / s, exact
-    // x = v / s, |x| <= 1 + 2^-24; digit j carries weight 2^(-7-8j)
-    float rh = v.h * inv * 128.f, rl = v.l * inv * 128.f;
-    __nv_bfloat16 *g = G + p * 32 + lane;
-    const int64_t pstride = Lcap * 32;
-    g[0] = __float2bfloat16_rn(0.f);   // the zero plane
-#pragma unroll
-    for (int j = 0; j < NDIG; j++) {
-        const float a = rint_small(rh);   // |rh| <= 128 + 2^-9, so |a| <= 128
-        float e;
-        two_sum(rh - a, rl, rh, e);        // rh - a is exact, |.| <= 1/2
-        rl = e;
-        rh *= 256.f;
-        rl *= 256.f;
-        g[(int64_t)(NDIG - j) * pstride] = __float2bfloat16_rn(a);   // exact: |a| <= 128
+    warp_digits(v, G + p * 32 + lane, Lcap * 32, gs + p);
+}
+
+// Shared memory and tensor memory of one 128 x 32 output tile, and the
+// steps every tile kernel takes: set-up (barriers, tensor memory), the TMA
+// copies of both operands' digit planes with the twelve MMAs (thread 0),
+// the wait for them (all threads), the fold of the seven diagonal sums,
+// and the tear-down.
+struct TileSmem {
+    uint64_t full_bar, mma_bar;
+    uint32_t tmem;
+    int abort;
+};
+__device__ __forceinline__ void tile_setup(TileSmem &t) {
+    if (threadIdx.x == 0) {
+        mbar_init(&t.full_bar, 1);
+        mbar_init(&t.mma_bar, 1);
+        t.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (lane == 0) gs[p] = __uint_as_float(sb);
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&t.tmem)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+// thread 0: A digits 5..0 of rows a_row.. (planes 1..6 of tmA), B digits
+// "6", 5..0 of rows b_row.. (planes 0..6 of tmB)
+__device__ __forceinline__ void tile_load(TileSmem &t, const CUtensorMap *tmA, const CUtensorMap *tmB,
+                                          uint8_t *sA, uint8_t *sB, int a_row, int b_row) {
+    mbar_expect_tx(&t.full_bar, A_BYTES + B_BYTES);
+    tma_3d(tmA, &t.full_bar, sA, 0, a_row, 1);
+    tma_3d(tmB, &t.full_bar, sB, 0, b_row, 0);
+}
+// thread 0, after tile_load: A digit i (smem plane 5 - i) against B planes
+// i..6 (digits 6 - i .. 0), diagonal d = i + (6 - c) at column (6 - d) 32;
+// i = 0 reaches every column and comes first.
+__device__ __forceinline__ void tile_mma(TileSmem &t, uint8_t *sA, uint8_t *sB) {
+    volatile int *abort = &t.abort;
+    if (mbar_wait(&t.full_bar, 0, abort, TRAIL_WAIT_NS)) {
+        tc_fence_after();
+        const uint64_t da0 = desc_sw64(su32(sA)), db0 = desc_sw64(su32(sB));
+#pragma unroll
+        for (int i = 0; i < NDIG; i++) {
+            const uint64_t da = da0 + (uint64_t)(((NDIG - 1 - i) * A_PLANE) >> 4);
+            const uint64_t db = db0 + (uint64_t)((i * B_PLANE) >> 4);
+            const uint32_t idesc = IDESC_M128 | ((uint32_t)(((NPLANE - i) * TC) >> 3) << 17);
+#pragma unroll
+            for (int kk = 0; kk < 2; kk++)   // K = 32: two steps of 16
+                mma_bf16(t.tmem, da + 2 * kk, db + 2 * kk, idesc, (i == 0 && kk == 0) ? 0u : 1u);
+        }
+    }
+    mma_commit(&t.mma_bar);   // arrives once every MMA issued above has completed
+}
+__device__ __forceinline__ bool tile_wait(TileSmem &t) {
+    volatile int *abort = &t.abort;
+    const bool ok = mbar_wait(&t.mma_bar, 0, abort, TRAIL_WAIT_NS) && !*abort;
+    tc_fence_after();
+    return ok;
+}
+// the 8 x NDIAG accumulators of columns col.. of this thread's TMEM lane
+__device__ __forceinline__ void tile_ld8(const TileSmem &t, int quarter, int col,
+                                         uint32_t (&dg)[NDIAG][8]) {
+    const uint32_t tl = t.tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+    for (int d = 0; d < NDIAG; d++) tmem_ld8(tl + (uint32_t)((NDIAG - 1 - d) * TC + col), dg[d]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int d = 0; d < NDIAG; d++) reg_fence8(dg[d]);
+}
+// a - c sum_d D_d 2^(-14-8d) in double-float: the two leading pairs exactly
+// by TwoSum, the three smallest terms (below 2^-24) in FP32; c = s_x s_y
+__device__ __forceinline__ F2 fold_sub(const uint32_t (&dg)[NDIAG][8], int k8, float c, F2 a) {
+    float h1, l1, h2, l2, h, e;
+    two_sum(__uint_as_float(dg[0][k8]) * 0x1p-14f, __uint_as_float(dg[1][k8]) * 0x1p-22f, h1, l1);
+    two_sum(__uint_as_float(dg[2][k8]) * 0x1p-30f, __uint_as_float(dg[3][k8]) * 0x1p-38f, h2, l2);
+    const float tail = __uint_as_float(dg[4][k8]) * 0x1p-46f +
+                       (__uint_as_float(dg[5][k8]) * 0x1p-54f + __uint_as_float(dg[6][k8]) * 0x1p-62f);
+    two_sum(h1, h2, h, e);
+    const float l = (((l1 + l2) + e) + tail) * c;
+    h *= c;
+    float sh, se;
+    two_sum(a.h, -h, sh, se);
+    se += a.l - l;
+    const float rh = sh + se;
+    return F2{rh, se - (rh - sh)};
+}
+__device__ __forceinline__ void tile_teardown(TileSmem &t, FactorState *st, int *flag) {
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem),
+                     "r"(TMEM_COLS));
+    }
+    if (threadIdx.x == 0 && t.abort) {
+        // let the copies land before the CTA's shared memory is released
+        const uint64_t t0 = gtime();
+        while (!mbar_try(&t.full_bar, 0) && gtime() - t0 < TRAIL_WAIT_NS) {
+        }
+        if (st) atomicOr(&st->flags, 2);
+        if (flag) atomicOr(flag, 1);
+    }
 }
 
 // Lower tiles of 128 rows x 32 columns: row block rb holds column blocks
@@ -144,34 +264,10 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = sm, *sB = sm + A_BYTES;
     F2 *stage = reinterpret_cast<F2 *>(sm);   // [TR][TC + 1], after the MMAs
-    __shared__ __align__(8) uint64_t full_bar, mma_bar;
-    __shared__ uint32_t tmem_sh;
-    __shared__ int abort_sh;
+    __shared__ __align__(8) TileSmem ts;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    if (threadIdx.x == 0) {
-        mbar_init(&full_bar, 1);
-        mbar_init(&mma_bar, 1);
-        abort_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         su32(&tmem_sh)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_sh;
-    volatile int *abort = &abort_sh;
-
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(&full_bar, A_BYTES + B_BYTES);
-        tma_3d(&tmA, &full_bar, sA, 0, (int)r0, 1);   // planes 1..6: A digits 5..0
-        tma_3d(&tmB, &full_bar, sB, 0, (int)c0, 0);   // planes 0..6: B digits "6", 5..0
-    }
+    tile_setup(ts);
+    if (threadIdx.x == 0) tile_load(ts, &tmA, &tmB, sA, sB, (int)r0, (int)c0);
 
     // this thread's row x and its 16 columns y = yb + k; the valid ones
     // (y < Ln, y <= x) are the prefix k < kv.  Their entries of A are read
@@ -195,69 +291,26 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
     }
 
-    if (threadIdx.x == 0) {
-        if (mbar_wait(&full_bar, 0, abort, TRAIL_WAIT_NS)) {
-            tc_fence_after();
-            const uint64_t da0 = desc_sw64(su32(sA)), db0 = desc_sw64(su32(sB));
-            // A digit i (smem plane 5 - i) against B planes i..6 (digits
-            // 6 - i .. 0): diagonal d = i + (6 - c) at column (6 - d) 32.
-            // i = 0 reaches every column and comes first.
-#pragma unroll
-            for (int i = 0; i < NDIG; i++) {
-                const uint64_t da = da0 + (uint64_t)(((NDIG - 1 - i) * A_PLANE) >> 4);
-                const uint64_t db = db0 + (uint64_t)((i * B_PLANE) >> 4);
-                const uint32_t idesc = IDESC_M128 | ((uint32_t)(((NPLANE - i) * TC) >> 3) << 17);
-#pragma unroll
-                for (int kk = 0; kk < 2; kk++)   // K = 32: two steps of 16
-                    mma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (i == 0 && kk == 0) ? 0u : 1u);
-            }
-        }
-        mma_commit(&mma_bar);   // arrives once every MMA issued above has completed
-    }
-    const bool ok = mbar_wait(&mma_bar, 0, abort, TRAIL_WAIT_NS) && !*abort;
-    tc_fence_after();
-
+    if (threadIdx.x == 0) tile_mma(ts, sA, sB);
+    const bool ok = tile_wait(ts);
     if (ok) {
-        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         F2 *up = An + yb * lda + x;                                   // upper entries
         F2 *sp = stage + (quarter * 32 + lane) * (TC + 1) + half * 16;   // lower, staged
 #pragma unroll
         for (int ps = 0; ps < 2; ps++) {
             uint32_t dg[NDIAG][8];
-#pragma unroll
-            for (int d = 0; d < NDIAG; d++)
-                tmem_ld8(tl + (uint32_t)((NDIAG - 1 - d) * TC + half * 16 + ps * 8), dg[d]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int d = 0; d < NDIAG; d++) reg_fence8(dg[d]);
+            tile_ld8(ts, quarter, half * 16 + ps * 8, dg);
 #pragma unroll
             for (int k8 = 0; k8 < 8; k8++) {
                 const int k = ps * 8 + k8;
                 if (k >= kv) break;
-                // sum_d D_d 2^(-14-8d): the two leading pairs exactly by TwoSum,
-                // the three smallest terms (below 2^-24) in FP32
-                float h1, l1, h2, l2, h, e;
-                two_sum(__uint_as_float(dg[0][k8]) * 0x1p-14f, __uint_as_float(dg[1][k8]) * 0x1p-22f, h1, l1);
-                two_sum(__uint_as_float(dg[2][k8]) * 0x1p-30f, __uint_as_float(dg[3][k8]) * 0x1p-38f, h2, l2);
-                const float tail = __uint_as_float(dg[4][k8]) * 0x1p-46f +
-                                   (__uint_as_float(dg[5][k8]) * 0x1p-54f +
-                                    __uint_as_float(dg[6][k8]) * 0x1p-62f);
-                two_sum(h1, h2, h, e);
-                const float l = (((l1 + l2) + e) + tail) * cy[k];
-                h *= cy[k];
-                // A - (h + l), renormalised
-                float sh, se;
-                two_sum(av[k].h, -h, sh, se);
-                se += av[k].l - l;
-                const float rh = sh + se;
-                const F2 r{rh, se - (rh - sh)};
+                const F2 r = fold_sub(dg, k8, cy[k], av[k]);
                 up[k * lda] = r;
                 sp[k] = r;
             }
         }
     }
-    tc_fence_before();
-    __syncthreads();   // staged tile complete; every tensor-memory read done
+    __syncthreads();   // staged tile complete
     if (ok) {
         // lower entries A'[x, y], y < x: one 256-byte row segment per warp store
         for (int i = warp; i < TR; i += TTHREADS / 32) {
@@ -265,23 +318,168 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             if (xr < Ln && y < xr) An[xr * lda + y] = stage[i * (TC + 1) + lane];
         }
     }
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS));
+    tile_teardown(ts, st, nullptr);
+}
+
+// ------------------------------------------------- K = R11^-1 R12, blocked
+// Backward substitution in blocks of 32 rows, k = nblk-1 .. 0:
+//     X_k = U_k^{-1} B_k             (U_k: the k-th 32 x 32 diagonal block
+//                                     of R11, inverted in FP64 beforehand)
+//     B_i -= R[i, block k] X_k       for every row i < 32 k.
+// The updates are products of depth 32 on the tensor cores from exact digit
+// slices, as in the trailing update: the 32 entries of row i of R in block
+// column k (power-of-two scale per row) against the 32 entries of each
+// column of X_k (scale per column).  B (r x q, FP64 in memory) is updated in
+// double-float and stored back exactly (48 significant bits fit FP64);
+// X_k = U_k^{-1} B_k runs in double-float on the FP32 pipes.  Step k is two
+// launches: ksolve_prep_kernel (the digits of R's block column k for the
+// rows above it, and X_k with its digits) and ksolve_update_kernel.
+
+// Blocks [0, nrb): one warp per row i < rows_r (digits of R[i, 32k ..]);
+// blocks [nrb, ..): one warp per column c < q (X_k[:, c], written to B,
+// and its digits).
+__global__ void __launch_bounds__(256)
+ksolve_prep_kernel(const double *__restrict__ R, int64_t ldr, const double *__restrict__ DinvF,
+                   int64_t r, double *__restrict__ B, int64_t ldb, int64_t q, int64_t k,
+                   int64_t rows_r, int64_t nrb, __nv_bfloat16 *__restrict__ GR,
+                   float *__restrict__ gsR, int64_t Rcap, __nv_bfloat16 *__restrict__ GX,
+                   float *__restrict__ gsX, int64_t Qcap) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t c0 = k * 32;
+    const int nbk = (int)(r - c0 < 32 ? r - c0 : 32);
+    if (blockIdx.x < nrb) {
+        const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+        if (i >= rows_r) return;
+        const F2 v = lane < nbk ? d2df(R[i * ldr + c0 + lane]) : F2{0.f, 0.f};
+        warp_digits(v, GR + i * 32 + lane, Rcap * 32, gsR + i);
+        return;
     }
-    if (threadIdx.x == 0 && *abort) {
-        // let the copies land before the CTA's shared memory is released
-        const uint64_t t0 = gtime();
-        while (!mbar_try(&full_bar, 0) && gtime() - t0 < TRAIL_WAIT_NS) {
+    const int64_t c = (int64_t)(blockIdx.x - nrb) * 8 + warp;
+    if (c >= q) return;
+    // lane a holds B[c0 + a, c]; lane l forms X[l] = sum_a Uinv[l, a] B[a]
+    const F2 bv = lane < nbk ? d2df(B[(c0 + lane) * ldb + c]) : F2{0.f, 0.f};
+    const double *ui = DinvF + k * 1024 + lane * 32;
+    float sh = 0.f, sl = 0.f;
+#pragma unroll 8
+    for (int a2 = 0; a2 < 32; a2++) {
+        const F2 ba{__shfl_sync(0xffffffffu, bv.h, a2), __shfl_sync(0xffffffffu, bv.l, a2)};
+        df_acc_prod(sh, sl, d2df(ui[a2]), ba);
+    }
+    const F2 x = lane < nbk ? df_renorm(sh, sl) : F2{0.f, 0.f};
+    if (lane < nbk) B[(c0 + lane) * ldb + c] = f2d(x.h) + f2d(x.l);
+    warp_digits(x, GX + c * 32 + lane, Qcap * 32, gsX + c);
+}
+
+// Tiles of 128 rows (< rows) x 32 columns (< q) of B: B -= R[:, block k] X_k.
+// The tile of B is staged in shared memory (row-wise coalesced loads and
+// stores) while the copies and MMAs run.
+__global__ void __launch_bounds__(TTHREADS, 2)
+ksolve_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     double *__restrict__ B, int64_t ldb, int64_t rows, int64_t q,
+                     const float *__restrict__ gsR, const float *__restrict__ gsX, int *flag) {
+    const int64_t nnt = (q + TC - 1) / TC;
+    const int64_t r0 = (int64_t)(blockIdx.x / nnt) * TR, c0 = (int64_t)(blockIdx.x % nnt) * TC;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = sm, *sB = sm + A_BYTES;
+    double *stage = reinterpret_cast<double *>(sm + KS_STAGE_OFF);   // [TR][TC + 1]
+    __shared__ __align__(8) TileSmem ts;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    tile_setup(ts);
+    if (threadIdx.x == 0) tile_load(ts, &tmA, &tmB, sA, sB, (int)r0, (int)c0);
+    const bool cin = c0 + lane < q;
+    for (int i = warp; i < TR; i += TTHREADS / 32)
+        if (r0 + i < rows && cin) stage[i * (TC + 1) + lane] = B[(r0 + i) * ldb + c0 + lane];
+    if (threadIdx.x == 0) tile_mma(ts, sA, sB);
+    const bool ok = tile_wait(ts);
+    __syncthreads();   // staged tile of B visible
+    const int quarter = warp & 3, half = warp >> 2;
+    const int64_t x = r0 + quarter * 32 + lane;
+    if (ok && x < rows) {
+        const float sx = gsR[x];
+        double *sp = stage + (quarter * 32 + lane) * (TC + 1) + half * 16;
+#pragma unroll
+        for (int ps = 0; ps < 2; ps++) {
+            uint32_t dg[NDIAG][8];
+            tile_ld8(ts, quarter, half * 16 + ps * 8, dg);
+#pragma unroll
+            for (int k8 = 0; k8 < 8; k8++) {
+                const int kk = ps * 8 + k8;
+                const int64_t y = c0 + half * 16 + kk;
+                if (y >= q) break;
+                const F2 v = fold_sub(dg, k8, sx * gsX[y], d2df(sp[kk]));
+                sp[kk] = f2d(v.h) + f2d(v.l);
+            }
         }
-        atomicOr(&st->flags, 2);
     }
+    __syncthreads();   // updated tile complete
+    if (ok)
+        for (int i = warp; i < TR; i += TTHREADS / 32)
+            if (r0 + i < rows && cin) B[(r0 + i) * ldb + c0 + lane] = stage[i * (TC + 1) + lane];
+    tile_teardown(ts, nullptr, flag);
 }
 
 }  // namespace
 
 int64_t trail_tc_rows(int64_t L) { return (L + TR - 1) / TR * TR; }
+
+namespace {
+struct KsWs {
+    __nv_bfloat16 *GR, *GX;
+    float *gsR, *gsX;
+    int64_t Rcap, Qcap;
+};
+KsWs ksolve_carve(Arena &a, int64_t r, int64_t q) {
+    KsWs w;
+    w.Rcap = (r + TR - 1) / TR * TR;
+    w.Qcap = (q + TC - 1) / TC * TC;
+    w.GR = a.take<__nv_bfloat16>(NPLANE * w.Rcap * 32);
+    w.GX = a.take<__nv_bfloat16>(NPLANE * w.Qcap * 32);
+    w.gsR = a.take<float>(w.Rcap);
+    w.gsX = a.take<float>(w.Qcap);
+    return w;
+}
+}  // namespace
+
+size_t ksolve_tc_bytes(int64_t r, int64_t q) {
+    Arena a;
+    ksolve_carve(a, r, q);
+    return a.used + 256;
+}
+
+void ksolve_tc(cudaStream_t s, const double *R, int64_t ldr, const double *DinvF, int64_t r,
+               double *B, int64_t ldb, int64_t q, void *ws, int *flag) {
+    static const bool attr = [] {
+        ELM_CUDA(cudaFuncSetAttribute(ksolve_update_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TRAIL_SMEM));
+        return true;
+    }();
+    (void)attr;
+    if (r <= 0 || q <= 0) return;
+    Arena a;
+    a.base = (char *)ws;
+    a.cap = ksolve_tc_bytes(r, q);
+    const KsWs w = ksolve_carve(a, r, q);
+    // rows beyond r and columns beyond q are never written back; zero their
+    // digits once so that no stale bits reach the tensor cores
+    ELM_CUDA(cudaMemsetAsync(w.GR, 0, sizeof(__nv_bfloat16) * NPLANE * w.Rcap * 32, s));
+    ELM_CUDA(cudaMemsetAsync(w.GX, 0, sizeof(__nv_bfloat16) * NPLANE * w.Qcap * 32, s));
+    const CUtensorMap ma = make_map_planes(w.GR, w.Rcap, NPLANE, TR, NDIG);
+    const CUtensorMap mb = make_map_planes(w.GX, w.Qcap, NPLANE, TC, NPLANE);
+    const int64_t nblk = (r + 31) / 32, nnt = (q + TC - 1) / TC, nxb = (q + 7) / 8;
+    for (int64_t k = nblk - 1; k >= 0; k--) {
+        const int64_t rows = 32 * k, nrb = (rows + 7) / 8;
+        ksolve_prep_kernel<<<(unsigned)(nrb + nxb), 256, 0, s>>>(
+            R, ldr, DinvF, r, B, ldb, q, k, rows, nrb, w.GR, w.gsR, w.Rcap, w.GX, w.gsX, w.Qcap);
+        ELM_CHECK_LAUNCH();
+        if (rows == 0) continue;
+        const int64_t nmt = (rows + TR - 1) / TR;
+        ksolve_update_kernel<<<(unsigned)(nmt * nnt), TTHREADS, TRAIL_SMEM, s>>>(
+            ma, mb, B, ldb, rows, q, w.gsR, w.gsX, flag);
+        ELM_CHECK_LAUNCH();
+    }
+}
 
 void trailing_tc(cudaStream_t s, const double *A, double *An, int64_t lda, const double *P,
                  int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G, float *gs,

@@ -206,3 +206,43 @@ def test_mixed_factorisation_alone_is_double_float_accurate(elm, ctx, near_dup):
     beta = f.solve(torch.from_numpy(Z0).cuda()).cpu().numpy()
     f.close()
     assert rel(beta, ref) <= L * kappa * 2.0 ** -44
+
+
+def test_train_rank_deficient_k_on_tensor_cores(elm, ctx):
+    """r = 700 independent neurons and q = 150 duplicates or power-of-two
+    scaled copies: the mixed form forms K = R11^-1 R12 by 32-row blocks whose
+    updates run on the tensor cores (ragged last block, q not a multiple of
+    the 32-column tiles); rank exact, beta within the mixed bar."""
+    p = synth.make_problem(4000, 40, 700, 5, n_dup=100, n_scaled=50, x_kind="normal")
+    prob = problem(p)
+    res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
+    ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["rank"] == r == 700
+    assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
+
+
+def test_mixed_full_rank_route_of_a_rank_deficient_gram(elm, ctx):
+    """The mixed factorisation and the full-rank route without refinement on
+    a Gram of rank r = 900 with q = 197 exact duplicate columns (K = R11^-1
+    R12 on the tensor cores): rank as the oracle's, and the solve within
+    L kappa 2^-44 of the oracle's FP64 route (kappa of the independent
+    columns' Gram), where a K of single-float accuracy would miss by about
+    kappa 2^-24."""
+    import torch
+    rng = np.random.default_rng(8)
+    N, r, q, m = 4000, 900, 197, 3
+    H0 = rng.uniform(-1, 1, (N, r))
+    H = np.concatenate([H0, H0[:, rng.integers(0, r, q)]], axis=1)
+    H = H[:, rng.permutation(r + q)]
+    T = rng.standard_normal((N, m))
+    S0, Z0 = oracle.gram(H, T)
+    tau = 1e-9
+    r0, perm0, R0 = oracle.pivchol(S0, tau)
+    assert r0 == r
+    ref = oracle.frsolve(R0, r0, perm0, Z0)
+    f = elm.GramFactor(ctx, torch.from_numpy(S0).cuda(), m, elm.PREC_MIXED, tol_rank=tau)
+    assert f.rank == r
+    beta = f.solve(torch.from_numpy(Z0).cuda()).cpu().numpy()
+    f.close()
+    S1 = S0[np.ix_(perm0[:r0], perm0[:r0])]
+    assert rel(beta, ref) <= (r + q) * np.linalg.cond(S1) * 2.0 ** -44
