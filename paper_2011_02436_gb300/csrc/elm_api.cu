@@ -175,6 +175,10 @@ struct Solver {
     double *yb = nullptr, *v = nullptr, *w = nullptr;
     int *tflag = nullptr;
     char *kws = nullptr;   // the tensor-core K solve's digit planes
+    // I + K^T K on the tensor cores (mixed form): K^T, its digit planes, scales
+    double *Kt = nullptr, *khs = nullptr;
+    __nv_bfloat16 *kplanes = nullptr;
+    float *khsf = nullptr;
 };
 
 // The mixed form forms K = R11^{-1} R12 on the tensor cores (32-row blocks,
@@ -218,7 +222,13 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
             sv.DinvF2 = a.take<double>(trsm_dinv_doubles(q));
             sv.DinvB2 = a.take<double>(trsm_dinv_doubles(q));
             sv.f2 = factor_ws_carve(a, q);
-            if (df_k && ksolve_on_tensor_cores(r, q)) sv.kws = a.take<char>(ksolve_tc_bytes(r, q));
+            if (df_k && ksolve_on_tensor_cores(r, q)) {
+                sv.kws = a.take<char>(ksolve_tc_bytes(r, q));
+                sv.Kt = a.take<double>(q * r);
+                sv.kplanes = a.take<__nv_bfloat16>(oz_exact_planes_bytes(r, q, 0) / 2);
+                sv.khs = a.take<double>(oz_pad(q, 128));
+                sv.khsf = a.take<float>(oz_pad(q, 128));
+            }
         }
     });
     ELM_CUDA(cudaMemsetAsync(sv.tflag, 0, sizeof(int), s));
@@ -228,9 +238,19 @@ Solver solver_prepare(elm_ctx *ctx, cudaStream_t s, const double *R, const doubl
                                    q * sizeof(double), r, cudaMemcpyDeviceToDevice, s);
         if (sv.kws) ksolve_tc(s, R, ld, sv.DinvF, r, sv.K, q, q, sv.kws, sv.tflag);
         else trsm_bwd(s, Rt, ld, sv.DinvB, r, sv.K, q, q, sv.tflag, df_k);
-        syrk_f64(s, sv.K, r, q, q, sv.G2, q, sv.syrk_part, syrk_split);   // I + K^T K
-        // I + K^T K is SPD with eigenvalues >= 1: full rank q
-        factor_pivoted(s, sv.G2, q, q, 0.0, sv.f2, sv.R2, sv.Rt2, sv.ld2, ctx->sm_count);
+        if (sv.Kt) {
+            // I + K^T K to FP64 accuracy on the tensor cores (the Gram of K's
+            // columns, exact digit pairs)
+            transpose_f64(s, sv.K, r, q, q, sv.Kt, r);
+            oz_gram_exact(s, sv.Kt, r, r, q, 0, sv.kplanes, sv.khs, sv.khsf, sv.G2, q, sv.tflag,
+                          nullptr);
+            add_identity(s, sv.G2, q, q);
+        } else {
+            syrk_f64(s, sv.K, r, q, q, sv.G2, q, sv.syrk_part, syrk_split);   // I + K^T K
+        }
+        // I + K^T K is SPD with eigenvalues >= 1: full rank q (double-float
+        // factor for the mixed form, like the Gram's)
+        factor_pivoted(s, sv.G2, q, q, 0.0, sv.f2, sv.R2, sv.Rt2, sv.ld2, ctx->sm_count, df_k);
         trsm_prepare(s, sv.R2, sv.ld2, q, sv.DinvF2, sv.DinvB2);
     }
     return sv;

@@ -239,6 +239,8 @@ void sumsq(cudaStream_t s, const double *x, int64_t rows, int64_t cols, int64_t 
 void axpy_norms(cudaStream_t s, double *beta, const double *dB, int64_t count, double *out);
 // A (n x n) = I.
 void set_identity(cudaStream_t s, double *A, int64_t n);
+// A[i, i] += 1, i < n
+void add_identity(cudaStream_t s, double *A, int64_t n, int64_t lda);
 // B (cols x rows, ldb) = A^T for A (rows x cols, lda).
 void transpose_f64(cudaStream_t s, const double *A, int64_t rows, int64_t cols, int64_t lda,
                    double *B, int64_t ldb);

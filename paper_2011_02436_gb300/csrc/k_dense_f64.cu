@@ -598,6 +598,11 @@ __global__ void set_identity_kernel(double *__restrict__ A, int64_t n) {
     for (; e < n * n; e += (int64_t)gridDim.x * blockDim.x) A[e] = (e / n == e % n) ? 1.0 : 0.0;
 }
 
+__global__ void add_identity_kernel(double *__restrict__ A, int64_t n, int64_t lda) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) A[i * lda + i] += 1.0;
+}
+
 __global__ void sub_rows_kernel(const double *__restrict__ A, int64_t lda,
                                 const double *__restrict__ B, int64_t rows, int64_t m,
                                 double *__restrict__ out) {
@@ -1056,6 +1061,12 @@ void transpose_f64(cudaStream_t s, const double *A, int64_t rows, int64_t cols, 
 
 void set_identity(cudaStream_t s, double *A, int64_t n) {
     set_identity_kernel<<<blocks_for(n * n), 256, 0, s>>>(A, n);
+    ELM_CHECK_LAUNCH();
+}
+
+void add_identity(cudaStream_t s, double *A, int64_t n, int64_t lda) {
+    if (n <= 0) return;
+    add_identity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, n, lda);
     ELM_CHECK_LAUNCH();
 }
 
