@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <functional>
 #include <mutex>
@@ -1089,6 +1090,18 @@ void back_halves_on_lanes(elm_ctx *ctx, const std::vector<Problem> &Ps, int64_t 
         l->timing = ctx->timing;
         ELM_CUDA(cudaStreamWaitEvent(l->stream, ready, 0));
     }
+    // the lanes take the problems in descending order of their estimated
+    // back-half work (factorisation L^3/3, refinement 2 N L m), so that no
+    // large problem starts last and leaves one lane running alone
+    std::vector<int64_t> order((size_t)gn);
+    for (int64_t j = 0; j < gn; j++) order[(size_t)j] = j;
+    auto cost = [&](int64_t j) {
+        const elm_problem *q = Ps[(size_t)(i0 + j)].p;
+        const double L = (double)q->L;
+        return L * L * L / 3.0 + 2.0 * (double)q->N * L * (double)q->m;
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return cost(a) > cost(b); });
     std::atomic<int64_t> next{0};
     std::atomic<bool> stop{false};
     std::mutex mu;
@@ -1103,8 +1116,9 @@ void back_halves_on_lanes(elm_ctx *ctx, const std::vector<Problem> &Ps, int64_t 
         }
         for (;;) {
             if (stop.load()) return;
-            const int64_t j = next.fetch_add(1);
-            if (j >= gn) return;
+            const int64_t n = next.fetch_add(1);
+            if (n >= gn) return;
+            const int64_t j = order[(size_t)n];
             elm_result r{};
             try {
                 mark(lc, 2);
