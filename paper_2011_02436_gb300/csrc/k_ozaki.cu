@@ -583,7 +583,13 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         Unit U;
         Walk wk = walk_begin();
         while (ok && walk_next(wk, U)) {
-            const OzParams &Pu = BAT ? *U.P : P;
+            // batched mode: the unit's parameters copied once into this
+            // thread's own memory, which the epilogue's global stores cannot
+            // alias (read through U.P, every field would be reloaded after
+            // each store)
+            OzParams Pb;
+            if (BAT) Pb = *U.P;
+            const OzParams &Pu = BAT ? Pb : P;
             const int64_t t = U.t;
             const int c_lo = U.c_lo, c_hi = U.c_hi;
             const bool direct = (EPI != 0) && U.nchunk == 1;
