@@ -930,6 +930,12 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
     auto rows = [&](int64_t k) { return (int)(r - k * TB_ < TB_ ? r - k * TB_ : TB_); };
     // own block k2 takes part in the update of step k
     auto later = [&](int64_t k2, int64_t k) { return k2 < nblk && (REV ? k2 < k : k2 > k); };
+    // The slab window holds the nsl own blocks that take part in the most
+    // steps: a block is updated by every step before it (R^T x = b) or after
+    // it (R x = b), so the last of this CTA's blocks, or the first.
+    const int nmine = (int)((nblk - cr + CS - 1) / CS);
+    const int wlo = REV ? 0 : (nmine > nsl ? nmine - nsl : 0);
+    auto in_win = [&](int kl) { return kl >= wlo && kl < wlo + nsl; };
 
     // warp 1: inverse block of step s into dg[s % NDG] (if owned; else an
     // empty phase, so every buffer's phase count follows the step count)
@@ -948,23 +954,23 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
         }
     };
     // thread 0: the 32 x 32 tiles of C coupling block k_s with the own
-    // blocks to update (those inside the window nsl) into sl[s & 1], one
+    // blocks to update (those inside the window) into sl[s & 1], one
     // tensor-map copy per tile (rows past r read as zero)
     auto fill_slab = [&](int64_t s) {
         if (s >= nblk || threadIdx.x != 0) return;
         const int64_t k = blk(s);
         const int buf = (int)(s & 1);
         int cnt = 0;
-        for (int kl = 0; kl < nsl; kl++) cnt += later((int64_t)kl * CS + cr, k) ? 1 : 0;
+        for (int kl = wlo; kl < wlo + nsl; kl++) cnt += later((int64_t)kl * CS + cr, k) ? 1 : 0;
         if (!cnt) {
             mbar_arrive(&bar_sl[buf]);
             return;
         }
         mbar_expect(&bar_sl[buf], (uint32_t)cnt * TB_ * TB_ * 8);
-        for (int kl = 0; kl < nsl; kl++) {
+        for (int kl = wlo; kl < wlo + nsl; kl++) {
             const int64_t k2 = (int64_t)kl * CS + cr;
             if (!later(k2, k)) continue;
-            tma2d_g2s(&tmC, &bar_sl[buf], sl + ((size_t)buf * nsl + kl) * TB_ * TB_,
+            tma2d_g2s(&tmC, &bar_sl[buf], sl + ((size_t)buf * nsl + (kl - wlo)) * TB_ * TB_,
                       (int)(k2 * TB_), (int)(k * TB_));
         }
     };
@@ -974,8 +980,8 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
     // coefficient of x_{k_s*TB_+a} in equation k2*TB_+jj
     auto coef = [&](int64_t s, int kl, int a, int jj) {
         const int64_t k = blk(s), k2 = (int64_t)kl * CS + cr;
-        return kl < nsl ? sl[(((size_t)(s & 1) * nsl + kl) * TB_ + a) * TB_ + jj]
-                        : C[(k * TB_ + a) * ldc + k2 * TB_ + jj];
+        return in_win(kl) ? sl[(((size_t)(s & 1) * nsl + (kl - wlo)) * TB_ + a) * TB_ + jj]
+                          : C[(k * TB_ + a) * ldc + k2 * TB_ + jj];
     };
 
     // owner of step s: x = Dinv_k b_k with all warps (warp: column warp %
@@ -1119,8 +1125,8 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
                         ah[c] = bb[c].h;
                         al[c] = bb[c].l;
                     }
-                    if (kl < nsl) {
-                        const double *sp = sl + (((size_t)(s & 1) * nsl + kl) * TB_) * TB_ + a2;
+                    if (in_win(kl)) {
+                        const double *sp = sl + (((size_t)(s & 1) * nsl + (kl - wlo)) * TB_) * TB_ + a2;
 #pragma unroll 4
                         for (int a = 0; a < nb; a++) {
                             const F2 rv = d2df(sp[a * TB_]);
@@ -1142,8 +1148,8 @@ trsm_kernel(const __grid_constant__ CUtensorMap tmC, const double *__restrict__ 
                     double acc[CB];
 #pragma unroll
                     for (int c = 0; c < CB; c++) acc[c] = bb[c];
-                    if (kl < nsl) {
-                        const double *sp = sl + (((size_t)(s & 1) * nsl + kl) * TB_) * TB_ + a2;
+                    if (in_win(kl)) {
+                        const double *sp = sl + (((size_t)(s & 1) * nsl + (kl - wlo)) * TB_) * TB_ + a2;
 #pragma unroll 8
                         for (int a = 0; a < nb; a++) {
                             const double rv = sp[a * TB_];
@@ -1460,7 +1466,7 @@ void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, dou
 
 static std::atomic<int> g_tcluster{0};
 static std::mutex g_tcluster_mu;
-constexpr size_t TRSM_SMEM_MAX = 200 * 1024;   // trsm_launch's budget
+constexpr size_t TRSM_SMEM_MAX = 216 * 1024;   // trsm_launch's budget
 
 template <bool REV, int CB, bool DF = false>
 static void trsm_launch(cudaStream_t s, const double *C, int64_t ldc, const double *Dinv,
