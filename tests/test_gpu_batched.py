@@ -108,3 +108,28 @@ def test_lanes_do_not_change_results(elm, ctx):
     for i, r, b in zip(LANE_CASES, res, betas):
         assert r["status"] in (0, 5) and r["rank"] == int(g["rank"][i])
         assert rel(b, g["beta_%03d" % i]) <= bar_for(g, i, 1e-6)
+
+
+def test_lanes_rank_deficient_k_on_tensor_cores(elm, ctx):
+    """Rank-deficient problems whose K = R11^-1 R12 is formed on the tensor
+    cores (r >= 256, q >= 64) and whose trailing updates run on the tensor
+    cores, trained in one batched call on several lanes at once (each lane
+    its own workspaces for the digit planes): bit for bit the results of one
+    lane, ranks and betas as the oracle's."""
+    shapes = [(3000, 30, 400, 3, 80, 20), (2500, 20, 330, 5, 60, 40), (3500, 40, 520, 2, 100, 0),
+              (2800, 25, 300, 4, 70, 10)]
+    ps = [synth.make_problem(N, n, L, m, n_dup=d, n_scaled=sc, x_kind="normal",
+                             seed=synth.SEED_BASE + 7000 + 13 * i)
+          for i, (N, n, L, m, d, sc) in enumerate(shapes)]
+    out = {}
+    for lanes in (1, 4):
+        probs = [problem(p) for p in ps]
+        res = elm.elm_train(ctx, probs, precision=elm.PREC_MIXED, lanes=lanes, check=False)
+        out[lanes] = (res, [pr["beta"].cpu().numpy() for pr in probs])
+    for r1, b1, r4, b4 in zip(*out[1], *out[4]):
+        assert r1["rank"] == r4["rank"] and np.array_equal(b1, b4)
+    for p, r, b in zip(ps, *out[1]):
+        ref, rank, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+        assert r["status"] == 0 and r["form"] == elm.FORM_MIXED   # settled in the mixed form
+        assert r["rank"] == rank == p["rank"]
+        assert rel(b, ref) <= 1e-6

@@ -217,6 +217,7 @@ def test_train_rank_deficient_k_on_tensor_cores(elm, ctx):
     prob = problem(p)
     res = elm.elm_train(ctx, prob, precision=elm.PREC_MIXED)[0]
     ref, r, _ = oracle.train(p["X"], p["W"], p["b"], p["a"], p["act"], p["T"])
+    assert res["form"] == elm.FORM_MIXED   # settled in the mixed form, K on the tensor cores
     assert res["rank"] == r == 700
     assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-6
 
