@@ -473,7 +473,7 @@ void train_one(elm_ctx *ctx, const Problem &P, elm_result *res) {
     mark(ctx, 2);
     // Eq. 6, Algorithm 1 steps 3-4: permutation, rank, split
     factor_pivoted(s, S, lds, L, P.tau, f, R, Rt, tri_ld(L), ctx->sm_count, /*df=*/false,
-                   P.tune.panel_cs, P.tune.panel_nb);
+                   P.tune.panel_cs, P.tune.panel_nb, /*tc64=*/tc);
     mark(ctx, 3);
     int32_t fl = 0, xfl = 0;
     int terr = 0;

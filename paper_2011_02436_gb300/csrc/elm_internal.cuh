@@ -184,21 +184,27 @@ int64_t tri_ld(int64_t L);
 // about 2^-34), else FP64 throughout.
 // cs, nb: cluster size (8 or 16) and panel width of the pivot panels
 // (0: the built-in choice; nb is capped at the form's largest width).
+// tc64 (FP64 panels only): the trailing updates on the tensor cores from
+// exact seven-digit slices (FP64-level accuracy; the FP64 form with
+// tensor-core products).
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr,
-                    int sms, bool df = false, int cs = 0, int nb = 0);
+                    int sms, bool df = false, int cs = 0, int nb = 0, bool tc64 = false);
 
-// Mixed form's trailing update on the tensor cores: after a panel (st->steps
-// pivots, st->Lr columns left, compaction map rem) An[x, y] = A[rem x,
-// rem y] - sum_t P[t, rem x] P[t, rem y] on double-float pairs, from exact
-// 8-bit digit slices of the panel rows (G: 7 planes of trail_tc_rows(L) rows
-// x 32, gs: trail_tc_rows(L) scales).  Lup: an upper bound of st->Lr.
-// Panels of up to TRAIL_TC_K pivots (one K block of the digit planes).
+// Trailing update on the tensor cores: after a panel (st->steps pivots,
+// st->Lr columns left, compaction map rem) An[x, y] = A[rem x, rem y] -
+// sum_t P[t, rem x] P[t, rem y], from exact 8-bit digit slices of the panel
+// rows: double-float pairs in six digits (the mixed form), or FP64 values in
+// seven digits with an exact integer fold (f64; FP64-level accuracy).  G:
+// trail_tc_planes() planes of trail_tc_rows(L) rows x 32, gs:
+// trail_tc_rows(L) scales.  Lup: an upper bound of st->Lr.  Panels of up to
+// TRAIL_TC_K pivots (one K block of the digit planes).
 constexpr int TRAIL_TC_K = 32;
 int64_t trail_tc_rows(int64_t L);
+int trail_tc_planes();
 void trailing_tc(cudaStream_t s, const double *A, double *An, int64_t lda, const double *P,
                  int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G, float *gs,
-                 int64_t Lcap, int64_t Lup);
+                 int64_t Lcap, int64_t Lup, bool f64);
 
 // K = R11^{-1} B in place for the mixed form (B: r x q FP64, row stride ldb;
 // R: upper-triangular factor, row stride ldr; DinvF: the inverses of its

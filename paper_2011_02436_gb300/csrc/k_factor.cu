@@ -1271,7 +1271,7 @@ FactorWs factor_ws_carve(Arena &ar, int64_t L) {
     w.rem = ar.take<int32_t>(L);
     w.perm = ar.take<int32_t>(L);
     w.st = ar.take<FactorState>(1);
-    w.G = ar.take<__nv_bfloat16>(7 * trail_tc_rows(L) * 32);
+    w.G = ar.take<__nv_bfloat16>(trail_tc_planes() * trail_tc_rows(L) * 32);
     w.gs = ar.take<float>(trail_tc_rows(L));
     return w;
 }
@@ -1287,13 +1287,14 @@ struct FactorGraph {
 std::mutex g_fgraph_mu;
 std::map<std::string, FactorGraph> g_fgraph;
 void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, double tau,
-                    const FactorWs &w, double *R, double *Rt, int64_t ldr, bool df, int cs, int nb,
-                    int64_t wmax, size_t smem, PanelFn kpanel);
+                    const FactorWs &w, double *R, double *Rt, int64_t ldr, bool df, bool tc64,
+                    int cs, int nb, int64_t wmax, size_t smem, PanelFn kpanel);
 }  // namespace
 
 void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
                     double tau, const FactorWs &w, double *R, double *Rt, int64_t ldr, int sms,
-                    bool df, int cs_req, int nb_req) {
+                    bool df, int cs_req, int nb_req, bool tc64) {
+    tc64 = tc64 && !df;
     if (ldr < tri_ld(L)) throw ElmError(ELM_ERR_ARG, "factor stride below tri_ld(L)");
     if (L > ELM_MAX_L) throw ElmError(ELM_ERR_UNSUPPORTED, "L above ELM_MAX_L");
     int nb16, nb8;
@@ -1332,11 +1333,11 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
     // instead of two launches per panel.  (Workspaces are reused between
     // trainings of one shape, so the pointers repeat.)
     char key[320];
-    snprintf(key, sizeof key, "%p %ld %ld %a %p %p %p %p %p %p %p %p %p %p %p %p %p %ld %d %d %d",
+    snprintf(key, sizeof key, "%p %ld %ld %a %p %p %p %p %p %p %p %p %p %p %p %p %p %ld %d %d %d %d",
              (const void *)S, (long)lds, (long)L, tau, (void *)w.A0, (void *)w.A1,
              (void *)w.Rrow, (void *)w.P, (void *)w.dS, (void *)w.sc, (void *)w.act0,
              (void *)w.act1, (void *)w.rem, (void *)w.perm, (void *)w.st, (void *)R, (void *)Rt,
-             (long)ldr, (int)df, cs, nb);
+             (long)ldr, (int)df, (int)tc64, cs, nb);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     ELM_CUDA(cudaStreamIsCapturing(s, &cap));
     bool full = false;
@@ -1367,7 +1368,7 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
         ELM_CUDA(cudaStreamBeginCapture(cs_stream, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t graph = nullptr;
         try {
-            factor_enqueue(cs_stream, S, lds, L, tau, w, R, Rt, ldr, df, cs, nb, wmax, smem,
+            factor_enqueue(cs_stream, S, lds, L, tau, w, R, Rt, ldr, df, tc64, cs, nb, wmax, smem,
                            kpanel);
         } catch (...) {
             cudaStreamEndCapture(cs_stream, &graph);
@@ -1401,14 +1402,14 @@ void factor_pivoted(cudaStream_t s, const double *S, int64_t lds, int64_t L,
         return;
     }
     // inside a caller's capture, or the cache is full: enqueue directly
-    factor_enqueue(s, S, lds, L, tau, w, R, Rt, ldr, df, cs, nb, wmax, smem, kpanel);
+    factor_enqueue(s, S, lds, L, tau, w, R, Rt, ldr, df, tc64, cs, nb, wmax, smem, kpanel);
 }
 
 namespace {
 
 void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, double tau,
-                    const FactorWs &w, double *R, double *Rt, int64_t ldr, bool df, int cs, int nb,
-                    int64_t wmax, size_t smem, PanelFn kpanel) {
+                    const FactorWs &w, double *R, double *Rt, int64_t ldr, bool df, bool tc64,
+                    int cs, int nb, int64_t wmax, size_t smem, PanelFn kpanel) {
     ELM_CUDA(cudaMemsetAsync(w.st, 0, sizeof(FactorState), s));
     ELM_CUDA(cudaMemsetAsync(w.Rrow, 0, sizeof(double) * L * L, s));
     {
@@ -1445,8 +1446,9 @@ void factor_enqueue(cudaStream_t s, const double *S, int64_t lds, int64_t L, dou
         const int64_t Lup = L - (p + 1) * nb;
         if (Lup > 0) {
             int64_t T = (Lup + TT - 1) / TT;
-            if (df && Lup > TRAIL_TC_MIN && nb <= TRAIL_TC_K)
-                trailing_tc(s, Ac, An, L, w.P, L, w.rem, w.st, w.G, w.gs, trail_tc_rows(L), Lup);
+            if ((df || tc64) && Lup > TRAIL_TC_MIN && nb <= TRAIL_TC_K)
+                trailing_tc(s, Ac, An, L, w.P, L, w.rem, w.st, w.G, w.gs, trail_tc_rows(L), Lup,
+                            /*f64=*/tc64);
             else if (df)
                 trailing_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
                     (const F2 *)Ac, (F2 *)An, L, (const F2 *)w.P, L, w.rem, w.st);

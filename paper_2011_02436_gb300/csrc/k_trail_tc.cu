@@ -36,6 +36,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "df_arith.cuh"
 #include "elm_internal.cuh"
 #include "tc_ptx.cuh"
@@ -54,14 +56,29 @@ using namespace tcx;
 static_assert(TRAIL_TC_K == 32, "one 64-byte K row of bf16 digits per plane");
 constexpr int TR = 128;                    // tile rows (TMEM lanes)
 constexpr int TC = 32;                     // tile columns
-constexpr int NDIG = 6;                    // digits per panel entry
-constexpr int NDIAG = NDIG + 1;            // kept diagonals d = 0..6
-constexpr int NPLANE = NDIG + 1;           // digit planes incl. the zero plane
 constexpr uint32_t A_PLANE = TR * 64;      // bytes of one A plane (128 rows x 32 bf16)
 constexpr uint32_t B_PLANE = TC * 64;      // bytes of one B plane
-constexpr uint32_t A_BYTES = NDIG * A_PLANE;
-constexpr uint32_t B_BYTES = NPLANE * B_PLANE;
-constexpr uint32_t TMEM_COLS = 256;        // NDIAG x 32 = 224 used
+constexpr uint32_t TMEM_COLS = 256;        // NDIAG x 32 (224 or 256) used
+// The two digit schemes: double-float entries (the mixed form) in six
+// digits, FP64 entries (the FP64 form with tensor-core products) in seven;
+// the kept diagonals are d = 0 .. NDIG and plane 0 of B is the zero plane.
+template <bool F64>
+struct Scheme {
+    static constexpr int NDIG = F64 ? 7 : 6;
+    static constexpr int NDIAG = NDIG + 1;
+    static constexpr int NPLANE = NDIG + 1;
+    static constexpr uint32_t A_BYTES = NDIG * A_PLANE;
+    static constexpr uint32_t B_BYTES = NPLANE * B_PLANE;
+};
+using SDF = Scheme<false>;
+using S64 = Scheme<true>;
+// the mixed form's scheme (the K solve uses it)
+constexpr int NDIG = SDF::NDIG;
+constexpr int NDIAG = SDF::NDIAG;
+constexpr int NPLANE = SDF::NPLANE;
+constexpr uint32_t A_BYTES = SDF::A_BYTES;
+constexpr uint32_t B_BYTES = SDF::B_BYTES;
+constexpr int MAX_PLANES = S64::NPLANE;    // planes of the shared digit buffer
 constexpr int TTHREADS = 256;              // two warps per TMEM lane quarter
 // Dynamic shared memory: the operands (62 KB) and, once the MMAs are done,
 // the transposed output tile.  Asking for 100 KB keeps at most two CTAs on
@@ -70,9 +87,9 @@ constexpr size_t TRAIL_SMEM = 100 * 1024;
 constexpr uint64_t TRAIL_WAIT_NS = 2000000000ull;
 // kind::f16, bf16 x bf16 -> f32, K-major operands, M = 128 (N set per MMA)
 constexpr uint32_t IDESC_M128 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TR >> 4) << 24);
-static_assert(NDIAG * TC <= (int)TMEM_COLS, "diagonals exceed the allocation");
-static_assert((NPLANE - 0) * TC <= 256, "widest MMA above N = 256");
-static_assert(A_BYTES + B_BYTES + 1024 <= TRAIL_SMEM, "operands exceed shared memory");
+static_assert(S64::NDIAG * TC <= (int)TMEM_COLS, "diagonals exceed the allocation");
+static_assert(S64::NPLANE * TC <= 256, "widest MMA above N = 256");
+static_assert(S64::A_BYTES + S64::B_BYTES + 1024 <= TRAIL_SMEM, "operands exceed shared memory");
 static_assert((size_t)TR * (TC + 1) * 8 + 1024 <= TRAIL_SMEM, "output tile exceeds shared memory");
 // the K solve's staged tile of B sits after the operands
 constexpr size_t KS_STAGE_OFF = 64 * 1024;
@@ -115,10 +132,40 @@ __device__ __forceinline__ void warp_digits(F2 v, __nv_bfloat16 *g, int64_t pstr
     if ((threadIdx.x & 31) == 0) *sc = __uint_as_float(sb);
 }
 
+// The same for FP64 values in seven digits: s = 2^(E+1) for the largest
+// exponent E of the row (at least 2^-126, 1 for a zero row), |v| / s < 1;
+// X = rint(v / s 2^55) (|X| < 2^55, the part below 2^-56 s dropped) split
+// into balanced base-256 digits from the least significant one with
+// integer operations (digit 0 the rest, |digit| <= 128).
+__device__ __forceinline__ void warp_digits64(double v, __nv_bfloat16 *g, int64_t pstride,
+                                              float *sc) {
+    const uint32_t hw = (uint32_t)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+    const uint32_t m = __reduce_max_sync(0xffffffffu, hw);
+    int e = (int)(m >> 20) - 1023 + 1;   // exponent of s
+    if (m == 0u) e = 0;
+    e = e < -126 ? -126 : (e > 127 ? 127 : e);   // a float scale
+    const double inv = __longlong_as_double((long long)(1023 - e) << 52);   // 2^-e
+    long long X = __double2ll_rn(v * inv * 0x1p55);
+    float d[S64::NDIG];
+#pragma unroll
+    for (int j = S64::NDIG - 1; j >= 1; j--) {
+        const long long r = ((X + 128) & 255) - 128;
+        d[j] = (float)(int)r;
+        X = (X - r) >> 8;
+    }
+    d[0] = (float)(int)X;
+    g[0] = __float2bfloat16_rn(0.f);   // the zero plane
+#pragma unroll
+    for (int j = 0; j < S64::NDIG; j++)
+        g[(int64_t)(S64::NDIG - j) * pstride] = __float2bfloat16_rn(d[j]);   // exact
+    if ((threadIdx.x & 31) == 0) *sc = __uint_as_float((uint32_t)(e + 127) << 23);
+}
+
 // One warp per compacted column p < rows: scale and digits of its panel
 // entries P[t, rem p], t < steps (zero beyond, and for p >= Ln).
+template <bool F64>
 __global__ void __launch_bounds__(256)
-trail_digits_kernel(const F2 *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
+trail_digits_kernel(const double *__restrict__ P, int64_t ldp, const int32_t *__restrict__ rem,
                     const FactorState *__restrict__ st, __nv_bfloat16 *__restrict__ G,
                     float *__restrict__ gs, int64_t Lcap, int64_t rows) {
     const FactorState s = *st;
@@ -128,9 +175,14 @@ trail_digits_kernel(const F2 *__restrict__ P, int64_t ldp, const int32_t *__rest
     const int lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (p >= rows) return;
-    F2 v{0.f, 0.f};
-    if (p < Ln && lane < steps) v = P[(int64_t)lane * ldp + rem[p]];
-    warp_digits(v, G + p * 32 + lane, Lcap * 32, gs + p);
+    const bool in = p < Ln && lane < steps;
+    const int64_t i = in ? (int64_t)lane * ldp + rem[p] : 0;
+    if constexpr (F64) {
+        warp_digits64(in ? P[i] : 0.0, G + p * 32 + lane, Lcap * 32, gs + p);
+    } else {
+        warp_digits(in ? reinterpret_cast<const F2 *>(P)[i] : F2{0.f, 0.f}, G + p * 32 + lane,
+                    Lcap * 32, gs + p);
+    }
 }
 
 // Shared memory and tensor memory of one 128 x 32 output tile, and the
@@ -162,25 +214,27 @@ __device__ __forceinline__ void tile_setup(TileSmem &t) {
 }
 // thread 0: A digits 5..0 of rows a_row.. (planes 1..6 of tmA), B digits
 // "6", 5..0 of rows b_row.. (planes 0..6 of tmB)
+template <class S = SDF>
 __device__ __forceinline__ void tile_load(TileSmem &t, const CUtensorMap *tmA, const CUtensorMap *tmB,
                                           uint8_t *sA, uint8_t *sB, int a_row, int b_row) {
-    mbar_expect_tx(&t.full_bar, A_BYTES + B_BYTES);
+    mbar_expect_tx(&t.full_bar, S::A_BYTES + S::B_BYTES);
     tma_3d(tmA, &t.full_bar, sA, 0, a_row, 1);
     tma_3d(tmB, &t.full_bar, sB, 0, b_row, 0);
 }
 // thread 0, after tile_load: A digit i (smem plane 5 - i) against B planes
 // i..6 (digits 6 - i .. 0), diagonal d = i + (6 - c) at column (6 - d) 32;
 // i = 0 reaches every column and comes first.
+template <class S = SDF>
 __device__ __forceinline__ void tile_mma(TileSmem &t, uint8_t *sA, uint8_t *sB) {
     volatile int *abort = &t.abort;
     if (mbar_wait(&t.full_bar, 0, abort, TRAIL_WAIT_NS)) {
         tc_fence_after();
         const uint64_t da0 = desc_sw64(su32(sA)), db0 = desc_sw64(su32(sB));
 #pragma unroll
-        for (int i = 0; i < NDIG; i++) {
-            const uint64_t da = da0 + (uint64_t)(((NDIG - 1 - i) * A_PLANE) >> 4);
+        for (int i = 0; i < S::NDIG; i++) {
+            const uint64_t da = da0 + (uint64_t)(((S::NDIG - 1 - i) * A_PLANE) >> 4);
             const uint64_t db = db0 + (uint64_t)((i * B_PLANE) >> 4);
-            const uint32_t idesc = IDESC_M128 | ((uint32_t)(((NPLANE - i) * TC) >> 3) << 17);
+            const uint32_t idesc = IDESC_M128 | ((uint32_t)(((S::NPLANE - i) * TC) >> 3) << 17);
 #pragma unroll
             for (int kk = 0; kk < 2; kk++)   // K = 32: two steps of 16
                 mma_bf16(t.tmem, da + 2 * kk, db + 2 * kk, idesc, (i == 0 && kk == 0) ? 0u : 1u);
@@ -195,14 +249,15 @@ __device__ __forceinline__ bool tile_wait(TileSmem &t) {
     return ok;
 }
 // the 8 x NDIAG accumulators of columns col.. of this thread's TMEM lane
+template <int ND>
 __device__ __forceinline__ void tile_ld8(const TileSmem &t, int quarter, int col,
-                                         uint32_t (&dg)[NDIAG][8]) {
+                                         uint32_t (&dg)[ND][8]) {
     const uint32_t tl = t.tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-    for (int d = 0; d < NDIAG; d++) tmem_ld8(tl + (uint32_t)((NDIAG - 1 - d) * TC + col), dg[d]);
+    for (int d = 0; d < ND; d++) tmem_ld8(tl + (uint32_t)((ND - 1 - d) * TC + col), dg[d]);
     tmem_wait_ld();
 #pragma unroll
-    for (int d = 0; d < NDIAG; d++) reg_fence8(dg[d]);
+    for (int d = 0; d < ND; d++) reg_fence8(dg[d]);
 }
 // a - c sum_d D_d 2^(-14-8d) in double-float: the two leading pairs exactly
 // by TwoSum, the three smallest terms (below 2^-24) in FP32; c = s_x s_y
@@ -220,6 +275,34 @@ __device__ __forceinline__ F2 fold_sub(const uint32_t (&dg)[NDIAG][8], int k8, f
     se += a.l - l;
     const float rh = sh + se;
     return F2{rh, se - (rh - sh)};
+}
+// exact value of an integer |v| < 2^53 as a double, by integer operations
+__device__ __forceinline__ double i2d_exact(long long v) {
+    if (v == 0) return 0.0;
+    const unsigned long long sg = v < 0 ? 1ull << 63 : 0ull;
+    const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+    const int lz = __clzll((long long)a);
+    const unsigned long long mant = lz == 63 ? 0ull : (a << (lz + 1)) >> 12;   // below the leading one
+    return __longlong_as_double((long long)(sg | ((unsigned long long)(1023 + 63 - lz) << 52) | mant));
+}
+// a - c sum_d D_d 2^(-14-8d), d = 0..7, in FP64: the diagonals as integers
+// (exact, |D_d| < 2^22), folded exactly into two 47-bit integers, then one
+// FMA for their sum and one for the subtraction (c = s_x s_y exact)
+__device__ __forceinline__ double fold_sub64(const uint32_t (&dg)[S64::NDIAG][8], int k8, float c,
+                                             double a) {
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+        const int v = __float_as_int(__uint_as_float(dg[d][k8]) + 12582912.f) - 0x4B400000;
+        hi = hi * 256 + v;
+    }
+#pragma unroll
+    for (int d = 4; d < 8; d++) {
+        const int v = __float_as_int(__uint_as_float(dg[d][k8]) + 12582912.f) - 0x4B400000;
+        lo = lo * 256 + v;
+    }
+    const double sum = fma(i2d_exact(lo), 0x1p-70, i2d_exact(hi) * 0x1p-38);
+    return fma(-sum, f2d(c), a);   // c: a power of two, exact in both formats
 }
 __device__ __forceinline__ void tile_teardown(TileSmem &t, FactorState *st, int *flag) {
     tc_fence_before();
@@ -242,13 +325,20 @@ __device__ __forceinline__ void tile_teardown(TileSmem &t, FactorState *st, int 
 // Lower tiles of 128 rows x 32 columns: row block rb holds column blocks
 // 0 .. 4 rb + 3.  Warp 0 allocates tensor memory; thread 0 issues the two
 // TMA copies (all A planes of the tile's rows, all B planes of its columns)
-// and the twelve MMAs; all eight warps prefetch their entries of A, then
-// drain (warp w: TMEM lanes 32 (w mod 4) .., columns 16 (w / 4) ..).
+// and the MMAs; all eight warps prefetch their entries of A, then drain
+// (warp w: TMEM lanes 32 (w mod 4) .., columns 16 (w / 4) ..).  F64: the
+// active matrix holds FP64 values and the seven-digit scheme applies;
+// else double-float pairs and six digits.
+template <bool F64>
 __global__ void __launch_bounds__(TTHREADS, 2)
 trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const F2 *__restrict__ A, F2 *__restrict__ An, int64_t lda,
+                   const double *__restrict__ A, double *__restrict__ An, int64_t lda,
                    const int32_t *__restrict__ rem, const float *__restrict__ gs,
                    FactorState *st) {
+    using S = Scheme<F64>;
+    using V = typename std::conditional<F64, double, F2>::type;
+    const V *Av = reinterpret_cast<const V *>(A);
+    V *Anv = reinterpret_cast<V *>(An);
     const FactorState s = *st;
     if (s.done) return;
     const int64_t Ln = s.Lr;
@@ -262,12 +352,12 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = sm, *sB = sm + A_BYTES;
-    F2 *stage = reinterpret_cast<F2 *>(sm);   // [TR][TC + 1], after the MMAs
+    uint8_t *sA = sm, *sB = sm + S::A_BYTES;
+    V *stage = reinterpret_cast<V *>(sm);   // [TR][TC + 1], after the MMAs
     __shared__ __align__(8) TileSmem ts;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     tile_setup(ts);
-    if (threadIdx.x == 0) tile_load(ts, &tmA, &tmB, sA, sB, (int)r0, (int)c0);
+    if (threadIdx.x == 0) tile_load<S>(ts, &tmA, &tmB, sA, sB, (int)r0, (int)c0);
 
     // this thread's row x and its 16 columns y = yb + k; the valid ones
     // (y < Ln, y <= x) are the prefix k < kv.  Their entries of A are read
@@ -279,32 +369,34 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     kv = x < Ln ? (kv < 16 ? kv : 16) : 0;
     const int64_t rx = x < Ln ? rem[x] : 0;
     const float sx = x < Ln ? gs[x] : 0.f;
-    F2 av[16];
+    V av[16];
     float cy[16];   // s_x s_y, a product of two powers of two
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-        av[k] = F2{0.f, 0.f};
+        av[k] = V{};
         cy[k] = 0.f;
         if (k < kv) {
-            av[k] = A[(int64_t)rem[yb + k] * lda + rx];
+            av[k] = Av[(int64_t)rem[yb + k] * lda + rx];
             cy[k] = sx * gs[yb + k];
         }
     }
 
-    if (threadIdx.x == 0) tile_mma(ts, sA, sB);
+    if (threadIdx.x == 0) tile_mma<S>(ts, sA, sB);
     const bool ok = tile_wait(ts);
     if (ok) {
-        F2 *up = An + yb * lda + x;                                   // upper entries
-        F2 *sp = stage + (quarter * 32 + lane) * (TC + 1) + half * 16;   // lower, staged
+        V *up = Anv + yb * lda + x;                                   // upper entries
+        V *sp = stage + (quarter * 32 + lane) * (TC + 1) + half * 16;   // lower, staged
 #pragma unroll
         for (int ps = 0; ps < 2; ps++) {
-            uint32_t dg[NDIAG][8];
-            tile_ld8(ts, quarter, half * 16 + ps * 8, dg);
+            uint32_t dg[S::NDIAG][8];
+            tile_ld8<S::NDIAG>(ts, quarter, half * 16 + ps * 8, dg);
 #pragma unroll
             for (int k8 = 0; k8 < 8; k8++) {
                 const int k = ps * 8 + k8;
                 if (k >= kv) break;
-                const F2 r = fold_sub(dg, k8, cy[k], av[k]);
+                V r;
+                if constexpr (F64) r = fold_sub64(dg, k8, cy[k], av[k]);
+                else r = fold_sub(dg, k8, cy[k], av[k]);
                 up[k * lda] = r;
                 sp[k] = r;
             }
@@ -315,7 +407,7 @@ trailing_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         // lower entries A'[x, y], y < x: one 256-byte row segment per warp store
         for (int i = warp; i < TR; i += TTHREADS / 32) {
             const int64_t xr = r0 + i, y = c0 + lane;
-            if (xr < Ln && y < xr) An[xr * lda + y] = stage[i * (TC + 1) + lane];
+            if (xr < Ln && y < xr) Anv[xr * lda + y] = stage[i * (TC + 1) + lane];
         }
     }
     tile_teardown(ts, st, nullptr);
@@ -481,29 +573,41 @@ void ksolve_tc(cudaStream_t s, const double *R, int64_t ldr, const double *DinvF
     }
 }
 
-void trailing_tc(cudaStream_t s, const double *A, double *An, int64_t lda, const double *P,
-                 int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G, float *gs,
-                 int64_t Lcap, int64_t Lup) {
-    static const bool attr = [] {   // once per process, thread-safely
-        ELM_CUDA(cudaFuncSetAttribute(trailing_tc_kernel,
+namespace {
+template <bool F64>
+void trailing_tc_launch(cudaStream_t s, const double *A, double *An, int64_t lda, const double *P,
+                        int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G,
+                        float *gs, int64_t Lcap, int64_t Lup) {
+    using S = Scheme<F64>;
+    static const bool attr = [] {   // once per process and scheme, thread-safely
+        ELM_CUDA(cudaFuncSetAttribute(trailing_tc_kernel<F64>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)TRAIL_SMEM));
         return true;
     }();
     (void)attr;
-    if (Lup <= 0) return;
-    if (Lcap % TR || Lup > Lcap)
-        throw ElmError(ELM_ERR_ARG, "trailing update: bad sizes");
-    const CUtensorMap ma = make_map_planes(G, Lcap, NPLANE, TR, NDIG);
-    const CUtensorMap mb = make_map_planes(G, Lcap, NPLANE, TC, NPLANE);
+    const CUtensorMap ma = make_map_planes(G, Lcap, S::NPLANE, TR, S::NDIG);
+    const CUtensorMap mb = make_map_planes(G, Lcap, S::NPLANE, TC, S::NPLANE);
     const int64_t rows = trail_tc_rows(Lup);   // rows any tile reads
-    trail_digits_kernel<<<(unsigned)(rows / 8), 256, 0, s>>>((const F2 *)P, ldp, rem, st, G, gs,
-                                                             Lcap, rows);
+    trail_digits_kernel<F64><<<(unsigned)(rows / 8), 256, 0, s>>>(P, ldp, rem, st, G, gs, Lcap,
+                                                                  rows);
     ELM_CHECK_LAUNCH();
     const int64_t nrb = rows / TR;
-    trailing_tc_kernel<<<(unsigned)(2 * nrb * (nrb + 1)), TTHREADS, TRAIL_SMEM, s>>>(
-        ma, mb, (const F2 *)A, (F2 *)An, lda, rem, gs, st);
+    trailing_tc_kernel<F64><<<(unsigned)(2 * nrb * (nrb + 1)), TTHREADS, TRAIL_SMEM, s>>>(
+        ma, mb, A, An, lda, rem, gs, st);
     ELM_CHECK_LAUNCH();
+}
+}  // namespace
+
+int trail_tc_planes() { return MAX_PLANES; }
+
+void trailing_tc(cudaStream_t s, const double *A, double *An, int64_t lda, const double *P,
+                 int64_t ldp, const int32_t *rem, FactorState *st, __nv_bfloat16 *G, float *gs,
+                 int64_t Lcap, int64_t Lup, bool f64) {
+    if (Lup <= 0) return;
+    if (Lcap % TR || Lup > Lcap) throw ElmError(ELM_ERR_ARG, "trailing update: bad sizes");
+    if (f64) trailing_tc_launch<true>(s, A, An, lda, P, ldp, rem, st, G, gs, Lcap, Lup);
+    else trailing_tc_launch<false>(s, A, An, lda, P, ldp, rem, st, G, gs, Lcap, Lup);
 }
 
 }  // namespace elm

@@ -40,6 +40,10 @@ CASES = {
     "tanh_wide_m": lambda: synth.make_problem(2500, 54, 301, 26, act=synth.ACT_TANH),
     "ragged": lambda: synth.make_problem(1037, 13, 121, 3, x_kind="normal", x_dtype=np.float64),
     "tiny": lambda: synth.make_problem(65, 5, 7, 1, act=synth.ACT_TANH),
+    # more than 256 columns stay active for 40 panels: the trailing updates
+    # run on the tensor cores from seven-digit slices with the exact fold
+    "trailing_on_tensor_cores": lambda: synth.make_problem(6000, 64, 1200, 5, n_dup=30,
+                                                           n_scaled=10),
 }
 
 
@@ -52,7 +56,7 @@ def test_fp64_tc_matches_oracle(elm, ctx, case):
     assert res["form"] == elm.FORM_FP64_TC and res["status"] in (0, 5)
     assert res["rank"] == r == min(p["rank"], p["N"])
     assert rel(prob["beta"].cpu().numpy(), ref) <= 1e-9
-    if case in ("small_fp64", "sparse_pixels", "ragged"):
+    if case in ("small_fp64", "sparse_pixels", "ragged", "trailing_on_tensor_cores"):
         p64 = problem(p)
         elm.elm_train(ctx, p64, precision=elm.PREC_FP64)
         assert rel(prob["beta"].cpu().numpy(), p64["beta"].cpu().numpy()) <= 1e-10

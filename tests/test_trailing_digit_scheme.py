@@ -10,7 +10,9 @@ d = i + j of the pair products over 32 rows stays an integer below 2^22
 (exact in an FP32 accumulator, in any order); the dropped pairs (i + j > 6)
 move an entry by less than their bound; and the float32 fold of the seven
 exact diagonal sums, scaled and subtracted from a double-float entry, meets
-the double-float accuracy of the update it replaces."""
+the double-float accuracy of the update it replaces.  The FP64 variant
+(seven digits from an exact integer split, eight diagonals folded into two
+47-bit integers and two FMAs) meets FP64 accuracy."""
 from fractions import Fraction
 
 import numpy as np
@@ -147,3 +149,63 @@ def test_dropped_pairs_weigh_below_their_bound():
     bound = sum(K * 2.0 ** 14 * 2.0 ** -(14 + 8 * (i + j))
                 for i in range(NDIG) for j in range(NDIG) if i + j > NDIG)
     assert bound < 2.0 ** -46
+
+
+# --------------------------------------------------------------- FP64 scheme
+NDIG64 = 7
+
+
+def column_digits64(v):
+    """Scale 2^(E+1) (E: the largest exponent of the column) and the seven
+    balanced base-256 digits of rint(v / s 2^55), with integer operations in
+    the kernel's order (least significant digit first)."""
+    m = np.max(np.abs(v))
+    e = 0 if m == 0 else int(np.frexp(m)[1])      # m < 2^e
+    e = max(-126, min(127, e))
+    dig = np.zeros((NDIG64, len(v)), dtype=np.int64)
+    for k, x in enumerate(v):
+        X = int(np.rint(np.ldexp(x, 55 - e)))        # |X| < 2^55
+        for j in range(NDIG64 - 1, 0, -1):
+            r = ((X + 128) & 255) - 128
+            dig[j, k] = r
+            X = (X - r) >> 8
+        dig[0, k] = X
+    return 2.0 ** e, dig
+
+
+def test_fp64_digits_are_bf16_integers_and_exact_to_2_pow_minus_56():
+    rng = np.random.default_rng(21)
+    for _ in range(30):
+        v = rng.standard_normal(K) * 2.0 ** rng.integers(-40, 3)
+        v[rng.integers(0, K, 5)] = 0.0
+        s, d = column_digits64(v)
+        assert np.max(np.abs(d)) <= 128
+        for k in range(K):
+            rec = sum(Fraction(int(d[j, k])) * Fraction(2) ** (-7 - 8 * j) for j in range(NDIG64))
+            assert abs(rec * Fraction(s) - Fraction(float(v[k]))) <= Fraction(2) ** -56 * Fraction(s)
+
+
+def test_fp64_fold_meets_fp64_accuracy():
+    rng = np.random.default_rng(22)
+    worst = 0.0
+    for _ in range(40):
+        x = rng.standard_normal(K) * 2.0 ** rng.integers(-20, 2)
+        y = rng.standard_normal(K) * 2.0 ** rng.integers(-20, 2)
+        sx, dx = column_digits64(x)
+        sy, dy = column_digits64(y)
+        # diagonals d = 0..7 of the digit pairs, exact integers below 2^22
+        D = [sum(int(dx[i, k]) * int(dy[dgl - i, k]) for i in range(NDIG64)
+                 if 0 <= dgl - i < NDIG64 for k in range(K)) for dgl in range(NDIG64 + 1)]
+        assert all(abs(v) < 2 ** 22 for v in D)
+        hi = ((D[0] * 256 + D[1]) * 256 + D[2]) * 256 + D[3]
+        lo = ((D[4] * 256 + D[5]) * 256 + D[6]) * 256 + D[7]
+        assert abs(hi) < 2 ** 47 and abs(lo) < 2 ** 47
+        a = float(rng.standard_normal()) * sx * sy * 8
+        total = float(lo) * 2.0 ** -70 + float(hi) * 2.0 ** -38   # one rounding (the FMA)
+        got = a - total * (sx * sy)
+        exact = Fraction(a) - sum(Fraction(float(p)) * Fraction(float(q)) for p, q in zip(x, y))
+        err = abs(Fraction(got) - exact) / Fraction(sx * sy)
+        worst = max(worst, float(err))
+    # truncation of the operands (2^-56 each, 32 products) and two FP64
+    # roundings, on the scale s_x s_y of the products (up to 32 in size)
+    assert worst <= 2.0 ** -47
