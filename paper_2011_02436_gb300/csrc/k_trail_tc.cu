@@ -1,36 +1,40 @@
-// Trailing update of the mixed form's pivoted factorisation on the tensor
-// cores (Eq. 6; Algorithm 1, steps 3-4).  After a panel of up to 32 pivots
-// every remaining entry of the active matrix becomes
+// Trailing update of the pivoted factorisation on the tensor cores (Eq. 6;
+// Algorithm 1, steps 3-4).  After a panel of up to 32 pivots every
+// remaining entry of the active matrix becomes
 //     A'[x, y] = A[rem x, rem y] - sum_t P[t, rem x] P[t, rem y],
-// with rem the compaction map of the unpivoted columns.  A and the panel
-// rows P hold double-float pairs (h + l, two floats in eight bytes).
+// with rem the compaction map of the unpivoted columns.  Two schemes: the
+// mixed form holds A and the panel rows P as double-float pairs (h + l, two
+// floats in eight bytes), the FP64 form with tensor-core products as FP64.
 //
 // Digits.  The 32 panel entries of each remaining column x are scaled by a
-// power of two s_x >= their largest magnitude and split into six signed
-// 8-bit digits, integers |a_j| <= 128 (exact in bf16):
-//     P[t, x] / s_x = sum_{j<6} a_j 2^(-7-8j) + r,   |r| <= 2^-48.
+// power of two s_x and split into signed 8-bit digits, integers |a_j| <= 128
+// (exact in bf16), digit j of weight 2^(-7-8j): six digits of a
+// double-float entry (|r| <= 2^-48 s_x), or seven of an FP64 entry taken
+// from rint(v / s_x 2^55) by integer operations (|r| <= 2^-56 s_x).
 // Products.  For a digit pair (i, j) one tcgen05 MMA (kind::f16, bf16
 // operands, FP32 accumulator in tensor memory) sums the 32 products
-// |a_i b_j| <= 2^14 of a pair: at most 2^19 per pair and six pairs share the
-// weight 2^(-14-8d) of diagonal d = i + j, so every accumulator stays an
-// integer below 2^22 and the FP32 accumulation is exact in any order.
-// Pairs with i + j <= 6 are kept (26 of 36); the others weigh below 2^-48
-// of s_x s_y.  The drain folds the seven exact diagonal sums into a
-// double-float value (TwoSum, FP32 pipes), scales it by s_x s_y and
-// subtracts it from the double-float entry of A: about 2^-46 relative to
-// s_x s_y, like the double-float update it replaces, in about 45 FP32
-// instructions per entry instead of 32 products of 10.
+// |a_i b_j| <= 2^14 of a pair: at most 2^19 per pair, and at most seven
+// pairs share the weight 2^(-14-8d) of diagonal d = i + j, so every
+// accumulator stays an integer below 2^22 and the FP32 accumulation is
+// exact in any order.  Kept: pairs with i + j <= NDIG (26 of 36 pairs in
+// seven diagonals; 36 of 49 in eight); the others weigh below 2^-48
+// (2^-62) of s_x s_y.  The drain folds the exact diagonal sums and
+// subtracts them, scaled by s_x s_y, from A's entry: in double-float
+// (TwoSum on the FP32 pipes, about 2^-46 relative to s_x s_y, like the
+// double-float update, in about 45 FP32 instructions per entry instead of 32
+// products of 10), or exactly into two 47-bit integers and then two FP64
+// FMAs (FP64 accuracy, two FP64 instructions per entry instead of 32).
 // Symmetry.  The integer sums are symmetric in (x, y) and the scales are per
 // column, so bitwise-equal columns stay bitwise equal (ties in the pivot
-// search resolve as in the double-float update) and A' is exactly
-// symmetric; each lower tile also writes its mirror.
+// search resolve as before) and A' is exactly symmetric; each lower tile
+// also writes its mirror.
 //
 // Layout of the digit planes: G[c][p][32] bf16, p < Lcap (compacted column
 // index, Lcap a multiple of 128), K = 32 panel rows (zero past the panel's
-// pivots).  Plane c = 6 - j holds digit j (c = 1..6); plane 0 is all zeros
-// and stands for a seventh digit of the B operand, so that for every A
-// digit i the pairs (i, 6-i..0) form one MMA over B planes i..6 whose
-// diagonal d lands at tensor-memory column (6 - d) 32, with every MMA
+// pivots).  Plane c = NDIG - j holds digit j (c = 1..NDIG); plane 0 is all
+// zeros and stands for an extra digit of the B operand, so that for every A
+// digit i the pairs (i, NDIG-i..0) form one MMA over B planes i..NDIG whose
+// diagonal d lands at tensor-memory column (NDIG - d) 32, with every MMA
 // starting at column 0.
 #include <cuda.h>
 #include <cuda_bf16.h>
