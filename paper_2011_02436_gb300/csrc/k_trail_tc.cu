@@ -17,8 +17,8 @@
 // pairs share the weight 2^(-14-8d) of diagonal d = i + j, so every
 // accumulator stays an integer below 2^22 and the FP32 accumulation is
 // exact in any order.  Kept: pairs with i + j <= NDIG (26 of 36 pairs in
-// seven diagonals; 36 of 49 in eight); the others weigh below 2^-48
-// (2^-62) of s_x s_y.  The drain folds the exact diagonal sums and
+// seven diagonals; 34 of 49 in eight); the others weigh below 2^-48
+// (2^-56) of s_x s_y.  The drain folds the exact diagonal sums and
 // subtracts them, scaled by s_x s_y, from A's entry: in double-float
 // (TwoSum on the FP32 pipes, about 2^-46 relative to s_x s_y, like the
 // double-float update, in about 45 FP32 instructions per entry instead of 32
@@ -191,8 +191,8 @@ trail_digits_kernel(const double *__restrict__ P, int64_t ldp, const int32_t *__
 
 // Shared memory and tensor memory of one 128 x 32 output tile, and the
 // steps every tile kernel takes: set-up (barriers, tensor memory), the TMA
-// copies of both operands' digit planes with the twelve MMAs (thread 0),
-// the wait for them (all threads), the fold of the seven diagonal sums,
+// copies of both operands' digit planes with the MMAs (two per A digit,
+// thread 0), the wait for them (all threads), the fold of the diagonal sums,
 // and the tear-down.
 struct TileSmem {
     uint64_t full_bar, mma_bar;
