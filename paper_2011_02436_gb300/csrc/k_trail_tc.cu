@@ -291,7 +291,8 @@ __device__ __forceinline__ double i2d_exact(long long v) {
 }
 // a - c sum_d D_d 2^(-14-8d), d = 0..7, in FP64: the diagonals as integers
 // (exact, |D_d| < 2^22), folded exactly into two 47-bit integers, then one
-// FMA for their sum and one for the subtraction (c = s_x s_y exact)
+// FMA for their sum and one for the subtraction (c = s_x s_y exact): two
+// FP64 instructions per entry
 __device__ __forceinline__ double fold_sub64(const uint32_t (&dg)[S64::NDIAG][8], int k8, float c,
                                              double a) {
     long long hi = 0, lo = 0;
@@ -305,8 +306,12 @@ __device__ __forceinline__ double fold_sub64(const uint32_t (&dg)[S64::NDIAG][8]
         const int v = __float_as_int(__uint_as_float(dg[d][k8]) + 12582912.f) - 0x4B400000;
         lo = lo * 256 + v;
     }
-    const double sum = fma(i2d_exact(lo), 0x1p-70, i2d_exact(hi) * 0x1p-38);
-    return fma(-sum, f2d(c), a);   // c: a power of two, exact in both formats
+    // hi + lo 2^-32 rounded once; the 2^-38 joins the scale c (a power of two,
+    // exact in both formats) through its exponent bits
+    const double t = fma(i2d_exact(lo), 0x1p-32, i2d_exact(hi));
+    const double cd = f2d(c);
+    const double c38 = cd == 0.0 ? 0.0 : __longlong_as_double(__double_as_longlong(cd) - (38ll << 52));
+    return fma(-t, c38, a);
 }
 __device__ __forceinline__ void tile_teardown(TileSmem &t, FactorState *st, int *flag) {
     tc_fence_before();
