@@ -75,10 +75,6 @@ def peaks():
                 fp64=1.25)
 
 
-# DRAM bytes (read + write) of one Gram tensor-kernel launch per sample row,
-# from an ncu capture of the same kernel at 20000 rows (745.5 MB); the launch
-# streams the digit planes, whose size is proportional to the rows.
-GRAM_DRAM_BYTES_PER_ROW = (720.844544e6 + 24.663040e6) / 20000
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
@@ -497,7 +493,6 @@ def run_native(args):
             nJ = Lp // 128
             pairs = 36 if prec == elm.PREC_FP64_TC else 15
             issued += pairs * 2.0 * (nJ * (nJ + 1)) * 128 * 64 * Np
-        N_all = sum(p["X"].shape[0] for p in hosts)
         if prec == elm.PREC_FP64:
             # Gram on the FP64 pipe (nominal rate; the measured peaks have no FP64 entry)
             achieved = gram_fl / (ph_ms["gram"] * 1e-3) / 1e12
@@ -511,15 +506,12 @@ def run_native(args):
             # digit-pair products of the lower-triangle tiles, reported beside it
             achieved = gram_fl / (ph_ms["gram"] * 1e-3) / 1e12
             tc = prec == elm.PREC_FP64_TC
-            # the captured DRAM traffic per row holds for the sparse-pixel
-            # workload's mixed Gram (L = 2000) only
-            captured = args.workload == "sparse_pixels" and not tc
+            # DRAM counters are reported only for the kernel they were taken
+            # on; the Gram kernel's plane layout (blocks of 65536 samples,
+            # 3-D tensor maps) changed after its last capture
             roof = dict(bound="tensor", achieved=achieved, peak=pk["bf16"], unit="TFLOP/s",
-                        frac=achieved / pk["bf16"],
-                        traffic=GRAM_DRAM_BYTES_PER_ROW * N_all if captured else None,
-                        traffic_source=("ncu capture of the same kernel at 20000 rows "
-                                        "(745.5 MB), scaled by the rows") if captured
-                        else "no capture of this kernel at this shape",
+                        frac=achieved / pk["bf16"], traffic=None,
+                        traffic_source="no DRAM capture of the current Gram kernel",
                         kernel=("ozaki_kernel (FP64-accurate Gram, 8 digits x 7 bits, 36 pairs "
                                 "in two launches)") if tc
                         else "ozaki_kernel (Gram, 5 digits x 7 bits, 15 pairs)",
