@@ -13,11 +13,15 @@ for the largest remaining diagonal runs on the integer pipes, and it takes
   (the conversion that loads the equilibrated Gram), the two kinds that
   meet in one comparison;
 * the conversion of a double to a truncated pair keeps it to 2^-47;
+* the warp-wide choice takes the largest key, then the lowest original
+  index, and the index word holds every accepted size;
 * the FP64 reciprocal square root (a float seed, then one third-order step)
   is accurate to the last bit or two for any seed within the documented
   2-ulp error of the hardware's float reciprocal square root, and its
   double-float counterpart to about 2^-44.
 """
+import os
+import re
 import struct
 from fractions import Fraction
 
@@ -272,3 +276,41 @@ def test_double_float_reciprocal_square_root():
     # 2^-24 |y0 r / 2| and the double-float r (about 2^-46) bound the error
     # by 2^-43.8
     assert worst <= 2.0 ** -43.5, worst
+
+
+def warp_best(keys, ords):
+    """The panel's warp-wide choice: the largest 64-bit key by two 32-bit
+    maximum reductions (high words, then low words among the lanes holding
+    the largest high word), then the smallest ord among the lanes holding
+    that key."""
+    kh = [k >> 32 for k in keys]
+    mh = max(kh)
+    ml = max((k & 0xFFFFFFFF) if h == mh else 0 for k, h in zip(keys, kh))
+    mk = (mh << 32) | ml
+    return mk, min(o if k == mk else 0xFFFFFFFF for k, o in zip(keys, ords))
+
+
+def test_warp_choice_takes_the_largest_diagonal_then_the_lowest_index():
+    rng = np.random.default_rng(7)
+    for trial in range(300):
+        # few distinct diagonals, so that ties are common; keys of double-float pairs
+        pool = [rn_pair(x) for x in np.abs(sample_doubles(rng, 4, -30, 5))]
+        picks = rng.integers(0, len(pool), 32)
+        keys = [dfkey(*pool[p]) for p in picks]
+        orig = rng.permutation(16384)[:32]
+        ords = [(int(g) << 14) | int(x) for g, x in zip(orig, rng.integers(0, 16384, 32))]
+        mk, mo = warp_best(keys, ords)
+        best = max(range(32), key=lambda i: (float(pool[picks[i]][0]) + float(pool[picks[i]][1]),
+                                             -int(orig[i])))
+        assert mk == keys[best] and mo == ords[best]
+
+
+def test_candidate_order_word_holds_every_index():
+    # ord = orig << 14 | x in 32 bits: both indices below 2^14 for every
+    # accepted size, so the packing loses nothing and compares orig first
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "include", "elm.h")
+    max_l = int(re.search(r"#define ELM_MAX_L (\d+)", open(hdr).read()).group(1))
+    assert max_l <= 1 << 14
+    hi = ((max_l - 1) << 14) | (max_l - 1)
+    assert hi < 1 << 32
