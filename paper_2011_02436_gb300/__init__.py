@@ -19,6 +19,9 @@ from . import _lib
 ACT_SIGMOID, ACT_TANH = 0, 1
 F32, F64 = 0, 1
 PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
+# largest padded sample and input counts of the mixed form's exact products
+# (beyond them a mixed request runs the FP64 form with tensor-core products)
+MIXED_MAX_ROWS, MIXED_MAX_INPUTS = 8257536, 64512
 OK = 0
 
 

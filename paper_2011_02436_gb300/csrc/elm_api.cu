@@ -1456,7 +1456,11 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
         int *err = nullptr;
         OzHidWs hw{};
         char *xws = nullptr;
-        const bool mixed = precision == ELM_PREC_MIXED, tc = precision == ELM_PREC_FP64_TC;
+        // mixed beyond the sizes its exact products hold: the FP64-accurate
+        // tensor-core pre-activation instead
+        const bool fits = mixed_fits(N, n);
+        const bool mixed = precision == ELM_PREC_MIXED && fits;
+        const bool tc = precision == ELM_PREC_FP64_TC || (precision == ELM_PREC_MIXED && !fits);
         const bool dev_out = on_device(Ht);
         with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
             Xs = stage(ar, s, X, N, n, ldx, xsz);
@@ -1593,17 +1597,21 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
         for (int64_t i = 0; i < count; i++) {
             Problem &P = plan[i];
             P.p = &probs[i];
-            P.prec = o.precision;
+            // a mixed problem larger than its exact products hold (int64
+            // running sums) trains in the FP64 form with tensor-core products
+            P.prec = o.precision == ELM_PREC_MIXED && !mixed_fits(probs[i].N, probs[i].n)
+                         ? ELM_PREC_FP64_TC
+                         : o.precision;
             P.max_refine = o.max_refine >= 0 ? o.max_refine
-                                             : (o.precision == ELM_PREC_MIXED ? 12 : 2);
+                                             : (P.prec == ELM_PREC_MIXED ? 12 : 2);
             // default rank threshold on the unit-diagonal scale: L 2^-52 for
             // the FP64 Gram; the mixed Gram drops digit pairs below 2^-34 of
             // the leading term, so its threshold sits above that level
             const double tau64 = (double)probs[i].L * ldexp(1.0, -52);
             P.tau64 = o.tol_rank > 0.0 ? o.tol_rank : tau64;
             P.tau = o.tol_rank > 0.0 ? o.tol_rank
-                                     : (o.precision == ELM_PREC_MIXED ? fmax(tau64, ldexp(1.0, -32))
-                                                                      : tau64);
+                                     : (P.prec == ELM_PREC_MIXED ? fmax(tau64, ldexp(1.0, -32))
+                                                                 : tau64);
             // mixed form: stop three orders below its 1e-6 accuracy target
             // (its Gram matrix alone limits beta to about 1e-10); once an
             // update is that small the remaining error is smaller still
@@ -1914,7 +1922,8 @@ int elm_rows_create(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t
         ELM_CUDA(cudaSetDevice(ctx->device));
         h = new elm_rows;
         h->ctx = ctx;
-        h->precision = precision;
+        // a mixed row block larger than the mixed products hold: FP64
+        h->precision = precision == ELM_PREC_MIXED && !mixed_fits(N, n) ? ELM_PREC_FP64 : precision;
         h->N = N;
         h->L = L;
         h->m = m;

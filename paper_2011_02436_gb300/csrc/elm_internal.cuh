@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "elm.h"
+#include "mixed_limits.h"
 
 #define ELM_CUDA(call)                                                         \
     do {                                                                       \

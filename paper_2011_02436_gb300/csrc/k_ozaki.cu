@@ -1158,6 +1158,17 @@ CUtensorMap make_map_planes(const __nv_bfloat16 *base, int64_t rows, int planes,
 // 2^-34 grid, chunks of 1024 samples).
 constexpr int HID_PX = 6, HID_PW = 6, HID_TMAX = 7, HID_BITS = 7;
 constexpr int GRAM_PH = GRAM_PH_, GRAM_TMAX = 6, GRAM_BITS = GRAM_BITS_;
+// the mixed form's size limits (mixed_limits.h) hold for these schemes
+static_assert(HID_PX == HID_PW, "the pair count per diagonal assumes equal digit counts");
+static_assert(chunk_slabs<GRAM_BITS>() * SK == MIXED_CHUNK &&
+                  chunk_slabs<HID_BITS>() * SK == MIXED_CHUNK,
+              "exact chunk length");
+static_assert(mixed_chunk_bound(GRAM_PH, GRAM_TMAX, GRAM_BITS, MIXED_CHUNK) *
+                      (double)(MIXED_MAX_ROWS / MIXED_CHUNK) < TWO_POW_63,
+              "Gram running sums exceed int64 within MIXED_MAX_ROWS");
+static_assert(mixed_chunk_bound(HID_PW, HID_TMAX, HID_BITS, MIXED_CHUNK) *
+                      (double)(MIXED_MAX_INPUTS / MIXED_CHUNK) < TWO_POW_63,
+              "hidden-layer running sums exceed int64 within MIXED_MAX_INPUTS");
 
 int64_t oz_pad(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
 
