@@ -60,15 +60,19 @@ enum { ELM_F32 = 0, ELM_F64 = 1 };               /* element type of X           
  * 7-bit digits, and every digit pair above 2^-68 summed exactly (FP64-level
  * products; activation, factorisation, solves and refinement in FP64); the
  * mixed form hands the problems its Gram cannot settle to this form.
- * Size limits of ELM_PREC_MIXED: its products sum exact integers into int64
- * per output element, which holds any data up to ELM_MIXED_MAX_ROWS samples
- * (N rounded up to 64) and ELM_MIXED_MAX_INPUTS inputs (n rounded up to 32).
- * Beyond them elm_train trains the problem in the ELM_PREC_FP64_TC form
- * (elm_result.form says so), elm_hidden computes the ELM_PREC_FP64_TC
- * pre-activation, and elm_rows_create builds an FP64 row block. */
+ * Size limits: the tensor-core products sum exact integers into int64 per
+ * output element, which holds any data up to ELM_MIXED_MAX_ROWS samples (N
+ * rounded up to 64) and ELM_MIXED_MAX_INPUTS inputs (n rounded up to 32)
+ * in ELM_PREC_MIXED, and up to ELM_EXACT_MAX_K of either in
+ * ELM_PREC_FP64_TC.  Beyond its limits a request takes the next form:
+ * elm_train trains a mixed problem in the ELM_PREC_FP64_TC form and an
+ * ELM_PREC_FP64_TC problem in the ELM_PREC_FP64 form (elm_result.form says
+ * which), elm_hidden computes the pre-activation the same way, and
+ * elm_rows_create builds an FP64 row block. */
 enum { ELM_PREC_FP64 = 0, ELM_PREC_MIXED = 1, ELM_PREC_FP64_TC = 2 };
 #define ELM_MIXED_MAX_ROWS 8257536   /* 8064 chunks of 1024 samples */
 #define ELM_MIXED_MAX_INPUTS 64512   /* 63 chunks of 1024 inputs    */
+#define ELM_EXACT_MAX_K 212735488    /* 415499 chunks of 512        */
 
 /* Largest hidden-layer width L the factorisation kernels accept. */
 #define ELM_MAX_L 16384

@@ -19,9 +19,10 @@ from . import _lib
 ACT_SIGMOID, ACT_TANH = 0, 1
 F32, F64 = 0, 1
 PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
-# largest padded sample and input counts of the mixed form's exact products
-# (beyond them a mixed request runs the FP64 form with tensor-core products)
-MIXED_MAX_ROWS, MIXED_MAX_INPUTS = 8257536, 64512
+# largest padded sample and input counts of the exact tensor-core products:
+# beyond them a mixed request runs the FP64 form with tensor-core products,
+# and one of that form beyond EXACT_MAX_K the FP64 form
+MIXED_MAX_ROWS, MIXED_MAX_INPUTS, EXACT_MAX_K = 8257536, 64512, 212735488
 OK = 0
 
 

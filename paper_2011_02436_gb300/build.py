@@ -31,7 +31,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INC, "elm.h")]
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(INC, "elm.h")])
 
 
 def up_to_date() -> bool:

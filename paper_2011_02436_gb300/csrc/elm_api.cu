@@ -1456,11 +1456,10 @@ int elm_hidden(elm_ctx *ctx, const void *X, int x_dtype, int64_t N, int64_t n, i
         int *err = nullptr;
         OzHidWs hw{};
         char *xws = nullptr;
-        // mixed beyond the sizes its exact products hold: the FP64-accurate
-        // tensor-core pre-activation instead
-        const bool fits = mixed_fits(N, n);
-        const bool mixed = precision == ELM_PREC_MIXED && fits;
-        const bool tc = precision == ELM_PREC_FP64_TC || (precision == ELM_PREC_MIXED && !fits);
+        // beyond the sizes a form's exact products hold: the next form (mixed,
+        // then FP64-accurate tensor cores, then FP64)
+        const int prec = route_precision(precision, N, n);
+        const bool mixed = prec == ELM_PREC_MIXED, tc = prec == ELM_PREC_FP64_TC;
         const bool dev_out = on_device(Ht);
         with_arena(&ctx->ws, &ctx->ws_size, s, [&](Arena &ar) {
             Xs = stage(ar, s, X, N, n, ldx, xsz);
@@ -1597,11 +1596,9 @@ int elm_train(elm_ctx *ctx, const elm_problem *probs, int64_t count,
         for (int64_t i = 0; i < count; i++) {
             Problem &P = plan[i];
             P.p = &probs[i];
-            // a mixed problem larger than its exact products hold (int64
-            // running sums) trains in the FP64 form with tensor-core products
-            P.prec = o.precision == ELM_PREC_MIXED && !mixed_fits(probs[i].N, probs[i].n)
-                         ? ELM_PREC_FP64_TC
-                         : o.precision;
+            // a problem larger than its form's exact products hold (int64
+            // running sums) trains in the next form
+            P.prec = route_precision(o.precision, probs[i].N, probs[i].n);
             P.max_refine = o.max_refine >= 0 ? o.max_refine
                                              : (P.prec == ELM_PREC_MIXED ? 12 : 2);
             // default rank threshold on the unit-diagonal scale: L 2^-52 for

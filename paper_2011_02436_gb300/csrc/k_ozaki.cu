@@ -1163,11 +1163,11 @@ static_assert(HID_PX == HID_PW, "the pair count per diagonal assumes equal digit
 static_assert(chunk_slabs<GRAM_BITS>() * SK == MIXED_CHUNK &&
                   chunk_slabs<HID_BITS>() * SK == MIXED_CHUNK,
               "exact chunk length");
-static_assert(mixed_chunk_bound(GRAM_PH, GRAM_TMAX, GRAM_BITS, MIXED_CHUNK) *
-                      (double)(MIXED_MAX_ROWS / MIXED_CHUNK) < TWO_POW_63,
+static_assert(sums_fit(chunk_bound(GRAM_PH, 2, GRAM_TMAX, GRAM_BITS, MIXED_CHUNK),
+                       MIXED_MAX_ROWS, MIXED_CHUNK),
               "Gram running sums exceed int64 within MIXED_MAX_ROWS");
-static_assert(mixed_chunk_bound(HID_PW, HID_TMAX, HID_BITS, MIXED_CHUNK) *
-                      (double)(MIXED_MAX_INPUTS / MIXED_CHUNK) < TWO_POW_63,
+static_assert(sums_fit(chunk_bound(HID_PW, 2, HID_TMAX, HID_BITS, MIXED_CHUNK),
+                       MIXED_MAX_INPUTS, MIXED_CHUNK),
               "hidden-layer running sums exceed int64 within MIXED_MAX_INPUTS");
 
 int64_t oz_pad(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
@@ -1356,6 +1356,11 @@ void oz_gram(cudaStream_t s, const __nv_bfloat16 *planes, const double *hs, int6
 // 2^24) in a second launch that adds its FP64 result to the first.  The
 // dropped pairs weigh at most 2^-56 relative, the FP64 conversions 2^-53.
 constexpr int EX_PH = 8, EX_BITS = 7;
+// the two bands below hold their int64 running sums up to EXACT_MAX_K
+static_assert(sums_fit(chunk_bound(4, 2, 5, EX_BITS, chunk_slabs<EX_BITS>() * SK), EXACT_MAX_K,
+                       chunk_slabs<EX_BITS>() * SK) &&
+                  sums_fit(chunk_bound(EX_PH, 6, 9, EX_BITS, 16 * SK), EXACT_MAX_K, 16 * SK),
+              "FP64-accurate bands exceed int64 within EXACT_MAX_K");
 
 size_t oz_exact_planes_bytes(int64_t N, int64_t L, int64_t m) {
     return (size_t)EX_PH * oz_pad(L + m, BM) * oz_pad(N, BN) * 2;

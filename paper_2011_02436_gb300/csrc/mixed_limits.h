@@ -1,20 +1,22 @@
-// Largest problems whose mixed-form tensor-core products stay exact (host
-// code; no CUDA dependencies).
+// Largest problems whose tensor-core products stay exact (host code; no
+// CUDA dependencies).
 //
-// The mixed Gram (Eqs. 9-13: five 7-bit digits per operand, kept diagonals
-// t = 2..6, chunks of 1024 samples) and the mixed hidden layer's
-// pre-activation (Eq. 1: six digits, t = 2..7, chunks of 1024 inputs) add
-// each chunk's exact diagonal sums into one int64 running sum per output
-// element, diagonal t weighted 2^(7 (TMAX - t)).  A digit is an integer of
-// magnitude at most 64 and diagonal t pairs min(t - 1, 2 P + 1 - t) digits,
+// The tensor kernels add each K chunk's exact diagonal sums of digit
+// products into one int64 running sum per output element, diagonal t = p + q
+// weighted 2^(7 (TMAX - t)).  A digit is an integer of magnitude at most 64
+// and diagonal t pairs min(t - 1, 2 P + 1 - t) of the P digits per operand,
 // so one chunk adds at most
-//     C = sum_t pairs(t) 2^12 1024 2^(7 (TMAX - t))
-// in magnitude: about 2^50.02 for the Gram and 2^57.02 for the hidden
-// layer.  The running sums therefore stay below 2^63 for up to 8064 chunks
-// of samples (8 257 536 samples) and 63 chunks of inputs (64 512 inputs),
-// whatever the data.  A larger problem trains in the FP64 form with
-// tensor-core products instead, whose digit bands weigh at most 2^21 per
-// unit.
+//     C = sum_{t = TMIN}^{TMAX} pairs(t) 2^12 chunk 2^(7 (TMAX - t))
+// in magnitude, whatever the data:
+//   * mixed Gram (Eqs. 9-13; P = 5, t = 2..6, chunks of 1024): about 2^50.02,
+//     so 8064 chunks of samples (8 257 536 samples);
+//   * mixed hidden layer (Eq. 1; P = 6, t = 2..7, chunks of 1024): about
+//     2^57.02, so 63 chunks of inputs (64 512 inputs);
+//   * FP64-accurate products (P = 8): the band t = 2..5 (four planes, chunks
+//     of 1024) about 2^43.02, the band t = 6..9 (chunks of 512) about 2^44.34,
+//     so 415 499 chunks of 512 (212 735 488 samples or inputs).
+// A mixed request beyond its limits runs the FP64-accurate tensor-core form,
+// and one beyond that form's limit the FP64 form.
 #pragma once
 #include <stdint.h>
 
@@ -23,17 +25,22 @@ namespace elm {
 constexpr int64_t MIXED_CHUNK = 1024;                   // K elements per exact chunk
 constexpr int64_t MIXED_MAX_ROWS = 8064 * MIXED_CHUNK;  // samples N, padded to 64
 constexpr int64_t MIXED_MAX_INPUTS = 63 * MIXED_CHUNK;  // inputs n, padded to 32
+constexpr int64_t EXACT_MAX_K = 415499 * 512;           // FP64-accurate products: N and n
 #ifdef ELM_MIXED_MAX_ROWS
-static_assert(ELM_MIXED_MAX_ROWS == MIXED_MAX_ROWS && ELM_MIXED_MAX_INPUTS == MIXED_MAX_INPUTS,
+static_assert(ELM_MIXED_MAX_ROWS == MIXED_MAX_ROWS && ELM_MIXED_MAX_INPUTS == MIXED_MAX_INPUTS &&
+                  ELM_EXACT_MAX_K == EXACT_MAX_K,
               "the public limits match");
+static_assert(ELM_PREC_FP64 == 0 && ELM_PREC_MIXED == 1 && ELM_PREC_FP64_TC == 2,
+              "route_precision's codes");
 #endif
 
 // Largest magnitude one chunk adds to a running sum: P digits of `bits` bits
-// per operand, diagonals 2..tmax, `chunk` products per diagonal pair.  Exact
-// in double for the sizes used (below 2^58, integer).
-constexpr double mixed_chunk_bound(int P, int tmax, int bits, int64_t chunk) {
+// per operand, diagonals tmin..tmax, `chunk` products per digit pair.  The
+// result is an integer with at most 36 significant bits times a power of
+// two, exact in double, and so are its products with the chunk counts.
+constexpr double chunk_bound(int P, int tmin, int tmax, int bits, int64_t chunk) {
     double c = 0.0;
-    for (int t = 2; t <= tmax; t++) {
+    for (int t = tmin; t <= tmax; t++) {
         const int pairs = t - 1 < 2 * P + 1 - t ? t - 1 : 2 * P + 1 - t;
         double w = 1.0;
         for (int i = 0; i < bits * (tmax - t); i++) w *= 2.0;
@@ -42,18 +49,29 @@ constexpr double mixed_chunk_bound(int P, int tmax, int bits, int64_t chunk) {
     }
     return c;
 }
-
 constexpr double TWO_POW_63 = 9223372036854775808.0;
-static_assert(mixed_chunk_bound(5, 6, 7, MIXED_CHUNK) * (double)(MIXED_MAX_ROWS / MIXED_CHUNK) <
-                  TWO_POW_63,
-              "mixed Gram running sums exceed int64");
-static_assert(mixed_chunk_bound(6, 7, 7, MIXED_CHUNK) * (double)(MIXED_MAX_INPUTS / MIXED_CHUNK) <
-                  TWO_POW_63,
-              "mixed hidden-layer running sums exceed int64");
+constexpr bool sums_fit(double per_chunk, int64_t K, int64_t chunk) {
+    return per_chunk * (double)((K + chunk - 1) / chunk) < TWO_POW_63;
+}
+static_assert(sums_fit(chunk_bound(5, 2, 6, 7, 1024), MIXED_MAX_ROWS, 1024), "mixed Gram");
+static_assert(sums_fit(chunk_bound(6, 2, 7, 7, 1024), MIXED_MAX_INPUTS, 1024), "mixed hidden");
+static_assert(sums_fit(chunk_bound(4, 2, 5, 7, 1024), EXACT_MAX_K, 1024), "exact band 2..5");
+static_assert(sums_fit(chunk_bound(8, 6, 9, 7, 512), EXACT_MAX_K, 512), "exact band 6..9");
 
 // True when N samples and n inputs fit the mixed form's exact products.
 inline bool mixed_fits(int64_t N, int64_t n) {
     return (N + 63) / 64 * 64 <= MIXED_MAX_ROWS && (n + 31) / 32 * 32 <= MIXED_MAX_INPUTS;
+}
+// The same for the FP64-accurate tensor-core products.
+inline bool exact_fits(int64_t N, int64_t n) {
+    return (N + 63) / 64 * 64 <= EXACT_MAX_K && (n + 31) / 32 * 32 <= EXACT_MAX_K;
+}
+// The form a request for `precision` (0 FP64, 1 mixed, 2 FP64-accurate
+// tensor cores, as ELM_PREC_*) runs in for N samples and n inputs.
+inline int route_precision(int precision, int64_t N, int64_t n) {
+    if (precision == 1 && !mixed_fits(N, n)) precision = 2;
+    if (precision == 2 && !exact_fits(N, n)) precision = 0;
+    return precision;
 }
 
 }  // namespace elm
