@@ -11,7 +11,9 @@ sum, in double-float.  Checked here against exact rational arithmetic: the
 error stays below 2^-47 of sum_j |H[i, j] beta[j]| (measured 2^-50 to 2^-53
 for 64 to 1000 neurons; T's own truncation to a pair is part of the target),
 which is what lets the refinement converge to the least-squares solution of
-the double-float H."""
+the double-float H.  The product H^T R of the same step sums each split of
+the samples into one unnormalised pair; its error grows with the split's
+length, pinned below as measured."""
 import struct
 from fractions import Fraction
 
@@ -114,3 +116,40 @@ def test_residual_within_2_pow_minus_47_of_the_products():
                     for a, b in zip(h_row, beta))
         worst = max(worst, float(abs(got - want) / scale))
     assert worst <= 2.0 ** -47, worst
+
+
+def htr_element(h_col, r_col, chunk):
+    """G[j] = sum_i H[i, j] R[i]: one thread per neuron and split of the
+    samples, an unnormalised pair over the split's samples, each split's pair
+    added into one double, the splits summed in order in FP64."""
+    g = 0.0
+    for i0 in range(0, len(h_col), chunk):
+        sh = sl = f32(0)
+        for h, r in zip(h_col[i0:i0 + chunk], r_col[i0:i0 + chunk]):
+            sh, sl = acc_prod(sh, sl, h, r)
+        g += float(sh) + float(sl)
+    return g
+
+
+def test_normal_equations_residual_grows_with_the_split_length():
+    """The split's pair is never renormalised, so the low word's own
+    roundings grow with the split length k: measured up to about k 2^-51.4 of
+    sum |H R| when every product has one sign (2^-45 to 2^-51 with mixed
+    signs, as a least-squares residual has), checked here against k 2^-50.
+    Splits of 448, 1984 and 13184 samples: what the split count gives for
+    2000 neurons on 60000 samples, 6000 on 100000 and 8000 on 500000."""
+    rng = np.random.default_rng(5)
+    for chunk, N, same_sign in ((64, 64, True), (448, 1344, False), (448, 448, True),
+                                (1984, 3968, False), (1984, 1984, True), (13184, 13184, True)):
+        h_col = [pair(1.0 / (1.0 + np.exp(-v))) for v in rng.normal(size=N)]
+        r = rng.normal(scale=1e-4, size=N)
+        if same_sign:
+            r = np.abs(r)
+        r_col = [pair(v) for v in r]
+        F = [(Fraction(float(a[0])) + Fraction(float(a[1])),
+              Fraction(float(b[0])) + Fraction(float(b[1]))) for a, b in zip(h_col, r_col)]
+        exact = sum(a * b for a, b in F)
+        scale = sum(abs(a * b) for a, b in F)
+        got = htr_element(h_col, r_col, chunk)
+        rel = float(abs(Fraction(got) - exact) / scale)
+        assert rel <= chunk * 2.0 ** -50, (chunk, same_sign, rel)
