@@ -1054,9 +1054,14 @@ void act_rows_f64(cudaStream_t s, double *Ht, int64_t ldh, int64_t L, int64_t N,
 void transpose_f64(cudaStream_t s, const double *A, int64_t rows, int64_t cols, int64_t lda,
                    double *B, int64_t ldb) {
     if (rows <= 0 || cols <= 0) return;
-    dim3 g((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-    transpose_f64_kernel<<<g, 256, 0, s>>>(A, rows, cols, lda, B, ldb);
-    ELM_CHECK_LAUNCH();
+    // rows in slices of at most 65535 row blocks (the grid's y limit)
+    constexpr int64_t RMAX = 65535 * 32;
+    for (int64_t r0 = 0; r0 < rows; r0 += RMAX) {
+        const int64_t rr = rows - r0 < RMAX ? rows - r0 : RMAX;
+        dim3 g((unsigned)((cols + 31) / 32), (unsigned)((rr + 31) / 32));
+        transpose_f64_kernel<<<g, 256, 0, s>>>(A + r0 * lda, rr, cols, lda, B + r0, ldb);
+        ELM_CHECK_LAUNCH();
+    }
 }
 
 void set_identity(cudaStream_t s, double *A, int64_t n) {
