@@ -17,7 +17,7 @@ PROG = r"""
 #include <vector>
 #include "oz_tiles.cuh"
 int main() {
-    for (int64_t nJ = 1; nJ <= 140; nJ++) {          // up to (16384 + 26) / 128 row blocks
+    for (int64_t nJ = 1; nJ <= 320; nJ++) {          // L + m up to 40960 (128-row blocks)
         const int64_t n = nJ * (nJ + 1);
         std::vector<char> seen(n, 0);
         for (int64_t t = 0; t < n; t++) {
