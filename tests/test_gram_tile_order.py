@@ -1,7 +1,8 @@
 """The order in which the tensor kernel walks the Gram's lower triangle of
 128 x 64 tiles (paper_2011_02436_gb300/csrc/oz_tiles.cuh, shared by host and
 device code): every tile exactly once and inside the triangle for every
-size up to the largest hidden layer, and a wave of 152 consecutive tiles
+size up to 320 row blocks (the augmented Gram [H T] of the largest hidden
+layer with thousands of targets), and a wave of 152 consecutive tiles
 touches few operand row blocks (except in a last super-row of only one or
 two row blocks, which the walk covers row after row).  Compiled as host C++."""
 import os
