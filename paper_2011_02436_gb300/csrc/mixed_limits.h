@@ -1,5 +1,5 @@
 // Largest problems whose tensor-core products stay exact (host code; no
-// CUDA dependencies).
+// CUDA dependencies: the public header only).
 //
 // The tensor kernels add each K chunk's exact diagonal sums of digit
 // products into one int64 running sum per output element, diagonal t = p + q
@@ -20,19 +20,17 @@
 #pragma once
 #include <stdint.h>
 
+#include "elm.h"
+
 namespace elm {
 
 constexpr int64_t MIXED_CHUNK = 1024;                   // K elements per exact chunk
 constexpr int64_t MIXED_MAX_ROWS = 8064 * MIXED_CHUNK;  // samples N, padded to 64
 constexpr int64_t MIXED_MAX_INPUTS = 63 * MIXED_CHUNK;  // inputs n, padded to 32
 constexpr int64_t EXACT_MAX_K = 415499 * 512;           // FP64-accurate products: N and n
-#ifdef ELM_MIXED_MAX_ROWS
 static_assert(ELM_MIXED_MAX_ROWS == MIXED_MAX_ROWS && ELM_MIXED_MAX_INPUTS == MIXED_MAX_INPUTS &&
                   ELM_EXACT_MAX_K == EXACT_MAX_K,
               "the public limits match");
-static_assert(ELM_PREC_FP64 == 0 && ELM_PREC_MIXED == 1 && ELM_PREC_FP64_TC == 2,
-              "route_precision's codes");
-#endif
 
 // Largest magnitude one chunk adds to a running sum: P digits of `bits` bits
 // per operand, diagonals tmin..tmax, `chunk` products per digit pair.  The
@@ -66,11 +64,11 @@ inline bool mixed_fits(int64_t N, int64_t n) {
 inline bool exact_fits(int64_t N, int64_t n) {
     return (N + 63) / 64 * 64 <= EXACT_MAX_K && (n + 31) / 32 * 32 <= EXACT_MAX_K;
 }
-// The form a request for `precision` (0 FP64, 1 mixed, 2 FP64-accurate
-// tensor cores, as ELM_PREC_*) runs in for N samples and n inputs.
+// The form (ELM_PREC_*) a request for `precision` runs in for N samples and
+// n inputs.
 inline int route_precision(int precision, int64_t N, int64_t n) {
-    if (precision == 1 && !mixed_fits(N, n)) precision = 2;
-    if (precision == 2 && !exact_fits(N, n)) precision = 0;
+    if (precision == ELM_PREC_MIXED && !mixed_fits(N, n)) precision = ELM_PREC_FP64_TC;
+    if (precision == ELM_PREC_FP64_TC && !exact_fits(N, n)) precision = ELM_PREC_FP64;
     return precision;
 }
 
